@@ -1,0 +1,769 @@
+/*
+ * gsref.c -- plain FP64 CPU oracle for point-set geodesic shooting with the
+ * Barnes-Hut approximation (arXiv 1907.04834).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference that the CUDA path is
+ * checked against.  It shares no code, header, table or constant with the CUDA
+ * library; only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg load it.  Nothing here is tuned: every sum is a plain loop in
+ * the order the definition states (OpenMP only splits the independent target
+ * points across threads; each target's sum keeps its sequential order).
+ *
+ * Notation (Sec. 2.1): q_i, p_i in R^3, i = 0..N-1; d_ij = q_i - q_j;
+ * g_ij = G(|d_ij|) = exp(-|d_ij|^2 / (2 sigma^2)) (reading R1: unnormalised
+ * Gaussian, G(0) = 1); c_ij = p_i . p_j.
+ * Hamiltonian (Sec. 2.1, with the 1/2 of reading R2):
+ *     H(q,p) = 1/2 sum_i sum_j g_ij c_ij.
+ * Hamilton's equations (Eq. 1):
+ *     dq_i/dt =  dH/dp_i = F_i   = sum_j g_ij p_j                (j = i included, R3)
+ *     dp_i/dt = -dH/dq_i = Phi_i = sigma^-2 sum_j c_ij g_ij d_ij
+ * Time discretisation (Sec. 2.1, "discretized in time"; reading R4):
+ *     explicit Euler, h = 1/T, q^{k+1} = q^k + h F^k, p^{k+1} = p^k + h Phi^k.
+ * Objective (Eq. 2, reading R5):  E(p0) = H(q0,p0) + lambda sum_i |q_i^T - X_i|^2.
+ * Backward stage (Sec. 2.2, reading R6): discrete adjoint of the Euler map,
+ *     alpha = dE/dq, beta = dE/dp; alpha^T = 2 lambda (q^T - X), beta^T = 0,
+ *     alpha^k = alpha^{k+1} + h [ (dF/dq)^T alpha^{k+1} + (dPhi/dq)^T beta^{k+1} ]
+ *     beta^k  = beta^{k+1}  + h [ (dF/dp)^T alpha^{k+1} + (dPhi/dp)^T beta^{k+1} ]
+ *     dE/dp0  = beta^0 + F(q0, p0).
+ *   Written out per pair (a = alpha^{k+1}, b = beta^{k+1}, w_ij = b_i - b_j):
+ *     (dF/dq)^T a   |_i = -sigma^-2 sum_j g_ij ((a_i.p_j) + (a_j.p_i)) d_ij
+ *     (dPhi/dq)^T b |_i =  sigma^-2 sum_j c_ij g_ij (w_ij - (w_ij.d_ij) d_ij / sigma^2)
+ *     (dF/dp)^T a   |_i =  sum_j g_ij a_j
+ *     (dPhi/dp)^T b |_i =  sigma^-2 sum_j g_ij (w_ij.d_ij) p_j
+ *
+ * Barnes-Hut (Sec. 2.2), rebuilt at every forward and backward step (R13):
+ *   - root cell = FP32 bounding box of the FP32-rounded positions; cells are
+ *     per-axis bisections; a point's child octant at depth d is bit (9-d) of its
+ *     10-bit quantised coordinates (reading R7: ext = hi-lo; inv = 1024/ext;
+ *     u = (x-lo)*inv; k = min((uint32)u, 1023); k = 0 when ext == 0; all FP32,
+ *     round to nearest, no contraction); octant = (kx_b << 2) | (ky_b << 1) | kz_b.
+ *   - points are inserted one by one in index order with the three-case rule
+ *     (internal -> descend; empty leaf -> store; occupied leaf -> split into
+ *     eight and pass both points down); depth 10 cannot split and keeps a list.
+ *   - node statistics updated as each point is passed to a node: n, total
+ *     momentum P = sum p, position sum (centroid = sum q / n, reading R8), the
+ *     FP32 "actual range" [lo, hi]; the backward stage adds A = sum alpha and
+ *     B = sum beta.
+ *   - traversal for a target point m (three cases of Sec. 2.2): a node with
+ *     n >= 2 whose actual range lies farther than the threshold from q_m is one
+ *     interaction with its summary; a leaf is computed exactly point by point;
+ *     any other node is opened.  "Farther than the threshold" (reading R9) is
+ *     dist^2(q32_m, [lo,hi]) > r*r in FP32, with r = (float)(thresh * sigma),
+ *     dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
+ *   - summary interaction (Eq. 4 and the replacement rules after it, with the
+ *     n_k multiplicity of readings R10/R11): the node acts as one source point
+ *     at the centroid with momentum P, position derivative A and momentum
+ *     derivative B/n.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#if !defined(FLT_EVAL_METHOD) || FLT_EVAL_METHOD != 0
+#error "the FP32 decision rule needs FLT_EVAL_METHOD == 0 (no excess precision)"
+#endif
+
+#define GSREF_EXACT 0
+#define GSREF_BH 1
+#define MAX_DEPTH 10
+
+/* ------------------------------------------------------------------------ */
+/* Pair interactions.  A "source" s is either a point or a node summary.      */
+/* ------------------------------------------------------------------------ */
+
+/* Forward contribution of source (qs, ps) to target (qm, pm): Eq. 1 / Eq. 3. */
+static void fwd_pair(const double *qm, const double *pm, const double *qs,
+                     const double *ps, double sigma, double *f, double *phi) {
+  double d0 = qm[0] - qs[0], d1 = qm[1] - qs[1], d2 = qm[2] - qs[2];
+  double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  double g = exp(-r2 / (2.0 * sigma * sigma));
+  double c = pm[0] * ps[0] + pm[1] * ps[1] + pm[2] * ps[2];
+  f[0] += g * ps[0];
+  f[1] += g * ps[1];
+  f[2] += g * ps[2];
+  phi[0] += c * g * d0;
+  phi[1] += c * g * d1;
+  phi[2] += c * g * d2;
+}
+
+/* Adjoint contribution of source (qs, ps, as, bs) to target m (formulas in the
+ * header).  da and db receive the bracketed sums without the factor h; the
+ * sigma^-2 factors are applied per term so the code reads like the formula. */
+static void adj_pair(const double *qm, const double *pm, const double *am,
+                     const double *bm, const double *qs, const double *ps,
+                     const double *as, const double *bs, double sigma,
+                     double *da, double *db) {
+  double s2 = sigma * sigma;
+  double d[3] = {qm[0] - qs[0], qm[1] - qs[1], qm[2] - qs[2]};
+  double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  double g = exp(-r2 / (2.0 * s2));
+  double c = pm[0] * ps[0] + pm[1] * ps[1] + pm[2] * ps[2];
+  double am_ps = am[0] * ps[0] + am[1] * ps[1] + am[2] * ps[2];
+  double as_pm = as[0] * pm[0] + as[1] * pm[1] + as[2] * pm[2];
+  double w[3] = {bm[0] - bs[0], bm[1] - bs[1], bm[2] - bs[2]};
+  double wd = w[0] * d[0] + w[1] * d[1] + w[2] * d[2];
+  for (int a = 0; a < 3; a++) {
+    da[a] += -(g * (am_ps + as_pm) * d[a]) / s2;
+    da[a] += (c * g * (w[a] - wd * d[a] / s2)) / s2;
+    db[a] += g * as[a];
+    db[a] += (g * wd * ps[a]) / s2;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact all-pairs right-hand sides.                                         */
+/* ------------------------------------------------------------------------ */
+
+static void rhs_exact_row(int64_t N, const double *q, const double *p,
+                          double sigma, int64_t i, double *F, double *Phi) {
+  double f[3] = {0, 0, 0}, ph[3] = {0, 0, 0};
+  for (int64_t j = 0; j < N; j++)
+    fwd_pair(q + 3 * i, p + 3 * i, q + 3 * j, p + 3 * j, sigma, f, ph);
+  for (int a = 0; a < 3; a++) {
+    F[a] = f[a];
+    Phi[a] = ph[a] / (sigma * sigma);
+  }
+}
+
+static void adj_exact_row(int64_t N, const double *q, const double *p,
+                          const double *al, const double *be, double sigma,
+                          int64_t i, double *dA, double *dB) {
+  double da[3] = {0, 0, 0}, db[3] = {0, 0, 0};
+  for (int64_t j = 0; j < N; j++)
+    adj_pair(q + 3 * i, p + 3 * i, al + 3 * i, be + 3 * i, q + 3 * j,
+             p + 3 * j, al + 3 * j, be + 3 * j, sigma, da, db);
+  for (int a = 0; a < 3; a++) {
+    dA[a] = da[a];
+    dB[a] = db[a];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pointer octree built by the paper's insertion rule.                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int depth;
+  int leaf;          /* 1 = leaf (holds points), 0 = internal */
+  int64_t child[8];  /* internal: child node ids, -1 = empty cell */
+  int64_t head, tail;/* leaf: member list (in insertion order) */
+  int64_t n;         /* statistics: number of points passed to this node */
+  double sq[3], sp[3], sa[3], sb[3];
+  float lo[3], hi[3];
+} onode;
+
+typedef struct {
+  onode *nodes;
+  int64_t count, cap;
+  int64_t *next;     /* member list links, one per point */
+  uint32_t *kq;      /* quantised coordinates, 3 per point */
+  float *q32;        /* FP32-rounded positions, 3 per point */
+  const double *q, *p, *al, *be;
+} otree;
+
+static int64_t new_node(otree *t, int depth) {
+  if (t->count == t->cap) {
+    t->cap = t->cap ? 2 * t->cap : 64;
+    t->nodes = (onode *)realloc(t->nodes, (size_t)t->cap * sizeof(onode));
+  }
+  onode *nd = &t->nodes[t->count];
+  memset(nd, 0, sizeof(*nd));
+  nd->depth = depth;
+  nd->leaf = 1;
+  nd->head = nd->tail = -1;
+  for (int c = 0; c < 8; c++) nd->child[c] = -1;
+  for (int a = 0; a < 3; a++) {
+    nd->lo[a] = INFINITY;
+    nd->hi[a] = -INFINITY;
+  }
+  return t->count++;
+}
+
+/* Statistics update when point i is passed to node k (Sec. 2.2). */
+static void add_stats(otree *t, int64_t k, int64_t i) {
+  onode *nd = &t->nodes[k];
+  nd->n += 1;
+  for (int a = 0; a < 3; a++) {
+    nd->sq[a] += t->q[3 * i + a];
+    nd->sp[a] += t->p[3 * i + a];
+    if (t->al) nd->sa[a] += t->al[3 * i + a];
+    if (t->be) nd->sb[a] += t->be[3 * i + a];
+    float x = t->q32[3 * i + a];
+    if (x < nd->lo[a]) nd->lo[a] = x;
+    if (x > nd->hi[a]) nd->hi[a] = x;
+  }
+}
+
+static int octant(const otree *t, int64_t i, int depth) {
+  int b = 9 - depth;
+  return (int)((((t->kq[3 * i + 0] >> b) & 1u) << 2) |
+               (((t->kq[3 * i + 1] >> b) & 1u) << 1) |
+               ((t->kq[3 * i + 2] >> b) & 1u));
+}
+
+static void leaf_append(otree *t, int64_t k, int64_t i) {
+  onode *nd = &t->nodes[k];
+  t->next[i] = -1;
+  if (nd->tail < 0) nd->head = i;
+  else t->next[nd->tail] = i;
+  nd->tail = i;
+}
+
+/* Pass point i to node k: the three-case recursion of Sec. 2.2. */
+static void insert(otree *t, int64_t k, int64_t i) {
+  for (;;) {
+    add_stats(t, k, i);
+    onode *nd = &t->nodes[k];
+    if (!nd->leaf) { /* case 1: internal node, descend */
+      int o = octant(t, i, nd->depth);
+      if (nd->child[o] < 0) {
+        int64_t c = new_node(t, nd->depth + 1);
+        t->nodes[k].child[o] = c;
+      }
+      k = t->nodes[k].child[o];
+      continue;
+    }
+    if (nd->head < 0) { /* case 2: empty leaf, store and stop */
+      leaf_append(t, k, i);
+      return;
+    }
+    if (nd->depth == MAX_DEPTH) { /* finest cell: keep a list */
+      leaf_append(t, k, i);
+      return;
+    }
+    /* case 3: occupied leaf -> subdivide, pass the resident point down, then
+     * continue passing point i down from this (now internal) node.  The
+     * resident point's statistics are already counted in this node. */
+    int64_t e = nd->head;
+    nd->leaf = 0;
+    nd->head = nd->tail = -1;
+    int oe = octant(t, e, nd->depth);
+    int64_t ce = new_node(t, t->nodes[k].depth + 1);
+    t->nodes[k].child[oe] = ce;
+    add_stats(t, ce, e);
+    leaf_append(t, ce, e);
+    /* point i: descend from the new internal node without re-counting it */
+    int oi = octant(t, i, t->nodes[k].depth);
+    if (t->nodes[k].child[oi] < 0) {
+      int64_t ci = new_node(t, t->nodes[k].depth + 1);
+      t->nodes[k].child[oi] = ci;
+    }
+    k = t->nodes[k].child[oi];
+  }
+}
+
+/* Quantised coordinates of reading R7 from the FP32 positions. */
+static void quantise(int64_t N, const float *q32, float lo[3], float hi[3],
+                     uint32_t *kq) {
+  for (int a = 0; a < 3; a++) {
+    lo[a] = INFINITY;
+    hi[a] = -INFINITY;
+  }
+  for (int64_t i = 0; i < N; i++)
+    for (int a = 0; a < 3; a++) {
+      if (q32[3 * i + a] < lo[a]) lo[a] = q32[3 * i + a];
+      if (q32[3 * i + a] > hi[a]) hi[a] = q32[3 * i + a];
+    }
+  for (int a = 0; a < 3; a++) {
+    float ext = hi[a] - lo[a];
+    float inv = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    for (int64_t i = 0; i < N; i++) {
+      uint32_t k = 0;
+      if (ext > 0.0f) {
+        float u = (q32[3 * i + a] - lo[a]) * inv;
+        k = (uint32_t)u;
+        if (k > 1023u) k = 1023u;
+      }
+      kq[3 * i + a] = k;
+    }
+  }
+}
+
+static void tree_build(otree *t, int64_t N, const double *q, const double *p,
+                       const double *al, const double *be) {
+  memset(t, 0, sizeof(*t));
+  t->q = q;
+  t->p = p;
+  t->al = al;
+  t->be = be;
+  t->next = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+  t->kq = (uint32_t *)malloc((size_t)N * 3 * sizeof(uint32_t));
+  t->q32 = (float *)malloc((size_t)N * 3 * sizeof(float));
+  for (int64_t i = 0; i < 3 * N; i++) t->q32[i] = (float)q[i];
+  float lo[3], hi[3];
+  quantise(N, t->q32, lo, hi, t->kq);
+  new_node(t, 0); /* root */
+  for (int64_t i = 0; i < N; i++) insert(t, 0, i);
+}
+
+static void tree_free(otree *t) {
+  free(t->nodes);
+  free(t->next);
+  free(t->kq);
+  free(t->q32);
+}
+
+/* Threshold r*r of reading R9, in FP32. */
+static float far_threshold(double thresh, double sigma) {
+  float r = (float)(thresh * sigma);
+  return r * r;
+}
+
+/* Reading R9: is the node's actual range farther than the threshold? */
+static int is_far(const float *x, const onode *nd, float thr) {
+  float dd[3];
+  for (int a = 0; a < 3; a++) {
+    float t = 0.0f;
+    float u = nd->lo[a] - x[a];
+    float v = x[a] - nd->hi[a];
+    if (u > t) t = u;
+    if (v > t) t = v;
+    dd[a] = t;
+  }
+  float d2 = dd[0] * dd[0];
+  d2 = d2 + dd[1] * dd[1];
+  d2 = d2 + dd[2] * dd[2];
+  return d2 > thr;
+}
+
+/* Interaction lists are produced by the same traversal, so tests can check
+ * which sources each target took (kind 0 = point, 1 = node summary). */
+typedef struct {
+  int64_t *kind, *id;
+  int64_t len, cap;
+} ilist;
+
+typedef struct {
+  const otree *t;
+  double sigma;
+  float thr;
+  int adjoint;
+  int64_t m;
+  double acc0[3], acc1[3];
+  int64_t n_point, n_node;
+  ilist *list;
+} visit_ctx;
+
+static void record(visit_ctx *v, int64_t kind, int64_t id) {
+  if (!v->list) return;
+  if (v->list->len < v->list->cap) {
+    v->list->kind[v->list->len] = kind;
+    v->list->id[v->list->len] = id;
+  }
+  v->list->len++;
+}
+
+static void point_source(visit_ctx *v, int64_t s) {
+  const otree *t = v->t;
+  int64_t m = v->m;
+  if (!v->adjoint)
+    fwd_pair(t->q + 3 * m, t->p + 3 * m, t->q + 3 * s, t->p + 3 * s, v->sigma,
+             v->acc0, v->acc1);
+  else
+    adj_pair(t->q + 3 * m, t->p + 3 * m, t->al + 3 * m, t->be + 3 * m,
+             t->q + 3 * s, t->p + 3 * s, t->al + 3 * s, t->be + 3 * s,
+             v->sigma, v->acc0, v->acc1);
+  v->n_point++;
+  record(v, 0, s);
+}
+
+static void node_source(visit_ctx *v, int64_t k) {
+  const otree *t = v->t;
+  const onode *nd = &t->nodes[k];
+  int64_t m = v->m;
+  double n = (double)nd->n;
+  double qc[3] = {nd->sq[0] / n, nd->sq[1] / n, nd->sq[2] / n};
+  if (!v->adjoint) {
+    fwd_pair(t->q + 3 * m, t->p + 3 * m, qc, nd->sp, v->sigma, v->acc0,
+             v->acc1);
+  } else {
+    double bavg[3] = {nd->sb[0] / n, nd->sb[1] / n, nd->sb[2] / n};
+    adj_pair(t->q + 3 * m, t->p + 3 * m, t->al + 3 * m, t->be + 3 * m, qc,
+             nd->sp, nd->sa, bavg, v->sigma, v->acc0, v->acc1);
+  }
+  v->n_node++;
+  record(v, 1, k);
+}
+
+static void visit(visit_ctx *v, int64_t k) {
+  const otree *t = v->t;
+  const onode *nd = &t->nodes[k];
+  if (nd->n == 0) return;
+  if (nd->n >= 2 && is_far(t->q32 + 3 * v->m, nd, v->thr)) {
+    node_source(v, k); /* case 2: summarised far node */
+    return;
+  }
+  if (nd->leaf) { /* case 1 (and a finest-cell list): exact */
+    for (int64_t s = nd->head; s >= 0; s = t->next[s]) point_source(v, s);
+    return;
+  }
+  for (int c = 0; c < 8; c++) /* case 3: open the node */
+    if (nd->child[c] >= 0) visit(v, nd->child[c]);
+}
+
+static void bh_target(const otree *t, double sigma, float thr, int adjoint,
+                      int64_t m, double *o0, double *o1, int64_t *np,
+                      int64_t *nn, ilist *list) {
+  visit_ctx v;
+  memset(&v, 0, sizeof(v));
+  v.t = t;
+  v.sigma = sigma;
+  v.thr = thr;
+  v.adjoint = adjoint;
+  v.m = m;
+  v.list = list;
+  visit(&v, 0);
+  for (int a = 0; a < 3; a++) {
+    o0[a] = v.acc0[a];
+    o1[a] = v.acc1[a];
+  }
+  *np = v.n_point;
+  *nn = v.n_node;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public right-hand sides.                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Forward right-hand side (F, Phi) of Eq. 1 for every point.  mode 0 = exact
+ * all pairs (Sec. 2.1); mode 1 = Barnes-Hut (Sec. 2.2).  counts (optional,
+ * 2 entries) receives the number of point-point and point-node interactions. */
+void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
+               int mode, double thresh, double *F, double *Phi,
+               int64_t *counts) {
+  int64_t np_tot = 0, nn_tot = 0;
+  if (mode == GSREF_EXACT) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++)
+      rhs_exact_row(N, q, p, sigma, i, F + 3 * i, Phi + 3 * i);
+    np_tot = N * N;
+  } else {
+    otree t;
+    tree_build(&t, N, q, p, NULL, NULL);
+    float thr = far_threshold(thresh, sigma);
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
+    for (int64_t i = 0; i < N; i++) {
+      int64_t a, b;
+      bh_target(&t, sigma, thr, 0, i, F + 3 * i, Phi + 3 * i, &a, &b, NULL);
+      for (int c = 0; c < 3; c++) Phi[3 * i + c] /= sigma * sigma;
+      np_tot += a;
+      nn_tot += b;
+    }
+    tree_free(&t);
+  }
+  if (counts) {
+    counts[0] = np_tot;
+    counts[1] = nn_tot;
+  }
+}
+
+/* Exact forward right-hand side for selected rows only (sampled parity). */
+void gsref_rhs_rows(int64_t N, const double *q, const double *p, double sigma,
+                    int64_t nrows, const int64_t *rows, double *F,
+                    double *Phi) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrows; r++)
+    rhs_exact_row(N, q, p, sigma, rows[r], F + 3 * r, Phi + 3 * r);
+}
+
+/* Adjoint right-hand side: dA, dB such that alpha^k = a + h dA and
+ * beta^k = b + h dB (a = alpha^{k+1}, b = beta^{k+1}). */
+void gsref_adj_rhs(int64_t N, const double *q, const double *p,
+                   const double *al, const double *be, double sigma, int mode,
+                   double thresh, double *dA, double *dB, int64_t *counts) {
+  int64_t np_tot = 0, nn_tot = 0;
+  if (mode == GSREF_EXACT) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++)
+      adj_exact_row(N, q, p, al, be, sigma, i, dA + 3 * i, dB + 3 * i);
+    np_tot = N * N;
+  } else {
+    otree t;
+    tree_build(&t, N, q, p, al, be);
+    float thr = far_threshold(thresh, sigma);
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
+    for (int64_t i = 0; i < N; i++) {
+      int64_t a, b;
+      bh_target(&t, sigma, thr, 1, i, dA + 3 * i, dB + 3 * i, &a, &b, NULL);
+      np_tot += a;
+      nn_tot += b;
+    }
+    tree_free(&t);
+  }
+  if (counts) {
+    counts[0] = np_tot;
+    counts[1] = nn_tot;
+  }
+}
+
+void gsref_adj_rhs_rows(int64_t N, const double *q, const double *p,
+                        const double *al, const double *be, double sigma,
+                        int64_t nrows, const int64_t *rows, double *dA,
+                        double *dB) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrows; r++)
+    adj_exact_row(N, q, p, al, be, sigma, rows[r], dA + 3 * r, dB + 3 * r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shooting and its gradient.                                                 */
+/* ------------------------------------------------------------------------ */
+
+static double half_p_dot_F(int64_t N, const double *p, const double *F) {
+  double s = 0.0;
+  for (int64_t i = 0; i < 3 * N; i++) s += p[i] * F[i];
+  return 0.5 * s;
+}
+
+/* Geodesic shooting (Eq. 1, Euler, h = 1/T).  H (optional, 2 entries) gets
+ * H(q^0,p^0) and H(q^T,p^T) = 1/2 sum_i p_i . F_i in the same mode. */
+void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
+                 int T, int mode, double thresh, double *q1, double *p1,
+                 double *H) {
+  double *F = (double *)malloc((size_t)N * 3 * sizeof(double));
+  double *Phi = (double *)malloc((size_t)N * 3 * sizeof(double));
+  double h = 1.0 / (double)T;
+  memcpy(q1, q0, (size_t)N * 3 * sizeof(double));
+  memcpy(p1, p0, (size_t)N * 3 * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, F, Phi, NULL);
+    if (k == 0 && H) H[0] = half_p_dot_F(N, p1, F);
+    for (int64_t i = 0; i < 3 * N; i++) {
+      q1[i] += h * F[i];
+      p1[i] += h * Phi[i];
+    }
+  }
+  if (H) {
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, F, Phi, NULL);
+    H[1] = half_p_dot_F(N, p1, F);
+  }
+  free(F);
+  free(Phi);
+}
+
+/* Objective (Eq. 2) and its gradient with respect to p0 by the discrete
+ * adjoint.  E gets {total, H(q0,p0), lambda * sum |q^T - X|^2}; q1 (optional)
+ * gets q^T.  The whole trajectory is stored (plain, no checkpointing). */
+void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
+                      const double *X, double sigma, int T, double lambda,
+                      int mode, double thresh, double *E, double *grad,
+                      double *q1) {
+  size_t sz = (size_t)N * 3;
+  double *qs = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
+  double *ps = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
+  double *F = (double *)malloc(sz * sizeof(double));
+  double *F0 = (double *)malloc(sz * sizeof(double));
+  double *Phi = (double *)malloc(sz * sizeof(double));
+  double *al = (double *)malloc(sz * sizeof(double));
+  double *be = (double *)malloc(sz * sizeof(double));
+  double *dA = (double *)malloc(sz * sizeof(double));
+  double *dB = (double *)malloc(sz * sizeof(double));
+  double h = 1.0 / (double)T;
+  memcpy(qs, q0, sz * sizeof(double));
+  memcpy(ps, p0, sz * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    double *qk = qs + (size_t)k * sz, *pk = ps + (size_t)k * sz;
+    gsref_rhs(N, qk, pk, sigma, mode, thresh, F, Phi, NULL);
+    if (k == 0) memcpy(F0, F, sz * sizeof(double));
+    for (size_t i = 0; i < sz; i++) {
+      qk[sz + i] = qk[i] + h * F[i];
+      pk[sz + i] = pk[i] + h * Phi[i];
+    }
+  }
+  const double *qT = qs + (size_t)T * sz;
+  double data = 0.0;
+  for (size_t i = 0; i < sz; i++) {
+    double r = qT[i] - X[i];
+    data += r * r;
+  }
+  double H0 = half_p_dot_F(N, p0, F0);
+  E[0] = H0 + lambda * data;
+  E[1] = H0;
+  E[2] = lambda * data;
+  for (size_t i = 0; i < sz; i++) {
+    al[i] = 2.0 * lambda * (qT[i] - X[i]);
+    be[i] = 0.0;
+  }
+  for (int k = T - 1; k >= 0; k--) {
+    gsref_adj_rhs(N, qs + (size_t)k * sz, ps + (size_t)k * sz, al, be, sigma,
+                  mode, thresh, dA, dB, NULL);
+    for (size_t i = 0; i < sz; i++) {
+      al[i] += h * dA[i];
+      be[i] += h * dB[i];
+    }
+  }
+  for (size_t i = 0; i < sz; i++) grad[i] = be[i] + F0[i];
+  if (q1) memcpy(q1, qT, sz * sizeof(double));
+  free(qs);
+  free(ps);
+  free(F);
+  free(F0);
+  free(Phi);
+  free(al);
+  free(be);
+  free(dA);
+  free(dB);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree inspection for tests.                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Per-point quantised coordinates and the 30-bit Morton code of reading R7
+ * (bit 3b+2 = x bit b, 3b+1 = y bit b, 3b = z bit b). */
+void gsref_morton(int64_t N, const double *q, uint32_t *kq, uint32_t *code) {
+  float *q32 = (float *)malloc((size_t)N * 3 * sizeof(float));
+  for (int64_t i = 0; i < 3 * N; i++) q32[i] = (float)q[i];
+  float lo[3], hi[3];
+  quantise(N, q32, lo, hi, kq);
+  for (int64_t i = 0; i < N; i++) {
+    uint32_t c = 0;
+    for (int b = 0; b < 10; b++) {
+      c |= ((kq[3 * i + 0] >> b) & 1u) << (3 * b + 2);
+      c |= ((kq[3 * i + 1] >> b) & 1u) << (3 * b + 1);
+      c |= ((kq[3 * i + 2] >> b) & 1u) << (3 * b);
+    }
+    code[i] = c;
+  }
+  free(q32);
+}
+
+typedef struct {
+  const otree *t;
+  int64_t *order;   /* DFS point order */
+  int64_t npos;
+  int64_t *remap;   /* pool id -> preorder id */
+  int64_t nid;
+} dfs_ctx;
+
+static void dfs(dfs_ctx *c, int64_t k) {
+  const onode *nd = &c->t->nodes[k];
+  c->remap[k] = c->nid++;
+  if (nd->leaf) {
+    for (int64_t s = nd->head; s >= 0; s = c->t->next[s]) c->order[c->npos++] = s;
+    return;
+  }
+  for (int o = 0; o < 8; o++)
+    if (nd->child[o] >= 0) dfs(c, nd->child[o]);
+}
+
+/* Builds the tree on (q, p, alpha, beta) (alpha/beta may be NULL) and exports
+ * it in DFS preorder (children in octant order).  order[N] gets the DFS point
+ * order.  For each node (up to cap): info[6*k..] = {depth, leaf, n, first
+ * DFS position of its points, number of non-empty children, parent preorder
+ * id (-1 for the root)}; stat[12*k..] = {sum q (3), sum p (3), sum alpha (3),
+ * sum beta (3)} in FP64 (12 per node) and range[6*k..] = {lo (3), hi (3)} in FP32.
+ * Returns the number of nodes. */
+int64_t gsref_tree(int64_t N, const double *q, const double *p,
+                   const double *al, const double *be, int64_t *order,
+                   int64_t cap, int64_t *info, double *stat, float *range) {
+  otree t;
+  tree_build(&t, N, q, p, al, be);
+  dfs_ctx c;
+  c.t = &t;
+  c.order = order;
+  c.npos = 0;
+  c.remap = (int64_t *)malloc((size_t)t.count * sizeof(int64_t));
+  c.nid = 0;
+  dfs(&c, 0);
+  /* first DFS position of each node: smallest position among its members,
+   * found by a second walk that tracks the running position */
+  int64_t *first = (int64_t *)malloc((size_t)t.count * sizeof(int64_t));
+  int64_t *parent = (int64_t *)malloc((size_t)t.count * sizeof(int64_t));
+  for (int64_t k = 0; k < t.count; k++) parent[k] = -1;
+  for (int64_t k = 0; k < t.count; k++)
+    if (!t.nodes[k].leaf)
+      for (int o = 0; o < 8; o++)
+        if (t.nodes[k].child[o] >= 0) parent[t.nodes[k].child[o]] = k;
+  {
+    /* explicit-stack walk in the same order as dfs() */
+    int64_t *stack = (int64_t *)malloc((size_t)(t.count + 1) * sizeof(int64_t));
+    int64_t sp = 0, pos = 0;
+    stack[sp++] = 0;
+    while (sp) {
+      int64_t k = stack[--sp];
+      first[k] = pos;
+      if (t.nodes[k].leaf) {
+        for (int64_t s = t.nodes[k].head; s >= 0; s = t.next[s]) pos++;
+      } else {
+        for (int o = 7; o >= 0; o--)
+          if (t.nodes[k].child[o] >= 0) stack[sp++] = t.nodes[k].child[o];
+      }
+    }
+    free(stack);
+  }
+  for (int64_t k = 0; k < t.count; k++) {
+    int64_t id = c.remap[k];
+    if (id >= cap) continue;
+    const onode *nd = &t.nodes[k];
+    int nc = 0;
+    if (!nd->leaf)
+      for (int o = 0; o < 8; o++)
+        if (nd->child[o] >= 0) nc++;
+    info[6 * id + 0] = nd->depth;
+    info[6 * id + 1] = nd->leaf;
+    info[6 * id + 2] = nd->n;
+    info[6 * id + 3] = first[k];
+    info[6 * id + 4] = nc;
+    info[6 * id + 5] = parent[k] >= 0 ? c.remap[parent[k]] : -1;
+    for (int a = 0; a < 3; a++) {
+      stat[12 * id + a] = nd->sq[a];
+      stat[12 * id + 3 + a] = nd->sp[a];
+      stat[12 * id + 6 + a] = nd->sa[a];
+      stat[12 * id + 9 + a] = nd->sb[a];
+      range[6 * id + a] = nd->lo[a];
+      range[6 * id + 3 + a] = nd->hi[a];
+    }
+  }
+  int64_t count = t.count;
+  free(first);
+  free(parent);
+  free(c.remap);
+  tree_free(&t);
+  return count;
+}
+
+/* Interaction list of target m under Barnes-Hut: kind[r] = 0 (point, id =
+ * point index) or 1 (node summary, id = preorder node id as exported by
+ * gsref_tree).  Returns the list length (entries beyond cap are dropped). */
+int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
+                      double sigma, double thresh, int64_t m, int64_t cap,
+                      int64_t *kind, int64_t *id) {
+  otree t;
+  tree_build(&t, N, q, p, NULL, NULL);
+  dfs_ctx c;
+  int64_t *order = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+  c.t = &t;
+  c.order = order;
+  c.npos = 0;
+  c.remap = (int64_t *)malloc((size_t)t.count * sizeof(int64_t));
+  c.nid = 0;
+  dfs(&c, 0);
+  ilist L;
+  L.kind = kind;
+  L.id = id;
+  L.len = 0;
+  L.cap = cap;
+  double o0[3], o1[3];
+  int64_t a, b;
+  bh_target(&t, sigma, far_threshold(thresh, sigma), 0, m, o0, o1, &a, &b, &L);
+  for (int64_t r = 0; r < L.len && r < cap; r++)
+    if (kind[r] == 1) id[r] = c.remap[id[r]];
+  free(order);
+  free(c.remap);
+  tree_free(&t);
+  return L.len;
+}
+
+int gsref_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
