@@ -1,0 +1,175 @@
+/*
+ * gs.h -- C ABI of libgs, GPU point-set geodesic shooting with the exact
+ * all-pairs flow and its Barnes-Hut approximation (arXiv 1907.04834).
+ *
+ * The problem (Sec. 2.1): N template points q(0) = q0 in R^3 with initial
+ * momenta p(0) = p0 evolve under the Hamiltonian H(q,p) = 1/2 <p, K(q) p>,
+ * K's 3x3 blocks G(|q_i - q_j|) I_3 with G(r) = exp(-r^2 / (2 sigma^2)):
+ *     dq_i/dt = F_i   = sum_j G(|q_i-q_j|) p_j                      (Eq. 1, 3)
+ *     dp_i/dt = Phi_i = sigma^-2 sum_j (p_i.p_j) G(|q_i-q_j|) (q_i-q_j)  (Eq. 1)
+ * integrated by explicit Euler over t in [0, 1] with T steps (h = 1/T).  The
+ * registration objective (Eq. 2) is
+ *     E(p0) = H(q0, p0) + lambda sum_i |q_i(1) - X_i|^2
+ * and its gradient with respect to p0 comes from the discrete adjoint of the
+ * Euler scheme (the "backward stage" of Sec. 2.2).  In GS_BH mode every
+ * forward and backward step evaluates the sums with the octree approximation
+ * of Sec. 2.2: nodes whose points all lie farther than thresh_sigmas * sigma
+ * from a point act as one source (centroid, total momentum, Eq. 4 and the
+ * replacements after it); leaves are summed exactly.
+ *
+ * Conventions shared by every call:
+ *   - Arrays of points are row-major N x 3 float64 (x, y, z per point), i.e.
+ *     the layout of a contiguous (N, 3) tensor.  Each pointer may be host or
+ *     device memory (detected per pointer with cudaPointerGetAttributes);
+ *     device pointers must be on the context's device.  Inputs are only read.
+ *     The caller owns all inputs and outputs; the context owns its workspace
+ *     (grown on demand, reused across calls, freed by gs_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it.  A call whose outputs are all device
+ *     pointers returns without waiting; a call with any host output
+ *     synchronises the stream before returning.
+ *   - Arithmetic: per-pair sums in FP32 (exp on the MUFU ex2 unit) with
+ *     compensated accumulation; point state, Euler update, energies and
+ *     reductions in FP64.
+ *   - Errors: host-side checks return GS_ERR_INVALID_ARG before any work is
+ *     enqueued; CUDA failures return GS_ERR_CUDA / GS_ERR_OOM.  Conditions
+ *     detected on the device (non-finite results, a bounded wait that ran
+ *     out) are recorded in a device status word that the next synchronising
+ *     call, or gs_sync, returns.  gs_last_error gives a message.
+ *   - A context is bound to one device and is not thread-safe; use one
+ *     context per host thread.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter (nothing enqueued) */
+  GS_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GS_ERR_OOM = 3,         /* workspace allocation failed */
+  GS_ERR_NONFINITE = 4,   /* NaN/Inf in a result (device-detected) */
+  GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  GS_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve */
+} gs_status;
+
+typedef enum gs_mode {
+  GS_EXACT = 0, /* all pairs, O(N^2) per step (Sec. 2.1) */
+  GS_BH = 1     /* octree / threshold approximation (Sec. 2.2) */
+} gs_mode;
+
+typedef struct gs_params {
+  double sigma;          /* Gaussian kernel width, > 0, same unit as q */
+  double lambda;         /* data-term weight of Eq. 2, >= 0 */
+  double thresh_sigmas;  /* GS_BH: a node is summarised when all its points
+                            lie farther than thresh_sigmas * sigma (paper: 3) */
+  int32_t T;             /* Euler steps over t in [0, 1], >= 1 */
+  int32_t mode;          /* gs_mode */
+  int32_t ckpt_every;    /* gs_shoot_grad: 0 = keep every step's state for the
+                            backward pass; k > 0 = keep every k-th state and
+                            recompute the others (memory (T/k + k) x N) */
+  uint32_t flags;        /* reserved, must be 0 */
+} gs_params;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Creates a context on CUDA device `device`.  *out receives the handle. */
+gs_status gs_create(int device, gs_ctx **out);
+
+/* Frees the context and its workspace (waits for its pending work). */
+void gs_destroy(gs_ctx *ctx);
+
+/* Message for the last error of this context ("" if none).  Valid until the
+ * next call on the context. */
+const char *gs_last_error(const gs_ctx *ctx);
+
+/* Waits for `stream`, then returns and clears the device status word. */
+gs_status gs_sync(gs_ctx *ctx, void *stream);
+
+/*
+ * Geodesic shooting (Sec. 2.1 Eq. 1, Euler with T steps; GS_BH: Sec. 2.2 at
+ * every step).  q0, p0: N x 3 inputs.  q1, p1: N x 3 outputs q(1), p(1)
+ * (either may be NULL).  H: NULL or 2 doubles receiving H(q0,p0) and
+ * H(q(1),p(1)) = 1/2 sum_i p_i . F_i (the energy drift check; the second
+ * costs one more right-hand-side evaluation).  N >= 1.
+ */
+gs_status gs_shoot(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
+                   const gs_params *prm, double *q1, double *p1, double *H,
+                   void *stream);
+
+/*
+ * Objective of Eq. 2 and its gradient with respect to p0 (discrete adjoint,
+ * backward stage of Sec. 2.2).  X: N x 3 targets.  E: 3 doubles {E, H(q0,p0),
+ * lambda sum |q(1) - X|^2}.  grad: N x 3 dE/dp0.  q1: NULL or N x 3 q(1).
+ * In GS_BH mode the backward steps use the tree approximation as the paper
+ * prescribes (summaries of alpha and beta), which is not the derivative of
+ * the discontinuous Barnes-Hut forward map.
+ */
+gs_status gs_shoot_grad(gs_ctx *ctx, const double *q0, const double *p0,
+                        const double *X, int64_t N, const gs_params *prm,
+                        double *E, double *grad, double *q1, void *stream);
+
+/*
+ * Many independent registrations in one launch per step.  S >= 1 subjects;
+ * offsets: host array of S+1 increasing int64, subject s owns rows
+ * [offsets[s], offsets[s+1]) of q0, p0, X, grad (each offsets[S] x 3);
+ * every subject has >= 1 point.  E: S x 3 doubles as in gs_shoot_grad.
+ * All subjects share prm.  Points interact only within their subject.
+ */
+gs_status gs_shoot_batched(gs_ctx *ctx, int32_t S, const int64_t *offsets,
+                           const double *q0, const double *p0,
+                           const double *X, const gs_params *prm, double *E,
+                           double *grad, void *stream);
+
+/* ---- single-step entry points (one right-hand side, for checks) ---------- */
+
+/* One forward right-hand side at state (q, p): F, Phi as in Eq. 1 (GS_BH:
+ * Sec. 2.2 summaries).  counts: NULL or 2 int64 {point-point interactions,
+ * point-node interactions} (GS_EXACT reports N*N and 0). */
+gs_status gs_rhs(gs_ctx *ctx, const double *q, const double *p, int64_t N,
+                 const gs_params *prm, double *F, double *Phi, int64_t *counts,
+                 void *stream);
+
+/* One adjoint right-hand side: with a = alpha^{k+1}, b = beta^{k+1} given in
+ * `al`, `be`, the backward step is alpha^k = a + h dA, beta^k = b + h dB.
+ * counts as in gs_rhs. */
+gs_status gs_adj_rhs(gs_ctx *ctx, const double *q, const double *p,
+                     const double *al, const double *be, int64_t N,
+                     const gs_params *prm, double *dA, double *dB,
+                     int64_t *counts, void *stream);
+
+/*
+ * Octree of Sec. 2.2 for positions q (N x 3), built as the GS_BH steps build
+ * it.  codes: N uint32 30-bit Morton codes per input point (bit 3b+2 = x bit
+ * b, 3b+1 = y, 3b = z, of the 10-bit quantised coordinates of the FP32
+ * position within the FP32 bounding box).  order: N int32, points sorted
+ * stably by code.  nodes: up to `cap` records of 4 int32 {depth, first,
+ * count, skip} in depth-first preorder: cells holding >= 2 points that have
+ * >= 2 non-empty child cells (or sit at depth 10), and single-point leaves
+ * (depth = -1); members are order[first .. first+count); skip = preorder
+ * index after the node's subtree.  range: NULL or cap x 6 float {lo, hi} of
+ * each node's FP32 "actual range".  *n_nodes receives the node count
+ * (N + internal nodes).  Any of codes/order/nodes/range may be NULL.
+ */
+gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
+                  int32_t *order, int32_t *nodes, float *range, int64_t cap,
+                  int64_t *n_nodes, void *stream);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+/* Measured device-wide issue rates of the units the pair kernels use, in
+ * lane-operations per second: out[0] scalar FP32 FMA, out[1] FP32 operations
+ * through packed f32x2 FMA (two per lane per instruction), out[2] MUFU ex2.
+ * Runs short synthetic kernels on `device` (about 10 ms); no context needed. */
+gs_status gs_alu_peaks(int device, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

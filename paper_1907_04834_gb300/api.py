@@ -1,0 +1,209 @@
+"""Python face of libgs: tensors in, tensors out, one C-ABI call each.
+
+Inputs are float64 ``(N, 3)`` tensors, on a CUDA device (outputs are then
+allocated there and the call is asynchronous on the current stream) or on
+the CPU (the library stages them and the call returns finished results).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+from ._lib import GS_BH, GS_EXACT, GSError, make_params
+
+_ctxs: dict[int, "Context"] = {}
+_lock = threading.Lock()
+
+
+class Context:
+    """A libgs context (workspace + device status) bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        st = self.lib.gs_create(int(device), ctypes.byref(h))
+        if st != 0:
+            raise GSError(st, f"gs_create(device={device}) failed")
+        self.handle = h
+        self.device = int(device)
+
+    def check(self, st: int):
+        if st != 0:
+            raise GSError(st, self.lib.gs_last_error(self.handle).decode())
+
+    def sync(self, stream=None):
+        self.check(self.lib.gs_sync(self.handle, _stream_ptr(self.device, stream)))
+
+    def close(self):
+        if self.handle:
+            self.lib.gs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def context(device: int | None = None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+    with _lock:
+        if device not in _ctxs:
+            _ctxs[device] = Context(device)
+        return _ctxs[device]
+
+
+def _stream_ptr(device, stream=None):
+    if not torch.cuda.is_available():
+        return None
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _pts(t, name, n=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64 (got {t.dtype})")
+    if t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError(f"{name} must have shape (N, 3) (got {tuple(t.shape)})")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} has {t.shape[0]} rows, expected {n}")
+    return t.contiguous()
+
+
+def _device_of(t: torch.Tensor) -> int | None:
+    return t.device.index if t.is_cuda else None
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ctx_for(t: torch.Tensor) -> Context:
+    d = _device_of(t)
+    return context(d if d is not None else None)
+
+
+def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, stream=None):
+    """Geodesic shooting (Eq. 1, Euler).  Returns (q1, p1, H) with H = None or
+    the tensor [H(q0,p0), H(q1,p1)]."""
+    q0 = _pts(q0, "q0")
+    p0 = _pts(p0, "p0", q0.shape[0])
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, 0.0, thresh)
+    q1, p1 = torch.empty_like(q0), torch.empty_like(q0)
+    H = torch.empty(2, dtype=torch.float64, device=q0.device) if with_H else None
+    c.check(c.lib.gs_shoot(c.handle, _ptr(q0), _ptr(p0), q0.shape[0], ctypes.byref(prm), _ptr(q1),
+                           _ptr(p1), _ptr(H), _stream_ptr(c.device, stream)))
+    return q1, p1, H
+
+
+def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_every=0,
+               stream=None):
+    """Objective of Eq. 2 and dE/dp0.  Returns (E, grad, q1) with
+    E = [E, H(q0,p0), lambda |q1 - X|^2]."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every)
+    E = torch.empty(3, dtype=torch.float64, device=q0.device)
+    grad, q1 = torch.empty_like(q0), torch.empty_like(q0)
+    c.check(c.lib.gs_shoot_grad(c.handle, _ptr(q0), _ptr(p0), _ptr(X), n, ctypes.byref(prm),
+                                _ptr(E), _ptr(grad), _ptr(q1), _stream_ptr(c.device, stream)))
+    return E, grad, q1
+
+
+def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.0, stream=None):
+    """Independent registrations of the subjects delimited by ``offsets``
+    (S+1 increasing ints).  Returns (E (S, 3), grad (N, 3))."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
+    off = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
+    S = off.numel() - 1
+    if S < 1 or int(off[-1]) != n:
+        raise ValueError("offsets must have S+1 entries ending at N")
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, lam, thresh)
+    E = torch.empty((S, 3), dtype=torch.float64, device=q0.device)
+    grad = torch.empty_like(q0)
+    c.check(c.lib.gs_shoot_batched(c.handle, S, _ptr(off), _ptr(q0), _ptr(p0), _ptr(X),
+                                   ctypes.byref(prm), _ptr(E), _ptr(grad),
+                                   _stream_ptr(c.device, stream)))
+    return E, grad
+
+
+def rhs(q, p, sigma, mode="exact", thresh=3.0, stream=None):
+    """One forward right-hand side: (F, Phi, (point pairs, node pairs))."""
+    q = _pts(q, "q")
+    p = _pts(p, "p", q.shape[0])
+    c = _ctx_for(q)
+    prm = make_params(sigma, 1, mode, 0.0, thresh)
+    F, Phi = torch.empty_like(q), torch.empty_like(q)
+    cnt = (ctypes.c_int64 * 2)()
+    c.check(c.lib.gs_rhs(c.handle, _ptr(q), _ptr(p), q.shape[0], ctypes.byref(prm), _ptr(F),
+                         _ptr(Phi), cnt, _stream_ptr(c.device, stream)))
+    return F, Phi, (cnt[0], cnt[1])
+
+
+def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, stream=None):
+    """One adjoint right-hand side: (dA, dB, counts)."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    p, al, be = _pts(p, "p", n), _pts(al, "al", n), _pts(be, "be", n)
+    c = _ctx_for(q)
+    prm = make_params(sigma, 1, mode, 0.0, thresh)
+    dA, dB = torch.empty_like(q), torch.empty_like(q)
+    cnt = (ctypes.c_int64 * 2)()
+    c.check(c.lib.gs_adj_rhs(c.handle, _ptr(q), _ptr(p), _ptr(al), _ptr(be), n,
+                             ctypes.byref(prm), _ptr(dA), _ptr(dB), cnt,
+                             _stream_ptr(c.device, stream)))
+    return dA, dB, (cnt[0], cnt[1])
+
+
+def tree(q, stream=None):
+    """The octree the Barnes-Hut steps build on q: dict with ``codes`` (N,)
+    Morton codes, ``order`` (N,), ``nodes`` (M, 4) {depth, first, count,
+    skip} in preorder (depth -1 = single-point leaf), ``range`` (M, 6)."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    c = _ctx_for(q)
+    cap = 2 * n + 8
+    dev = q.device
+    codes = torch.empty(n, dtype=torch.int32, device=dev)
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    nodes = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    rng = torch.empty((cap, 6), dtype=torch.float32, device=dev)
+    m = ctypes.c_int64()
+    c.check(c.lib.gs_tree(c.handle, _ptr(q), n, _ptr(codes), _ptr(order), _ptr(nodes), _ptr(rng),
+                          cap, ctypes.byref(m), _stream_ptr(c.device, stream)))
+    M = m.value
+    return dict(codes=codes, order=order, nodes=nodes[:M], range=rng[:M], n_nodes=M)
+
+
+class GeodesicShoot(torch.autograd.Function):
+    """E(p0) of Eq. 2 as an autograd function of p0; the backward pass returns
+    the adjoint gradient computed together with E."""
+
+    @staticmethod
+    def forward(ctx, p0, q0, X, sigma, T, lam, mode, thresh, ckpt_every):
+        E, grad, _ = shoot_grad(q0, p0.detach(), X, sigma, T, lam, mode, thresh, ckpt_every)
+        ctx.save_for_backward(grad)
+        return E[0]
+
+    @staticmethod
+    def backward(ctx, gE):
+        (grad,) = ctx.saved_tensors
+        return gE * grad, None, None, None, None, None, None, None, None
+
+
+def energy(p0, q0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_every=0):
+    """Differentiable registration objective E(p0) (Eq. 2)."""
+    return GeodesicShoot.apply(p0, q0, X, sigma, T, lam, mode, thresh, ckpt_every)

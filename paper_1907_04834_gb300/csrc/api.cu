@@ -1,0 +1,651 @@
+// api.cu -- the C ABI of libgs (include/gs.h): contexts, argument checks,
+// host/device pointer handling, workspace, and the step drivers that chain
+// the kernels for shooting, the adjoint and the single-step calls.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gs.h"
+#include "kernels.h"
+#include "tree.h"
+
+namespace gs {
+
+// Owning device buffer that only grows.
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace gs
+
+using namespace gs;
+
+struct gs_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  int* d_status = nullptr;  // device status word (ST_* bits)
+  // staging of host inputs / outputs
+  DevMem in_q, in_p, in_a, in_b, in_X, out_a, out_b;
+  // solver state
+  DevMem q, p, al, be, F0, pf, r2, scal;
+  DevMem packs, raws, abpacks, ckpt;
+  DevMem part, tickets;
+  size_t tickets_n = 0;
+  TreeWork tree;  // Barnes-Hut workspace (tree.h)
+};
+
+namespace {
+
+// scal slots (doubles)
+enum { SC_CENTER = 0, SC_H0 = 3, SC_H1 = 4, SC_DATA = 5, SC_E = 6, SC_N = 16 };
+
+constexpr double kLog2e = 1.4426950408889634;
+
+gs_status fail(gs_ctx* c, gs_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+gs_status cuda_fail(gs_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
+  if (!prm) return fail(c, GS_ERR_INVALID_ARG, "params is NULL");
+  if (!(prm->sigma > 0.0) || !std::isfinite(prm->sigma))
+    return fail(c, GS_ERR_INVALID_ARG, "sigma must be finite and > 0 (got %g)", prm->sigma);
+  if (prm->T < 1 || prm->T > 1000000)
+    return fail(c, GS_ERR_INVALID_ARG, "T must be in [1, 1e6] (got %d)", prm->T);
+  if (prm->mode != GS_EXACT && prm->mode != GS_BH)
+    return fail(c, GS_ERR_INVALID_ARG, "mode must be GS_EXACT or GS_BH (got %d)", prm->mode);
+  if (prm->mode == GS_BH && (!(prm->thresh_sigmas > 0.0) || std::isnan(prm->thresh_sigmas)))
+    return fail(c, GS_ERR_INVALID_ARG, "thresh_sigmas must be > 0 (got %g)", prm->thresh_sigmas);
+  if (need_lambda && (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda)))
+    return fail(c, GS_ERR_INVALID_ARG, "lambda must be finite and >= 0 (got %g)", prm->lambda);
+  if (prm->ckpt_every < 0)
+    return fail(c, GS_ERR_INVALID_ARG, "ckpt_every must be >= 0 (got %d)", prm->ckpt_every);
+  if (prm->flags != 0) return fail(c, GS_ERR_INVALID_ARG, "flags must be 0");
+  return GS_OK;
+}
+
+gs_status check_n(gs_ctx* c, int64_t N) {
+  if (N < 1 || N > (int64_t(1) << 30))
+    return fail(c, GS_ERR_INVALID_ARG, "N must be in [1, 2^30] (got %lld)", (long long)N);
+  return GS_OK;
+}
+
+// Is `ptr` device memory of this context's device?  Host memory (pageable or
+// pinned) is reported as host.
+gs_status locate(gs_ctx* c, const void* ptr, const char* name, bool* on_device) {
+  if (!ptr) return fail(c, GS_ERR_INVALID_ARG, "%s is NULL", name);
+  if (reinterpret_cast<uintptr_t>(ptr) % 8 != 0)
+    return fail(c, GS_ERR_INVALID_ARG, "%s is not 8-byte aligned", name);
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *on_device = false;
+    return GS_OK;
+  }
+  if (a.type == cudaMemoryTypeDevice) {
+    if (a.device != c->device)
+      return fail(c, GS_ERR_INVALID_ARG, "%s lives on device %d, context on %d", name, a.device,
+                  c->device);
+    *on_device = true;
+  } else {
+    *on_device = (a.type == cudaMemoryTypeManaged);
+  }
+  return GS_OK;
+}
+
+// Device view of an input array of n doubles (staged if it is host memory).
+gs_status input(gs_ctx* c, const double* user, size_t n, const char* name, DevMem& stage,
+                cudaStream_t st, const double** out) {
+  bool dev = false;
+  gs_status s = locate(c, user, name, &dev);
+  if (s != GS_OK) return s;
+  if (dev) {
+    *out = user;
+    return GS_OK;
+  }
+  CK(stage.ensure(n * sizeof(double)), "staging allocation");
+  CK(cudaMemcpyAsync(stage.p, user, n * sizeof(double), cudaMemcpyHostToDevice, st), "H2D copy");
+  *out = stage.as<double>();
+  return GS_OK;
+}
+
+// Output check: returns whether `user` is host memory (then the call syncs).
+gs_status output(gs_ctx* c, const void* user, const char* name, bool* host) {
+  bool dev = false;
+  gs_status s = locate(c, user, name, &dev);
+  if (s != GS_OK) return s;
+  *host = !dev;
+  return GS_OK;
+}
+
+gs_status copy_out(gs_ctx* c, void* user, const void* src, size_t bytes, cudaStream_t st) {
+  CK(cudaMemcpyAsync(user, src, bytes, cudaMemcpyDefault, st), "result copy");
+  return GS_OK;
+}
+
+gs_status read_status(gs_ctx* c, cudaStream_t st) {
+  int h = 0;
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  CK(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (h) CK(cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
+  if (h & ST_TIMEOUT)
+    return fail(c, GS_ERR_TIMEOUT, "a bounded device-side wait gave up (data not delivered)");
+  if (h & ST_NONFINITE) return fail(c, GS_ERR_NONFINITE, "non-finite value in a result");
+  return GS_OK;
+}
+
+// ------------------------------------------------------------------ solver
+struct Solver {
+  gs_ctx* c;
+  cudaStream_t st;
+  int64_t N, Npad;
+  int T, mode;
+  double sigma, s, h, lambda;
+  float thr;  // Barnes-Hut threshold (r*r, FP32)
+  ExactGeom gf, ga;
+  size_t pack_f4;  // float4 per pack slot
+  int slots;       // pack slots allocated
+
+  float4* pack(int k) const { return c->packs.as<float4>() + (size_t)k * pack_f4; }
+  float4* raw(int k) const { return c->raws.as<float4>() + (size_t)k * Npad; }
+  float4* abpack(int k) const { return c->abpacks.as<float4>() + (size_t)k * pack_f4; }
+  double* scal(int k) const { return c->scal.as<double>() + k; }
+};
+
+int choose_J(int n_itiles, int n_jtiles, int slots) {
+  // smallest J giving >= 2 full waves, then the J (up to 4 waves) whose last
+  // wave is fullest
+  int best = 1;
+  double best_eff = -1.0;
+  int jmin = std::max(1, (2 * slots + n_itiles - 1) / n_itiles);
+  int jmax = std::max(jmin, (6 * slots + n_itiles - 1) / n_itiles);
+  jmin = std::min(jmin, n_jtiles);
+  jmax = std::min(jmax, n_jtiles);
+  for (int J = jmin; J <= jmax; J++) {
+    double waves = (double)n_itiles * J / slots;
+    double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = J;
+    }
+  }
+  return std::max(1, std::min(best, n_jtiles));
+}
+
+gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int slots,
+                      bool adjoint, cudaStream_t st) {
+  S.c = c;
+  S.st = st;
+  S.N = N;
+  S.Npad = (N + EX_TILE - 1) / EX_TILE * EX_TILE;
+  S.T = prm->T;
+  S.mode = prm->mode;
+  S.sigma = prm->sigma;
+  S.s = std::sqrt(kLog2e / (2.0 * prm->sigma * prm->sigma));
+  S.h = 1.0 / (double)prm->T;
+  S.lambda = prm->lambda;
+  {
+    float r = (float)(prm->thresh_sigmas * prm->sigma);
+    S.thr = r * r;
+  }
+  S.pack_f4 = (size_t)(S.Npad / 2) * 3;
+  S.slots = slots;
+  ExactGeom g;
+  g.N = N;
+  g.Npad = S.Npad;
+  g.n_itiles = (int)(S.Npad / EX_NT);
+  g.n_jtiles = (int)(S.Npad / EX_TILE);
+  g.J = choose_J(g.n_itiles, g.n_jtiles, 3 * c->num_sms);
+  S.gf = g;
+  g.J = choose_J(g.n_itiles, g.n_jtiles, 2 * c->num_sms);
+  S.ga = g;
+  const size_t n3 = (size_t)N * 3;
+  CK(c->q.ensure(n3 * 8), "workspace");
+  CK(c->p.ensure(n3 * 8), "workspace");
+  CK(c->F0.ensure(n3 * 8), "workspace");
+  CK(c->pf.ensure((size_t)N * 8), "workspace");
+  CK(c->scal.ensure(SC_N * 8), "workspace");
+  // pack slots: zero-filled so padding sources carry p = 0 (and a = b = 0)
+  size_t pbytes = (size_t)slots * S.pack_f4 * sizeof(float4);
+  CK(c->packs.ensure(pbytes), "workspace");
+  CK(launch_pad_zero(c->packs.as<float4>(), S.pack_f4, slots, N, S.Npad, st), "pad");
+  if (S.mode == GS_BH) {
+    size_t rb = (size_t)slots * S.Npad * sizeof(float4);
+    CK(c->raws.ensure(rb), "workspace");
+  }
+  if (adjoint) {
+    CK(c->al.ensure(n3 * 8), "workspace");
+    CK(c->be.ensure(n3 * 8), "workspace");
+    CK(c->r2.ensure((size_t)N * 8), "workspace");
+    size_t ab = 2 * S.pack_f4 * sizeof(float4);
+    CK(c->abpacks.ensure(ab), "workspace");
+    CK(launch_pad_zero(c->abpacks.as<float4>(), S.pack_f4, 2, N, S.Npad, st), "pad");
+  }
+  if (S.mode == GS_EXACT) {
+    int J = std::max(S.gf.J, S.ga.J);
+    CK(c->part.ensure((size_t)J * 15 * S.Npad * sizeof(float2)), "workspace");
+    size_t tn = (size_t)S.gf.n_itiles;
+    if (c->tickets_n < tn) {
+      CK(c->tickets.ensure(tn * sizeof(unsigned)), "workspace");
+      c->tickets_n = tn;
+    }
+    CK(cudaMemsetAsync(c->tickets.p, 0, tn * sizeof(unsigned), st), "memset");
+  } else {
+    gs_status s = tree_reserve(c->tree, N, adjoint, st);
+    if (s != GS_OK) return fail(c, s, "Barnes-Hut workspace allocation failed");
+  }
+  return GS_OK;
+}
+
+// Loads (q, p) into the state, computes the recentring point and the pack of
+// slot 0 (and its raw FP32 positions in Barnes-Hut mode).
+gs_status solver_load(Solver& S, const double* q0, const double* p0, int slot) {
+  gs_ctx* c = S.c;
+  size_t b = (size_t)S.N * 3 * sizeof(double);
+  CK(cudaMemcpyAsync(c->q.p, q0, b, cudaMemcpyDeviceToDevice, S.st), "state copy");
+  CK(cudaMemcpyAsync(c->p.p, p0, b, cudaMemcpyDeviceToDevice, S.st), "state copy");
+  CK(launch_bbox_center(c->q.as<double>(), S.N, S.scal(SC_CENTER), S.st), "center");
+  CK(launch_pack(c->q.as<double>(), c->p.as<double>(), S.N, S.scal(SC_CENTER), S.s, S.pack(slot),
+                 S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
+     "pack");
+  return GS_OK;
+}
+
+FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
+  FwdEpi e{};
+  e.q = S.c->q.as<double>();
+  e.p = S.c->p.as<double>();
+  e.pack_next = next_slot >= 0 ? S.pack(next_slot) : nullptr;
+  e.raw_next = (next_slot >= 0 && S.mode == GS_BH) ? S.raw(next_slot) : nullptr;
+  e.center = S.scal(SC_CENTER);
+  e.s = S.s;
+  e.phi_scale = 1.0 / (S.sigma * S.sigma * S.s);
+  e.h = h;
+  e.N = S.N;
+  return e;
+}
+
+// One forward right-hand side on pack slot `slot` with epilogue `e`.
+gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
+  gs_ctx* c = S.c;
+  if (S.mode == GS_EXACT) {
+    CK(launch_exact_fwd(S.pack(slot), S.gf, c->part.as<float2>(), c->tickets.as<unsigned>(), e,
+                        c->d_status, S.st),
+       "exact forward kernel");
+    if (counts) {
+      counts[0] = S.N * S.N;
+      counts[1] = 0;
+    }
+    return GS_OK;
+  }
+  BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  gs_status s = bh_forward(c->tree, b, e, c->d_status, counts, S.st);
+  if (s != GS_OK) return fail(c, s, "Barnes-Hut forward step failed: %s", bh_last_error());
+  return GS_OK;
+}
+
+AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) {
+  AdjEpi e{};
+  e.al = S.c->al.as<double>();
+  e.be = S.c->be.as<double>();
+  e.pack_next = next_ab >= 0 ? S.abpack(next_ab) : nullptr;
+  e.F0 = last ? S.c->F0.as<double>() : nullptr;
+  e.grad = grad;
+  e.inv_s2 = 1.0 / (S.sigma * S.sigma);
+  e.inv_s = 1.0 / S.s;
+  e.h = h;
+  e.N = S.N;
+  return e;
+}
+
+gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts) {
+  gs_ctx* c = S.c;
+  if (S.mode == GS_EXACT) {
+    CK(launch_exact_adj(S.pack(slot), S.abpack(ab), S.ga, c->part.as<float2>(),
+                        c->tickets.as<unsigned>(), e, c->d_status, S.st),
+       "exact adjoint kernel");
+    if (counts) {
+      counts[0] = S.N * S.N;
+      counts[1] = 0;
+    }
+    return GS_OK;
+  }
+  BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  gs_status s = bh_adjoint(c->tree, b, S.abpack(ab), e, c->d_status, counts, S.st);
+  if (s != GS_OK) return fail(c, s, "Barnes-Hut adjoint step failed: %s", bh_last_error());
+  return GS_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+gs_status gs_create(int device, gs_ctx** out) {
+  if (!out) return GS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return GS_ERR_INVALID_ARG;
+  }
+  gs_ctx* c = new gs_ctx();
+  c->device = device;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete c;
+    return GS_ERR_CUDA;
+  }
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) !=
+          cudaSuccess ||
+      cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess || exact_setup() != cudaSuccess ||
+      tree_setup() != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return GS_ERR_CUDA;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+void gs_destroy(gs_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (DevMem* m : {&c->in_q, &c->in_p, &c->in_a, &c->in_b, &c->in_X, &c->out_a, &c->out_b,
+                      &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
+                      &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets})
+      m->release();
+    tree_release(c->tree);
+    if (c->d_status) cudaFree(c->d_status);
+  }
+  delete c;
+}
+
+const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+gs_status gs_sync(gs_ctx* c, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  return read_status(c, (cudaStream_t)stream);
+}
+
+gs_status gs_shoot(gs_ctx* c, const double* q0, const double* p0, int64_t N,
+                   const gs_params* prm, double* q1, double* p1, double* H, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hq = false, hp = false, hh = false;
+  if (q1 && (s = output(c, q1, "q1", &hq))) return s;
+  if (p1 && (s = output(c, p1, "p1", &hp))) return s;
+  if (H && (s = output(c, H, "H", &hh))) return s;
+  const double *dq0, *dp0;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)))
+    return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 2, false, st))) return s;
+  if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  for (int k = 0; k < S.T; k++) {
+    FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
+    if (k == 0 && H) e.pf_part = c->pf.as<double>();
+    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+    if (k == 0 && H) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+  }
+  if (H) {
+    FwdEpi e = fwd_epi(S, -1, 0.0);
+    e.pf_part = c->pf.as<double>();
+    if ((s = forward_rhs(S, S.T & 1, e, nullptr))) return s;
+    CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H1), st), "sum");
+    CK(launch_check_finite(S.scal(SC_H0), 2, c->d_status, st), "check");
+    if ((s = copy_out(c, H, S.scal(SC_H0), 2 * sizeof(double), st))) return s;
+  }
+  size_t b = (size_t)N * 3 * sizeof(double);
+  if (q1) {
+    CK(launch_check_finite(c->q.as<double>(), N * 3, c->d_status, st), "check");
+    if ((s = copy_out(c, q1, c->q.p, b, st))) return s;
+  }
+  if (p1) {
+    CK(launch_check_finite(c->p.as<double>(), N * 3, c->d_status, st), "check");
+    if ((s = copy_out(c, p1, c->p.p, b, st))) return s;
+  }
+  if (hq || hp || hh) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const double* X,
+                        int64_t N, const gs_params* prm, double* E, double* grad, double* q1,
+                        void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, true))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hE = false, hg = false, hq = false;
+  if ((s = output(c, E, "E", &hE)) || (s = output(c, grad, "grad", &hg))) return s;
+  if (q1 && (s = output(c, q1, "q1", &hq))) return s;
+  const double *dq0, *dp0, *dX;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)) ||
+      (s = input(c, X, (size_t)N * 3, "X", c->in_X, st, &dX)))
+    return s;
+  const int T = prm->T;
+  const int ck = prm->ckpt_every > 0 && prm->ckpt_every < T ? prm->ckpt_every : 0;
+  // pack slots: every step (store-all) or one segment (checkpointing)
+  const int slots = ck ? ck + 1 : T + 1;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, slots, true, st))) return s;
+  const size_t n3 = (size_t)N * 3, b3 = n3 * sizeof(double);
+  const int nck = ck ? (T + ck - 1) / ck : 0;
+  if (ck) CK(c->ckpt.ensure((size_t)nck * 2 * b3), "checkpoint allocation");
+  double* ckq = ck ? c->ckpt.as<double>() : nullptr;
+  if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  DevMem& gradbuf = c->out_a;
+  CK(gradbuf.ensure(b3), "workspace");
+  CK(c->out_b.ensure(b3), "workspace");
+
+  // ---- forward pass
+  for (int k = 0; k < T; k++) {
+    int in = ck ? (k & 1) : k, outs = ck ? ((k + 1) & 1) : k + 1;
+    if (ck && k % ck == 0) {
+      double* dst = ckq + (size_t)(k / ck) * 2 * n3;
+      CK(cudaMemcpyAsync(dst, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
+      CK(cudaMemcpyAsync(dst + n3, c->p.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    }
+    FwdEpi e = fwd_epi(S, outs, S.h);
+    if (k == 0) {
+      e.F_out = c->F0.as<double>();
+      e.pf_part = c->pf.as<double>();
+    }
+    if ((s = forward_rhs(S, in, e, nullptr))) return s;
+  }
+  CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+  CK(cudaMemcpyAsync(c->out_b.p, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "q1 copy");
+  // ---- adjoint initialisation and objective
+  CK(launch_adjoint_init(c->q.as<double>(), dX, N, S.lambda, c->al.as<double>(),
+                         c->be.as<double>(), S.abpack(0), c->r2.as<double>(), st),
+     "adjoint init");
+  CK(launch_sum(c->r2.as<double>(), N, S.lambda, S.scal(SC_DATA), st), "sum");
+  CK(launch_energy(S.scal(SC_H0), S.scal(SC_DATA), S.scal(SC_E), st), "energy");
+  // ---- backward pass
+  int ab = 0;
+  auto back_step = [&](int k, int slot) -> gs_status {
+    AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, gradbuf.as<double>());
+    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr);
+    ab ^= 1;
+    return r;
+  };
+  if (!ck) {
+    for (int k = T - 1; k >= 0; k--)
+      if ((s = back_step(k, k))) return s;
+  } else {
+    for (int seg = nck - 1; seg >= 0; seg--) {
+      const int k0 = seg * ck, k1 = std::min(T, k0 + ck);
+      const double* src = ckq + (size_t)seg * 2 * n3;
+      CK(cudaMemcpyAsync(c->q.p, src, b3, cudaMemcpyDeviceToDevice, st), "restore");
+      CK(cudaMemcpyAsync(c->p.p, src + n3, b3, cudaMemcpyDeviceToDevice, st), "restore");
+      CK(launch_pack(c->q.as<double>(), c->p.as<double>(), N, S.scal(SC_CENTER), S.s, S.pack(0),
+                     S.mode == GS_BH ? S.raw(0) : nullptr, st),
+         "pack");
+      for (int k = k0; k < k1 - 1; k++) {
+        FwdEpi e = fwd_epi(S, k - k0 + 1, S.h);
+        if ((s = forward_rhs(S, k - k0, e, nullptr))) return s;
+      }
+      for (int k = k1 - 1; k >= k0; k--)
+        if ((s = back_step(k, k - k0))) return s;
+    }
+  }
+  CK(launch_check_finite(S.scal(SC_E), 3, c->d_status, st), "check");
+  CK(launch_check_finite(gradbuf.as<double>(), (int64_t)n3, c->d_status, st), "check");
+  if ((s = copy_out(c, E, S.scal(SC_E), 3 * sizeof(double), st))) return s;
+  if ((s = copy_out(c, grad, gradbuf.p, b3, st))) return s;
+  if (q1 && (s = copy_out(c, q1, c->out_b.p, b3, st))) return s;
+  if (hE || hg || hq) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_rhs(gs_ctx* c, const double* q, const double* p, int64_t N, const gs_params* prm,
+                 double* F, double* Phi, int64_t* counts, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hF = false, hP = false;
+  if ((s = output(c, F, "F", &hF)) || (s = output(c, Phi, "Phi", &hP))) return s;
+  const double *dq, *dp;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)))
+    return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 1, false, st))) return s;
+  if ((s = solver_load(S, dq, dp, 0))) return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  CK(c->out_a.ensure(b3), "workspace");
+  CK(c->out_b.ensure(b3), "workspace");
+  FwdEpi e = fwd_epi(S, -1, 0.0);
+  e.F_out = c->out_a.as<double>();
+  e.Phi_out = c->out_b.as<double>();
+  int64_t cnt[2] = {0, 0};
+  if ((s = forward_rhs(S, 0, e, cnt))) return s;
+  if ((s = copy_out(c, F, c->out_a.p, b3, st)) || (s = copy_out(c, Phi, c->out_b.p, b3, st)))
+    return s;
+  if (counts) {
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    if (S.mode == GS_BH) bh_counts(c->tree, cnt);
+    counts[0] = cnt[0];
+    counts[1] = cnt[1];
+  }
+  if (hF || hP || counts) return read_status(c, st);
+  return GS_OK;
+}
+
+gs_status gs_adj_rhs(gs_ctx* c, const double* q, const double* p, const double* al,
+                     const double* be, int64_t N, const gs_params* prm, double* dA, double* dB,
+                     int64_t* counts, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hA = false, hB = false;
+  if ((s = output(c, dA, "dA", &hA)) || (s = output(c, dB, "dB", &hB))) return s;
+  const double *dq, *dp, *da, *db;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)) ||
+      (s = input(c, al, (size_t)N * 3, "al", c->in_a, st, &da)) ||
+      (s = input(c, be, (size_t)N * 3, "be", c->in_b, st, &db)))
+    return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 1, true, st))) return s;
+  if ((s = solver_load(S, dq, dp, 0))) return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  CK(cudaMemcpyAsync(c->al.p, da, b3, cudaMemcpyDeviceToDevice, st), "copy");
+  CK(cudaMemcpyAsync(c->be.p, db, b3, cudaMemcpyDeviceToDevice, st), "copy");
+  // adjoint pack: alpha and beta as FP32 (no recentring/scaling)
+  CK(launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, S.abpack(0), st), "pack");
+  CK(c->out_a.ensure(b3), "workspace");
+  CK(c->out_b.ensure(b3), "workspace");
+  AdjEpi e = adj_epi(S, -1, 0.0, false, nullptr);
+  e.dA_out = c->out_a.as<double>();
+  e.dB_out = c->out_b.as<double>();
+  int64_t cnt[2] = {0, 0};
+  if ((s = adjoint_rhs(S, 0, 0, e, cnt))) return s;
+  if ((s = copy_out(c, dA, c->out_a.p, b3, st)) || (s = copy_out(c, dB, c->out_b.p, b3, st)))
+    return s;
+  if (counts) {
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    if (S.mode == GS_BH) bh_counts(c->tree, cnt);
+    counts[0] = cnt[0];
+    counts[1] = cnt[1];
+  }
+  if (hA || hB || counts) return read_status(c, st);
+  return GS_OK;
+}
+
+}  // extern "C"

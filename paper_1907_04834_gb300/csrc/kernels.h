@@ -1,0 +1,52 @@
+// kernels.h -- host-side declarations of the libgs kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gs {
+
+// ---- exact all-pairs kernels (exact.cu)
+constexpr int EX_NT = 256;     // target points per block (one per thread)
+constexpr int EX_TILE = 512;   // source points per shared-memory tile
+constexpr int EX_STAGES = 3;   // bulk-copy pipeline depth
+
+struct ExactGeom {
+  int64_t N;     // points
+  int64_t Npad;  // N rounded up to EX_TILE (padding sources have p = 0)
+  int n_itiles;  // Npad / EX_NT
+  int n_jtiles;  // Npad / EX_TILE
+  int J;         // source splits per target tile (1 <= J <= n_jtiles)
+};
+
+cudaError_t exact_setup();
+cudaError_t launch_exact_fwd(const float4* pk, const ExactGeom& g, float2* part,
+                             unsigned* tickets, const FwdEpi& e, int* status, cudaStream_t st);
+cudaError_t launch_exact_adj(const float4* pk, const float4* ab, const ExactGeom& g, float2* part,
+                             unsigned* tickets, const AdjEpi& e, int* status, cudaStream_t st);
+
+// ---- small helpers (util.cu)
+cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st);
+cudaError_t launch_pack(const double* q, const double* p, int64_t N, const double* center,
+                        double s, float4* pack, float4* raw, cudaStream_t st);
+// zero the padding points [N, Npad) of `slots` consecutive packs
+cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, int64_t Npad,
+                            cudaStream_t st);
+// adjoint pack of (alpha, beta) as FP32 (no recentring or scaling)
+cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, float4* abpack,
+                           cudaStream_t st);
+// alpha = 2 lambda (q - X), beta = 0, adjoint pack; r2[i] = |q_i - X_i|^2
+cudaError_t launch_adjoint_init(const double* q, const double* X, int64_t N, double lambda,
+                                double* al, double* be, float4* abpack, double* r2,
+                                cudaStream_t st);
+// out[slot] = scale * Sum_{i<n} x[i] (single block, fixed order)
+cudaError_t launch_sum(const double* x, int64_t n, double scale, double* out, cudaStream_t st);
+// E = {H + data, H, data} from two sums
+cudaError_t launch_energy(const double* H, const double* data, double* E, cudaStream_t st);
+// grad = beta + F0 (when the adjoint had no steps to fuse it into)
+cudaError_t launch_axpy_grad(const double* be, const double* F0, int64_t n3, double* grad,
+                             cudaStream_t st);
+cudaError_t launch_check_finite(const double* x, int64_t n, int* status, cudaStream_t st);
+
+}  // namespace gs

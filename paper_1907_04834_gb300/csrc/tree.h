@@ -1,0 +1,40 @@
+// tree.h -- Barnes-Hut octree build and traversal (Sec. 2.2): host interface.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "gs.h"
+
+namespace gs {
+
+// Workspace of the octree steps (owned by a context).
+struct TreeWork {
+  void* mem = nullptr;  // one allocation, carved into the arrays below
+  size_t bytes = 0;
+  int64_t cap_n = 0;    // points it was sized for
+  bool adjoint = false;
+  int64_t* d_counts = nullptr;  // interaction counters {point, node}
+};
+
+// Inputs of one tree step: pack = scaled recentred FP32 positions and
+// momenta (pair layout), raw = FP32 positions {x, y, z, 0}.
+struct BHStep {
+  int64_t N, Npad;
+  double s;       // coordinate scale of the pack
+  float thr;      // far threshold r*r (FP32)
+  const float4* pack;
+  const float4* raw;
+};
+
+cudaError_t tree_setup();
+gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st);
+void tree_release(TreeWork& w);
+gs_status bh_forward(TreeWork& w, const BHStep& b, const FwdEpi& e, int* status,
+                     int64_t* counts, cudaStream_t st);
+gs_status bh_adjoint(TreeWork& w, const BHStep& b, const float4* abpack, const AdjEpi& e,
+                     int* status, int64_t* counts, cudaStream_t st);
+void bh_counts(TreeWork& w, int64_t* cnt);
+const char* bh_last_error();
+
+}  // namespace gs

@@ -1,0 +1,191 @@
+// util.cu -- small per-point kernels: recentring, packing, adjoint
+// initialisation, deterministic FP64 reductions, finiteness checks.
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kRedThreads = 1024;
+
+// Block-wide sum with a fixed reduction tree (deterministic).
+__device__ double block_sum(double v) {
+  __shared__ double sh[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+__global__ void k_bbox_center(const double* __restrict__ q, int64_t N, double* center) {
+  __shared__ double smin[3][32], smax[3][32];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+    for (int a = 0; a < 3; a++) {
+      double x = q[3 * i + a];
+      lo[a] = fmin(lo[a], x);
+      hi[a] = fmax(hi[a], x);
+    }
+  for (int a = 0; a < 3; a++)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fmin(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmax(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+    for (int a = 0; a < 3; a++) {
+      smin[a][w] = lo[a];
+      smax[a][w] = hi[a];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; a++) {
+      double mn = smin[a][0], mx = smax[a][0];
+      for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+        mn = fmin(mn, smin[a][k]);
+        mx = fmax(mx, smax[a][k]);
+      }
+      center[a] = 0.5 * (mn + mx);
+    }
+  }
+}
+
+__global__ void k_pack(const double* __restrict__ q, const double* __restrict__ p, int64_t N,
+                       const double* __restrict__ center, double s, float4* pack, float4* raw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const PackScale ps{center[0], center[1], center[2], s};
+  if (pack) pack_state(pack, i, q + 3 * i, p + 3 * i, ps);
+  if (raw)
+    raw[i] = make_float4((float)q[3 * i], (float)q[3 * i + 1], (float)q[3 * i + 2], 0.f);
+}
+
+__global__ void k_pad_zero(float4* base, size_t slot_f4, int64_t N, int64_t Npad) {
+  const int64_t i = N + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Npad) return;
+  pack_write(base + (size_t)blockIdx.y * slot_f4, i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_pack_ab(const double* __restrict__ al, const double* __restrict__ be,
+                          int64_t N, float4* abpack) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  pack_write(abpack, i, (float)al[3 * i], (float)al[3 * i + 1], (float)al[3 * i + 2],
+             (float)be[3 * i], (float)be[3 * i + 1], (float)be[3 * i + 2]);
+}
+
+__global__ void k_adjoint_init(const double* __restrict__ q, const double* __restrict__ X,
+                               int64_t N, double lambda, double* al, double* be, float4* abpack,
+                               double* r2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double a[3], s = 0.0;
+  for (int c = 0; c < 3; c++) {
+    double r = q[3 * i + c] - X[3 * i + c];
+    s += r * r;
+    a[c] = 2.0 * lambda * r;
+    al[3 * i + c] = a[c];
+    be[3 * i + c] = 0.0;
+  }
+  r2[i] = s;
+  pack_write(abpack, i, (float)a[0], (float)a[1], (float)a[2], 0.f, 0.f, 0.f);
+}
+
+__global__ void k_sum(const double* __restrict__ x, int64_t n, double scale, double* out) {
+  // each thread sums a contiguous chunk in order, then a fixed tree
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t a = (int64_t)threadIdx.x * chunk;
+  const int64_t b = a + chunk < n ? a + chunk : n;
+  double v = 0.0;
+  for (int64_t i = a; i < b; i++) v += x[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) *out = scale * v;
+}
+
+__global__ void k_energy(const double* H, const double* data, double* E) {
+  E[0] = *H + *data;
+  E[1] = *H;
+  E[2] = *data;
+}
+
+__global__ void k_axpy_grad(const double* be, const double* F0, int64_t n3, double* grad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n3) grad[i] = be[i] + F0[i];
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st) {
+  k_bbox_center<<<1, kRedThreads, 0, st>>>(q, N, center);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const double* q, const double* p, int64_t N, const double* center,
+                        double s, float4* pack, float4* raw, cudaStream_t st) {
+  k_pack<<<blocks_for(N, 256), 256, 0, st>>>(q, p, N, center, s, pack, raw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, int64_t Npad,
+                            cudaStream_t st) {
+  if (Npad <= N || slots <= 0) return cudaSuccess;
+  dim3 grid(blocks_for(Npad - N, 256), (unsigned)slots);
+  k_pad_zero<<<grid, 256, 0, st>>>(base, slot_f4, N, Npad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, float4* abpack,
+                           cudaStream_t st) {
+  k_pack_ab<<<blocks_for(N, 256), 256, 0, st>>>(al, be, N, abpack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(const double* q, const double* X, int64_t N, double lambda,
+                                double* al, double* be, float4* abpack, double* r2,
+                                cudaStream_t st) {
+  k_adjoint_init<<<blocks_for(N, 256), 256, 0, st>>>(q, X, N, lambda, al, be, abpack, r2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double* x, int64_t n, double scale, double* out, cudaStream_t st) {
+  k_sum<<<1, kRedThreads, 0, st>>>(x, n, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const double* H, const double* data, double* E, cudaStream_t st) {
+  k_energy<<<1, 1, 0, st>>>(H, data, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_grad(const double* be, const double* F0, int64_t n3, double* grad,
+                             cudaStream_t st) {
+  k_axpy_grad<<<blocks_for(n3, 256), 256, 0, st>>>(be, F0, n3, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, int64_t n, int* status, cudaStream_t st) {
+  unsigned b = blocks_for(n, 256);
+  if (b > 1024) b = 1024;
+  if (b == 0) b = 1;
+  k_check_finite<<<b, 256, 0, st>>>(x, n, status);
+  return cudaGetLastError();
+}
+
+}  // namespace gs
