@@ -648,4 +648,38 @@ gs_status gs_adj_rhs(gs_ctx* c, const double* q, const double* p, const double* 
   return GS_OK;
 }
 
+gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_t* order,
+                  int32_t* nodes, float* range, int64_t cap, int64_t* n_nodes, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N))) return s;
+  if (cap < 0) return fail(c, GS_ERR_INVALID_ARG, "cap must be >= 0");
+  bool h;
+  if (codes && (s = output(c, codes, "codes", &h))) return s;
+  if (order && (s = output(c, order, "order", &h))) return s;
+  if (nodes && (s = output(c, nodes, "nodes", &h))) return s;
+  if (range && (s = output(c, range, "range", &h))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* dq;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
+  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0};
+  Solver S;
+  if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
+  if ((s = solver_load(S, dq, dq, 0))) return s;
+  s = tree_export(c->tree, S.raw(0), S.pack(0), N, codes, order, nodes, range, cap, n_nodes, st);
+  if (s != GS_OK) return fail(c, s, "tree export failed: %s", bh_last_error());
+  return read_status(c, st);
+}
+
+gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const double* q0,
+                           const double* p0, const double* X, const gs_params* prm, double* E,
+                           double* grad, void* stream) {
+  (void)S, (void)offsets, (void)q0, (void)p0, (void)X, (void)prm, (void)E, (void)grad,
+      (void)stream;
+  if (!c) return GS_ERR_INVALID_ARG;
+  return fail(c, GS_ERR_UNSUPPORTED, "batched shooting is not built yet");
+}
+
 }  // extern "C"

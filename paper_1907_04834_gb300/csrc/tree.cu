@@ -1,27 +1,683 @@
-// tree.cu -- placeholder until the octree kernels land.
+// tree.cu -- Barnes-Hut octree of Sec. 2.2 built on the GPU every step:
+//   1. FP32 bounding box of the FP32 positions (the root cell);
+//   2. 10-bit quantised coordinates per axis and 30-bit Morton codes:
+//      ext = hi - lo, inv = 1024 / ext, u = (x - lo) * inv, k = min(trunc(u), 1023),
+//      k = 0 on a zero-extent axis (all FP32, round to nearest, no contraction);
+//   3. stable LSD radix sort of (code, index), 4 passes of 8 bits;
+//   4. the compressed octree in depth-first preorder (see tree_impl.h): one
+//      owner boundary per internal node, node offsets by a prefix sum of the
+//      per-position depth masks, skip pointers and parents by galloping search
+//      over the sorted codes;
+//   5. bottom-up aggregates (count, FP32 actual range, FP64 sums of scaled
+//      positions, momenta and, in the backward stage, alpha and beta): the
+//      last child to arrive at a node (atomic counter) finishes it.
+// The paper inserts points one at a time into a pointer tree; the node set,
+// the members of every node and the depth-first order are the same here (the
+// tests compare them bit for bit with the oracle's insertion tree).
+#include <algorithm>
+#include <cstdio>
+#include <utility>
+
+#include "kernels.h"
 #include "tree.h"
+#include "tree_impl.h"
 
 namespace gs {
-cudaError_t tree_setup() { return cudaSuccess; }
-gs_status tree_reserve(TreeWork&, int64_t, bool, cudaStream_t) { return GS_ERR_UNSUPPORTED; }
-void tree_release(TreeWork&) {}
-gs_status bh_forward(TreeWork&, const BHStep&, const FwdEpi&, int*, int64_t*, cudaStream_t) {
-  return GS_ERR_UNSUPPORTED;
-}
-gs_status bh_adjoint(TreeWork&, const BHStep&, const float4*, const AdjEpi&, int*, int64_t*,
-                     cudaStream_t) {
-  return GS_ERR_UNSUPPORTED;
-}
-void bh_counts(TreeWork&, int64_t* cnt) { cnt[0] = cnt[1] = 0; }
-const char* bh_last_error() { return "Barnes-Hut mode not built"; }
-}  // namespace gs
 
-extern "C" gs_status gs_tree(gs_ctx*, const double*, int64_t, uint32_t*, int32_t*, int32_t*,
-                             float*, int64_t, int64_t*, void*) {
-  return GS_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kBBoxThreads = 256;
+constexpr int kMaxBBoxBlocks = 1024;
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 4;  // keys per thread per tile (striped)
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+thread_local char g_err[256] = "";
+
+inline unsigned nblocks(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+// ---------------------------------------------------------------- bbox, Morton
+__global__ void k_bbox_partial(const float4* __restrict__ raw, int N, float* part) {
+  __shared__ float sh[6][kBBoxThreads / 32];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    float4 r = raw[i];
+    lo[0] = fminf(lo[0], r.x);
+    lo[1] = fminf(lo[1], r.y);
+    lo[2] = fminf(lo[2], r.z);
+    hi[0] = fmaxf(hi[0], r.x);
+    hi[1] = fmaxf(hi[1], r.y);
+    hi[2] = fmaxf(hi[2], r.z);
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int a = 0; a < 3; a++) {
+      lo[a] = fminf(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; a++) {
+      sh[a][w] = lo[a];
+      sh[3 + a][w] = hi[a];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kBBoxThreads / 32; k++)
+      for (int a = 0; a < 3; a++) {
+        sh[a][0] = fminf(sh[a][0], sh[a][k]);
+        sh[3 + a][0] = fmaxf(sh[3 + a][0], sh[3 + a][k]);
+      }
+    for (int a = 0; a < 6; a++) part[blockIdx.x * 6 + a] = sh[a][0];
+  }
 }
-extern "C" gs_status gs_shoot_batched(gs_ctx*, int32_t, const int64_t*, const double*,
-                                      const double*, const double*, const gs_params*, double*,
-                                      double*, void*) {
-  return GS_ERR_UNSUPPORTED;
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
 }
+
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float ext, float inv) {
+  if (!(ext > 0.f)) return 0u;
+  float u = __fmul_rn(__fsub_rn(x, lo), inv);
+  uint32_t k = __float2uint_rz(u);
+  return k > 1023u ? 1023u : k;
+}
+
+__global__ void k_morton(const float4* __restrict__ raw, int N, const float* __restrict__ part,
+                         int nparts, uint32_t* key, uint32_t* perm, uint32_t* codes, float* bbox) {
+  __shared__ float box[6];
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    float v = part[a];
+    for (int k = 1; k < nparts; k++)
+      v = a < 3 ? fminf(v, part[k * 6 + a]) : fmaxf(v, part[k * 6 + a]);
+    box[a] = v;
+    if (blockIdx.x == 0) bbox[a] = v;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 r = raw[i];
+  float ext[3], inv[3];
+  for (int a = 0; a < 3; a++) {
+    ext[a] = __fsub_rn(box[3 + a], box[a]);
+    inv[a] = ext[a] > 0.f ? __fdiv_rn(1024.0f, ext[a]) : 0.f;
+  }
+  const uint32_t kx = quantise(r.x, box[0], ext[0], inv[0]);
+  const uint32_t ky = quantise(r.y, box[1], ext[1], inv[1]);
+  const uint32_t kz = quantise(r.z, box[2], ext[2], inv[2]);
+  const uint32_t c = (spread10(kx) << 2) | (spread10(ky) << 1) | spread10(kz);
+  key[i] = c;
+  perm[i] = (uint32_t)i;
+  codes[i] = c;
+}
+
+// ---------------------------------------------------------------- scans
+struct Ident {
+  __device__ uint32_t operator()(uint32_t v) const { return v; }
+};
+struct Popc {
+  __device__ uint32_t operator()(uint32_t v) const { return (uint32_t)__popc(v); }
+};
+
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const uint32_t before = w > 0 ? warp_tot[w - 1] : 0u;
+  if (total) *total = warp_tot[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+template <class Op>
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int n, uint32_t* bsum, Op op) {
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; k++)
+    if (base + k < n) s += op(in[base + k]);
+  uint32_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_bsums(uint32_t* bsum, int nb) {
+  uint32_t carry = 0;
+  for (int c0 = 0; c0 < nb; c0 += SCAN_THREADS) {
+    const int i = c0 + threadIdx.x;
+    uint32_t v = i < nb ? bsum[i] : 0u, tot;
+    uint32_t ex = block_excl_scan(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+template <class Op>
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, int n, const uint32_t* bsum,
+                             uint32_t* out, Op op) {
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS], s = 0;
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = base + k < n ? op(in[base + k]) : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t ex = bsum[blockIdx.x] + block_excl_scan(s, &tot);
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = bsum[blockIdx.x] + tot;
+}
+
+// exclusive scan of op(in[0..n)) into out[0..n], out[n] = total
+template <class Op>
+cudaError_t scan(const uint32_t* in, int n, uint32_t* bsum, uint32_t* out, Op op,
+                 cudaStream_t st) {
+  const int nb = (int)nblocks(n, SCAN_TILE);
+  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, bsum, op);
+  k_scan_bsums<<<1, SCAN_THREADS, 0, st>>>(bsum, nb);
+  k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, n, bsum, out, op);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+// hist layout: digit-major, hist[d * nb + block].
+__global__ void k_rs_hist(const uint32_t* __restrict__ key, int N, int shift, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0u;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    const int i = base + r * RS_THREADS + threadIdx.x;
+    if (i < N) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: key order within a tile is round-major then thread, i.e.
+// the input order; ranks among equal digits follow it.
+__global__ void k_rs_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
+                             int N, int shift, const uint32_t* __restrict__ hscan,
+                             uint32_t* key_out, uint32_t* val_out) {
+  constexpr int W = RS_THREADS / 32;
+  __shared__ uint32_t run[256];     // keys of each digit placed so far in this tile
+  __shared__ uint32_t wcnt[W][256]; // per-warp counts in the current round
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = 0u;
+  const uint32_t goff = hscan[threadIdx.x * gridDim.x + blockIdx.x];
+  __shared__ uint32_t gbase[256];
+  gbase[threadIdx.x] = goff;
+  const int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    for (int k = 0; k < W; k++) wcnt[k][threadIdx.x] = 0u;
+    __syncthreads();
+    const int i = base + r * RS_THREADS + threadIdx.x;
+    const bool valid = i < N;
+    uint32_t k = 0, v = 0, d = 256u;
+    if (valid) {
+      k = key[i];
+      v = val[i];
+      d = (k >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank_w = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank_w == 0) wcnt[w][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    // thread t owns digit t: prefix over warps, then advance the running count
+    {
+      uint32_t acc = run[threadIdx.x];
+      for (int k2 = 0; k2 < W; k2++) {
+        uint32_t c = wcnt[k2][threadIdx.x];
+        wcnt[k2][threadIdx.x] = acc;
+        acc += c;
+      }
+      run[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = gbase[d] + wcnt[w][d] + (uint32_t)rank_w;
+      key_out[pos] = k;
+      val_out[pos] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- node list
+__device__ __forceinline__ int delta_at(const uint32_t* sk, int i) {
+  const uint32_t x = sk[i] ^ sk[i + 1];
+  return x == 0u ? 10 : (__clz(x) - 2) / 3;
+}
+
+// smallest j <= i with sk[j] >> sh == sk[i] >> sh
+__device__ int gallop_left(const uint32_t* sk, int i, int sh) {
+  const uint32_t pre = sk[i] >> sh;
+  int good = i, bad = -1, step = 1;
+  while (true) {
+    const int j = good - step;
+    if (j < 0) break;
+    if ((sk[j] >> sh) == pre) {
+      good = j;
+      step <<= 1;
+    } else {
+      bad = j;
+      break;
+    }
+  }
+  int L = bad + 1, R = good;
+  while (L < R) {
+    const int mid = (L + R) >> 1;
+    if ((sk[mid] >> sh) == pre) R = mid;
+    else L = mid + 1;
+  }
+  return L;
+}
+
+// largest j >= i with sk[j] >> sh == sk[i] >> sh
+__device__ int gallop_right(const uint32_t* sk, int i, int N, int sh) {
+  const uint32_t pre = sk[i] >> sh;
+  int good = i, bad = N, step = 1;
+  while (true) {
+    const int j = good + step;
+    if (j >= N) break;
+    if ((sk[j] >> sh) == pre) {
+      good = j;
+      step <<= 1;
+    } else {
+      bad = j;
+      break;
+    }
+  }
+  int L = good, R = bad - 1;
+  while (L < R) {
+    const int mid = (L + R + 1) >> 1;
+    if ((sk[mid] >> sh) == pre) L = mid;
+    else R = mid - 1;
+  }
+  return L;
+}
+
+// Boundary i (between sorted i and i+1) owns the internal node of depth
+// D = delta_i that it is the first depth-D split of.
+__global__ void k_owners(const uint32_t* __restrict__ sk, int N, uint32_t* mask, int32_t* own_a,
+                         int32_t* own_b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N - 1) return;
+  const int D = delta_at(sk, i);
+  const int sh = 30 - 3 * D;
+  const int a = gallop_left(sk, i, sh);
+  bool owner;
+  if (D == 10) owner = (a == i);
+  else owner = (sk[a] >> (sh - 3)) == (sk[i] >> (sh - 3));
+  if (owner) {
+    own_a[i] = a;
+    own_b[i] = gallop_right(sk, i + 1, N, sh);
+    atomicOr(&mask[a], 1u << D);
+  } else {
+    own_a[i] = -1;
+  }
+}
+
+__device__ __forceinline__ int node_id(const uint32_t* offs, const uint32_t* mask, int a, int D) {
+  return a + (int)offs[a] + __popc(mask[a] & ((1u << D) - 1u));
+}
+
+// parent of a node spanning sorted [a, b]: the cell of depth
+// max(delta_{a-1}, delta_b) that contains it (-1 when there is none)
+__device__ int parent_of(const uint32_t* sk, const uint32_t* offs, const uint32_t* mask, int N,
+                         int a, int b) {
+  int Dp = -1;
+  if (a > 0) Dp = delta_at(sk, a - 1);
+  if (b < N - 1) Dp = max(Dp, delta_at(sk, b));
+  if (Dp < 0) return -1;
+  const int pa = gallop_left(sk, a, 30 - 3 * Dp);
+  return node_id(offs, mask, pa, Dp);
+}
+
+__global__ void k_write_nodes(const uint32_t* __restrict__ sk, int N,
+                              const uint32_t* __restrict__ mask, const uint32_t* __restrict__ offs,
+                              const int32_t* __restrict__ own_a, const int32_t* __restrict__ own_b,
+                              int2* nsc, int2* ninfo, int32_t* nparent, int32_t* acnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  // the leaf of sorted point i
+  const int leaf = i + (int)offs[i + 1];
+  nsc[leaf] = make_int2(leaf + 1, 1);
+  ninfo[leaf] = make_int2(-1, i);
+  nparent[leaf] = parent_of(sk, offs, mask, N, i, i);
+  acnt[leaf] = 0;
+  // the internal node owned by boundary i
+  if (i < N - 1 && own_a[i] >= 0) {
+    const int a = own_a[i], b = own_b[i], D = delta_at(sk, i);
+    const int id = node_id(offs, mask, a, D);
+    nsc[id] = make_int2(b + 1 + (int)offs[b + 1], b - a + 1);
+    ninfo[id] = make_int2(D, a);
+    nparent[id] = parent_of(sk, offs, mask, N, a, b);
+    acnt[id] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- aggregates
+__global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
+                            const float4* __restrict__ pack, const float4* __restrict__ abpack) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool adj = abpack != nullptr;
+  const int o = (int)t.perm[i];
+  int x = i + (int)t.offs[i + 1];
+  {
+    const float4 r = raw[o];
+    t.nbox[2 * x] = make_float4(r.x, r.y, r.z, __int_as_float(x + 1));
+    t.nbox[2 * x + 1] = make_float4(r.x, r.y, r.z, __int_as_float(1));
+    float a[3], b[3];
+    pack_read(pack, o, a, b);
+    t.nrec[4 * x] = make_float4(a[0], a[1], a[2], 0.f);
+    t.nrec[4 * x + 1] = make_float4(b[0], b[1], b[2], 0.f);
+    if (adj) {
+      pack_read(abpack, o, a, b);
+      t.nrec[4 * x + 2] = make_float4(a[0], a[1], a[2], 0.f);
+      t.nrec[4 * x + 3] = make_float4(b[0], b[1], b[2], 0.f);
+    }
+  }
+  int nx = 1;
+  while (true) {
+    const int par = t.nparent[x];
+    if (par < 0) break;
+    const int2 sc = t.nsc[par];
+    __threadfence();
+    const int old = atomicAdd(&t.acnt[par], nx);
+    if (old + nx != sc.y) break;
+    __threadfence();
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double S[12];
+    for (int k = 0; k < 12; k++) S[k] = 0.0;
+    int c = par + 1;
+    while (c < sc.x) {
+      const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
+      lo[0] = fminf(lo[0], bl.x);
+      lo[1] = fminf(lo[1], bl.y);
+      lo[2] = fminf(lo[2], bl.z);
+      hi[0] = fmaxf(hi[0], bh.x);
+      hi[1] = fmaxf(hi[1], bh.y);
+      hi[2] = fmaxf(hi[2], bh.z);
+      const int cskip = __float_as_int(bl.w);
+      if (cskip == c + 1) {
+        const float4 r0 = __ldcg(&t.nrec[4 * c]), r1 = __ldcg(&t.nrec[4 * c + 1]);
+        S[0] += r0.x, S[1] += r0.y, S[2] += r0.z;
+        S[3] += r1.x, S[4] += r1.y, S[5] += r1.z;
+        if (adj) {
+          const float4 r2 = __ldcg(&t.nrec[4 * c + 2]), r3 = __ldcg(&t.nrec[4 * c + 3]);
+          S[6] += r2.x, S[7] += r2.y, S[8] += r2.z;
+          S[9] += r3.x, S[10] += r3.y, S[11] += r3.z;
+        }
+      } else {
+        const int ns = adj ? 12 : 6;
+        for (int k = 0; k < ns; k++) S[k] += __ldcg(&t.isum[12 * (size_t)c + k]);
+      }
+      c = cskip;
+    }
+    const double n = (double)sc.y;
+    for (int k = 0; k < 12; k++) t.isum[12 * (size_t)par + k] = S[k];
+    t.nrec[4 * par] = make_float4((float)(S[0] / n), (float)(S[1] / n), (float)(S[2] / n), 0.f);
+    t.nrec[4 * par + 1] = make_float4((float)S[3], (float)S[4], (float)S[5], 0.f);
+    if (adj) {
+      t.nrec[4 * par + 2] = make_float4((float)S[6], (float)S[7], (float)S[8], 0.f);
+      t.nrec[4 * par + 3] =
+          make_float4((float)(S[9] / n), (float)(S[10] / n), (float)(S[11] / n), 0.f);
+    }
+    t.nbox[2 * par] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
+    t.nbox[2 * par + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(sc.y));
+    x = par;
+    nx = sc.y;
+  }
+}
+
+// ---------------------------------------------------------------- layout
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t off[32];
+  size_t total;
+};
+
+// Carves one allocation for capacity n points (2n nodes).
+TreeArrays carve(void* mem, int64_t n, size_t* bytes_out) {
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2;
+  const size_t nb_rs = nblocks(n, RS_TILE), nb_bb = kMaxBBoxBlocks;
+  const size_t hist_n = 256 * nb_rs + 1;
+  const size_t bsum_n = nblocks((int64_t)std::max<size_t>(hist_n, N1), SCAN_TILE) + 1;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t o_key = take(4 * N1), o_perm = take(4 * N1), o_key2 = take(4 * N1),
+               o_perm2 = take(4 * N1), o_codes = take(4 * N1), o_mask = take(4 * N1),
+               o_offs = take(4 * (N1 + 1)), o_oa = take(4 * N1), o_ob = take(4 * N1),
+               o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
+               o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
+               o_nbox = take(32 * M), o_nrec = take(64 * M), o_nsc = take(8 * M),
+               o_ninfo = take(8 * M), o_npar = take(4 * M), o_acnt = take(4 * M),
+               o_isum = take(96 * M), o_cnt = take(16);
+  *bytes_out = o;
+  TreeArrays t{};
+  if (!mem) return t;
+  char* b = static_cast<char*>(mem);
+  t.key = (uint32_t*)(b + o_key);
+  t.perm = (uint32_t*)(b + o_perm);
+  t.key_alt = (uint32_t*)(b + o_key2);
+  t.perm_alt = (uint32_t*)(b + o_perm2);
+  t.codes = (uint32_t*)(b + o_codes);
+  t.mask = (uint32_t*)(b + o_mask);
+  t.offs = (uint32_t*)(b + o_offs);
+  t.own_a = (int32_t*)(b + o_oa);
+  t.own_b = (int32_t*)(b + o_ob);
+  t.hist = (uint32_t*)(b + o_hist);
+  t.hscan = (uint32_t*)(b + o_hscan);
+  t.bsum = (uint32_t*)(b + o_bsum);
+  t.bbox_part = (float*)(b + o_bbp);
+  t.bbox = (float*)(b + o_bb);
+  t.nbox = (float4*)(b + o_nbox);
+  t.nrec = (float4*)(b + o_nrec);
+  t.nsc = (int2*)(b + o_nsc);
+  t.ninfo = (int2*)(b + o_ninfo);
+  t.nparent = (int32_t*)(b + o_npar);
+  t.acnt = (int32_t*)(b + o_acnt);
+  t.isum = (double*)(b + o_isum);
+  t.counts = (int64_t*)(b + o_cnt);
+  return t;
+}
+
+#define TRY(x)                             \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+// Steps 1-5 for one state.  abpack = NULL for the forward stage.
+cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* pack,
+                  const float4* abpack, cudaStream_t st) {
+  const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
+  k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
+  k_morton<<<nblocks(N, 256), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb, t.key, t.perm,
+                                            t.codes, t.bbox);
+  TRY(cudaGetLastError());
+  // radix sort, 4 passes of 8 bits (the 30-bit codes end in key/perm)
+  const int nb = (int)nblocks(N, RS_TILE);
+  uint32_t *k0 = t.key, *v0 = t.perm, *k1 = t.key_alt, *v1 = t.perm_alt;
+  for (int pass = 0; pass < 4; pass++) {
+    k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, N, 8 * pass, t.hist);
+    TRY(scan(t.hist, 256 * nb, t.bsum, t.hscan, Ident(), st));
+    k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, N, 8 * pass, t.hscan, k1, v1);
+    TRY(cudaGetLastError());
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  // node list
+  TRY(cudaMemsetAsync(t.mask, 0, sizeof(uint32_t) * (size_t)N, st));
+  if (N > 1) k_owners<<<nblocks(N - 1, 256), 256, 0, st>>>(t.key, N, t.mask, t.own_a, t.own_b);
+  TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
+  k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, N, t.mask, t.offs, t.own_a, t.own_b,
+                                                 t.nsc, t.ninfo, t.nparent, t.acnt);
+  k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host API
+cudaError_t tree_setup() { return cudaSuccess; }
+
+gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st) {
+  (void)st;
+  if (N > (int64_t(1) << 30)) return GS_ERR_INVALID_ARG;
+  if (w.mem && w.cap_n >= N) return GS_OK;
+  if (w.mem) cudaFree(w.mem);
+  w.mem = nullptr;
+  size_t bytes = 0;
+  carve(nullptr, N, &bytes);
+  if (cudaMalloc(&w.mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    w.mem = nullptr;
+    w.cap_n = 0;
+    return GS_ERR_OOM;
+  }
+  w.bytes = bytes;
+  w.cap_n = N;
+  w.adjoint = adjoint;
+  size_t b2;
+  w.d_counts = carve(w.mem, N, &b2).counts;
+  return GS_OK;
+}
+
+void tree_release(TreeWork& w) {
+  if (w.mem) cudaFree(w.mem);
+  w.mem = nullptr;
+  w.cap_n = 0;
+}
+
+const char* bh_last_error() { return g_err; }
+
+static gs_status cuda_err(cudaError_t e) {
+  snprintf(g_err, sizeof g_err, "%s", cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
+gs_status bh_forward(TreeWork& w, const BHStep& b, const FwdEpi& e, int* status, int64_t* counts,
+                     cudaStream_t st) {
+  (void)status;
+  size_t bytes;
+  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  cudaError_t err;
+  if (counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = build(t, (int)b.N, b.raw, b.pack, nullptr, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = launch_bh_traverse_fwd(t, (int)b.N, b.raw, b.thr, e, counts ? t.counts : nullptr,
+                                    st)) != cudaSuccess)
+    return cuda_err(err);
+  return GS_OK;
+}
+
+gs_status bh_adjoint(TreeWork& w, const BHStep& b, const float4* abpack, const AdjEpi& e,
+                     int* status, int64_t* counts, cudaStream_t st) {
+  (void)status;
+  size_t bytes;
+  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  cudaError_t err;
+  if (counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = build(t, (int)b.N, b.raw, b.pack, abpack, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = launch_bh_traverse_adj(t, (int)b.N, b.raw, b.thr, e, counts ? t.counts : nullptr,
+                                    st)) != cudaSuccess)
+    return cuda_err(err);
+  return GS_OK;
+}
+
+void bh_counts(TreeWork& w, int64_t* cnt) {
+  cnt[0] = cnt[1] = 0;
+  if (w.d_counts) cudaMemcpy(cnt, w.d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost);
+}
+
+namespace {
+__global__ void k_export_nodes(TreeArrays t, int m, int32_t* nodes, float* range) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= m) return;
+  const int2 inf = t.ninfo[x], sc = t.nsc[x];
+  nodes[4 * x + 0] = inf.x;
+  nodes[4 * x + 1] = inf.y;
+  nodes[4 * x + 2] = sc.y;
+  nodes[4 * x + 3] = sc.x;
+  const float4 lo = t.nbox[2 * x], hi = t.nbox[2 * x + 1];
+  range[6 * x + 0] = lo.x;
+  range[6 * x + 1] = lo.y;
+  range[6 * x + 2] = lo.z;
+  range[6 * x + 3] = hi.x;
+  range[6 * x + 4] = hi.y;
+  range[6 * x + 5] = hi.z;
+}
+}  // namespace
+
+gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
+                      uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,
+                      int64_t* n_nodes, cudaStream_t st) {
+  size_t bytes;
+  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  cudaError_t err;
+  if ((err = build(t, (int)N, raw, pack, nullptr, st)) != cudaSuccess) return cuda_err(err);
+  uint32_t nint = 0;
+  if ((err = cudaMemcpyAsync(&nint, t.offs + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_err(err);
+  const int64_t M = N + (int64_t)nint;
+  if (n_nodes) *n_nodes = M;
+  if (codes && (err = cudaMemcpyAsync(codes, t.codes, 4 * N, cudaMemcpyDefault, st)) != cudaSuccess)
+    return cuda_err(err);
+  if (order && (err = cudaMemcpyAsync(order, t.perm, 4 * N, cudaMemcpyDefault, st)) != cudaSuccess)
+    return cuda_err(err);
+  const int64_t m = std::min(M, cap);
+  if ((nodes || range) && m > 0) {
+    int32_t* dn = nullptr;
+    float* dr = nullptr;
+    if ((err = cudaMalloc(&dn, 16 * m)) != cudaSuccess ||
+        (err = cudaMalloc(&dr, 24 * m)) != cudaSuccess) {
+      if (dn) cudaFree(dn);
+      return cuda_err(err);
+    }
+    k_export_nodes<<<nblocks(m, 256), 256, 0, st>>>(t, (int)m, dn, dr);
+    err = cudaGetLastError();
+    if (err == cudaSuccess && nodes) err = cudaMemcpyAsync(nodes, dn, 16 * m, cudaMemcpyDefault, st);
+    if (err == cudaSuccess && range) err = cudaMemcpyAsync(range, dr, 24 * m, cudaMemcpyDefault, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaFree(dn);
+    cudaFree(dr);
+    if (err != cudaSuccess) return cuda_err(err);
+  }
+  return GS_OK;
+}
+
+}  // namespace gs

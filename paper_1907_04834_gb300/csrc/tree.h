@@ -35,6 +35,10 @@ gs_status bh_forward(TreeWork& w, const BHStep& b, const FwdEpi& e, int* status,
 gs_status bh_adjoint(TreeWork& w, const BHStep& b, const float4* abpack, const AdjEpi& e,
                      int* status, int64_t* counts, cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
+// Builds the tree on one state and exports it (see gs_tree in gs.h).
+gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
+                      uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,
+                      int64_t* n_nodes, cudaStream_t st);
 const char* bh_last_error();
 
 }  // namespace gs

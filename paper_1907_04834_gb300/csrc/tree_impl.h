@@ -1,0 +1,71 @@
+// tree_impl.h -- device-side layout of the Barnes-Hut octree shared by the
+// build (tree.cu) and the traversal (traverse.cu) kernels.
+//
+// Points are sorted by 30-bit Morton code (10 levels; bit 3b+2 = x bit b).
+// Nodes are stored in depth-first preorder, children in Morton order:
+//   * an internal node is a cell that holds >= 2 points and has >= 2
+//     non-empty child cells (a chain of single-child cells has the same
+//     members and the same actual range as its lowest cell, so it takes the
+//     same decision and the same summary: it is stored once), or a depth-10
+//     cell holding >= 2 points (its children are its points);
+//   * a leaf is one point.
+// Node x's subtree occupies preorder indices [x, skip(x)); a leaf has
+// skip = x + 1, so traversal is a forward scan that either steps into a node
+// (x + 1) or jumps over it (skip(x)).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gs {
+
+struct TreeArrays {
+  // per point (capacity N)
+  uint32_t* key;    // sorted Morton codes (after the sort)
+  uint32_t* perm;   // sorted position -> original index
+  uint32_t* key_alt;
+  uint32_t* perm_alt;
+  uint32_t* codes;  // Morton code per original index (before the sort)
+  uint32_t* mask;   // bit D set: an internal node of depth D starts here
+  uint32_t* offs;   // N + 1: exclusive prefix count of internal nodes
+  int32_t* own_a;   // per boundary i (between sorted i, i+1): node start or -1
+  int32_t* own_b;   // node end (inclusive)
+  // scratch
+  uint32_t* hist;   // radix histograms / scan input
+  uint32_t* hscan;  // scanned histograms
+  uint32_t* bsum;   // scan block sums
+  float* bbox_part; // per-block bounding boxes
+  float* bbox;      // 6 floats: lo, hi
+  // per node (capacity 2N), preorder index
+  float4* nbox;     // 2 per node: {lo.xyz, skip (int bits)}, {hi.xyz, count (int bits)}
+  float4* nrec;     // 4 per node: source record {xs}, {P}, {A}, {B / n}
+  int2* nsc;        // {skip, count} written at build time
+  int2* ninfo;      // {depth (-1 = leaf), first sorted position}
+  int32_t* nparent; // preorder id of the parent, -1 for the root
+  int32_t* acnt;    // arrival counters of the bottom-up pass
+  double* isum;     // 12 per node: sums of xs, p, a, b over members
+  int64_t* counts;  // {point interactions, node interactions}
+};
+
+__device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
+  return N + (int)t.offs[N];
+}
+
+// FP32 distance-squared from a point to an axis-aligned box, no contraction:
+// dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
+__device__ __forceinline__ float box_dist2(float x, float y, float z, const float4& lo,
+                                           const float4& hi) {
+  float dx = fmaxf(fmaxf(__fsub_rn(lo.x, x), 0.f), __fsub_rn(x, hi.x));
+  float dy = fmaxf(fmaxf(__fsub_rn(lo.y, y), 0.f), __fsub_rn(y, hi.y));
+  float dz = fmaxf(fmaxf(__fsub_rn(lo.z, z), 0.f), __fsub_rn(z, hi.z));
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// counts: NULL or 2 int64 accumulating {point, node} interactions
+cudaError_t launch_bh_traverse_fwd(const TreeArrays& t, int N, const float4* raw, float thr,
+                                   const FwdEpi& e, int64_t* counts, cudaStream_t st);
+cudaError_t launch_bh_traverse_adj(const TreeArrays& t, int N, const float4* raw, float thr,
+                                   const AdjEpi& e, int64_t* counts, cudaStream_t st);
+
+}  // namespace gs

@@ -14,9 +14,16 @@ def npy(t):
     return t.detach().cpu().numpy()
 
 
-def max_rel(a, b):
-    """max |a - b| / max |b|"""
-    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+def max_rel(a, b, floor=1e-300):
+    """max |a - b| / max(max |b|, floor).  The floor matters only when every
+    reference value is far below the physical scale (e.g. all weights
+    underflow: FP32 exp flushes below 2^-126 where FP64 does not)."""
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
+
+
+def phi_floor(p, sigma):
+    """1e-12 of the natural size of Phi, |p|^2 / sigma."""
+    return 1e-12 * float(np.abs(p).max()) ** 2 / sigma
 
 
 def rel_l2(a, b):

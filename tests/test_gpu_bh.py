@@ -1,0 +1,102 @@
+"""Parity of the Barnes-Hut CUDA path (Sec. 2.2: octree, three-case
+traversal, Eq. 4 summaries, backward-stage replacements) with the oracle's
+Barnes-Hut.  On a shared state both sides take the same accept/open
+decisions (FP32 rule), so interaction counts match exactly and values agree
+to FP32 rounding; trajectories within 1e-5 sigma, gradients within 1e-4."""
+import numpy as np
+import pytest
+
+import paper_1907_04834_gb300 as gs
+from paper_1907_04834_gb300 import inputs
+from gpu_util import dt, npy, max_rel, rel_l2, phi_floor
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("blobs", 1, 1, 3.0), ("blobs", 2, 2, 3.0), ("blobs", 777, 3, 3.0),
+         ("slab", 3000, 4, 3.0), ("blobs", 4000, 5, 1.0), ("ellipsoid", 1000, 1001, 2.0),
+         ("sphere", 5000, 6, 3.0)]
+
+
+@pytest.mark.parametrize("geom,n,seed,th", CASES)
+def test_bh_rhs_matches_oracle(oracle, geom, n, seed, th):
+    w = inputs.make(geom, max(n, 2), seed)
+    q, p = w.q0[:n], w.p0[:n]
+    F, Phi, cnt = gs.rhs(dt(q), dt(p), w.sigma, mode="bh", thresh=th)
+    Fo, Phio, cnto = oracle.rhs(q, p, w.sigma, mode=1, thresh=th)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(F), Fo) <= 1e-5
+    if n > 1:
+        assert max_rel(npy(Phi), Phio, phi_floor(p, w.sigma)) <= 1e-5
+
+
+@pytest.mark.parametrize("geom,n,seed,th", CASES)
+def test_bh_adjoint_rhs_matches_oracle(oracle, geom, n, seed, th):
+    w = inputs.make(geom, max(n, 2), seed)
+    q, p = w.q0[:n], w.p0[:n]
+    rng = np.random.default_rng(seed)
+    al, be = rng.normal(size=q.shape), rng.normal(scale=0.1, size=q.shape)
+    dA, dB, cnt = gs.adj_rhs(dt(q), dt(p), dt(al), dt(be), w.sigma, mode="bh", thresh=th)
+    dAo, dBo, cnto = oracle.adj_rhs(q, p, al, be, w.sigma, mode=1, thresh=th)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(dA), dAo, 1e-12 * np.abs(al).max() * np.abs(p).max() / w.sigma) <= 1e-5
+    assert max_rel(npy(dB), dBo) <= 1e-5
+
+
+@pytest.mark.parametrize("geom,n,seed,T,th", [("slab", 3000, 11, 20, 3.0),
+                                              ("blobs", 2500, 12, 20, 3.0),
+                                              ("ellipsoid", 1000, 1001, 10, 2.0)])
+def test_bh_shoot_matches_oracle(oracle, geom, n, seed, T, th):
+    w = inputs.make(geom, n, seed, T=T)
+    q1, p1, H = gs.shoot(dt(w.q0), dt(w.p0), w.sigma, w.T, mode="bh", thresh=th, with_H=True)
+    q1o, p1o, Ho = oracle.shoot(w.q0, w.p0, w.sigma, w.T, mode=1, thresh=th)
+    assert np.abs(npy(q1) - q1o).max() <= 1e-5 * w.sigma
+    np.testing.assert_allclose(npy(H), Ho, rtol=1e-6)
+    # the approximation's own error against exact shooting (reported)
+    q1e, _, _ = oracle.shoot(w.q0, w.p0, w.sigma, w.T)
+    print(f"\nBH vs exact {geom} N={n}: max|dq1|/sigma = {np.abs(q1o - q1e).max() / w.sigma:.3e}")
+
+
+@pytest.mark.parametrize("geom,n,seed,T", [("slab", 2000, 13, 8), ("blobs", 1500, 14, 6)])
+def test_bh_gradient_matches_oracle(oracle, geom, n, seed, T):
+    w = inputs.make(geom, n, seed, T=T)
+    E, g, q1 = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), w.sigma, w.T, w.lam, mode="bh")
+    Eo, go, q1o = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, w.T, w.lam, mode=1)
+    assert rel_l2(npy(g), go) <= 1e-4
+    np.testing.assert_allclose(npy(E), Eo, rtol=1e-6)
+    assert np.abs(npy(q1) - q1o).max() <= 1e-5 * w.sigma
+    _, ge, _ = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, w.T, w.lam)
+    print(f"\nBH grad vs exact grad {geom} N={n}: rel L2 = {rel_l2(go, ge):.3e}")
+
+
+def test_bh_checkpointing_is_bit_exact():
+    w = inputs.make("blobs", 2000, 15, T=9)
+    a = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), w.sigma, w.T, w.lam, mode="bh")
+    b = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), w.sigma, w.T, w.lam, mode="bh", ckpt_every=4)
+    for x, y in zip(a, b):
+        assert np.array_equal(npy(x), npy(y))
+
+
+def test_infinite_threshold_equals_exact():
+    w = inputs.make("blobs", 3000, 16)
+    F, Phi, cnt = gs.rhs(dt(w.q0), dt(w.p0), w.sigma, mode="bh", thresh=1e30)
+    Fe, Phie, _ = gs.rhs(dt(w.q0), dt(w.p0), w.sigma)
+    assert cnt == (3000 * 3000, 0)
+    assert max_rel(npy(F), npy(Fe)) <= 1e-5
+    assert max_rel(npy(Phi), npy(Phie)) <= 1e-5
+
+
+def test_bh_fullsize_single_step(oracle):
+    """N = 100,000 blobs at sigma = 1.5: one Barnes-Hut forward and one
+    backward right-hand side against the full oracle, identical decisions."""
+    w = inputs.config("blobs100k")
+    F, Phi, cnt = gs.rhs(dt(w.q0), dt(w.p0), w.sigma, mode="bh")
+    Fo, Phio, cnto = oracle.rhs(w.q0, w.p0, w.sigma, mode=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(F), Fo) <= 1e-5 and max_rel(npy(Phi), Phio) <= 1e-5
+    rng = np.random.default_rng(1)
+    al, be = rng.normal(size=w.q0.shape), rng.normal(scale=0.1, size=w.q0.shape)
+    dA, dB, cnt = gs.adj_rhs(dt(w.q0), dt(w.p0), dt(al), dt(be), w.sigma, mode="bh")
+    dAo, dBo, cnto = oracle.adj_rhs(w.q0, w.p0, al, be, w.sigma, mode=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(dA), dAo) <= 1e-5 and max_rel(npy(dB), dBo) <= 1e-5
+    print(f"\nN=100k BH interactions per point: {cnt[0] / w.N:.0f} point + {cnt[1] / w.N:.0f} node")

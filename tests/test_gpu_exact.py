@@ -10,7 +10,7 @@ import torch
 
 import paper_1907_04834_gb300 as gs
 from paper_1907_04834_gb300 import inputs
-from gpu_util import dt, npy, max_rel, rel_l2
+from gpu_util import dt, npy, max_rel, rel_l2, phi_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +26,7 @@ def test_rhs_matches_oracle(oracle, geom, n, seed):
     assert cnt == (n * n, 0)
     assert max_rel(npy(F), Fo) <= 1e-5
     if n > 1:
-        assert max_rel(npy(Phi), Phio) <= 1e-5
+        assert max_rel(npy(Phi), Phio, phi_floor(w.p0, w.sigma)) <= 1e-5
     else:
         assert np.all(npy(Phi) == 0)
 
@@ -39,7 +39,7 @@ def test_adjoint_rhs_matches_oracle(oracle, geom, n, seed):
     be = rng.normal(scale=0.1, size=w.q0.shape)
     dA, dB, _ = gs.adj_rhs(dt(w.q0), dt(w.p0), dt(al), dt(be), w.sigma)
     dAo, dBo, _ = oracle.adj_rhs(w.q0, w.p0, al, be, w.sigma)
-    assert max_rel(npy(dA), dAo) <= 1e-5
+    assert max_rel(npy(dA), dAo, 1e-12 * np.abs(al).max() * np.abs(w.p0).max() / w.sigma) <= 1e-5
     assert max_rel(npy(dB), dBo) <= 1e-5
 
 
