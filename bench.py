@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: ms per shooting gradient (forward + adjoint) at N = 100,000,
+Barnes-Hut against plain exact, on synthetic blob point clouds.
+
+One step = one Barnes-Hut shooting gradient and one exact ("plain")
+shooting gradient of the objective of Eq. 2 (T = 20 Euler steps forward, 20
+adjoint steps back) on N = 100,000 points drawn from 8 anisotropic Gaussian
+blobs in a 60 mm cube, sigma = 1.5 mm, threshold 3 sigma.  `value` is the
+Barnes-Hut ms per gradient (the paper's method); the plain exact figure, the
+speed-up and pair-interaction rates ride along.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run, one rank per GPU) each
+rank computes its own replica of the workload (the shooting of one point set
+does not shard without an exchange step); value aggregates all ranks'
+gradients over the slowest rank's time.  --impl reference times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per shooting gradient (fwd+adjoint) at N=100k vs plain; pair-interactions/s"
+UNIT = "ms/gradient"
+WORKLOAD = "blobs100k"
+THRESH = 3.0
+# FP32 pipe: 128 lanes per SM per clock (one FADD/FMUL/FFMA lane-op each),
+# 152 SMs, maximum SM clock 2070 MHz.
+ALU_PEAK_OPS = 152 * 128 * 2.07e9
+OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 40, "bh_fwd": 16, "bh_adj": 40}
+# algorithmic bytes per point of one tree build (read FP32 positions + pack,
+# sort passes, node records written): see the design notes
+TREE_BYTES_PER_POINT = 250.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1907_04834_gb300 import inputs
+    return inputs.config(WORKLOAD)
+
+
+def config_dict(w, extra=None):
+    d = {"workload": f"{WORKLOAD}: N={w.N} points from 8 anisotropic Gaussian blobs (std 2-6 mm) "
+                     f"in a 60 mm cube, sigma={w.sigma} mm, T={w.T} Euler steps, lambda={w.lam}, "
+                     f"Barnes-Hut threshold {THRESH:g} sigma",
+         "N": w.N, "T": w.T, "sigma": w.sigma, "lambda": w.lam, "thresh_sigmas": THRESH,
+         "step": "one Barnes-Hut gradient + one exact (plain) gradient, fwd + adjoint",
+         "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.p = None
+        self.lines = []
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if device_id:
+                cmd += ["-i", device_id]
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                      text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- dist
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate_ranks(values, world, op="max"):
+    """Reduce a list of floats over ranks (identity when world == 1)."""
+    if world == 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.cpu().tolist()
+
+
+# --------------------------------------------------------------------- CPU baseline
+def oracle_timing(w, bh_reps=2, rows=4000):
+    """Times the FP64 oracle on a bounded sample: Barnes-Hut forward + adjoint
+    right-hand side at full N (bh_reps times), exact forward + adjoint on
+    `rows` sampled rows; extrapolates to ms per gradient (x T steps each)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(0)
+    al = rng.normal(size=w.q0.shape)
+    be = rng.normal(scale=0.1, size=w.q0.shape)
+    t0 = time.perf_counter()
+    for _ in range(bh_reps):
+        oracle.rhs(w.q0, w.p0, w.sigma, mode=1, thresh=THRESH)
+        oracle.adj_rhs(w.q0, w.p0, al, be, w.sigma, mode=1, thresh=THRESH)
+    bh_step = (time.perf_counter() - t0) / bh_reps
+    idx = np.sort(rng.choice(w.N, rows, replace=False))
+    t0 = time.perf_counter()
+    oracle.rhs_rows(w.q0, w.p0, w.sigma, idx)
+    oracle.adj_rhs_rows(w.q0, w.p0, al, be, w.sigma, idx)
+    ex_step = (time.perf_counter() - t0) * w.N / rows
+    return {"bh_ms": 1e3 * bh_step * w.T, "exact_ms": 1e3 * ex_step * w.T,
+            "cores": oracle.num_threads(),
+            "sample": f"{bh_reps} x (one Barnes-Hut forward + one adjoint right-hand side at full "
+                      f"N={w.N}), x T={w.T}; exact: forward + adjoint on {rows} sampled rows, "
+                      f"x N/rows x T"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    w = workload()
+    rng = np.random.default_rng(0)
+    al = rng.normal(size=w.q0.shape)
+    be = rng.normal(scale=0.1, size=w.q0.shape)
+
+    def step():
+        t0 = time.perf_counter()
+        oracle.rhs(w.q0, w.p0, w.sigma, mode=1, thresh=THRESH)
+        oracle.adj_rhs(w.q0, w.p0, al, be, w.sigma, mode=1, thresh=THRESH)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts) * w.T
+    sample = (f"each step: one Barnes-Hut forward + one adjoint right-hand side of the FP64 oracle "
+              f"at full N={w.N}, extrapolated x T={w.T} to one gradient")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, {"parallelism": "host cores"}),
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+def source_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel_class)
+        if not d:
+            return None
+        src = os.path.join(ROOT, d["source"])
+        if source_sha(src) != d["source_sha"]:
+            return None
+        return float(d["bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1907_04834_gb300 import native
+    native.build()
+    import paper_1907_04834_gb300 as gs
+    w = workload()
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    q0, p0, X = t(w.q0), t(w.p0), t(w.X)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def bh_grad():
+        return gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH)
+
+    def plain_grad():
+        return gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="exact")
+
+    # interactions per step at t = 0 (the per-gradient count is estimated as 2T x this)
+    _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
+    bh_inter_step = cnt[0] + cnt[1]
+    for _ in range(args.warmup):
+        bh_grad()
+        plain_grad()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = str(local)
+    gs.timing(True)
+    gs.timing_read()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(uuid)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        bh_grad()
+        ev[k][1].record()
+        plain_grad()
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    kern, launches = gs.timing_read()
+    gs.timing(False)
+    bh_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    pl_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    tot_bh, tot_pl = aggregate_ranks([sum(bh_ms), sum(pl_ms)], ws, "max")
+    grads = args.steps * ws
+    value = tot_bh / grads
+    plain = tot_pl / grads
+    step_ms = (tot_bh + tot_pl) / args.steps
+    pair_bh = 2 * w.T * bh_inter_step
+    pair_pl = 2 * w.T * w.N * w.N
+
+    # roofline of the dominant kernel class in the timed region
+    dom = max(kern, key=lambda k: kern[k][1])
+    nl, ms = kern[dom]
+    per_launch_s = ms / max(nl, 1) * 1e-3
+    if dom == "tree_build":
+        alg = TREE_BYTES_PER_POINT * w.N
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        roof = {"bound": "hbm", "achieved": alg / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s"}
+    else:
+        units = w.N * w.N if dom.startswith("exact") else bh_inter_step
+        alg = OPS_PER_PAIR[dom] * units
+        roof = {"bound": "alu", "achieved": alg / per_launch_s / 1e12,
+                "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["launch_ms"] = per_launch_s * 1e3
+    roof["share"] = ms / max(sum(v[1] for v in kern.values()), 1e-9)
+    tr = measured_traffic(dom)
+    roof["traffic"] = tr
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(w, {"parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"}),
+            "plain_ms_per_gradient": plain, "speedup_vs_plain": plain / value,
+            "pair_interactions_per_s": {"bh": pair_bh * grads / (tot_bh * 1e-3),
+                                        "plain": pair_pl * grads / (tot_pl * 1e-3)},
+            "exact_equivalent_pairs_per_s_bh": pair_pl * grads / (tot_bh * 1e-3),
+            "shooting_steps_per_s_bh": 2 * w.T * grads / (tot_bh * 1e-3),
+            "bh_interactions_per_point_step": bh_inter_step / w.N,
+            "roofline": roof,
+            "kernels": {k: {"launch_groups": v[0], "ms": v[1]} for k, v in kern.items()},
+            "gpu_launches": launches, "wall_s": wall, "clocks": ck}
+
+    if rank == 0 and args.e2e_steps > 0:
+        # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
+        h = lambda a: torch.as_tensor(a, dtype=torch.float64).pin_memory()
+        hq, hp, hX = h(w.q0), h(w.p0), h(w.X)
+        gs.shoot_grad(hq, hp, hX, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH)
+        es = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            E, g, q1 = gs.shoot_grad(hq, hp, hX, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH)
+            es.append((time.perf_counter() - t0) * 1e3)
+        line["e2e"] = {"value": statistics.median(es), "unit": UNIT,
+                       "h2d_bytes_per_step": 3 * w.N * 3 * 8,
+                       "d2h_bytes_per_step": (3 + 2 * w.N * 3) * 8}
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            ob = oracle_timing(w)
+            line["cpu_baseline"] = {"value": ob["bh_ms"], "unit": UNIT, "cores": ob["cores"],
+                                    "kind": "oracle", "sample": ob["sample"],
+                                    "plain_value": ob["exact_ms"]}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

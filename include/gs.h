@@ -162,6 +162,28 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
 
 /* ---- diagnostics ---------------------------------------------------------- */
 
+/* Kernel classes timed by gs_timing. */
+enum {
+  GS_K_EXACT_FWD = 0,  /* exact forward pair kernel */
+  GS_K_EXACT_ADJ = 1,  /* exact adjoint pair kernel */
+  GS_K_TREE_BUILD = 2, /* octree build: bbox, Morton, sort, nodes, aggregates */
+  GS_K_BH_FWD = 3,     /* Barnes-Hut forward traversal */
+  GS_K_BH_ADJ = 4,     /* Barnes-Hut adjoint traversal */
+  GS_K_COUNT = 5
+};
+
+/* enable != 0: subsequent calls bracket each launch group of the classes
+ * above with CUDA events on the call's stream (small overhead per group). */
+gs_status gs_timing(gs_ctx *ctx, int enable);
+
+/* Waits for the recorded events and returns, per class, the number of timed
+ * launch groups (launches[GS_K_COUNT]) and their summed device time in ms
+ * (ms[GS_K_COUNT]) since the previous read; total_launches (may be NULL)
+ * receives the number of kernels this library launched (all kinds, this
+ * process) since the previous read. */
+gs_status gs_timing_read(gs_ctx *ctx, int64_t *launches, double *ms,
+                         int64_t *total_launches);
+
 /* Measured device-wide issue rates of the units the pair kernels use, in
  * lane-operations per second: out[0] scalar FP32 FMA, out[1] FP32 operations
  * through packed f32x2 FMA (two per lane per instruction), out[2] MUFU ex2.

@@ -81,6 +81,14 @@ def _device_of(t: torch.Tensor) -> int | None:
     return t.device.index if t.is_cuda else None
 
 
+def _like(t: torch.Tensor, shape=None) -> torch.Tensor:
+    """Output buffer beside input t (pinned host memory for pinned inputs)."""
+    shape = tuple(t.shape) if shape is None else shape
+    if not t.is_cuda and t.is_pinned():
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    return torch.empty(shape, dtype=torch.float64, device=t.device)
+
+
 def _ptr(t: torch.Tensor | None):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -97,8 +105,8 @@ def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, stream=None)
     p0 = _pts(p0, "p0", q0.shape[0])
     c = _ctx_for(q0)
     prm = make_params(sigma, T, mode, 0.0, thresh)
-    q1, p1 = torch.empty_like(q0), torch.empty_like(q0)
-    H = torch.empty(2, dtype=torch.float64, device=q0.device) if with_H else None
+    q1, p1 = _like(q0), _like(q0)
+    H = _like(q0, (2,)) if with_H else None
     c.check(c.lib.gs_shoot(c.handle, _ptr(q0), _ptr(p0), q0.shape[0], ctypes.byref(prm), _ptr(q1),
                            _ptr(p1), _ptr(H), _stream_ptr(c.device, stream)))
     return q1, p1, H
@@ -113,8 +121,8 @@ def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_ever
     p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
     c = _ctx_for(q0)
     prm = make_params(sigma, T, mode, lam, thresh, ckpt_every)
-    E = torch.empty(3, dtype=torch.float64, device=q0.device)
-    grad, q1 = torch.empty_like(q0), torch.empty_like(q0)
+    E = _like(q0, (3,))
+    grad, q1 = _like(q0), _like(q0)
     c.check(c.lib.gs_shoot_grad(c.handle, _ptr(q0), _ptr(p0), _ptr(X), n, ctypes.byref(prm),
                                 _ptr(E), _ptr(grad), _ptr(q1), _stream_ptr(c.device, stream)))
     return E, grad, q1
@@ -186,6 +194,34 @@ def tree(q, stream=None):
                           cap, ctypes.byref(m), _stream_ptr(c.device, stream)))
     M = m.value
     return dict(codes=codes, order=order, nodes=nodes[:M], range=rng[:M], n_nodes=M)
+
+
+def timing(enable: bool = True, device: int | None = None):
+    """Turns per-kernel-class event timing on or off (see gs_timing)."""
+    c = context(device)
+    c.check(c.lib.gs_timing(c.handle, int(bool(enable))))
+
+
+def timing_read(device: int | None = None):
+    """{class: (launch groups, ms)} since the last read, and the number of
+    kernels the library launched meanwhile."""
+    c = context(device)
+    n = len(_lib.KERNEL_CLASSES)
+    la = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_double * n)()
+    tot = ctypes.c_int64()
+    c.check(c.lib.gs_timing_read(c.handle, la, ms, ctypes.byref(tot)))
+    return {k: (la[i], ms[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}, tot.value
+
+
+def alu_peaks(device: int = 0):
+    """Measured lane-op rates: (FP32 FMA, FP32 via f32x2 FMA, MUFU ex2) per s."""
+    lib = _lib.load()
+    out = (ctypes.c_double * 3)()
+    st = lib.gs_alu_peaks(int(device), out)
+    if st != 0:
+        raise GSError(st, "gs_alu_peaks failed")
+    return tuple(out)
 
 
 class GeodesicShoot(torch.autograd.Function):

@@ -45,6 +45,15 @@ struct DevMem {
 using namespace gs;
 
 struct gs_ctx {
+  // kernel timing (gs_timing): events around each timed launch group
+  struct Timed {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> pool;
+  long long launch_mark = 0;
   int device = 0;
   int num_sms = 0;
   std::string err;
@@ -60,6 +69,38 @@ struct gs_ctx {
 };
 
 namespace {
+
+// Brackets the launches of one kernel class with events on `st` when the
+// context's timing is on.
+struct KTimer {
+  gs_ctx* c;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  static cudaEvent_t get(gs_ctx* c) {
+    if (!c->pool.empty()) {
+      cudaEvent_t e = c->pool.back();
+      c->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  KTimer(gs_ctx* c_, int cls_, cudaStream_t st_) : c(c_), cls(cls_), st(st_) {
+    if (c->timing && (a = get(c))) cudaEventRecord(a, st);
+  }
+  ~KTimer() {
+    if (!a) return;
+    cudaEvent_t b = get(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->pending.push_back({cls, a, b});
+  }
+};
 
 // scal slots (doubles)
 enum { SC_CENTER = 0, SC_H0 = 3, SC_H1 = 4, SC_DATA = 5, SC_E = 6, SC_N = 16 };
@@ -323,6 +364,7 @@ FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
 gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
   gs_ctx* c = S.c;
   if (S.mode == GS_EXACT) {
+    KTimer tm(c, GS_K_EXACT_FWD, S.st);
     CK(launch_exact_fwd(S.pack(slot), S.gf, c->part.as<float2>(), c->tickets.as<unsigned>(), e,
                         c->d_status, S.st),
        "exact forward kernel");
@@ -333,7 +375,15 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
     return GS_OK;
   }
   BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
-  gs_status s = bh_forward(c->tree, b, e, c->d_status, counts, S.st);
+  gs_status s;
+  {
+    KTimer tm(c, GS_K_TREE_BUILD, S.st);
+    s = bh_build(c->tree, b, nullptr, counts != nullptr, S.st);
+  }
+  if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_FWD, S.st);
+    s = bh_traverse_fwd(c->tree, b, e, counts != nullptr, S.st);
+  }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut forward step failed: %s", bh_last_error());
   return GS_OK;
 }
@@ -355,6 +405,7 @@ AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) 
 gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts) {
   gs_ctx* c = S.c;
   if (S.mode == GS_EXACT) {
+    KTimer tm(c, GS_K_EXACT_ADJ, S.st);
     CK(launch_exact_adj(S.pack(slot), S.abpack(ab), S.ga, c->part.as<float2>(),
                         c->tickets.as<unsigned>(), e, c->d_status, S.st),
        "exact adjoint kernel");
@@ -365,7 +416,15 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     return GS_OK;
   }
   BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
-  gs_status s = bh_adjoint(c->tree, b, S.abpack(ab), e, c->d_status, counts, S.st);
+  gs_status s;
+  {
+    KTimer tm(c, GS_K_TREE_BUILD, S.st);
+    s = bh_build(c->tree, b, S.abpack(ab), counts != nullptr, S.st);
+  }
+  if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_ADJ, S.st);
+    s = bh_traverse_adj(c->tree, b, e, counts != nullptr, S.st);
+  }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut adjoint step failed: %s", bh_last_error());
   return GS_OK;
 }
@@ -414,12 +473,51 @@ void gs_destroy(gs_ctx* c) {
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets})
       m->release();
     tree_release(c->tree);
+    for (auto& t : c->pending) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
     if (c->d_status) cudaFree(c->d_status);
   }
   delete c;
 }
 
 const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+gs_status gs_timing(gs_ctx* c, int enable) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->timing = enable != 0;
+  return GS_OK;
+}
+
+gs_status gs_timing_read(gs_ctx* c, int64_t* launches, double* ms, int64_t* total_launches) {
+  if (!c || !launches || !ms) return GS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  for (int k = 0; k < GS_K_COUNT; k++) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  gs_status rc = GS_OK;
+  for (auto& t : c->pending) {
+    float v = 0.f;
+    if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&v, t.a, t.b) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(c, GS_ERR_CUDA, "timing event failed");
+    }
+    if (t.cls >= 0 && t.cls < GS_K_COUNT) {
+      launches[t.cls] += 1;
+      ms[t.cls] += v;
+    }
+    c->pool.push_back(t.a);
+    c->pool.push_back(t.b);
+  }
+  c->pending.clear();
+  const long long now = launches_total();
+  if (total_launches) *total_launches = now - c->launch_mark;
+  c->launch_mark = now;
+  return rc;
+}
 
 gs_status gs_sync(gs_ctx* c, void* stream) {
   if (!c) return GS_ERR_INVALID_ARG;

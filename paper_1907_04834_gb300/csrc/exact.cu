@@ -307,6 +307,7 @@ cudaError_t launch_exact_fwd(const float4* pk, const ExactGeom& g, float2* part,
                              unsigned* tickets, const FwdEpi& e, int* status, cudaStream_t st) {
   dim3 grid(g.n_itiles, g.J);
   k_exact_fwd<<<grid, EX_NT, exact_fwd_smem(), st>>>(pk, g, part, tickets, e, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -314,6 +315,7 @@ cudaError_t launch_exact_adj(const float4* pk, const float4* ab, const ExactGeom
                              unsigned* tickets, const AdjEpi& e, int* status, cudaStream_t st) {
   dim3 grid(g.n_itiles, g.J);
   k_exact_adj<<<grid, EX_NT, exact_adj_smem(), st>>>(pk, ab, g, part, tickets, e, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,11 @@
 
 namespace gs {
 
+// Process-wide count of kernel launches issued by this library (every
+// launcher adds the number of kernels it enqueues).
+void note_launches(int n);
+long long launches_total();
+
 // ---- exact all-pairs kernels (exact.cu)
 constexpr int EX_NT = 256;     // target points per block (one per thread)
 constexpr int EX_TILE = 512;   // source points per shared-memory tile

@@ -545,6 +545,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, N, t.mask, t.offs, t.own_a, t.own_b,
                                                  t.nsc, t.ninfo, t.nparent, t.acnt);
   k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack);
+  note_launches(2 + 4 * 5 + (N > 1 ? 1 : 0) + 3 + 2);
   return cudaGetLastError();
 }
 
@@ -589,32 +590,33 @@ static gs_status cuda_err(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
 }
 
-gs_status bh_forward(TreeWork& w, const BHStep& b, const FwdEpi& e, int* status, int64_t* counts,
-                     cudaStream_t st) {
-  (void)status;
+gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
+                   cudaStream_t st) {
   size_t bytes;
   TreeArrays t = carve(w.mem, w.cap_n, &bytes);
   cudaError_t err;
-  if (counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess) return cuda_err(err);
-  if ((err = build(t, (int)b.N, b.raw, b.pack, nullptr, st)) != cudaSuccess) return cuda_err(err);
-  if ((err = launch_bh_traverse_fwd(t, (int)b.N, b.raw, b.thr, e, counts ? t.counts : nullptr,
-                                    st)) != cudaSuccess)
+  if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
     return cuda_err(err);
+  if ((err = build(t, (int)b.N, b.raw, b.pack, abpack, st)) != cudaSuccess) return cuda_err(err);
   return GS_OK;
 }
 
-gs_status bh_adjoint(TreeWork& w, const BHStep& b, const float4* abpack, const AdjEpi& e,
-                     int* status, int64_t* counts, cudaStream_t st) {
-  (void)status;
+gs_status bh_traverse_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
+                          cudaStream_t st) {
   size_t bytes;
   TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  cudaError_t err;
-  if (counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess) return cuda_err(err);
-  if ((err = build(t, (int)b.N, b.raw, b.pack, abpack, st)) != cudaSuccess) return cuda_err(err);
-  if ((err = launch_bh_traverse_adj(t, (int)b.N, b.raw, b.thr, e, counts ? t.counts : nullptr,
-                                    st)) != cudaSuccess)
-    return cuda_err(err);
-  return GS_OK;
+  cudaError_t err = launch_bh_traverse_fwd(t, (int)b.N, b.raw, b.thr, e,
+                                           counts ? t.counts : nullptr, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
+gs_status bh_traverse_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
+                          cudaStream_t st) {
+  size_t bytes;
+  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  cudaError_t err = launch_bh_traverse_adj(t, (int)b.N, b.raw, b.thr, e,
+                                           counts ? t.counts : nullptr, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
 void bh_counts(TreeWork& w, int64_t* cnt) {
@@ -669,6 +671,7 @@ gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_
       return cuda_err(err);
     }
     k_export_nodes<<<nblocks(m, 256), 256, 0, st>>>(t, (int)m, dn, dr);
+    note_launches(1);
     err = cudaGetLastError();
     if (err == cudaSuccess && nodes) err = cudaMemcpyAsync(nodes, dn, 16 * m, cudaMemcpyDefault, st);
     if (err == cudaSuccess && range) err = cudaMemcpyAsync(range, dr, 24 * m, cudaMemcpyDefault, st);

@@ -30,10 +30,14 @@ struct BHStep {
 cudaError_t tree_setup();
 gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st);
 void tree_release(TreeWork& w);
-gs_status bh_forward(TreeWork& w, const BHStep& b, const FwdEpi& e, int* status,
-                     int64_t* counts, cudaStream_t st);
-gs_status bh_adjoint(TreeWork& w, const BHStep& b, const float4* abpack, const AdjEpi& e,
-                     int* status, int64_t* counts, cudaStream_t st);
+// Builds the tree of one state (abpack = NULL in the forward stage).
+gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
+                   cudaStream_t st);
+// Traverses the tree built last; counts != NULL accumulates interactions.
+gs_status bh_traverse_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
+                          cudaStream_t st);
+gs_status bh_traverse_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
+                          cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
 // Builds the tree on one state and exports it (see gs_tree in gs.h).
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,

@@ -1,5 +1,6 @@
 // util.cu -- small per-point kernels: recentring, packing, adjoint
 // initialisation, deterministic FP64 reductions, finiteness checks.
+#include <atomic>
 #include <cfloat>
 
 #include "common.cuh"
@@ -130,16 +131,23 @@ __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* sta
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+std::atomic<long long> g_launches{0};
+
 }  // namespace
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st) {
   k_bbox_center<<<1, kRedThreads, 0, st>>>(q, N, center);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const double* q, const double* p, int64_t N, const double* center,
                         double s, float4* pack, float4* raw, cudaStream_t st) {
   k_pack<<<blocks_for(N, 256), 256, 0, st>>>(q, p, N, center, s, pack, raw);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -148,12 +156,14 @@ cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, 
   if (Npad <= N || slots <= 0) return cudaSuccess;
   dim3 grid(blocks_for(Npad - N, 256), (unsigned)slots);
   k_pad_zero<<<grid, 256, 0, st>>>(base, slot_f4, N, Npad);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, float4* abpack,
                            cudaStream_t st) {
   k_pack_ab<<<blocks_for(N, 256), 256, 0, st>>>(al, be, N, abpack);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -161,22 +171,26 @@ cudaError_t launch_adjoint_init(const double* q, const double* X, int64_t N, dou
                                 double* al, double* be, float4* abpack, double* r2,
                                 cudaStream_t st) {
   k_adjoint_init<<<blocks_for(N, 256), 256, 0, st>>>(q, X, N, lambda, al, be, abpack, r2);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(const double* x, int64_t n, double scale, double* out, cudaStream_t st) {
   k_sum<<<1, kRedThreads, 0, st>>>(x, n, scale, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_energy(const double* H, const double* data, double* E, cudaStream_t st) {
   k_energy<<<1, 1, 0, st>>>(H, data, E);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_grad(const double* be, const double* F0, int64_t n3, double* grad,
                              cudaStream_t st) {
   k_axpy_grad<<<blocks_for(n3, 256), 256, 0, st>>>(be, F0, n3, grad);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -185,6 +199,7 @@ cudaError_t launch_check_finite(const double* x, int64_t n, int* status, cudaStr
   if (b > 1024) b = 1024;
   if (b == 0) b = 1;
   k_check_finite<<<b, 256, 0, st>>>(x, n, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
