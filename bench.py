@@ -39,7 +39,7 @@ THRESH = 3.0
 # FP32 pipe: 128 lanes per SM per clock (one FADD/FMUL/FFMA lane-op each),
 # 152 SMs, maximum SM clock 2070 MHz.
 ALU_PEAK_OPS = 152 * 128 * 2.07e9
-OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 40, "bh_fwd": 16, "bh_adj": 40}
+OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 40, "bh_fwd": 16, "bh_adj": 40, "bh_walk": 16}
 # algorithmic bytes per point of one tree build (read FP32 positions + pack,
 # sort passes, node records written): see the design notes
 TREE_BYTES_PER_POINT = 250.0

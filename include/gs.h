@@ -162,14 +162,22 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
 
 /* ---- diagnostics ---------------------------------------------------------- */
 
+/* Tuning options of a context:
+ *   "bh_list_cap": entries recorded per interaction list of the Barnes-Hut
+ *   walk (two lists per 32 points); 0 = default (8192, reduced to keep the
+ *   lists within 4 GB).  A list that outgrows it is finished by a slower
+ *   fused walk-and-evaluate pass; results are the same either way. */
+gs_status gs_set_option(gs_ctx *ctx, const char *name, int64_t value);
+
 /* Kernel classes timed by gs_timing. */
 enum {
   GS_K_EXACT_FWD = 0,  /* exact forward pair kernel */
   GS_K_EXACT_ADJ = 1,  /* exact adjoint pair kernel */
   GS_K_TREE_BUILD = 2, /* octree build: bbox, Morton, sort, nodes, aggregates */
-  GS_K_BH_FWD = 3,     /* Barnes-Hut forward traversal */
-  GS_K_BH_ADJ = 4,     /* Barnes-Hut adjoint traversal */
-  GS_K_COUNT = 5
+  GS_K_BH_FWD = 3,     /* Barnes-Hut forward evaluation of the interaction lists */
+  GS_K_BH_ADJ = 4,     /* Barnes-Hut adjoint evaluation of the interaction lists */
+  GS_K_BH_WALK = 5,    /* Barnes-Hut tree walk (decisions, interaction lists) */
+  GS_K_COUNT = 6
 };
 
 /* enable != 0: subsequent calls bracket each launch group of the classes

@@ -19,7 +19,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_NONFINITE, GS_ERR_TIM
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_NONFINITE", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
 GS_EXACT, GS_BH = 0, 1
-KERNEL_CLASSES = ("exact_fwd", "exact_adj", "tree_build", "bh_fwd", "bh_adj")
+KERNEL_CLASSES = ("exact_fwd", "exact_adj", "tree_build", "bh_fwd", "bh_adj", "bh_walk")
 
 
 class GSError(RuntimeError):
@@ -60,6 +60,7 @@ _SIGS = {
     "gs_tree": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "gs_alu_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gs_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "gs_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, _i64]),
     "gs_timing_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
 }
 

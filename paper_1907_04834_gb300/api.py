@@ -196,6 +196,12 @@ def tree(q, stream=None):
     return dict(codes=codes, order=order, nodes=nodes[:M], range=rng[:M], n_nodes=M)
 
 
+def set_option(name: str, value: int, device: int | None = None):
+    """Sets a tuning option of the device's context (see gs_set_option)."""
+    c = context(device)
+    c.check(c.lib.gs_set_option(c.handle, name.encode(), int(value)))
+
+
 def timing(enable: bool = True, device: int | None = None):
     """Turns per-kernel-class event timing on or off (see gs_timing)."""
     c = context(device)

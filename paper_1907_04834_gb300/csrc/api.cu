@@ -381,8 +381,12 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
     s = bh_build(c->tree, b, nullptr, counts != nullptr, S.st);
   }
   if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_WALK, S.st);
+    s = bh_walk(c->tree, b, counts != nullptr, S.st);
+  }
+  if (s == GS_OK) {
     KTimer tm(c, GS_K_BH_FWD, S.st);
-    s = bh_traverse_fwd(c->tree, b, e, counts != nullptr, S.st);
+    s = bh_eval_fwd(c->tree, b, e, counts != nullptr, S.st);
   }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut forward step failed: %s", bh_last_error());
   return GS_OK;
@@ -422,8 +426,12 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     s = bh_build(c->tree, b, S.abpack(ab), counts != nullptr, S.st);
   }
   if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_WALK, S.st);
+    s = bh_walk(c->tree, b, counts != nullptr, S.st);
+  }
+  if (s == GS_OK) {
     KTimer tm(c, GS_K_BH_ADJ, S.st);
-    s = bh_traverse_adj(c->tree, b, e, counts != nullptr, S.st);
+    s = bh_eval_adj(c->tree, b, e, counts != nullptr, S.st);
   }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut adjoint step failed: %s", bh_last_error());
   return GS_OK;
@@ -484,6 +492,17 @@ void gs_destroy(gs_ctx* c) {
 }
 
 const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
+  if (!c || !name) return GS_ERR_INVALID_ARG;
+  if (strcmp(name, "bh_list_cap") == 0) {
+    if (value < 0 || value > (int64_t(1) << 24))
+      return fail(c, GS_ERR_INVALID_ARG, "bh_list_cap must be in [0, 2^24]");
+    c->tree.lcap_req = (int)value;
+    return GS_OK;
+  }
+  return fail(c, GS_ERR_INVALID_ARG, "unknown option '%s'", name);
+}
 
 gs_status gs_timing(gs_ctx* c, int enable) {
   if (!c) return GS_ERR_INVALID_ARG;

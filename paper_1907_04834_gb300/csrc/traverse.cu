@@ -1,25 +1,33 @@
 // traverse.cu -- Barnes-Hut traversal of Sec. 2.2 (Fig. 1), forward (Eq. 4
 // and the momentum-dot replacement) and backward (alpha, beta replaced by
-// their node averages), one warp per 32 Morton-consecutive points.
+// their node averages), for groups of 32 Morton-consecutive points.
 //
-// The warp walks the preorder node array once, front to back.  At node x
-// every lane applies its own point's rule (three cases of Sec. 2.2):
-//   leaf                     -> exact interaction with that point;
+// Every lane applies its own point's rule at each node it reaches (three
+// cases of Sec. 2.2):
+//   leaf                          -> exact interaction with that point;
 //   internal, range farther than the threshold -> one interaction with the
-//                               node summary; the lane then ignores x's
-//                               subtree (resume = skip(x));
-//   internal, otherwise      -> open x.
-// The warp steps into x when any lane opens it, else jumps to skip(x).  A
-// lane's interactions are exactly those of its own recursive traversal;
-// lanes that have already summarised an ancestor stay idle inside it.
-// Node boxes are staged 32 at a time in shared memory (the walk only moves
-// forward) with a bit mask of which are leaves; a run of consecutive leaves
-// is queued in one step (lanes change activity only at their resume points,
-// so the run is cut at the first one).  Interactions are queued as (node,
-// lane mask) and evaluated in batches of >= 32, two sources per f32x2
-// instruction, with the records staged in shared memory.  A far node acts as
-// one source at its centroid with momentum P, position derivative A and
-// momentum derivative B/n, so the pair arithmetic is the exact kernel's.
+//                                    node summary; the lane then ignores the
+//                                    node's subtree (resume = skip);
+//   internal, otherwise           -> open the node.
+// Nodes are in depth-first preorder, so a group walks the node array forward,
+// stepping into a node when any lane opens it and jumping to skip otherwise.
+// A lane's interactions are exactly those of its own recursive traversal.
+//
+// Two phases:
+//   walk     -- decisions only, few registers.  The node range is cut in two
+//               slices at the group's middle point; the second slice starts
+//               by testing the ancestors of its first node, which gives every
+//               lane the state it would have there.  Each slice emits an
+//               ordered list of (node, lane mask) entries; runs of
+//               consecutive leaves are appended in one step (a lane changes
+//               activity only at its resume point, so a run is cut there).
+//   evaluate -- one warp per list streams its entries, stages the source
+//               records in shared memory and evaluates two sources per f32x2
+//               instruction (a far node acts as one source at its centroid
+//               with momentum P, derivative A and momentum derivative B/n).
+// A slice whose list outgrows its capacity saves its walk state; a fused
+// walk+evaluate kernel resumes it from there.  Partial sums are combined in
+// a fixed order, so results are deterministic.
 #include <climits>
 
 #include "kernels.h"
@@ -29,259 +37,515 @@ namespace gs {
 
 namespace {
 
+constexpr unsigned FULL = 0xffffffffu;
 constexpr int TR_WARPS = 4;
-constexpr int TR_BUF = 32;  // flush when this many interactions are queued
-constexpr int TR_CAP = 64;  // queue capacity (a leaf run adds at most 32)
+constexpr int TR_BUF = 32;
+constexpr int TR_CAP = 64;
 
-template <bool ADJ>
-__global__ void __launch_bounds__(TR_WARPS * 32)
-    k_bh_traverse(TreeArrays t, int N, const float4* __restrict__ raw, float thr, FwdEpi fe,
-                  AdjEpi ae, int64_t* counts) {
-  constexpr int NR = ADJ ? 12 : 6;   // record components used
-  constexpr int NC = ADJ ? 15 : 6;   // accumulated components
-  __shared__ float4 s_box[TR_WARPS][32][2];
-  __shared__ __align__(16) float s_soa[TR_WARPS][NR][TR_CAP];
-  __shared__ int s_node[TR_WARPS][TR_CAP];
-  __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int wg = blockIdx.x * TR_WARPS + w;
-  if (wg * 32 >= N) return;  // the whole warp leaves together
-  const int i = wg * 32 + lane;
-  const bool valid = i < N;
-  const int M = total_nodes(t, N);
-  const int ii = valid ? i : N - 1;
-  const int o = (int)t.perm[ii];
+// Per-lane own data (record of the lane's point).
+struct Own {
+  int i, o;  // sorted position, original index
+  bool valid;
+  float4 m0, m1, m2, m3;  // record: xs, p, a, b
+};
+
+__device__ __forceinline__ Own load_own(const TreeArrays& t, int N, int g, int lane, bool adj) {
+  Own w;
+  w.i = g * 32 + lane;
+  w.valid = w.i < N;
+  const int ii = w.valid ? w.i : N - 1;
+  w.o = (int)t.perm[ii];
   const int leaf = ii + (int)t.offs[ii + 1];
-  const float4 rr = raw[o];
-  float4 m0 = t.nrec[4 * leaf], m1 = t.nrec[4 * leaf + 1];
-  float4 m2 = make_float4(0.f, 0.f, 0.f, 0.f), m3 = m2;
-  if constexpr (ADJ) {
-    m2 = t.nrec[4 * leaf + 2];
-    m3 = t.nrec[4 * leaf + 3];
+  w.m0 = t.nrec[4 * leaf];
+  w.m1 = t.nrec[4 * leaf + 1];
+  w.m2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  w.m3 = w.m2;
+  if (adj) {
+    w.m2 = t.nrec[4 * leaf + 2];
+    w.m3 = t.nrec[4 * leaf + 3];
   }
-  // own position/momentum (and alpha, beta) duplicated into f32x2 pairs
-  const f2 X = f2_dup(m0.x), Y = f2_dup(m0.y), Z = f2_dup(m0.z);
-  const f2 U = f2_dup(m1.x), V = f2_dup(m1.y), W = f2_dup(m1.z);
-  const f2 AX = f2_dup(m2.x), AY = f2_dup(m2.y), AZ = f2_dup(m2.z);
-  const f2 BX = f2_dup(m3.x), BY = f2_dup(m3.y), BZ = f2_dup(m3.z);
-  int resume = valid ? 0 : INT_MAX;
+  return w;
+}
+
+// Slices of the node range for group g: [0, L-D), [L-D, L), [L, L+D),
+// [L+D, M) where L is the leaf of the group's middle point and
+// D = clamp(M / 32, 256, 4096).  Any cut points give the same interactions;
+// these spread a group's work over four warps.  D depends only on the
+// current tree, so results are reproducible.
+__device__ __forceinline__ int slice_start(const TreeArrays& t, const BHLists& L, int N, int g,
+                                           int k) {
+  if (k == 0) return 0;
+  const int i = min(g * 32 + 16, N - 1);
+  const int mid = i + (int)t.offs[i + 1];
+  const int M = total_nodes(t, N);
+  const int D = min(max(M >> 5, 256), 4096);
+  if (k == 1) return max(0, mid - D);
+  if (k == 2) return mid;
+  return min(M, mid + D);
+}
+
+__device__ __forceinline__ int slice_end(const TreeArrays& t, const BHLists& L, int N, int g,
+                                         int k) {
+  return k == BH_SLICES - 1 ? total_nodes(t, N) : slice_start(t, L, N, g, k + 1);
+}
+
+// Resume point of this lane at node s: test the ancestors of s from the root
+// down; the first one this lane finds far makes it skip past s.
+__device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float rz, float thr,
+                         int resume) {
+  int path[12];
+  int n = 0;
+  for (int a = t.nparent[s]; a >= 0 && n < 12; a = t.nparent[a]) path[n++] = a;
+  for (int k = n - 1; k >= 0; k--) {
+    const int a = path[k];
+    if (resume > a) continue;
+    const float4 lo = t.nbox[2 * a], hi = t.nbox[2 * a + 1];
+    if (box_dist2(rx, ry, rz, lo, hi) > thr) resume = __float_as_int(lo.w);
+  }
+  return resume;
+}
+
+// ------------------------------------------------------------------ evaluation
+template <bool ADJ>
+struct Acc {
+  static constexpr int NC = ADJ ? 15 : 6;
   Kahan K[NC];
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-  for (int c = 0; c < NC; c++) K[c].zero();
-  long long np = 0, nn = 0;
-  int cnt = 0, base = INT_MIN / 2, x = 0;
-  unsigned leafmask = 0u;
+    for (int c = 0; c < NC; c++) K[c].zero();
+  }
+};
 
-  // Evaluates the queued interactions, two sources per f32x2 instruction;
-  // a lane whose bit is clear gets weight 0.
-  auto flush = [&]() {
-    __syncwarp();
-    for (int e = lane; e < cnt; e += 32) {
-      const int nd = s_node[w][e];
-      const float4 r0 = t.nrec[4 * nd], r1 = t.nrec[4 * nd + 1];
-      s_soa[w][0][e] = r0.x, s_soa[w][1][e] = r0.y, s_soa[w][2][e] = r0.z;
-      s_soa[w][3][e] = r1.x, s_soa[w][4][e] = r1.y, s_soa[w][5][e] = r1.z;
-      if constexpr (ADJ) {
-        const float4 r2 = t.nrec[4 * nd + 2], r3 = t.nrec[4 * nd + 3];
-        s_soa[w][6][e] = r2.x, s_soa[w][7][e] = r2.y, s_soa[w][8][e] = r2.z;
-        s_soa[w][9][e] = r3.x, s_soa[w][10][e] = r3.y, s_soa[w][11][e] = r3.z;
-      }
+// Evaluates sources e in [0, n) (n even) whose records are staged in soa
+// (component-major, stride TR_CAP) and whose lane masks are in mask[].
+template <bool ADJ>
+__device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const unsigned* mask,
+                                           int n, int lane, const Own& me) {
+  const f2 X = f2_dup(me.m0.x), Y = f2_dup(me.m0.y), Z = f2_dup(me.m0.z);
+  const f2 U = f2_dup(me.m1.x), V = f2_dup(me.m1.y), W = f2_dup(me.m1.z);
+  auto ld = [&](int c, int e) { return *reinterpret_cast<const f2*>(soa + c * TR_CAP + e); };
+  if constexpr (!ADJ) {
+    f2 fx = 0, fy = 0, fz = 0, hx = 0, hy = 0, hz = 0;
+#pragma unroll 2
+    for (int e = 0; e < n; e += 2) {
+      const bool b0 = (mask[e] >> lane) & 1u, b1 = (mask[e + 1] >> lane) & 1u;
+      const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
+      f2 r = f2_mul(dx, dx);
+      r = f2_fma(dy, dy, r);
+      r = f2_fma(dz, dz, r);
+      float r0, r1;
+      f2_split(r, r0, r1);
+      const f2 g = f2_make(b0 ? ex2_neg(r0) : 0.f, b1 ? ex2_neg(r1) : 0.f);
+      const f2 PX = ld(3, e), PY = ld(4, e), PZ = ld(5, e);
+      fx = f2_fma(g, PX, fx);
+      fy = f2_fma(g, PY, fy);
+      fz = f2_fma(g, PZ, fz);
+      f2 c = f2_mul(U, PX);
+      c = f2_fma(V, PY, c);
+      c = f2_fma(W, PZ, c);
+      const f2 cg = f2_mul(c, g);
+      hx = f2_fma(cg, dx, hx);
+      hy = f2_fma(cg, dy, hy);
+      hz = f2_fma(cg, dz, hz);
     }
-    if (cnt & 1) {  // pad to an even count with an empty entry
-      if (lane == 0) s_mask[w][cnt] = 0u;
-      if (lane < NR) s_soa[w][lane][cnt] = 0.f;
+    A.K[0].add(f2_sum(fx));
+    A.K[1].add(f2_sum(fy));
+    A.K[2].add(f2_sum(fz));
+    A.K[3].add(f2_sum(hx));
+    A.K[4].add(f2_sum(hy));
+    A.K[5].add(f2_sum(hz));
+  } else {
+    const f2 AX = f2_dup(me.m2.x), AY = f2_dup(me.m2.y), AZ = f2_dup(me.m2.z);
+    const f2 BX = f2_dup(me.m3.x), BY = f2_dup(me.m3.y), BZ = f2_dup(me.m3.z);
+    f2 a1x = 0, a1y = 0, a1z = 0, a2x = 0, a2y = 0, a2z = 0, a3x = 0, a3y = 0, a3z = 0;
+    f2 b1x = 0, b1y = 0, b1z = 0, b2x = 0, b2y = 0, b2z = 0;
+    for (int e = 0; e < n; e += 2) {
+      const bool b0 = (mask[e] >> lane) & 1u, b1 = (mask[e + 1] >> lane) & 1u;
+      const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
+      f2 r = f2_mul(dx, dx);
+      r = f2_fma(dy, dy, r);
+      r = f2_fma(dz, dz, r);
+      float r0, r1;
+      f2_split(r, r0, r1);
+      const f2 g = f2_make(b0 ? ex2_neg(r0) : 0.f, b1 ? ex2_neg(r1) : 0.f);
+      const f2 PX = ld(3, e), PY = ld(4, e), PZ = ld(5, e);
+      const f2 QX = ld(6, e), QY = ld(7, e), QZ = ld(8, e);  // a_j (or A)
+      f2 c = f2_mul(U, PX);
+      c = f2_fma(V, PY, c);
+      c = f2_fma(W, PZ, c);
+      f2 sa = f2_mul(AX, PX);  // a_i . p_j
+      sa = f2_fma(AY, PY, sa);
+      sa = f2_fma(AZ, PZ, sa);
+      sa = f2_fma(QX, U, sa);  // + a_j . p_i
+      sa = f2_fma(QY, V, sa);
+      sa = f2_fma(QZ, W, sa);
+      const f2 gs = f2_mul(g, sa);
+      a1x = f2_fma(gs, dx, a1x);
+      a1y = f2_fma(gs, dy, a1y);
+      a1z = f2_fma(gs, dz, a1z);
+      const f2 wx = f2_sub(BX, ld(9, e)), wy = f2_sub(BY, ld(10, e)), wz = f2_sub(BZ, ld(11, e));
+      f2 wd = f2_mul(wx, dx);
+      wd = f2_fma(wy, dy, wd);
+      wd = f2_fma(wz, dz, wd);
+      const f2 cg = f2_mul(c, g);
+      a2x = f2_fma(cg, wx, a2x);
+      a2y = f2_fma(cg, wy, a2y);
+      a2z = f2_fma(cg, wz, a2z);
+      const f2 cw = f2_mul(cg, wd);
+      a3x = f2_fma(cw, dx, a3x);
+      a3y = f2_fma(cw, dy, a3y);
+      a3z = f2_fma(cw, dz, a3z);
+      b1x = f2_fma(g, QX, b1x);
+      b1y = f2_fma(g, QY, b1y);
+      b1z = f2_fma(g, QZ, b1z);
+      const f2 gw = f2_mul(g, wd);
+      b2x = f2_fma(gw, PX, b2x);
+      b2y = f2_fma(gw, PY, b2y);
+      b2z = f2_fma(gw, PZ, b2z);
     }
-    __syncwarp();
-    auto ld = [&](int c, int e) { return *reinterpret_cast<const f2*>(&s_soa[w][c][e]); };
-    if constexpr (!ADJ) {
-      f2 fx = 0, fy = 0, fz = 0, hx = 0, hy = 0, hz = 0;
-      for (int e = 0; e < cnt; e += 2) {
-        const bool b0 = (s_mask[w][e] >> lane) & 1u, b1 = (s_mask[w][e + 1] >> lane) & 1u;
-        const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
-        f2 r = f2_mul(dx, dx);
-        r = f2_fma(dy, dy, r);
-        r = f2_fma(dz, dz, r);
-        float r0, r1;
-        f2_split(r, r0, r1);
-        const f2 g = f2_make(b0 ? ex2_neg(r0) : 0.f, b1 ? ex2_neg(r1) : 0.f);
-        const f2 PX = ld(3, e), PY = ld(4, e), PZ = ld(5, e);
-        fx = f2_fma(g, PX, fx);
-        fy = f2_fma(g, PY, fy);
-        fz = f2_fma(g, PZ, fz);
-        f2 c = f2_mul(U, PX);
-        c = f2_fma(V, PY, c);
-        c = f2_fma(W, PZ, c);
-        const f2 cg = f2_mul(c, g);
-        hx = f2_fma(cg, dx, hx);
-        hy = f2_fma(cg, dy, hy);
-        hz = f2_fma(cg, dz, hz);
-      }
-      K[0].add(f2_sum(fx));
-      K[1].add(f2_sum(fy));
-      K[2].add(f2_sum(fz));
-      K[3].add(f2_sum(hx));
-      K[4].add(f2_sum(hy));
-      K[5].add(f2_sum(hz));
-    } else {
-      f2 a1x = 0, a1y = 0, a1z = 0, a2x = 0, a2y = 0, a2z = 0, a3x = 0, a3y = 0, a3z = 0;
-      f2 b1x = 0, b1y = 0, b1z = 0, b2x = 0, b2y = 0, b2z = 0;
-      for (int e = 0; e < cnt; e += 2) {
-        const bool b0 = (s_mask[w][e] >> lane) & 1u, b1 = (s_mask[w][e + 1] >> lane) & 1u;
-        const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
-        f2 r = f2_mul(dx, dx);
-        r = f2_fma(dy, dy, r);
-        r = f2_fma(dz, dz, r);
-        float r0, r1;
-        f2_split(r, r0, r1);
-        const f2 g = f2_make(b0 ? ex2_neg(r0) : 0.f, b1 ? ex2_neg(r1) : 0.f);
-        const f2 PX = ld(3, e), PY = ld(4, e), PZ = ld(5, e);
-        const f2 QX = ld(6, e), QY = ld(7, e), QZ = ld(8, e);  // a_j (or A)
-        f2 c = f2_mul(U, PX);
-        c = f2_fma(V, PY, c);
-        c = f2_fma(W, PZ, c);
-        f2 sa = f2_mul(AX, PX);  // a_i . p_j
-        sa = f2_fma(AY, PY, sa);
-        sa = f2_fma(AZ, PZ, sa);
-        sa = f2_fma(QX, U, sa);  // + a_j . p_i
-        sa = f2_fma(QY, V, sa);
-        sa = f2_fma(QZ, W, sa);
-        const f2 gs = f2_mul(g, sa);
-        a1x = f2_fma(gs, dx, a1x);
-        a1y = f2_fma(gs, dy, a1y);
-        a1z = f2_fma(gs, dz, a1z);
-        const f2 wx = f2_sub(BX, ld(9, e)), wy = f2_sub(BY, ld(10, e)),
-                 wz = f2_sub(BZ, ld(11, e));
-        f2 wd = f2_mul(wx, dx);
-        wd = f2_fma(wy, dy, wd);
-        wd = f2_fma(wz, dz, wd);
-        const f2 cg = f2_mul(c, g);
-        a2x = f2_fma(cg, wx, a2x);
-        a2y = f2_fma(cg, wy, a2y);
-        a2z = f2_fma(cg, wz, a2z);
-        const f2 cw = f2_mul(cg, wd);
-        a3x = f2_fma(cw, dx, a3x);
-        a3y = f2_fma(cw, dy, a3y);
-        a3z = f2_fma(cw, dz, a3z);
-        b1x = f2_fma(g, QX, b1x);
-        b1y = f2_fma(g, QY, b1y);
-        b1z = f2_fma(g, QZ, b1z);
-        const f2 gw = f2_mul(g, wd);
-        b2x = f2_fma(gw, PX, b2x);
-        b2y = f2_fma(gw, PY, b2y);
-        b2z = f2_fma(gw, PZ, b2z);
-      }
-      K[0].add(f2_sum(a1x));
-      K[1].add(f2_sum(a1y));
-      K[2].add(f2_sum(a1z));
-      K[3].add(f2_sum(a2x));
-      K[4].add(f2_sum(a2y));
-      K[5].add(f2_sum(a2z));
-      K[6].add(f2_sum(a3x));
-      K[7].add(f2_sum(a3y));
-      K[8].add(f2_sum(a3z));
-      K[9].add(f2_sum(b1x));
-      K[10].add(f2_sum(b1y));
-      K[11].add(f2_sum(b1z));
-      K[12].add(f2_sum(b2x));
-      K[13].add(f2_sum(b2y));
-      K[14].add(f2_sum(b2z));
-    }
-    __syncwarp();
-    cnt = 0;
-  };
+    A.K[0].add(f2_sum(a1x));
+    A.K[1].add(f2_sum(a1y));
+    A.K[2].add(f2_sum(a1z));
+    A.K[3].add(f2_sum(a2x));
+    A.K[4].add(f2_sum(a2y));
+    A.K[5].add(f2_sum(a2z));
+    A.K[6].add(f2_sum(a3x));
+    A.K[7].add(f2_sum(a3y));
+    A.K[8].add(f2_sum(a3z));
+    A.K[9].add(f2_sum(b1x));
+    A.K[10].add(f2_sum(b1y));
+    A.K[11].add(f2_sum(b1z));
+    A.K[12].add(f2_sum(b2x));
+    A.K[13].add(f2_sum(b2y));
+    A.K[14].add(f2_sum(b2z));
+  }
+}
 
-  while (x < M) {
-    if (x >= base + 32) {  // stage the next 32 node boxes
+// Stages the records of queued nodes[0, n) into soa (padding n to even).
+template <bool ADJ>
+__device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nodes,
+                                             unsigned* mask, float* soa, int n, int lane) {
+  for (int e = lane; e < n; e += 32) {
+    const int nd = nodes[e];
+    const float4 r0 = t.nrec[4 * nd], r1 = t.nrec[4 * nd + 1];
+    soa[0 * TR_CAP + e] = r0.x, soa[1 * TR_CAP + e] = r0.y, soa[2 * TR_CAP + e] = r0.z;
+    soa[3 * TR_CAP + e] = r1.x, soa[4 * TR_CAP + e] = r1.y, soa[5 * TR_CAP + e] = r1.z;
+    if constexpr (ADJ) {
+      const float4 r2 = t.nrec[4 * nd + 2], r3 = t.nrec[4 * nd + 3];
+      soa[6 * TR_CAP + e] = r2.x, soa[7 * TR_CAP + e] = r2.y, soa[8 * TR_CAP + e] = r2.z;
+      soa[9 * TR_CAP + e] = r3.x, soa[10 * TR_CAP + e] = r3.y, soa[11 * TR_CAP + e] = r3.z;
+    }
+  }
+  if (n & 1) {
+    if (lane == 0) mask[n] = 0u;
+    if (lane < (ADJ ? 12 : 6)) soa[lane * TR_CAP + n] = 0.f;
+    n++;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------------ walk
+// Walks nodes [x, end) for one group.  At each node the lanes still active
+// (no summarised ancestor) take their decision; `sink` receives runs of
+// entries (first node, count, lane mask): a summarised node, a run of
+// consecutive leaves, or -- when an opened node's children are all leaves --
+// those children at once.  sink.fits(n) false stops the walk before node x
+// (x and resume are then the state to resume from).  Returns false if stopped.
+template <bool COUNT, class Sink>
+__device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
+                                           int end, const float4& rr, float thr, int& resume,
+                                           Sink& sink, int lane, long long& np, long long& nn) {
+  int base = INT_MIN / 2;
+  // window bit masks (bit j = node base + j): leaf, "all children leaves"
+  unsigned leafmask = 0u, botmask = 0u;
+  while (x < end) {
+    int off = x - base;
+    if ((unsigned)off >= 32u) {  // stage the next 32 node boxes
       __syncwarp();
       base = x;
+      off = 0;
       const int j = base + lane;
-      bool lf = false;
-      if (j < M) {
+      bool lf = false, bt = false;
+      if (j < end) {
         const float4 lo = t.nbox[2 * j], hi = t.nbox[2 * j + 1];
-        s_box[w][lane][0] = lo;
-        s_box[w][lane][1] = hi;
-        lf = __float_as_int(lo.w) == j + 1;
+        sbox[lane][0] = lo;
+        sbox[lane][1] = hi;
+        const int sk = __float_as_int(lo.w), cn = __float_as_int(hi.w);
+        lf = sk == j + 1;
+        // children all leaves, at most 32 of them, subtree inside the range
+        bt = !lf && sk - j == cn + 1 && cn <= 32 && sk <= end;
       }
       leafmask = __ballot_sync(FULL, lf);
+      botmask = __ballot_sync(FULL, bt);
       __syncwarp();
     }
-    const int off = x - base;
     if ((leafmask >> off) & 1u) {
-      // a run of consecutive leaves: every lane active at x stays active
-      // until the first resume point inside the run
+      // a run of consecutive leaves; lanes change activity only at their
+      // resume points, so the run is cut at the first one inside it
       const unsigned rest = ~(leafmask >> off);
       int r = rest ? __ffs(rest) - 1 : 32 - off;
-      const int lim = resume > x ? resume : INT_MAX;
-      const int rmin = __reduce_min_sync(FULL, lim);
-      if (rmin - x < r) r = rmin - x;
+      const int rmin = __reduce_min_sync(FULL, resume > x ? resume : INT_MAX);
+      r = min(r, rmin - x);
       const unsigned mk = __ballot_sync(FULL, resume <= x);
       if (mk) {
-        if (lane < r) {
-          s_node[w][cnt + lane] = x + lane;
-          s_mask[w][cnt + lane] = mk;
-        }
-        np += (long long)__popc(mk) * r;
-        cnt += r;
-        if (cnt >= TR_BUF) flush();
+        if (!sink.fits(r)) return false;
+        sink.add(x, r, mk);
+        if (COUNT) np += (long long)__popc(mk) * r;
       }
       x += r;
       continue;
     }
-    // internal node: each active lane decides far (summarise) or open
-    const float4 bl = s_box[w][off][0], bh = s_box[w][off][1];
+    const float4 bl = sbox[off][0], bh = sbox[off][1];
     const int skip = __float_as_int(bl.w);
     const bool active = x >= resume;
     const bool far = active && box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr;
-    if (far) resume = skip;
     const unsigned mt = __ballot_sync(FULL, far), mo = __ballot_sync(FULL, active && !far);
-    if (mt) {
-      if (lane == 0) {
-        s_node[w][cnt] = x;
-        s_mask[w][cnt] = mt;
-      }
-      nn += __popc(mt);
-      if (++cnt >= TR_BUF) flush();
+    // an opened node whose children are all leaves: take them at once
+    const bool bottom = mo && ((botmask >> off) & 1u);
+    if (mt | (bottom ? 1u : 0u)) {
+      const int cn = bottom ? __float_as_int(bh.w) : 0;
+      // stop before x (state unchanged) when the sink is full
+      if (!sink.fits((mt ? 1 : 0) + cn)) return false;
+      if (mt) sink.add(x, 1, mt);
+      if (bottom) sink.add(x + 1, cn, mo);
+      if (COUNT) nn += __popc(mt), np += (long long)__popc(mo) * cn;
     }
-    x = mo ? x + 1 : skip;
+    if (far) resume = skip;
+    x = (mo && !bottom) ? x + 1 : skip;
   }
-  if (cnt) flush();
+  return true;
+}
 
-  if (counts && lane == 0) {
+// Sink of the list walk: entries buffered in shared memory, written to the
+// list 32 at a time.
+struct ListSink {
+  int2* out;     // list storage
+  int2* buf;     // TR_CAP entries in shared memory
+  int room;      // entries the list can still take
+  int written, cnt, lane;
+  __device__ __forceinline__ bool fits(int n) const { return cnt + n <= room; }
+  __device__ __forceinline__ void add(int node0, int n, unsigned mask) {
+    if (lane < n) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
+    cnt += n;
+    if (cnt >= TR_BUF) {
+      __syncwarp();
+      out[written + lane] = buf[lane];
+      __syncwarp();
+      if (lane < cnt - 32) buf[lane] = buf[32 + lane];
+      __syncwarp();
+      written += 32;
+      room -= 32;
+      cnt -= 32;
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    __syncwarp();
+    if (lane < cnt) out[written + lane] = buf[lane];
+    written += cnt;
+    cnt = 0;
+  }
+};
+
+// One warp per (group, slice): emits the ordered interaction list.
+template <bool COUNT>
+__global__ void __launch_bounds__(TR_WARPS * 32)
+    k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
+              int64_t* counts) {
+  __shared__ float4 s_box[TR_WARPS][32][2];
+  __shared__ int2 s_ent[TR_WARPS][TR_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * TR_WARPS + w;
+  const int G = (N + 31) / 32;
+  if (l >= G * BH_SLICES) return;
+  const int g = l / BH_SLICES, k = l % BH_SLICES;
+  const int i = g * 32 + lane;
+  const bool valid = i < N;
+  const float4 rr = raw[(int)t.perm[valid ? i : N - 1]];
+  int x = slice_start(t, L, N, g, k);
+  const int end = slice_end(t, L, N, g, k);
+  int resume = valid ? 0 : INT_MAX;
+  if (k > 0 && valid) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
+  ListSink sink{L.ent + (size_t)l * L.cap, s_ent[w], L.cap, 0, 0, lane};
+  long long np = 0, nn = 0;
+  const bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
+  sink.finish();
+  if (lane == 0) {
+    L.len[l] = sink.written;
+    L.ovf_x[l] = done ? -1 : x;
+  }
+  if (!done) L.ovf_res[(size_t)l * 32 + lane] = resume;
+  if (COUNT && lane == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
   }
-  if (!valid) return;
+}
+
+// ------------------------------------------------------------------ evaluate
+// One warp per list: partial sums of its entries, part[(l*NC + c)*32 + lane].
+template <bool ADJ>
+__global__ void __launch_bounds__(TR_WARPS * 32)
+    k_bh_eval(TreeArrays t, int N, BHLists L) {
+  constexpr int NR = ADJ ? 12 : 6;
+  constexpr int NC = Acc<ADJ>::NC;
+  __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
+  __shared__ int s_node[TR_WARPS][TR_CAP];
+  __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * TR_WARPS + w;
+  const int G = (N + 31) / 32;
+  if (l >= G * BH_SLICES) return;
+  const Own me = load_own(t, N, l / BH_SLICES, lane, ADJ);
+  Acc<ADJ> A;
+  A.zero();
+  const int n = L.len[l];
+  const int2* src = L.ent + (size_t)l * L.cap;
+  for (int c0 = 0; c0 < n; c0 += TR_CAP) {
+    const int cn = min(TR_CAP, n - c0);
+    __syncwarp();
+    for (int e = lane; e < cn; e += 32) {
+      const int2 v = src[c0 + e];
+      s_node[w][e] = v.x;
+      s_mask[w][e] = (unsigned)v.y;
+    }
+    __syncwarp();
+    const int ce = stage_records<ADJ>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
+    __syncwarp();
+    eval_batch<ADJ>(A, s_soa[w], s_mask[w], ce, lane, me);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; c++) L.part[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
+}
+
+// ------------------------------------------------------------------ fallback
+// Sink that evaluates queued entries in place (batches of >= 32).
+template <bool ADJ>
+struct EvalSink {
+  const TreeArrays* t;
+  int* node;
+  unsigned* mask;
+  float* soa;
+  Acc<ADJ>* A;
+  const Own* me;
+  int cnt, lane;
+  __device__ __forceinline__ bool fits(int) const { return true; }
+  __device__ __forceinline__ void flush() {
+    __syncwarp();
+    const int ce = stage_records<ADJ>(*t, node, mask, soa, cnt, lane);
+    __syncwarp();
+    eval_batch<ADJ>(*A, soa, mask, ce, lane, *me);
+    __syncwarp();
+    cnt = 0;
+  }
+  __device__ __forceinline__ void add(int node0, int n, unsigned mk) {
+    if (lane < n) {
+      node[cnt + lane] = node0 + lane;
+      mask[cnt + lane] = mk;
+    }
+    cnt += n;
+    if (cnt >= TR_BUF) flush();
+  }
+};
+
+// Resumes an overflowed slice from its saved state, walking and evaluating
+// in one pass; partial sums go to L.fb[(l*NC + c)*32 + lane].
+template <bool ADJ, bool COUNT>
+__global__ void __launch_bounds__(TR_WARPS * 32)
+    k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
+                  int64_t* counts) {
+  constexpr int NR = ADJ ? 12 : 6;
+  constexpr int NC = Acc<ADJ>::NC;
+  __shared__ float4 s_box[TR_WARPS][32][2];
+  __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
+  __shared__ int s_node[TR_WARPS][TR_CAP];
+  __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l = blockIdx.x * TR_WARPS + w;
+  const int G = (N + 31) / 32;
+  if (l >= G * BH_SLICES) return;
+  int x = L.ovf_x[l];
+  if (x < 0) return;
+  const int g = l / BH_SLICES, k = l % BH_SLICES;
+  const Own me = load_own(t, N, g, lane, ADJ);
+  const float4 rr = raw[me.o];
+  const int end = slice_end(t, L, N, g, k);
+  int resume = L.ovf_res[(size_t)l * 32 + lane];
+  Acc<ADJ> A;
+  A.zero();
+  EvalSink<ADJ> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane};
+  long long np = 0, nn = 0;
+  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
+  if (sink.cnt) sink.flush();
+#pragma unroll
+  for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
+  if (COUNT && lane == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
+  }
+}
+
+// ------------------------------------------------------------------ combine
+// Per point: the slices' partial sums (and resumed parts) in a fixed order,
+// then the epilogue.
+template <bool ADJ>
+__global__ void k_bh_combine(TreeArrays t, int N, BHLists L, FwdEpi fe, AdjEpi ae) {
+  constexpr int NC = Acc<ADJ>::NC;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int g = i >> 5, lane = i & 31;
   double acc[NC];
 #pragma unroll
-  for (int c = 0; c < NC; c++) {
-    const float2 v = K[c].out();
-    acc[c] = (double)v.x + (double)v.y;
+  for (int c = 0; c < NC; c++) acc[c] = 0.0;
+  for (int k = 0; k < BH_SLICES; k++) {
+    const int l = g * BH_SLICES + k;
+    const bool ov = L.ovf_x[l] >= 0;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      const float2 v = L.part[((size_t)l * NC + c) * 32 + lane];
+      acc[c] += (double)v.x + (double)v.y;
+      if (ov) {
+        const float2 u = L.fb[((size_t)l * NC + c) * 32 + lane];
+        acc[c] += (double)u.x + (double)u.y;
+      }
+    }
   }
+  const int o = (int)t.perm[i];
   if constexpr (!ADJ) fwd_epilogue(o, acc, acc + 3, fe);
   else adj_epilogue(o, acc, acc + 3, acc + 6, acc + 9, acc + 12, ae);
 }
 
-inline unsigned tr_blocks(int N) {
-  const int warps = (N + 31) / 32;
-  return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS);
+inline unsigned list_blocks(int N) {
+  const int lists = (N + 31) / 32 * BH_SLICES;
+  return (unsigned)((lists + TR_WARPS - 1) / TR_WARPS);
 }
 
 }  // namespace
 
-cudaError_t launch_bh_traverse_fwd(const TreeArrays& t, int N, const float4* raw, float thr,
-                                   const FwdEpi& e, int64_t* counts, cudaStream_t st) {
-  k_bh_traverse<false><<<tr_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, e, AdjEpi{},
-                                                               counts);
+cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
+                           const BHLists& L, int64_t* counts, cudaStream_t st) {
+  if (counts) k_bh_walk<true><<<list_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
+  else k_bh_walk<false><<<list_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bh_traverse_adj(const TreeArrays& t, int N, const float4* raw, float thr,
-                                   const AdjEpi& e, int64_t* counts, cudaStream_t st) {
-  k_bh_traverse<true><<<tr_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, FwdEpi{}, e,
-                                                              counts);
-  note_launches(1);
+template <bool ADJ>
+static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr,
+                        const BHLists& L, const FwdEpi& fe, const AdjEpi& ae, int64_t* counts,
+                        cudaStream_t st) {
+  const unsigned nb = list_blocks(N);
+  const unsigned nc = (unsigned)((N + 255) / 256);
+  if (counts) k_bh_fallback<ADJ, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
+  else k_bh_fallback<ADJ, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
+  k_bh_eval<ADJ><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L);
+  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, fe, ae);
+}
+
+cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
+                           const BHLists& L, bool adj, const FwdEpi& fe, const AdjEpi& ae,
+                           int64_t* counts, cudaStream_t st) {
+  if (!adj) eval_launch<false>(t, N, raw, thr, L, fe, ae, counts, st);
+  else eval_launch<true>(t, N, raw, thr, L, fe, ae, counts, st);
+  note_launches(3);
   return cudaGetLastError();
 }
 

@@ -552,12 +552,55 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
 }  // namespace
 
 // ---------------------------------------------------------------- host API
+namespace {
+constexpr int kListCap = 8192;                 // entries per list (slice)
+constexpr size_t kListBudget = size_t(4) << 30; // bytes of list storage at most
+
+size_t lists_bytes(int64_t n, int cap) {
+  const size_t nl = (size_t)((n + 31) / 32) * BH_SLICES;
+  return align_up(nl * cap * sizeof(int2)) + 3 * align_up(nl * 4) + align_up(nl * 32 * 4) +
+         2 * align_up(nl * 15 * 32 * sizeof(float2));
+}
+
+BHLists carve_lists(void* mem, int64_t n, int cap) {
+  const size_t nl = (size_t)((n + 31) / 32) * BH_SLICES;
+  char* b = static_cast<char*>(mem);
+  BHLists L;
+  size_t o = 0;
+  L.ent = (int2*)(b + o);
+  o += align_up(nl * cap * sizeof(int2));
+  L.len = (int*)(b + o);
+  o += align_up(nl * 4);
+  L.ovf_x = (int*)(b + o);
+  o += align_up(nl * 4);
+  L.ovf_res = (int*)(b + o);
+  o += align_up(nl * 32 * 4);
+  o += align_up(nl * 4);
+  L.part = (float2*)(b + o);
+  o += align_up(nl * 15 * 32 * sizeof(float2));
+  L.fb = (float2*)(b + o);
+  L.cap = cap;
+  return L;
+}
+}  // namespace
+
 cudaError_t tree_setup() { return cudaSuccess; }
+
+// Entries per interaction list: the requested value, else kListCap reduced
+// to keep all lists within kListBudget.
+static int list_cap(const TreeWork& w, int64_t N) {
+  if (w.lcap_req > 0) return w.lcap_req;
+  const size_t nl = (size_t)((N + 31) / 32) * BH_SLICES;
+  int cap = kListCap;
+  while (cap > 1024 && nl * (size_t)cap * sizeof(int2) > kListBudget) cap /= 2;
+  return cap;
+}
 
 gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st) {
   (void)st;
   if (N > (int64_t(1) << 30)) return GS_ERR_INVALID_ARG;
-  if (w.mem && w.cap_n >= N) return GS_OK;
+  if (w.mem && w.cap_n >= N && list_cap(w, w.cap_n) == w.lcap) return GS_OK;
+  N = std::max<int64_t>(N, w.cap_n);
   if (w.mem) cudaFree(w.mem);
   w.mem = nullptr;
   size_t bytes = 0;
@@ -573,12 +616,28 @@ gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st) {
   w.adjoint = adjoint;
   size_t b2;
   w.d_counts = carve(w.mem, N, &b2).counts;
+  // list capacity: kListCap entries per slice within the storage budget
+  const int cap = list_cap(w, N);
+  if (w.lmem) cudaFree(w.lmem);
+  w.lmem = nullptr;
+  w.lbytes = lists_bytes(N, cap);
+  if (cudaMalloc(&w.lmem, w.lbytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(w.mem);
+    w.mem = nullptr;
+    w.lmem = nullptr;
+    w.cap_n = 0;
+    return GS_ERR_OOM;
+  }
+  w.lcap = cap;
   return GS_OK;
 }
 
 void tree_release(TreeWork& w) {
   if (w.mem) cudaFree(w.mem);
+  if (w.lmem) cudaFree(w.lmem);
   w.mem = nullptr;
+  w.lmem = nullptr;
   w.cap_n = 0;
 }
 
@@ -601,21 +660,32 @@ gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero
   return GS_OK;
 }
 
-gs_status bh_traverse_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
-                          cudaStream_t st) {
+gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st) {
   size_t bytes;
   TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  cudaError_t err = launch_bh_traverse_fwd(t, (int)b.N, b.raw, b.thr, e,
-                                           counts ? t.counts : nullptr, st);
+  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
+  cudaError_t err =
+      launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
-gs_status bh_traverse_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
-                          cudaStream_t st) {
+gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
+                      cudaStream_t st) {
   size_t bytes;
   TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  cudaError_t err = launch_bh_traverse_adj(t, (int)b.N, b.raw, b.thr, e,
-                                           counts ? t.counts : nullptr, st);
+  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, false, e, AdjEpi{},
+                                   counts ? t.counts : nullptr, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
+gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
+                      cudaStream_t st) {
+  size_t bytes;
+  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, true, FwdEpi{}, e,
+                                   counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 

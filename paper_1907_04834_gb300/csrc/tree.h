@@ -15,6 +15,10 @@ struct TreeWork {
   int64_t cap_n = 0;    // points it was sized for
   bool adjoint = false;
   int64_t* d_counts = nullptr;  // interaction counters {point, node}
+  void* lmem = nullptr;         // interaction lists (tree_impl.h BHLists)
+  size_t lbytes = 0;
+  int lcap = 0;                 // entries per list
+  int lcap_req = 0;             // requested entries per list (0 = default)
 };
 
 // Inputs of one tree step: pack = scaled recentred FP32 positions and
@@ -33,11 +37,14 @@ void tree_release(TreeWork& w);
 // Builds the tree of one state (abpack = NULL in the forward stage).
 gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
                    cudaStream_t st);
-// Traverses the tree built last; counts != NULL accumulates interactions.
-gs_status bh_traverse_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
-                          cudaStream_t st);
-gs_status bh_traverse_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
-                          cudaStream_t st);
+// Walks the tree built last and records the interaction lists.
+gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st);
+// Evaluates the recorded lists (forward or backward stage) and applies the
+// epilogue.
+gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
+                      cudaStream_t st);
+gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
+                      cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
 // Builds the tree on one state and exports it (see gs_tree in gs.h).
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,

@@ -48,6 +48,18 @@ struct TreeArrays {
   int64_t* counts;  // {point interactions, node interactions}
 };
 
+// Interaction lists of one traversal: BH_SLICES per group of 32 points.
+constexpr int BH_SLICES = 4;
+struct BHLists {
+  int2* ent;     // lists x cap entries {node, lane mask}
+  int* len;      // entries recorded per list
+  int* ovf_x;    // per list: node where recording stopped (-1 = complete)
+  int* ovf_res;  // per list x 32: lane resume points at ovf_x
+  float2* part;  // per list x 15 x 32: partial sums of the recorded entries
+  float2* fb;    // per list x 15 x 32: partial sums of the resumed remainder
+  int cap;       // entries per list
+};
+
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
   return N + (int)t.offs[N];
 }
@@ -63,9 +75,11 @@ __device__ __forceinline__ float box_dist2(float x, float y, float z, const floa
 }
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions
-cudaError_t launch_bh_traverse_fwd(const TreeArrays& t, int N, const float4* raw, float thr,
-                                   const FwdEpi& e, int64_t* counts, cudaStream_t st);
-cudaError_t launch_bh_traverse_adj(const TreeArrays& t, int N, const float4* raw, float thr,
-                                   const AdjEpi& e, int64_t* counts, cudaStream_t st);
+cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
+                           const BHLists& L, int64_t* counts, cudaStream_t st);
+// fallback for overflowed lists, evaluation, fixed-order combine + epilogue
+cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
+                           const BHLists& L, bool adj, const FwdEpi& fe, const AdjEpi& ae,
+                           int64_t* counts, cudaStream_t st);
 
 }  // namespace gs
