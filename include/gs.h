@@ -163,10 +163,12 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
 /* ---- diagnostics ---------------------------------------------------------- */
 
 /* Tuning options of a context:
- *   "bh_list_cap": entries recorded per interaction list of the Barnes-Hut
- *   walk (two lists per 32 points); 0 = default (8192, reduced to keep the
- *   lists within 4 GB).  A list that outgrows it is finished by a slower
- *   fused walk-and-evaluate pass; results are the same either way. */
+ *   "bh_list_cap": interaction-list storage of the Barnes-Hut walk, in
+ *   entries per list on average (four lists per 32 points, one pool per
+ *   kept step); 0 = default (a budget of up to 24 GB, at most a quarter of
+ *   the free memory, shared by the kept steps).  Slices whose lists do not
+ *   fit are evaluated by a slower fused walk-and-evaluate pass that gives
+ *   bit-identical results. */
 gs_status gs_set_option(gs_ctx *ctx, const char *name, int64_t value);
 
 /* Kernel classes timed by gs_timing. */

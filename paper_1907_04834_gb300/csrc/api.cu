@@ -267,8 +267,9 @@ int choose_J(int n_itiles, int n_jtiles, int slots) {
   return std::max(1, std::min(best, n_jtiles));
 }
 
+// slots: pack slots; tree_slots: Barnes-Hut tree/list slots kept at once.
 gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int slots,
-                      bool adjoint, cudaStream_t st) {
+                      bool adjoint, cudaStream_t st, int tree_slots = 1) {
   S.c = c;
   S.st = st;
   S.N = N;
@@ -326,7 +327,7 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     }
     CK(cudaMemsetAsync(c->tickets.p, 0, tn * sizeof(unsigned), st), "memset");
   } else {
-    gs_status s = tree_reserve(c->tree, N, adjoint, st);
+    gs_status s = tree_reserve(c->tree, N, tree_slots, st);
     if (s != GS_OK) return fail(c, s, "Barnes-Hut workspace allocation failed");
   }
   return GS_OK;
@@ -360,8 +361,9 @@ FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
   return e;
 }
 
-// One forward right-hand side on pack slot `slot` with epilogue `e`.
-gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
+// One forward right-hand side on pack slot `slot` with epilogue `e`
+// (Barnes-Hut: tree and interaction lists built in tree slot `tslot`).
+gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int tslot = 0) {
   gs_ctx* c = S.c;
   if (S.mode == GS_EXACT) {
     KTimer tm(c, GS_K_EXACT_FWD, S.st);
@@ -374,7 +376,7 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts) {
     }
     return GS_OK;
   }
-  BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
   gs_status s;
   {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -406,7 +408,11 @@ AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) 
   return e;
 }
 
-gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts) {
+// One adjoint right-hand side.  Barnes-Hut: with reuse, tree slot `tslot`
+// holds the forward stage's tree and lists for this same state; only the
+// sums of alpha and beta are recomputed.  Without, everything is rebuilt.
+gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts,
+                      int tslot = 0, bool reuse = false) {
   gs_ctx* c = S.c;
   if (S.mode == GS_EXACT) {
     KTimer tm(c, GS_K_EXACT_ADJ, S.st);
@@ -419,15 +425,20 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     }
     return GS_OK;
   }
-  BHStep b{S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
   gs_status s;
-  {
+  if (reuse) {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
-    s = bh_build(c->tree, b, S.abpack(ab), counts != nullptr, S.st);
-  }
-  if (s == GS_OK) {
-    KTimer tm(c, GS_K_BH_WALK, S.st);
-    s = bh_walk(c->tree, b, counts != nullptr, S.st);
+    s = bh_aggregate(c->tree, b, S.abpack(ab), counts != nullptr, S.st);
+  } else {
+    {
+      KTimer tm(c, GS_K_TREE_BUILD, S.st);
+      s = bh_build(c->tree, b, S.abpack(ab), counts != nullptr, S.st);
+    }
+    if (s == GS_OK) {
+      KTimer tm(c, GS_K_BH_WALK, S.st);
+      s = bh_walk(c->tree, b, counts != nullptr, S.st);
+    }
   }
   if (s == GS_OK) {
     KTimer tm(c, GS_K_BH_ADJ, S.st);
@@ -613,7 +624,10 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
   // pack slots: every step (store-all) or one segment (checkpointing)
   const int slots = ck ? ck + 1 : T + 1;
   Solver S;
-  if ((s = solver_init(c, S, N, prm, slots, true, st))) return s;
+  // Barnes-Hut: one tree slot per step kept for the backward stage (a
+  // segment's steps with checkpointing)
+  const int tslots = prm->mode == GS_BH ? (ck ? ck : T) : 1;
+  if ((s = solver_init(c, S, N, prm, slots, true, st, tslots))) return s;
   const size_t n3 = (size_t)N * 3, b3 = n3 * sizeof(double);
   const int nck = ck ? (T + ck - 1) / ck : 0;
   if (ck) CK(c->ckpt.ensure((size_t)nck * 2 * b3), "checkpoint allocation");
@@ -636,7 +650,7 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
       e.F_out = c->F0.as<double>();
       e.pf_part = c->pf.as<double>();
     }
-    if ((s = forward_rhs(S, in, e, nullptr))) return s;
+    if ((s = forward_rhs(S, in, e, nullptr, ck ? 0 : k))) return s;
   }
   CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
   CK(cudaMemcpyAsync(c->out_b.p, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "q1 copy");
@@ -650,7 +664,7 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
   int ab = 0;
   auto back_step = [&](int k, int slot) -> gs_status {
     AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, gradbuf.as<double>());
-    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr);
+    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr, slot, true);
     ab ^= 1;
     return r;
   };
@@ -666,9 +680,13 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
       CK(launch_pack(c->q.as<double>(), c->p.as<double>(), N, S.scal(SC_CENTER), S.s, S.pack(0),
                      S.mode == GS_BH ? S.raw(0) : nullptr, st),
          "pack");
-      for (int k = k0; k < k1 - 1; k++) {
-        FwdEpi e = fwd_epi(S, k - k0 + 1, S.h);
-        if ((s = forward_rhs(S, k - k0, e, nullptr))) return s;
+      for (int k = k0; k < k1; k++) {
+        // the last step of the segment only builds its tree and lists
+        // (its state update is not needed): the adjoint reuses them
+        if (S.mode == GS_BH || k < k1 - 1) {
+          FwdEpi e = fwd_epi(S, k < k1 - 1 ? k - k0 + 1 : -1, k < k1 - 1 ? S.h : 0.0);
+          if ((s = forward_rhs(S, k - k0, e, nullptr, k - k0))) return s;
+        }
       }
       for (int k = k1 - 1; k >= k0; k--)
         if ((s = back_step(k, k - k0))) return s;

@@ -25,9 +25,10 @@
 //               records in shared memory and evaluates two sources per f32x2
 //               instruction (a far node acts as one source at its centroid
 //               with momentum P, derivative A and momentum derivative B/n).
-// A slice whose list outgrows its capacity saves its walk state; a fused
-// walk+evaluate kernel resumes it from there.  Partial sums are combined in
-// a fixed order, so results are deterministic.
+// A slice whose list outgrows its capacity is walked again by a fused
+// walk+evaluate kernel that batches entries exactly as the list evaluation
+// does, so results do not depend on the capacity.  Partial sums are combined
+// in a fixed order: results are deterministic.
 #include <climits>
 
 #include "kernels.h"
@@ -40,7 +41,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TR_WARPS = 4;
 constexpr int TR_BUF = 32;
-constexpr int TR_CAP = 64;
+constexpr int TR_CAP = BH_CHUNK;  // staging capacity (one chunk)
 
 // Per-lane own data (record of the lane's point).
 struct Own {
@@ -316,32 +317,57 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
   return true;
 }
 
-// Sink of the list walk: entries buffered in shared memory, written to the
-// list 32 at a time.
+// Sink of the list walk: entries buffered in shared memory and written to
+// the list BH_CHUNK at a time in chunks taken from the pool.  When the pool
+// is exhausted the list is abandoned (the slice is re-walked later).
+constexpr int kReserve = 8;  // chunks reserved from the pool at a time
 struct ListSink {
-  int2* out;     // list storage
-  int2* buf;     // TR_CAP entries in shared memory
-  int room;      // entries the list can still take
-  int written, cnt, lane;
-  __device__ __forceinline__ bool fits(int n) const { return cnt + n <= room; }
+  const BHLists* L;
+  int2* buf;     // BH_CHUNK entries in shared memory
+  int head, tail, written, cnt, lane;
+  bool ovf;
+  int res_next, res_end;  // chunks reserved by this warp, not yet used
+  __device__ __forceinline__ bool fits(int) const { return !ovf; }
+  __device__ __forceinline__ void put_chunk(int n) {
+    if (res_next == res_end) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(L->used, kReserve);
+      c = __shfl_sync(FULL, c, 0);
+      res_next = c;
+      res_end = c + kReserve;
+    }
+    const int c = res_next++;
+    if (c >= L->n_chunks) {
+      ovf = true;
+      return;
+    }
+    int2* dst = L->ent + (size_t)c * BH_CHUNK;
+    for (int e = lane; e < n; e += 32) dst[e] = buf[e];
+    if (lane == 0) {
+      if (tail < 0) head = c;
+      else L->next[tail] = c;
+    }
+    tail = c;
+    written += n;
+  }
   __device__ __forceinline__ void add(int node0, int n, unsigned mask) {
-    if (lane < n) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
-    cnt += n;
-    if (cnt >= TR_BUF) {
-      __syncwarp();
-      out[written + lane] = buf[lane];
-      __syncwarp();
-      if (lane < cnt - 32) buf[lane] = buf[32 + lane];
-      __syncwarp();
-      written += 32;
-      room -= 32;
-      cnt -= 32;
+    while (n > 0 && !ovf) {
+      const int take = min(n, BH_CHUNK - cnt);
+      if (lane < take) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
+      cnt += take;
+      node0 += take;
+      n -= take;
+      if (cnt == BH_CHUNK) {
+        __syncwarp();
+        put_chunk(BH_CHUNK);
+        __syncwarp();
+        cnt = 0;
+      }
     }
   }
   __device__ __forceinline__ void finish() {
     __syncwarp();
-    if (lane < cnt) out[written + lane] = buf[lane];
-    written += cnt;
+    if (cnt && !ovf) put_chunk(cnt);
     cnt = 0;
   }
 };
@@ -352,7 +378,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
               int64_t* counts) {
   __shared__ float4 s_box[TR_WARPS][32][2];
-  __shared__ int2 s_ent[TR_WARPS][TR_CAP];
+  __shared__ int2 s_ent[TR_WARPS][BH_CHUNK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * TR_WARPS + w;
   const int G = (N + 31) / 32;
@@ -365,16 +391,17 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int end = slice_end(t, L, N, g, k);
   int resume = valid ? 0 : INT_MAX;
   if (k > 0 && valid) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
-  ListSink sink{L.ent + (size_t)l * L.cap, s_ent[w], L.cap, 0, 0, lane};
+  ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  const bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
+  bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
   sink.finish();
+  done = done && !sink.ovf;
   if (lane == 0) {
+    L.head[l] = sink.head;
     L.len[l] = sink.written;
     L.ovf_x[l] = done ? -1 : x;
   }
-  if (!done) L.ovf_res[(size_t)l * 32 + lane] = resume;
-  if (COUNT && lane == 0) {
+  if (COUNT && done && lane == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
   }
@@ -394,19 +421,22 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int l = blockIdx.x * TR_WARPS + w;
   const int G = (N + 31) / 32;
   if (l >= G * BH_SLICES) return;
+  if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
   const Own me = load_own(t, N, l / BH_SLICES, lane, ADJ);
   Acc<ADJ> A;
   A.zero();
   const int n = L.len[l];
-  const int2* src = L.ent + (size_t)l * L.cap;
-  for (int c0 = 0; c0 < n; c0 += TR_CAP) {
-    const int cn = min(TR_CAP, n - c0);
+  int chunk = L.head[l];
+  for (int c0 = 0; c0 < n; c0 += BH_CHUNK) {
+    const int cn = min(BH_CHUNK, n - c0);
+    const int2* src = L.ent + (size_t)chunk * BH_CHUNK;
     __syncwarp();
     for (int e = lane; e < cn; e += 32) {
-      const int2 v = src[c0 + e];
+      const int2 v = src[e];
       s_node[w][e] = v.x;
       s_mask[w][e] = (unsigned)v.y;
     }
+    if (c0 + BH_CHUNK < n) chunk = L.next[chunk];
     __syncwarp();
     const int ce = stage_records<ADJ>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
     __syncwarp();
@@ -417,7 +447,9 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 }
 
 // ------------------------------------------------------------------ fallback
-// Sink that evaluates queued entries in place (batches of >= 32).
+// Sink that evaluates queued entries in place, in chunks of BH_CHUNK entries
+// aligned exactly like the list evaluation's chunks, so a slice gives the
+// same sums whichever path evaluates it.
 template <bool ADJ>
 struct EvalSink {
   const TreeArrays* t;
@@ -437,17 +469,22 @@ struct EvalSink {
     cnt = 0;
   }
   __device__ __forceinline__ void add(int node0, int n, unsigned mk) {
-    if (lane < n) {
-      node[cnt + lane] = node0 + lane;
-      mask[cnt + lane] = mk;
+    while (n > 0) {
+      const int take = min(n, BH_CHUNK - cnt);
+      if (lane < take) {
+        node[cnt + lane] = node0 + lane;
+        mask[cnt + lane] = mk;
+      }
+      cnt += take;
+      node0 += take;
+      n -= take;
+      if (cnt == BH_CHUNK) flush();
     }
-    cnt += n;
-    if (cnt >= TR_BUF) flush();
   }
 };
 
-// Resumes an overflowed slice from its saved state, walking and evaluating
-// in one pass; partial sums go to L.fb[(l*NC + c)*32 + lane].
+// Evaluates a slice whose list overflowed: walks it again from its start and
+// evaluates in place; partial sums go to L.fb[(l*NC + c)*32 + lane].
 template <bool ADJ, bool COUNT>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
@@ -462,13 +499,14 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int l = blockIdx.x * TR_WARPS + w;
   const int G = (N + 31) / 32;
   if (l >= G * BH_SLICES) return;
-  int x = L.ovf_x[l];
-  if (x < 0) return;
+  if (L.ovf_x[l] < 0) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
   const Own me = load_own(t, N, g, lane, ADJ);
   const float4 rr = raw[me.o];
+  int x = slice_start(t, L, N, g, k);
   const int end = slice_end(t, L, N, g, k);
-  int resume = L.ovf_res[(size_t)l * 32 + lane];
+  int resume = me.valid ? 0 : INT_MAX;
+  if (k > 0 && me.valid) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane};
@@ -497,15 +535,11 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, FwdEpi fe, AdjEpi a
   for (int c = 0; c < NC; c++) acc[c] = 0.0;
   for (int k = 0; k < BH_SLICES; k++) {
     const int l = g * BH_SLICES + k;
-    const bool ov = L.ovf_x[l] >= 0;
+    const float2* src = L.ovf_x[l] >= 0 ? L.fb : L.part;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      const float2 v = L.part[((size_t)l * NC + c) * 32 + lane];
+      const float2 v = src[((size_t)l * NC + c) * 32 + lane];
       acc[c] += (double)v.x + (double)v.y;
-      if (ov) {
-        const float2 u = L.fb[((size_t)l * NC + c) * 32 + lane];
-        acc[c] += (double)u.x + (double)u.y;
-      }
     }
   }
   const int o = (int)t.perm[i];

@@ -382,17 +382,22 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, int N,
 }
 
 // ---------------------------------------------------------------- aggregates
+// write_box = false: the boxes (and skips) of this tree are already stored;
+// only the sums and source records are recomputed (backward-stage reuse).
 __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
-                            const float4* __restrict__ pack, const float4* __restrict__ abpack) {
+                            const float4* __restrict__ pack, const float4* __restrict__ abpack,
+                            bool write_box) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const bool adj = abpack != nullptr;
   const int o = (int)t.perm[i];
   int x = i + (int)t.offs[i + 1];
   {
-    const float4 r = raw[o];
-    t.nbox[2 * x] = make_float4(r.x, r.y, r.z, __int_as_float(x + 1));
-    t.nbox[2 * x + 1] = make_float4(r.x, r.y, r.z, __int_as_float(1));
+    if (write_box) {
+      const float4 r = raw[o];
+      t.nbox[2 * x] = make_float4(r.x, r.y, r.z, __int_as_float(x + 1));
+      t.nbox[2 * x + 1] = make_float4(r.x, r.y, r.z, __int_as_float(1));
+    }
     float a[3], b[3];
     pack_read(pack, o, a, b);
     t.nrec[4 * x] = make_float4(a[0], a[1], a[2], 0.f);
@@ -418,13 +423,13 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     int c = par + 1;
     while (c < sc.x) {
       const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
+      const int cskip = __float_as_int(bl.w);
       lo[0] = fminf(lo[0], bl.x);
       lo[1] = fminf(lo[1], bl.y);
       lo[2] = fminf(lo[2], bl.z);
       hi[0] = fmaxf(hi[0], bh.x);
       hi[1] = fmaxf(hi[1], bh.y);
       hi[2] = fmaxf(hi[2], bh.z);
-      const int cskip = __float_as_int(bl.w);
       if (cskip == c + 1) {
         const float4 r0 = __ldcg(&t.nrec[4 * c]), r1 = __ldcg(&t.nrec[4 * c + 1]);
         S[0] += r0.x, S[1] += r0.y, S[2] += r0.z;
@@ -449,8 +454,10 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
       t.nrec[4 * par + 3] =
           make_float4((float)(S[9] / n), (float)(S[10] / n), (float)(S[11] / n), 0.f);
     }
-    t.nbox[2 * par] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
-    t.nbox[2 * par + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(sc.y));
+    if (write_box) {
+      t.nbox[2 * par] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
+      t.nbox[2 * par + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(sc.y));
+    }
     x = par;
     nx = sc.y;
   }
@@ -459,14 +466,12 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
 // ---------------------------------------------------------------- layout
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-struct Layout {
-  size_t off[32];
-  size_t total;
-};
+size_t n_lists(int64_t n) { return (size_t)((n + 31) / 32) * BH_SLICES; }
 
-// Carves one allocation for capacity n points (2n nodes).
-TreeArrays carve(void* mem, int64_t n, size_t* bytes_out) {
-  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2;
+// Shared scratch of one workspace (capacity n points, 2n + 2 nodes); with
+// mem == NULL only the size is computed.
+size_t carve_shared(void* mem, int64_t n, TreeArrays* t, BHLists* L) {
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(n);
   const size_t nb_rs = nblocks(n, RS_TILE), nb_bb = kMaxBBoxBlocks;
   const size_t hist_n = 256 * nb_rs + 1;
   const size_t bsum_n = nblocks((int64_t)std::max<size_t>(hist_n, N1), SCAN_TILE) + 1;
@@ -476,41 +481,69 @@ TreeArrays carve(void* mem, int64_t n, size_t* bytes_out) {
     o = align_up(o + bytes);
     return at;
   };
-  const size_t o_key = take(4 * N1), o_perm = take(4 * N1), o_key2 = take(4 * N1),
-               o_perm2 = take(4 * N1), o_codes = take(4 * N1), o_mask = take(4 * N1),
-               o_offs = take(4 * (N1 + 1)), o_oa = take(4 * N1), o_ob = take(4 * N1),
-               o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
+  const size_t o_key = take(4 * N1), o_key2 = take(4 * N1), o_perm2 = take(4 * N1),
+               o_codes = take(4 * N1), o_mask = take(4 * N1), o_oa = take(4 * N1),
+               o_ob = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
-               o_nbox = take(32 * M), o_nrec = take(64 * M), o_nsc = take(8 * M),
-               o_ninfo = take(8 * M), o_npar = take(4 * M), o_acnt = take(4 * M),
-               o_isum = take(96 * M), o_cnt = take(16);
-  *bytes_out = o;
-  TreeArrays t{};
-  if (!mem) return t;
-  char* b = static_cast<char*>(mem);
-  t.key = (uint32_t*)(b + o_key);
-  t.perm = (uint32_t*)(b + o_perm);
-  t.key_alt = (uint32_t*)(b + o_key2);
-  t.perm_alt = (uint32_t*)(b + o_perm2);
-  t.codes = (uint32_t*)(b + o_codes);
-  t.mask = (uint32_t*)(b + o_mask);
-  t.offs = (uint32_t*)(b + o_offs);
-  t.own_a = (int32_t*)(b + o_oa);
-  t.own_b = (int32_t*)(b + o_ob);
-  t.hist = (uint32_t*)(b + o_hist);
-  t.hscan = (uint32_t*)(b + o_hscan);
-  t.bsum = (uint32_t*)(b + o_bsum);
-  t.bbox_part = (float*)(b + o_bbp);
-  t.bbox = (float*)(b + o_bb);
-  t.nbox = (float4*)(b + o_nbox);
-  t.nrec = (float4*)(b + o_nrec);
-  t.nsc = (int2*)(b + o_nsc);
-  t.ninfo = (int2*)(b + o_ninfo);
-  t.nparent = (int32_t*)(b + o_npar);
-  t.acnt = (int32_t*)(b + o_acnt);
-  t.isum = (double*)(b + o_isum);
-  t.counts = (int64_t*)(b + o_cnt);
-  return t;
+               o_nrec = take(64 * M), o_ninfo = take(8 * M), o_acnt = take(4 * M),
+               o_isum = take(96 * M), o_cnt = take(16),
+               o_part = take(nl * 15 * 32 * sizeof(float2)),
+               o_fb = take(nl * 15 * 32 * sizeof(float2));
+  if (mem) {
+    char* b = static_cast<char*>(mem);
+    t->key = (uint32_t*)(b + o_key);
+    t->key_alt = (uint32_t*)(b + o_key2);
+    t->perm_alt = (uint32_t*)(b + o_perm2);
+    t->codes = (uint32_t*)(b + o_codes);
+    t->mask = (uint32_t*)(b + o_mask);
+    t->own_a = (int32_t*)(b + o_oa);
+    t->own_b = (int32_t*)(b + o_ob);
+    t->hist = (uint32_t*)(b + o_hist);
+    t->hscan = (uint32_t*)(b + o_hscan);
+    t->bsum = (uint32_t*)(b + o_bsum);
+    t->bbox_part = (float*)(b + o_bbp);
+    t->bbox = (float*)(b + o_bb);
+    t->nrec = (float4*)(b + o_nrec);
+    t->ninfo = (int2*)(b + o_ninfo);
+    t->acnt = (int32_t*)(b + o_acnt);
+    t->isum = (double*)(b + o_isum);
+    t->counts = (int64_t*)(b + o_cnt);
+    L->part = (float2*)(b + o_part);
+    L->fb = (float2*)(b + o_fb);
+  }
+  return o;
+}
+
+// One step's tree and interaction lists (kept for the backward stage).
+size_t carve_slot(void* mem, int64_t n, int64_t chunks, TreeArrays* t, BHLists* L) {
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(n);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t o_perm = take(4 * N1), o_offs = take(4 * (N1 + 1)), o_npar = take(4 * M),
+               o_nsc = take(8 * M), o_nbox = take(32 * M),
+               o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
+               o_next = take(4 * (size_t)chunks), o_head = take(4 * nl), o_len = take(4 * nl),
+               o_ovx = take(4 * nl), o_used = take(4);
+  if (mem) {
+    char* b = static_cast<char*>(mem);
+    t->perm = (uint32_t*)(b + o_perm);
+    t->offs = (uint32_t*)(b + o_offs);
+    t->nparent = (int32_t*)(b + o_npar);
+    t->nsc = (int2*)(b + o_nsc);
+    t->nbox = (float4*)(b + o_nbox);
+    L->ent = (int2*)(b + o_ent);
+    L->next = (int*)(b + o_next);
+    L->head = (int*)(b + o_head);
+    L->len = (int*)(b + o_len);
+    L->ovf_x = (int*)(b + o_ovx);
+    L->used = (int*)(b + o_used);
+    L->n_chunks = (int)chunks;
+  }
+  return o;
 }
 
 #define TRY(x)                             \
@@ -544,7 +577,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
   TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, N, t.mask, t.offs, t.own_a, t.own_b,
                                                  t.nsc, t.ninfo, t.nparent, t.acnt);
-  k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack);
+  k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack, true);
   note_launches(2 + 4 * 5 + (N > 1 ? 1 : 0) + 3 + 2);
   return cudaGetLastError();
 }
@@ -553,92 +586,78 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
 
 // ---------------------------------------------------------------- host API
 namespace {
-constexpr int kListCap = 8192;                 // entries per list (slice)
-constexpr size_t kListBudget = size_t(4) << 30; // bytes of list storage at most
+constexpr size_t kListBudget = size_t(24) << 30;  // interaction-list pools, all slots
+constexpr int64_t kMinChunksPerList = 4;
+constexpr int64_t kEntriesPerPoint = 512;  // pool per slot: entries per point at most
 
-size_t lists_bytes(int64_t n, int cap) {
-  const size_t nl = (size_t)((n + 31) / 32) * BH_SLICES;
-  return align_up(nl * cap * sizeof(int2)) + 3 * align_up(nl * 4) + align_up(nl * 32 * 4) +
-         2 * align_up(nl * 15 * 32 * sizeof(float2));
-}
-
-BHLists carve_lists(void* mem, int64_t n, int cap) {
-  const size_t nl = (size_t)((n + 31) / 32) * BH_SLICES;
-  char* b = static_cast<char*>(mem);
-  BHLists L;
-  size_t o = 0;
-  L.ent = (int2*)(b + o);
-  o += align_up(nl * cap * sizeof(int2));
-  L.len = (int*)(b + o);
-  o += align_up(nl * 4);
-  L.ovf_x = (int*)(b + o);
-  o += align_up(nl * 4);
-  L.ovf_res = (int*)(b + o);
-  o += align_up(nl * 32 * 4);
-  o += align_up(nl * 4);
-  L.part = (float2*)(b + o);
-  o += align_up(nl * 15 * 32 * sizeof(float2));
-  L.fb = (float2*)(b + o);
-  L.cap = cap;
-  return L;
+// Views of the shared scratch and of slot `slot`.
+void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
+  *t = TreeArrays{};
+  *L = BHLists{};
+  carve_shared(w.mem, w.cap_n, t, L);
+  carve_slot(static_cast<char*>(w.smem) + (size_t)slot * w.slot_bytes, w.cap_n, w.lcap, t, L);
 }
 }  // namespace
 
 cudaError_t tree_setup() { return cudaSuccess; }
 
-// Entries per interaction list: the requested value, else kListCap reduced
-// to keep all lists within kListBudget.
-static int list_cap(const TreeWork& w, int64_t N) {
-  if (w.lcap_req > 0) return w.lcap_req;
-  const size_t nl = (size_t)((N + 31) / 32) * BH_SLICES;
-  int cap = kListCap;
-  while (cap > 1024 && nl * (size_t)cap * sizeof(int2) > kListBudget) cap /= 2;
-  return cap;
+// Chunks in each slot's pool: the requested number of entries per list times
+// the list count, else the slot's share of the storage budget (at most a
+// quarter of the free memory) capped at kEntriesPerPoint entries per point,
+// at least kMinChunksPerList chunks per list.
+// The pool size only decides how many slices take the slower re-walk path,
+// never the results.
+static int64_t pool_chunks(const TreeWork& w, int64_t N, int slots) {
+  const int64_t nl = (int64_t)n_lists(N);
+  if (w.lcap_req > 0) return std::max<int64_t>(1, nl * w.lcap_req / BH_CHUNK);
+  size_t budget = kListBudget;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, fr / 4);
+  else cudaGetLastError();
+  int64_t per_slot = (int64_t)(budget / (size_t)std::max(slots, 1) /
+                               (BH_CHUNK * sizeof(int2) + sizeof(int)));
+  per_slot = std::min(per_slot, N * kEntriesPerPoint / BH_CHUNK);
+  return std::max(per_slot, nl * kMinChunksPerList);
 }
 
-gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st) {
+gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st) {
   (void)st;
   if (N > (int64_t(1) << 30)) return GS_ERR_INVALID_ARG;
-  if (w.mem && w.cap_n >= N && list_cap(w, w.cap_n) == w.lcap) return GS_OK;
+  slots = std::max(slots, 1);
+  if (w.mem && w.cap_n >= N && w.nslots >= slots && w.lcap_req == w.lcap_from_req) return GS_OK;
   N = std::max<int64_t>(N, w.cap_n);
-  if (w.mem) cudaFree(w.mem);
-  w.mem = nullptr;
-  size_t bytes = 0;
-  carve(nullptr, N, &bytes);
-  if (cudaMalloc(&w.mem, bytes) != cudaSuccess) {
+  slots = std::max(slots, w.nslots);
+  tree_release(w);
+  const int64_t cap = pool_chunks(w, N, slots);
+  TreeArrays t;
+  BHLists L;
+  const size_t sb = carve_shared(nullptr, N, &t, &L);
+  const size_t slb = carve_slot(nullptr, N, cap, &t, &L);
+  if (cudaMalloc(&w.mem, sb) != cudaSuccess ||
+      cudaMalloc(&w.smem, slb * (size_t)slots) != cudaSuccess) {
     cudaGetLastError();
-    w.mem = nullptr;
-    w.cap_n = 0;
+    tree_release(w);
     return GS_ERR_OOM;
   }
-  w.bytes = bytes;
+  w.bytes = sb;
+  w.slot_bytes = slb;
+  w.nslots = slots;
   w.cap_n = N;
-  w.adjoint = adjoint;
-  size_t b2;
-  w.d_counts = carve(w.mem, N, &b2).counts;
-  // list capacity: kListCap entries per slice within the storage budget
-  const int cap = list_cap(w, N);
-  if (w.lmem) cudaFree(w.lmem);
-  w.lmem = nullptr;
-  w.lbytes = lists_bytes(N, cap);
-  if (cudaMalloc(&w.lmem, w.lbytes) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(w.mem);
-    w.mem = nullptr;
-    w.lmem = nullptr;
-    w.cap_n = 0;
-    return GS_ERR_OOM;
-  }
   w.lcap = cap;
+  w.lcap_from_req = w.lcap_req;
+  views(w, 0, &t, &L);
+  w.d_counts = t.counts;
   return GS_OK;
 }
 
 void tree_release(TreeWork& w) {
   if (w.mem) cudaFree(w.mem);
-  if (w.lmem) cudaFree(w.lmem);
+  if (w.smem) cudaFree(w.smem);
   w.mem = nullptr;
-  w.lmem = nullptr;
+  w.smem = nullptr;
   w.cap_n = 0;
+  w.nslots = 0;
+  w.d_counts = nullptr;
 }
 
 const char* bh_last_error() { return g_err; }
@@ -651,8 +670,9 @@ static gs_status cuda_err(cudaError_t e) {
 
 gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
                    cudaStream_t st) {
-  size_t bytes;
-  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
   cudaError_t err;
   if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
     return cuda_err(err);
@@ -660,20 +680,38 @@ gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero
   return GS_OK;
 }
 
+gs_status bh_aggregate(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
+                       cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  cudaError_t err;
+  if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
+    return cuda_err(err);
+  if ((err = cudaMemsetAsync(t.acnt, 0, sizeof(int32_t) * (2 * (size_t)b.N + 2), st)) !=
+      cudaSuccess)
+    return cuda_err(err);
+  k_aggregate<<<nblocks(b.N, 256), 256, 0, st>>>(t, (int)b.N, b.raw, b.pack, abpack, false);
+  note_launches(1);
+  err = cudaGetLastError();
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
 gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st) {
-  size_t bytes;
-  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
-  cudaError_t err =
-      launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, counts ? t.counts : nullptr, st);
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
+  if (err == cudaSuccess)
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
 gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts,
                       cudaStream_t st) {
-  size_t bytes;
-  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, false, e, AdjEpi{},
                                    counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
@@ -681,9 +719,9 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
 
 gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
                       cudaStream_t st) {
-  size_t bytes;
-  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
-  BHLists L = carve_lists(w.lmem, w.cap_n, w.lcap);
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, true, FwdEpi{}, e,
                                    counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
@@ -716,8 +754,9 @@ __global__ void k_export_nodes(TreeArrays t, int m, int32_t* nodes, float* range
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
                       uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,
                       int64_t* n_nodes, cudaStream_t st) {
-  size_t bytes;
-  TreeArrays t = carve(w.mem, w.cap_n, &bytes);
+  TreeArrays t;
+  BHLists L;
+  views(w, 0, &t, &L);
   cudaError_t err;
   if ((err = build(t, (int)N, raw, pack, nullptr, st)) != cudaSuccess) return cuda_err(err);
   uint32_t nint = 0;

@@ -9,21 +9,26 @@
 namespace gs {
 
 // Workspace of the octree steps (owned by a context).
+// Shared scratch (sort buffers, source records, partial sums) plus `nslots`
+// slots, each holding one step's tree and interaction lists so that the
+// backward stage can reuse the forward stage's decisions for the same state.
 struct TreeWork {
-  void* mem = nullptr;  // one allocation, carved into the arrays below
+  void* mem = nullptr;   // shared scratch
   size_t bytes = 0;
-  int64_t cap_n = 0;    // points it was sized for
-  bool adjoint = false;
+  void* smem = nullptr;  // slots
+  size_t slot_bytes = 0;
+  int nslots = 0;
+  int64_t cap_n = 0;     // points it was sized for
   int64_t* d_counts = nullptr;  // interaction counters {point, node}
-  void* lmem = nullptr;         // interaction lists (tree_impl.h BHLists)
-  size_t lbytes = 0;
-  int lcap = 0;                 // entries per list
-  int lcap_req = 0;             // requested entries per list (0 = default)
+  int64_t lcap = 0;      // chunks in each slot's interaction-list pool
+  int lcap_req = 0;      // requested entries per list (0 = budget-based pool)
+  int lcap_from_req = 0; // the request the current allocation was made for
 };
 
 // Inputs of one tree step: pack = scaled recentred FP32 positions and
 // momenta (pair layout), raw = FP32 positions {x, y, z, 0}.
 struct BHStep {
+  int slot;       // tree slot of this step
   int64_t N, Npad;
   double s;       // coordinate scale of the pack
   float thr;      // far threshold r*r (FP32)
@@ -32,12 +37,17 @@ struct BHStep {
 };
 
 cudaError_t tree_setup();
-gs_status tree_reserve(TreeWork& w, int64_t N, bool adjoint, cudaStream_t st);
+gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st);
 void tree_release(TreeWork& w);
 // Builds the tree of one state (abpack = NULL in the forward stage).
 gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
                    cudaStream_t st);
-// Walks the tree built last and records the interaction lists.
+// Recomputes the sums and source records of the tree stored in b.slot for
+// new (p, alpha, beta) -- the backward stage of the same state reuses the
+// forward stage's tree and lists.
+gs_status bh_aggregate(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,
+                       cudaStream_t st);
+// Walks the tree in b.slot and records the interaction lists there.
 gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st);
 // Evaluates the recorded lists (forward or backward stage) and applies the
 // epilogue.

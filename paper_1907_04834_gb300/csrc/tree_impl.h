@@ -49,15 +49,20 @@ struct TreeArrays {
 };
 
 // Interaction lists of one traversal: BH_SLICES per group of 32 points.
+// Entries live in a pool of chunks of BH_CHUNK entries; a list is the chain
+// of chunks starting at head[l] (next[c] links them in order).
 constexpr int BH_SLICES = 4;
+constexpr int BH_CHUNK = 64;
 struct BHLists {
-  int2* ent;     // lists x cap entries {node, lane mask}
-  int* len;      // entries recorded per list
-  int* ovf_x;    // per list: node where recording stopped (-1 = complete)
-  int* ovf_res;  // per list x 32: lane resume points at ovf_x
-  float2* part;  // per list x 15 x 32: partial sums of the recorded entries
-  float2* fb;    // per list x 15 x 32: partial sums of the resumed remainder
-  int cap;       // entries per list
+  int2* ent;      // pool: n_chunks x BH_CHUNK entries {node, lane mask}
+  int* next;      // per chunk: next chunk of the same list
+  int* head;      // per list: first chunk
+  int* len;       // per list: entries recorded
+  int* ovf_x;     // per list: >= 0 if the pool ran out (slice re-walked)
+  int* used;      // chunks taken from the pool (reset before each walk)
+  int n_chunks;   // pool size
+  float2* part;   // per list x 15 x 32: partial sums of the list
+  float2* fb;     // per list x 15 x 32: partial sums of a re-walked slice
 };
 
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
