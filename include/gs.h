@@ -200,6 +200,39 @@ gs_status gs_timing_read(gs_ctx *ctx, int64_t *launches, double *ms,
  * Runs short synthetic kernels on `device` (about 10 ms); no context needed. */
 gs_status gs_alu_peaks(int device, double *out);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* Largest N that gs_rhs_exact_noalloc accepts. */
+#define GS_RHS_NOALLOC_MAX_N 16384
+
+/*
+ * The exact forward right-hand side of gs_rhs (GS_EXACT: F and Phi at state
+ * (q, p)) computed without allocating any device memory.  The paper has no
+ * counterpart: it serves callers that cannot call cudaMalloc -- applications
+ * whose device memory is owned entirely by their own pool allocator, which
+ * forbids other allocations, and latency-critical loops in which an
+ * allocation's implicit device synchronisation is not acceptable.
+ *
+ * q, p, F, Phi: N x 3 float64 device buffers on the current CUDA device
+ * (host buffers are rejected with GS_ERR_INVALID_ARG); sigma > 0;
+ * 1 <= N <= GS_RHS_NOALLOC_MAX_N, larger N returns GS_ERR_INVALID_ARG.  No
+ * context is needed.  Work is enqueued on `stream` and the call returns
+ * without waiting; device-side conditions (a bounded wait that gave up) are
+ * not reported by this call.
+ *
+ * Scratch: one fixed array of about 6.4 MiB of device memory that every GPU
+ * loading the library holds until the process exits.  Every call on that
+ * GPU shares it and it keeps the previous call's contents (the call clears
+ * what must start at zero); calls whose GPU work overlaps -- on different
+ * streams or from concurrent host threads -- race on it, so serialise them.
+ * The first call on a device looks up the array's device address and sets
+ * up the kernel, with that device current; make that first call before any
+ * stream capture.
+ */
+gs_status gs_rhs_exact_noalloc(const double *q, const double *p, int64_t N,
+                               double sigma, double *F, double *Phi,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_NONFINITE, GS_ERR_TIM
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_NONFINITE", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
 GS_EXACT, GS_BH = 0, 1
+RHS_NOALLOC_MAX_N = 16384  # GS_RHS_NOALLOC_MAX_N in include/gs.h
 KERNEL_CLASSES = ("exact_fwd", "exact_adj", "tree_build", "bh_fwd", "bh_adj", "bh_walk")
 
 
@@ -61,6 +62,7 @@ _SIGS = {
     "gs_alu_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gs_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "gs_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, _i64]),
+    "gs_rhs_exact_noalloc": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp]),
     "gs_timing_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
 }
 
