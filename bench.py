@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", choices=["bh", "exact"],
+                    help="for profiler captures: two rounds of one forward and one adjoint "
+                         "right-hand side at the workload's initial state, then exit")
     return ap.parse_args()
 
 
@@ -357,8 +360,31 @@ def run_ours(args):
     return 0
 
 
+def run_probe(args):
+    import torch
+    from paper_1907_04834_gb300 import native
+    native.build()
+    import paper_1907_04834_gb300 as gs
+    w = workload()
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    q, p = t(w.q0), t(w.p0)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    al = torch.randn(q.shape, dtype=torch.float64, device=dev, generator=gen)
+    be = 0.1 * torch.randn(q.shape, dtype=torch.float64, device=dev, generator=gen)
+    mode = "bh" if args.probe == "bh" else "exact"
+    for _ in range(2):
+        gs.rhs(q, p, w.sigma, mode=mode, thresh=THRESH)
+        gs.adj_rhs(q, p, al, be, w.sigma, mode=mode, thresh=THRESH)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "N": w.N, "ok": True}))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

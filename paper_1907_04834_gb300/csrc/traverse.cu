@@ -350,20 +350,22 @@ struct ListSink {
     tail = c;
     written += n;
   }
+  // n <= 32 entries (a leaf run, a node's children or one node), so at most
+  // one chunk fills per call
   __device__ __forceinline__ void add(int node0, int n, unsigned mask) {
-    while (n > 0 && !ovf) {
-      const int take = min(n, BH_CHUNK - cnt);
-      if (lane < take) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
-      cnt += take;
-      node0 += take;
-      n -= take;
-      if (cnt == BH_CHUNK) {
-        __syncwarp();
-        put_chunk(BH_CHUNK);
-        __syncwarp();
-        cnt = 0;
-      }
+    if (ovf) return;
+    const int c2 = cnt + n;
+    if (lane < n && cnt + lane < BH_CHUNK) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
+    if (c2 < BH_CHUNK) {
+      cnt = c2;
+      return;
     }
+    __syncwarp();
+    put_chunk(BH_CHUNK);
+    __syncwarp();
+    const int rest = c2 - BH_CHUNK;
+    if (lane < rest) buf[lane] = make_int2(node0 + (n - rest) + lane, (int)mask);
+    cnt = rest;
   }
   __device__ __forceinline__ void finish() {
     __syncwarp();
