@@ -128,9 +128,11 @@ def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_ever
     return E, grad, q1
 
 
-def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.0, stream=None):
+def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.0,
+                  ckpt_every=0, stream=None):
     """Independent registrations of the subjects delimited by ``offsets``
-    (S+1 increasing ints).  Returns (E (S, 3), grad (N, 3))."""
+    (S+1 increasing ints, rows of q0/p0/X).  Returns (E (S, 3), grad (N, 3)),
+    E[s] = [E, H(q0,p0), lambda |q1 - X|^2] of subject s."""
     q0 = _pts(q0, "q0")
     n = q0.shape[0]
     p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
@@ -139,9 +141,9 @@ def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.
     if S < 1 or int(off[-1]) != n:
         raise ValueError("offsets must have S+1 entries ending at N")
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh)
-    E = torch.empty((S, 3), dtype=torch.float64, device=q0.device)
-    grad = torch.empty_like(q0)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every)
+    E = _like(q0, (S, 3))
+    grad = _like(q0)
     c.check(c.lib.gs_shoot_batched(c.handle, S, _ptr(off), _ptr(q0), _ptr(p0), _ptr(X),
                                    ctypes.byref(prm), _ptr(E), _ptr(grad),
                                    _stream_ptr(c.device, stream)))

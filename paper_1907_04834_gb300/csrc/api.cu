@@ -65,6 +65,8 @@ struct gs_ctx {
   DevMem packs, raws, abpacks, ckpt;
   DevMem part, tickets;
   size_t tickets_n = 0;
+  // many-subject calls: per-subject layout, queues, energies and gradients
+  DevMem bmeta, bout;
   TreeWork tree;  // Barnes-Hut workspace (tree.h)
 };
 
@@ -230,6 +232,8 @@ gs_status read_status(gs_ctx* c, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ solver
+struct Batch;
+
 struct Solver {
   gs_ctx* c;
   cudaStream_t st;
@@ -240,12 +244,109 @@ struct Solver {
   ExactGeom gf, ga;
   size_t pack_f4;  // float4 per pack slot
   int slots;       // pack slots allocated
+  // Many subjects (exact mode): subject s owns rows [off[s], off[s+1]) and
+  // pack entries [poff[s], poff[s] + npad[s]); persistent launches take
+  // their work-queue head from `queues` (one zeroed counter per launch).
+  const Batch* batch = nullptr;
 
   float4* pack(int k) const { return c->packs.as<float4>() + (size_t)k * pack_f4; }
   float4* raw(int k) const { return c->raws.as<float4>() + (size_t)k * Npad; }
   float4* abpack(int k) const { return c->abpacks.as<float4>() + (size_t)k * pack_f4; }
   double* scal(int k) const { return c->scal.as<double>() + k; }
 };
+
+// Layout of a many-subject call (host copy and device arrays in c->bmeta).
+struct Batch {
+  int S = 0;
+  int64_t N = 0, Ppad = 0;
+  std::vector<int64_t> off, poff;
+  std::vector<int> npad;
+  std::vector<int2> items;  // {subject, target tile}, largest subjects first
+  BatchInfo dev{};          // device views (queue unset)
+  double* E = nullptr;      // S x 3 energies (device)
+  int* queues = nullptr;
+  int n_queues = 0, next_queue = 0;
+  int fwd_blocks = 0, adj_blocks = 0;
+};
+
+// Host checks of the offsets and the per-subject layout.
+gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, Batch& b) {
+  if (S < 1 || S > (1 << 20)) return fail(c, GS_ERR_INVALID_ARG, "S must be in [1, 2^20]");
+  if (!offsets) return fail(c, GS_ERR_INVALID_ARG, "offsets is NULL");
+  bool dev = false;
+  gs_status s = locate(c, offsets, "offsets", &dev);
+  if (s != GS_OK) return s;
+  if (dev) return fail(c, GS_ERR_INVALID_ARG, "offsets must be host memory");
+  if (offsets[0] != 0) return fail(c, GS_ERR_INVALID_ARG, "offsets[0] must be 0");
+  b.S = S;
+  b.off.assign(offsets, offsets + S + 1);
+  b.poff.resize(S);
+  b.npad.resize(S);
+  int64_t pp = 0;
+  for (int k = 0; k < S; k++) {
+    const int64_t n = b.off[k + 1] - b.off[k];
+    if (n < 1 || n > (int64_t(1) << 30))
+      return fail(c, GS_ERR_INVALID_ARG, "subject %d has %lld points (need 1 .. 2^30)", k,
+                  (long long)n);
+    b.poff[k] = pp;
+    b.npad[k] = (int)((n + EX_TILE - 1) / EX_TILE * EX_TILE);
+    pp += b.npad[k];
+  }
+  b.N = b.off[S];
+  b.Ppad = pp;
+  if (b.N > (int64_t(1) << 30)) return fail(c, GS_ERR_INVALID_ARG, "offsets[S] must be <= 2^30");
+  std::vector<int> order(S);
+  for (int k = 0; k < S; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b2) { return b.npad[a] > b.npad[b2]; });
+  b.items.clear();
+  for (int k : order)
+    for (int t = 0; t < b.npad[k] / EX_NT; t++) b.items.push_back(make_int2(k, t));
+  return GS_OK;
+}
+
+// Device copy of the layout, the energies and `n_queues` zeroed queue heads.
+gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t S = (size_t)b.S;
+  const size_t o_off = 0, o_poff = o_off + up(8 * (S + 1)), o_cen = o_poff + up(8 * S),
+               o_E = o_cen + up(24 * S), o_npad = o_E + up(24 * S),
+               o_items = o_npad + up(4 * S), o_q = o_items + up(8 * b.items.size()),
+               total = o_q + up(4 * (size_t)n_queues);
+  CK(c->bmeta.ensure(total), "workspace");
+  char* base = c->bmeta.as<char>();
+  std::vector<char> h(o_q);
+  memcpy(h.data() + o_off, b.off.data(), 8 * (S + 1));
+  memcpy(h.data() + o_poff, b.poff.data(), 8 * S);
+  memcpy(h.data() + o_npad, b.npad.data(), 4 * S);
+  memcpy(h.data() + o_items, b.items.data(), 8 * b.items.size());
+  // synchronous copy: `h` is freed on return
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  CK(cudaMemcpy(base, h.data(), o_q, cudaMemcpyHostToDevice), "layout upload");
+  CK(cudaMemsetAsync(base + o_q, 0, 4 * (size_t)n_queues, st), "memset");
+  b.dev.items = reinterpret_cast<const int2*>(base + o_items);
+  b.dev.n_items = (int)b.items.size();
+  b.dev.off = reinterpret_cast<const int64_t*>(base + o_off);
+  b.dev.poff = reinterpret_cast<const int64_t*>(base + o_poff);
+  b.dev.npad = reinterpret_cast<const int*>(base + o_npad);
+  b.dev.centers = reinterpret_cast<const double*>(base + o_cen);
+  b.dev.queue = nullptr;
+  b.E = reinterpret_cast<double*>(base + o_E);
+  b.queues = reinterpret_cast<int*>(base + o_q);
+  b.n_queues = n_queues;
+  b.next_queue = 0;
+  b.fwd_blocks = std::max(1, std::min(b.dev.n_items, c->num_sms * batched_resident_blocks(false)));
+  b.adj_blocks = std::max(1, std::min(b.dev.n_items, c->num_sms * batched_resident_blocks(true)));
+  return GS_OK;
+}
+
+// Queue head for the next persistent launch.
+gs_status batch_take_queue(gs_ctx* c, Batch& b, BatchInfo* bi) {
+  if (b.next_queue >= b.n_queues) return fail(c, GS_ERR_INVALID_ARG, "internal: queue heads exhausted");
+  *bi = b.dev;
+  bi->queue = b.queues + b.next_queue++;
+  return GS_OK;
+}
 
 int choose_J(int n_itiles, int n_jtiles, int slots) {
   // smallest J giving >= 2 full waves, then the J (up to 4 waves) whose last
@@ -268,12 +369,27 @@ int choose_J(int n_itiles, int n_jtiles, int slots) {
 }
 
 // slots: pack slots; tree_slots: Barnes-Hut tree/list slots kept at once.
+// Zero every pack slot's padding sources (p = 0, and a = b = 0).
+gs_status pad_packs(Solver& S, float4* base, int nslots) {
+  gs_ctx* c = S.c;
+  if (S.batch)
+    CK(launch_batch_pad_zero(base, S.pack_f4, nslots, S.batch->dev.off, S.batch->dev.poff,
+                             S.batch->dev.npad, S.batch->S, S.st),
+       "pad");
+  else
+    CK(launch_pad_zero(base, S.pack_f4, nslots, S.N, S.Npad, S.st), "pad");
+  return GS_OK;
+}
+
+// batch: NULL for one point set; else the many-subject layout (exact mode).
 gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int slots,
-                      bool adjoint, cudaStream_t st, int tree_slots = 1) {
+                      bool adjoint, cudaStream_t st, int tree_slots = 1,
+                      const Batch* batch = nullptr) {
   S.c = c;
   S.st = st;
   S.N = N;
-  S.Npad = (N + EX_TILE - 1) / EX_TILE * EX_TILE;
+  S.batch = batch;
+  S.Npad = batch ? batch->Ppad : (N + EX_TILE - 1) / EX_TILE * EX_TILE;
   S.T = prm->T;
   S.mode = prm->mode;
   S.sigma = prm->sigma;
@@ -304,7 +420,8 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
   // pack slots: zero-filled so padding sources carry p = 0 (and a = b = 0)
   size_t pbytes = (size_t)slots * S.pack_f4 * sizeof(float4);
   CK(c->packs.ensure(pbytes), "workspace");
-  CK(launch_pad_zero(c->packs.as<float4>(), S.pack_f4, slots, N, S.Npad, st), "pad");
+  gs_status ps = pad_packs(S, c->packs.as<float4>(), slots);
+  if (ps != GS_OK) return ps;
   if (S.mode == GS_BH) {
     size_t rb = (size_t)slots * S.Npad * sizeof(float4);
     CK(c->raws.ensure(rb), "workspace");
@@ -315,9 +432,11 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     CK(c->r2.ensure((size_t)N * 8), "workspace");
     size_t ab = 2 * S.pack_f4 * sizeof(float4);
     CK(c->abpacks.ensure(ab), "workspace");
-    CK(launch_pad_zero(c->abpacks.as<float4>(), S.pack_f4, 2, N, S.Npad, st), "pad");
+    if ((ps = pad_packs(S, c->abpacks.as<float4>(), 2)) != GS_OK) return ps;
   }
-  if (S.mode == GS_EXACT) {
+  if (batch) {
+    if (S.mode != GS_EXACT) return fail(c, GS_ERR_INVALID_ARG, "internal: batched layout needs GS_EXACT");
+  } else if (S.mode == GS_EXACT) {
     int J = std::max(S.gf.J, S.ga.J);
     CK(c->part.ensure((size_t)J * 15 * S.Npad * sizeof(float2)), "workspace");
     size_t tn = (size_t)S.gf.n_itiles;
@@ -335,16 +454,34 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
 
 // Loads (q, p) into the state, computes the recentring point and the pack of
 // slot 0 (and its raw FP32 positions in Barnes-Hut mode).
+// Pack of the current state into pack slot `slot`.
+gs_status solver_pack(Solver& S, int slot) {
+  gs_ctx* c = S.c;
+  if (S.batch) {
+    const Batch& b = *S.batch;
+    CK(launch_batch_pack(c->q.as<double>(), c->p.as<double>(), S.N, b.dev.off, b.dev.poff, b.S,
+                         b.dev.centers, S.s, S.pack(slot), S.st),
+       "pack");
+    return GS_OK;
+  }
+  CK(launch_pack(c->q.as<double>(), c->p.as<double>(), S.N, S.scal(SC_CENTER), S.s, S.pack(slot),
+                 S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
+     "pack");
+  return GS_OK;
+}
+
 gs_status solver_load(Solver& S, const double* q0, const double* p0, int slot) {
   gs_ctx* c = S.c;
   size_t b = (size_t)S.N * 3 * sizeof(double);
   CK(cudaMemcpyAsync(c->q.p, q0, b, cudaMemcpyDeviceToDevice, S.st), "state copy");
   CK(cudaMemcpyAsync(c->p.p, p0, b, cudaMemcpyDeviceToDevice, S.st), "state copy");
-  CK(launch_bbox_center(c->q.as<double>(), S.N, S.scal(SC_CENTER), S.st), "center");
-  CK(launch_pack(c->q.as<double>(), c->p.as<double>(), S.N, S.scal(SC_CENTER), S.s, S.pack(slot),
-                 S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
-     "pack");
-  return GS_OK;
+  if (S.batch)
+    CK(launch_batch_centers(c->q.as<double>(), S.batch->dev.off, S.batch->S,
+                            const_cast<double*>(S.batch->dev.centers), S.st),
+       "center");
+  else
+    CK(launch_bbox_center(c->q.as<double>(), S.N, S.scal(SC_CENTER), S.st), "center");
+  return solver_pack(S, slot);
 }
 
 FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
@@ -365,6 +502,16 @@ FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
 // (Barnes-Hut: tree and interaction lists built in tree slot `tslot`).
 gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int tslot = 0) {
   gs_ctx* c = S.c;
+  if (S.batch) {
+    Batch& bt = *const_cast<Batch*>(S.batch);
+    BatchInfo bi;
+    gs_status qs = batch_take_queue(c, bt, &bi);
+    if (qs != GS_OK) return qs;
+    KTimer tm(c, GS_K_EXACT_FWD, S.st);
+    CK(launch_batched_fwd(S.pack(slot), bi, e, c->d_status, bt.fwd_blocks, S.st),
+       "batched forward kernel");
+    return GS_OK;
+  }
   if (S.mode == GS_EXACT) {
     KTimer tm(c, GS_K_EXACT_FWD, S.st);
     CK(launch_exact_fwd(S.pack(slot), S.gf, c->part.as<float2>(), c->tickets.as<unsigned>(), e,
@@ -414,6 +561,16 @@ AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) 
 gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts,
                       int tslot = 0, bool reuse = false) {
   gs_ctx* c = S.c;
+  if (S.batch) {
+    Batch& bt = *const_cast<Batch*>(S.batch);
+    BatchInfo bi;
+    gs_status qs = batch_take_queue(c, bt, &bi);
+    if (qs != GS_OK) return qs;
+    KTimer tm(c, GS_K_EXACT_ADJ, S.st);
+    CK(launch_batched_adj(S.pack(slot), S.abpack(ab), bi, e, c->d_status, bt.adj_blocks, S.st),
+       "batched adjoint kernel");
+    return GS_OK;
+  }
   if (S.mode == GS_EXACT) {
     KTimer tm(c, GS_K_EXACT_ADJ, S.st);
     CK(launch_exact_adj(S.pack(slot), S.abpack(ab), S.ga, c->part.as<float2>(),
@@ -445,6 +602,95 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     s = bh_eval_adj(c->tree, b, e, counts != nullptr, S.st);
   }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut adjoint step failed: %s", bh_last_error());
+  return GS_OK;
+}
+
+// Objective and gradient (Eq. 2 and the discrete adjoint) of one point set
+// of N rows (batch NULL) or of every subject of `batch`.  Inputs are device
+// arrays; E receives 3 doubles per subject, grad N x 3, q1 (optional) q(1).
+gs_status run_grad(gs_ctx* c, int64_t N, const double* dq0, const double* dp0, const double* dX,
+                   const gs_params* prm, Batch* batch, double* E, double* grad, double* q1,
+                   cudaStream_t st) {
+  gs_status s;
+  const int T = prm->T;
+  const int ck = prm->ckpt_every > 0 && prm->ckpt_every < T ? prm->ckpt_every : 0;
+  // pack slots: every step (store-all) or one segment (checkpointing)
+  const int slots = ck ? ck + 1 : T + 1;
+  Solver S;
+  // Barnes-Hut: one tree slot per step kept for the backward stage (a
+  // segment's steps with checkpointing)
+  const int tslots = prm->mode == GS_BH ? (ck ? ck : T) : 1;
+  if ((s = solver_init(c, S, N, prm, slots, true, st, tslots, batch))) return s;
+  const size_t n3 = (size_t)N * 3, b3 = n3 * sizeof(double);
+  const int nck = ck ? (T + ck - 1) / ck : 0;
+  if (ck) CK(c->ckpt.ensure((size_t)nck * 2 * b3), "checkpoint allocation");
+  double* ckq = ck ? c->ckpt.as<double>() : nullptr;
+  if ((s = solver_load(S, dq0, dp0, 0))) return s;
+
+  // ---- forward pass
+  for (int k = 0; k < T; k++) {
+    int in = ck ? (k & 1) : k, outs = ck ? ((k + 1) & 1) : k + 1;
+    if (ck && k % ck == 0) {
+      double* dst = ckq + (size_t)(k / ck) * 2 * n3;
+      CK(cudaMemcpyAsync(dst, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
+      CK(cudaMemcpyAsync(dst + n3, c->p.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    }
+    FwdEpi e = fwd_epi(S, outs, S.h);
+    if (k == 0) {
+      e.F_out = c->F0.as<double>();
+      e.pf_part = c->pf.as<double>();
+    }
+    if ((s = forward_rhs(S, in, e, nullptr, ck ? 0 : k))) return s;
+  }
+  if (q1) CK(cudaMemcpyAsync(q1, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "q1 copy");
+  // ---- adjoint initialisation and objective
+  if (batch) {
+    CK(launch_batch_adjoint_init(c->q.as<double>(), dX, N, batch->dev.off, batch->dev.poff,
+                                 batch->S, S.lambda, c->al.as<double>(), c->be.as<double>(),
+                                 S.abpack(0), c->r2.as<double>(), st),
+       "adjoint init");
+    CK(launch_segment_sum(c->pf.as<double>(), batch->dev.off, batch->S, 0.5, E + 1, 3, st), "sum");
+    CK(launch_segment_sum(c->r2.as<double>(), batch->dev.off, batch->S, S.lambda, E + 2, 3, st),
+       "sum");
+    CK(launch_batch_energy(E, batch->S, st), "energy");
+  } else {
+    CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+    CK(launch_adjoint_init(c->q.as<double>(), dX, N, S.lambda, c->al.as<double>(),
+                           c->be.as<double>(), S.abpack(0), c->r2.as<double>(), st),
+       "adjoint init");
+    CK(launch_sum(c->r2.as<double>(), N, S.lambda, S.scal(SC_DATA), st), "sum");
+    CK(launch_energy(S.scal(SC_H0), S.scal(SC_DATA), E, st), "energy");
+  }
+  // ---- backward pass
+  int ab = 0;
+  auto back_step = [&](int k, int slot) -> gs_status {
+    AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, grad);
+    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr, slot, true);
+    ab ^= 1;
+    return r;
+  };
+  if (!ck) {
+    for (int k = T - 1; k >= 0; k--)
+      if ((s = back_step(k, k))) return s;
+  } else {
+    for (int seg = nck - 1; seg >= 0; seg--) {
+      const int k0 = seg * ck, k1 = std::min(T, k0 + ck);
+      const double* src = ckq + (size_t)seg * 2 * n3;
+      CK(cudaMemcpyAsync(c->q.p, src, b3, cudaMemcpyDeviceToDevice, st), "restore");
+      CK(cudaMemcpyAsync(c->p.p, src + n3, b3, cudaMemcpyDeviceToDevice, st), "restore");
+      if ((s = solver_pack(S, 0))) return s;
+      for (int k = k0; k < k1; k++) {
+        // the last step of the segment only builds its tree and lists
+        // (its state update is not needed): the adjoint reuses them
+        if (S.mode == GS_BH || k < k1 - 1) {
+          FwdEpi e = fwd_epi(S, k < k1 - 1 ? k - k0 + 1 : -1, k < k1 - 1 ? S.h : 0.0);
+          if ((s = forward_rhs(S, k - k0, e, nullptr, k - k0))) return s;
+        }
+      }
+      for (int k = k1 - 1; k >= k0; k--)
+        if ((s = back_step(k, k - k0))) return s;
+    }
+  }
   return GS_OK;
 }
 
@@ -489,7 +735,7 @@ void gs_destroy(gs_ctx* c) {
     cudaDeviceSynchronize();
     for (DevMem* m : {&c->in_q, &c->in_p, &c->in_a, &c->in_b, &c->in_X, &c->out_a, &c->out_b,
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
-                      &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets})
+                      &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout})
       m->release();
     tree_release(c->tree);
     for (auto& t : c->pending) {
@@ -619,85 +865,71 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
       (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)) ||
       (s = input(c, X, (size_t)N * 3, "X", c->in_X, st, &dX)))
     return s;
-  const int T = prm->T;
-  const int ck = prm->ckpt_every > 0 && prm->ckpt_every < T ? prm->ckpt_every : 0;
-  // pack slots: every step (store-all) or one segment (checkpointing)
-  const int slots = ck ? ck + 1 : T + 1;
-  Solver S;
-  // Barnes-Hut: one tree slot per step kept for the backward stage (a
-  // segment's steps with checkpointing)
-  const int tslots = prm->mode == GS_BH ? (ck ? ck : T) : 1;
-  if ((s = solver_init(c, S, N, prm, slots, true, st, tslots))) return s;
-  const size_t n3 = (size_t)N * 3, b3 = n3 * sizeof(double);
-  const int nck = ck ? (T + ck - 1) / ck : 0;
-  if (ck) CK(c->ckpt.ensure((size_t)nck * 2 * b3), "checkpoint allocation");
-  double* ckq = ck ? c->ckpt.as<double>() : nullptr;
-  if ((s = solver_load(S, dq0, dp0, 0))) return s;
-  DevMem& gradbuf = c->out_a;
-  CK(gradbuf.ensure(b3), "workspace");
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  CK(c->out_a.ensure(b3), "workspace");
   CK(c->out_b.ensure(b3), "workspace");
-
-  // ---- forward pass
-  for (int k = 0; k < T; k++) {
-    int in = ck ? (k & 1) : k, outs = ck ? ((k + 1) & 1) : k + 1;
-    if (ck && k % ck == 0) {
-      double* dst = ckq + (size_t)(k / ck) * 2 * n3;
-      CK(cudaMemcpyAsync(dst, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
-      CK(cudaMemcpyAsync(dst + n3, c->p.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
-    }
-    FwdEpi e = fwd_epi(S, outs, S.h);
-    if (k == 0) {
-      e.F_out = c->F0.as<double>();
-      e.pf_part = c->pf.as<double>();
-    }
-    if ((s = forward_rhs(S, in, e, nullptr, ck ? 0 : k))) return s;
-  }
-  CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
-  CK(cudaMemcpyAsync(c->out_b.p, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "q1 copy");
-  // ---- adjoint initialisation and objective
-  CK(launch_adjoint_init(c->q.as<double>(), dX, N, S.lambda, c->al.as<double>(),
-                         c->be.as<double>(), S.abpack(0), c->r2.as<double>(), st),
-     "adjoint init");
-  CK(launch_sum(c->r2.as<double>(), N, S.lambda, S.scal(SC_DATA), st), "sum");
-  CK(launch_energy(S.scal(SC_H0), S.scal(SC_DATA), S.scal(SC_E), st), "energy");
-  // ---- backward pass
-  int ab = 0;
-  auto back_step = [&](int k, int slot) -> gs_status {
-    AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, gradbuf.as<double>());
-    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr, slot, true);
-    ab ^= 1;
-    return r;
-  };
-  if (!ck) {
-    for (int k = T - 1; k >= 0; k--)
-      if ((s = back_step(k, k))) return s;
-  } else {
-    for (int seg = nck - 1; seg >= 0; seg--) {
-      const int k0 = seg * ck, k1 = std::min(T, k0 + ck);
-      const double* src = ckq + (size_t)seg * 2 * n3;
-      CK(cudaMemcpyAsync(c->q.p, src, b3, cudaMemcpyDeviceToDevice, st), "restore");
-      CK(cudaMemcpyAsync(c->p.p, src + n3, b3, cudaMemcpyDeviceToDevice, st), "restore");
-      CK(launch_pack(c->q.as<double>(), c->p.as<double>(), N, S.scal(SC_CENTER), S.s, S.pack(0),
-                     S.mode == GS_BH ? S.raw(0) : nullptr, st),
-         "pack");
-      for (int k = k0; k < k1; k++) {
-        // the last step of the segment only builds its tree and lists
-        // (its state update is not needed): the adjoint reuses them
-        if (S.mode == GS_BH || k < k1 - 1) {
-          FwdEpi e = fwd_epi(S, k < k1 - 1 ? k - k0 + 1 : -1, k < k1 - 1 ? S.h : 0.0);
-          if ((s = forward_rhs(S, k - k0, e, nullptr, k - k0))) return s;
-        }
-      }
-      for (int k = k1 - 1; k >= k0; k--)
-        if ((s = back_step(k, k - k0))) return s;
-    }
-  }
-  CK(launch_check_finite(S.scal(SC_E), 3, c->d_status, st), "check");
-  CK(launch_check_finite(gradbuf.as<double>(), (int64_t)n3, c->d_status, st), "check");
-  if ((s = copy_out(c, E, S.scal(SC_E), 3 * sizeof(double), st))) return s;
-  if ((s = copy_out(c, grad, gradbuf.p, b3, st))) return s;
+  CK(c->scal.ensure(SC_N * 8), "workspace");
+  double* dE = c->scal.as<double>() + SC_E;
+  if ((s = run_grad(c, N, dq0, dp0, dX, prm, nullptr, dE, c->out_a.as<double>(),
+                    q1 ? c->out_b.as<double>() : nullptr, st)))
+    return s;
+  CK(launch_check_finite(dE, 3, c->d_status, st), "check");
+  CK(launch_check_finite(c->out_a.as<double>(), N * 3, c->d_status, st), "check");
+  if ((s = copy_out(c, E, dE, 3 * sizeof(double), st))) return s;
+  if ((s = copy_out(c, grad, c->out_a.p, b3, st))) return s;
   if (q1 && (s = copy_out(c, q1, c->out_b.p, b3, st))) return s;
   if (hE || hg || hq) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const double* q0,
+                           const double* p0, const double* X, const gs_params* prm, double* E,
+                           double* grad, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_params(c, prm, true))) return s;
+  Batch b;
+  if ((s = batch_plan(c, S, offsets, b))) return s;
+  const int64_t N = b.N;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hE = false, hg = false;
+  if ((s = output(c, E, "E", &hE)) || (s = output(c, grad, "grad", &hg))) return s;
+  const double *dq0, *dp0, *dX;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)) ||
+      (s = input(c, X, (size_t)N * 3, "X", c->in_X, st, &dX)))
+    return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  // per-launch queue heads: forward steps, checkpoint recomputation, adjoint
+  const int T = prm->T;
+  if ((s = batch_upload(c, b, prm->mode == GS_EXACT ? 3 * T + 2 : 0, st))) return s;
+  CK(c->bout.ensure(b3), "workspace");
+  double* dgrad = c->bout.as<double>();
+  if (prm->mode == GS_EXACT) {
+    if ((s = run_grad(c, N, dq0, dp0, dX, prm, &b, b.E, dgrad, nullptr, st))) return s;
+  } else {
+    // Barnes-Hut: one subject after another (largest first, so that the
+    // workspace is sized once), each with its own tree per step
+    std::vector<int> order(S);
+    for (int k = 0; k < S; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return b.off[x + 1] - b.off[x] > b.off[y + 1] - b.off[y];
+    });
+    for (int k : order) {
+      const int64_t o = b.off[k], n = b.off[k + 1] - o;
+      if ((s = run_grad(c, n, dq0 + 3 * o, dp0 + 3 * o, dX + 3 * o, prm, nullptr, b.E + 3 * k,
+                        dgrad + 3 * o, nullptr, st)))
+        return s;
+    }
+  }
+  CK(launch_check_finite(b.E, 3 * (int64_t)S, c->d_status, st), "check");
+  CK(launch_check_finite(dgrad, N * 3, c->d_status, st), "check");
+  if ((s = copy_out(c, E, b.E, 3 * (size_t)S * sizeof(double), st))) return s;
+  if ((s = copy_out(c, grad, dgrad, b3, st))) return s;
+  if (hE || hg) return read_status(c, st);
   CK(cudaGetLastError(), "launch");
   return GS_OK;
 }
@@ -808,13 +1040,5 @@ gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_
   return read_status(c, st);
 }
 
-gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const double* q0,
-                           const double* p0, const double* X, const gs_params* prm, double* E,
-                           double* grad, void* stream) {
-  (void)S, (void)offsets, (void)q0, (void)p0, (void)X, (void)prm, (void)E, (void)grad,
-      (void)stream;
-  if (!c) return GS_ERR_INVALID_ARG;
-  return fail(c, GS_ERR_UNSUPPORTED, "batched shooting is not built yet");
-}
 
 }  // extern "C"

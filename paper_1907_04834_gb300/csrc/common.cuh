@@ -190,8 +190,11 @@ struct FwdEpi {
   int64_t N;
 };
 
-__device__ __forceinline__ void fwd_epilogue(int64_t i, const double F[3], const double Sraw[3],
-                                             const FwdEpi& e) {
+// Epilogue of point i (state and output rows) whose pack entry is ipk, with
+// recentring point `center` (batched subjects have their own packs/centres).
+__device__ __forceinline__ void fwd_epilogue_at(int64_t i, int64_t ipk, const double* center,
+                                                const double F[3], const double Sraw[3],
+                                                const FwdEpi& e) {
   double Phi[3] = {Sraw[0] * e.phi_scale, Sraw[1] * e.phi_scale, Sraw[2] * e.phi_scale};
   double* q = e.q + 3 * i;
   double* p = e.p + 3 * i;
@@ -214,11 +217,16 @@ __device__ __forceinline__ void fwd_epilogue(int64_t i, const double F[3], const
       q[a] = qn[a];
       p[a] = pn[a];
     }
-    PackScale ps{e.center[0], e.center[1], e.center[2], e.s};
-    if (e.pack_next) pack_state(e.pack_next, i, qn, pn, ps);
+    PackScale ps{center[0], center[1], center[2], e.s};
+    if (e.pack_next) pack_state(e.pack_next, ipk, qn, pn, ps);
     if (e.raw_next)
-      e.raw_next[i] = make_float4((float)qn[0], (float)qn[1], (float)qn[2], 0.f);
+      e.raw_next[ipk] = make_float4((float)qn[0], (float)qn[1], (float)qn[2], 0.f);
   }
+}
+
+__device__ __forceinline__ void fwd_epilogue(int64_t i, const double F[3], const double Sraw[3],
+                                             const FwdEpi& e) {
+  fwd_epilogue_at(i, i, e.center, F, Sraw, e);
 }
 
 // Adjoint: finished sums A1 = Sum g (a_i.p_j + a_j.p_i) d_s, A2 = Sum c g w,
@@ -239,9 +247,10 @@ struct AdjEpi {
   int64_t N;
 };
 
-__device__ __forceinline__ void adj_epilogue(int64_t i, const double A1[3], const double A2[3],
-                                             const double A3[3], const double B1[3],
-                                             const double B2[3], const AdjEpi& e) {
+__device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const double A1[3],
+                                                const double A2[3], const double A3[3],
+                                                const double B1[3], const double B2[3],
+                                                const AdjEpi& e) {
   const double two_ln2 = 1.3862943611198906;  // 2 ln 2 = 1 / (s^2 sigma^2)
   double dA[3], dB[3];
   for (int a = 0; a < 3; a++) {
@@ -261,11 +270,17 @@ __device__ __forceinline__ void adj_epilogue(int64_t i, const double A1[3], cons
       e.be[3 * i + a] = bn[a];
     }
     if (e.pack_next)
-      pack_write(e.pack_next, i, (float)an[0], (float)an[1], (float)an[2], (float)bn[0],
+      pack_write(e.pack_next, ipk, (float)an[0], (float)an[1], (float)an[2], (float)bn[0],
                  (float)bn[1], (float)bn[2]);
     if (e.F0)
       for (int a = 0; a < 3; a++) e.grad[3 * i + a] = bn[a] + e.F0[3 * i + a];
   }
+}
+
+__device__ __forceinline__ void adj_epilogue(int64_t i, const double A1[3], const double A2[3],
+                                             const double A3[3], const double B1[3],
+                                             const double B2[3], const AdjEpi& e) {
+  adj_epilogue_at(i, i, A1, A2, A3, B1, B2, e);
 }
 
 }  // namespace gs

@@ -25,11 +25,54 @@ struct ExactGeom {
   int J;         // source splits per target tile (1 <= J <= n_jtiles)
 };
 
+// Many point sets ("subjects") in one launch: work items (subject, target
+// tile) in decreasing subject size, taken from `queue` by persistent blocks.
+// Subject s owns rows [off[s], off[s+1]) of the state and pack entries
+// [poff[s], poff[s] + npad[s]) (npad a multiple of EX_TILE, padding sources
+// with zero momentum).
+struct BatchInfo {
+  const int2* items;      // {subject, target tile}
+  int n_items;
+  const int64_t* off;     // S + 1 row offsets
+  const int64_t* poff;    // S pack offsets
+  const int* npad;        // S padded sizes
+  const double* centers;  // S x 3 recentring points
+  int* queue;             // next item (zeroed before each launch)
+};
+
 cudaError_t exact_setup();
 cudaError_t launch_exact_fwd(const float4* pk, const ExactGeom& g, float2* part,
                              unsigned* tickets, const FwdEpi& e, int* status, cudaStream_t st);
 cudaError_t launch_exact_adj(const float4* pk, const float4* ab, const ExactGeom& g, float2* part,
                              unsigned* tickets, const AdjEpi& e, int* status, cudaStream_t st);
+
+// resident blocks per SM of the persistent batched kernels
+int batched_resident_blocks(bool adjoint);
+cudaError_t launch_batched_fwd(const float4* pk, const BatchInfo& b, const FwdEpi& e, int* status,
+                               int blocks, cudaStream_t st);
+cudaError_t launch_batched_adj(const float4* pk, const float4* ab, const BatchInfo& b,
+                               const AdjEpi& e, int* status, int blocks, cudaStream_t st);
+
+// ---- batched helpers (util.cu)
+// centers[s] = bounding-box centre of subject s (one block per subject)
+cudaError_t launch_batch_centers(const double* q, const int64_t* off, int S, double* centers,
+                                 cudaStream_t st);
+// pack entries of every subject (and zero padding in `slots` consecutive packs)
+cudaError_t launch_batch_pack(const double* q, const double* p, int64_t N, const int64_t* off,
+                              const int64_t* poff, int S, const double* centers, double s,
+                              float4* pack, cudaStream_t st);
+cudaError_t launch_batch_pad_zero(float4* base, size_t slot_f4, int slots, const int64_t* off,
+                                  const int64_t* poff, const int* npad, int S, cudaStream_t st);
+// alpha = 2 lambda (q - X), beta = 0, adjoint pack; r2[i] = |q_i - X_i|^2
+cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t N,
+                                      const int64_t* off, const int64_t* poff, int S,
+                                      double lambda, double* al, double* be, float4* abpack,
+                                      double* r2, cudaStream_t st);
+// out[s * stride] = scale * Sum over rows of subject s of x (fixed order)
+cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
+                               double* out, int stride, cudaStream_t st);
+// E[s] = {H[s] + D[s], H[s], D[s]} from E[s*3+1] = H, E[s*3+2] = D
+cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st);
 
 // ---- small helpers (util.cu)
 cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st);

@@ -129,6 +129,112 @@ __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* sta
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
+// subject of row i: the last s with off[s] <= i
+__device__ __forceinline__ int subject_of(const int64_t* off, int S, int64_t i) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// one block per subject: centre of its bounding box
+__global__ void k_batch_centers(const double* __restrict__ q, const int64_t* __restrict__ off,
+                                double* centers) {
+  __shared__ double smin[3][32], smax[3][32];
+  const int s = blockIdx.x;
+  const int64_t a = off[s], b = off[s + 1];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x)
+    for (int c = 0; c < 3; c++) {
+      lo[c] = fmin(lo[c], q[3 * i + c]);
+      hi[c] = fmax(hi[c], q[3 * i + c]);
+    }
+  for (int c = 0; c < 3; c++)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[c] = fmin(lo[c], __shfl_down_sync(0xffffffffu, lo[c], o));
+      hi[c] = fmax(hi[c], __shfl_down_sync(0xffffffffu, hi[c], o));
+    }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int c = 0; c < 3; c++) {
+      smin[c][w] = lo[c];
+      smax[c][w] = hi[c];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 3; c++) {
+      double mn = smin[c][0], mx = smax[c][0];
+      for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+        mn = fmin(mn, smin[c][k]);
+        mx = fmax(mx, smax[c][k]);
+      }
+      centers[3 * s + c] = 0.5 * (mn + mx);
+    }
+}
+
+__global__ void k_batch_pack(const double* __restrict__ q, const double* __restrict__ p,
+                             int64_t N, const int64_t* __restrict__ off,
+                             const int64_t* __restrict__ poff, int S,
+                             const double* __restrict__ centers, double sc, float4* pack) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = subject_of(off, S, i);
+  const PackScale ps{centers[3 * s], centers[3 * s + 1], centers[3 * s + 2], sc};
+  pack_state(pack, poff[s] + (i - off[s]), q + 3 * i, p + 3 * i, ps);
+}
+
+// one block per (subject, pack slot): zero the subject's padding entries
+__global__ void k_batch_pad_zero(float4* base, size_t slot_f4, const int64_t* __restrict__ off,
+                                 const int64_t* __restrict__ poff, const int* __restrict__ npad) {
+  const int s = blockIdx.x;
+  float4* pk = base + (size_t)blockIdx.y * slot_f4;
+  const int64_t n = off[s + 1] - off[s];
+  for (int64_t j = n + threadIdx.x; j < npad[s]; j += blockDim.x)
+    pack_write(pk, poff[s] + j, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_batch_adjoint_init(const double* __restrict__ q, const double* __restrict__ X,
+                                     int64_t N, const int64_t* __restrict__ off,
+                                     const int64_t* __restrict__ poff, int S, double lambda,
+                                     double* al, double* be, float4* abpack, double* r2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int s = subject_of(off, S, i);
+  double a[3], t = 0.0;
+  for (int c = 0; c < 3; c++) {
+    const double r = q[3 * i + c] - X[3 * i + c];
+    t += r * r;
+    a[c] = 2.0 * lambda * r;
+    al[3 * i + c] = a[c];
+    be[3 * i + c] = 0.0;
+  }
+  r2[i] = t;
+  pack_write(abpack, poff[s] + (i - off[s]), (float)a[0], (float)a[1], (float)a[2], 0.f, 0.f,
+             0.f);
+}
+
+// one block per subject; each thread sums a contiguous chunk, then a fixed tree
+__global__ void k_segment_sum(const double* __restrict__ x, const int64_t* __restrict__ off,
+                              double scale, double* out, int stride) {
+  const int s = blockIdx.x;
+  const int64_t a = off[s], b = off[s + 1], n = b - a;
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t c0 = a + (int64_t)threadIdx.x * chunk;
+  const int64_t c1 = c0 + chunk < b ? c0 + chunk : b;
+  double v = 0.0;
+  for (int64_t i = c0; i < c1; i++) v += x[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[(size_t)s * stride] = scale * v;
+}
+
+__global__ void k_batch_energy(double* E, int S) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < S) E[3 * s] = E[3 * s + 1] + E[3 * s + 2];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 std::atomic<long long> g_launches{0};
@@ -137,6 +243,52 @@ std::atomic<long long> g_launches{0};
 
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+cudaError_t launch_batch_centers(const double* q, const int64_t* off, int S, double* centers,
+                                 cudaStream_t st) {
+  k_batch_centers<<<S, 256, 0, st>>>(q, off, centers);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pack(const double* q, const double* p, int64_t N, const int64_t* off,
+                              const int64_t* poff, int S, const double* centers, double s,
+                              float4* pack, cudaStream_t st) {
+  k_batch_pack<<<blocks_for(N, 256), 256, 0, st>>>(q, p, N, off, poff, S, centers, s, pack);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pad_zero(float4* base, size_t slot_f4, int slots, const int64_t* off,
+                                  const int64_t* poff, const int* npad, int S, cudaStream_t st) {
+  dim3 grid((unsigned)S, (unsigned)slots);
+  k_batch_pad_zero<<<grid, 256, 0, st>>>(base, slot_f4, off, poff, npad);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t N,
+                                      const int64_t* off, const int64_t* poff, int S,
+                                      double lambda, double* al, double* be, float4* abpack,
+                                      double* r2, cudaStream_t st) {
+  k_batch_adjoint_init<<<blocks_for(N, 256), 256, 0, st>>>(q, X, N, off, poff, S, lambda, al, be,
+                                                           abpack, r2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
+                               double* out, int stride, cudaStream_t st) {
+  k_segment_sum<<<S, kRedThreads, 0, st>>>(x, off, scale, out, stride);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st) {
+  k_batch_energy<<<blocks_for(S, 256), 256, 0, st>>>(E, S);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st) {
   k_bbox_center<<<1, kRedThreads, 0, st>>>(q, N, center);
