@@ -256,21 +256,28 @@ struct Solver {
 };
 
 // Layout of a many-subject call (host copy and device arrays in c->bmeta).
+// Exact mode pads every subject's pack to whole source tiles; Barnes-Hut
+// mode packs the subjects back to back (pack entry = row) and builds one
+// forest per step.
 struct Batch {
   int S = 0;
+  bool padded = true;
   int64_t N = 0, Ppad = 0;
   std::vector<int64_t> off, poff;
   std::vector<int> npad;
-  std::vector<int2> items;  // {subject, target tile}, largest subjects first
-  BatchInfo dev{};          // device views (queue unset)
-  double* E = nullptr;      // S x 3 energies (device)
+  std::vector<int2> items;   // exact: {subject, target tile}, largest subjects first
+  std::vector<int4> groups;  // Barnes-Hut: walk groups {first, count, off[s], off[s+1]}
+  BatchInfo dev{};           // device views (queue unset)
+  const int4* dgroups = nullptr;
+  float* sbox = nullptr;     // Barnes-Hut: 6 S floats of per-subject boxes
+  double* E = nullptr;       // S x 3 energies (device)
   int* queues = nullptr;
   int n_queues = 0, next_queue = 0;
   int fwd_blocks = 0, adj_blocks = 0;
 };
 
-// Host checks of the offsets and the per-subject layout.
-gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, Batch& b) {
+// Host checks of the offsets and the per-subject layout (padded: exact mode).
+gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, bool padded, Batch& b) {
   if (S < 1 || S > (1 << 20)) return fail(c, GS_ERR_INVALID_ARG, "S must be in [1, 2^20]");
   if (!offsets) return fail(c, GS_ERR_INVALID_ARG, "offsets is NULL");
   bool dev = false;
@@ -279,6 +286,7 @@ gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, Batch& b) {
   if (dev) return fail(c, GS_ERR_INVALID_ARG, "offsets must be host memory");
   if (offsets[0] != 0) return fail(c, GS_ERR_INVALID_ARG, "offsets[0] must be 0");
   b.S = S;
+  b.padded = padded;
   b.off.assign(offsets, offsets + S + 1);
   b.poff.resize(S);
   b.npad.resize(S);
@@ -288,18 +296,26 @@ gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, Batch& b) {
     if (n < 1 || n > (int64_t(1) << 30))
       return fail(c, GS_ERR_INVALID_ARG, "subject %d has %lld points (need 1 .. 2^30)", k,
                   (long long)n);
-    b.poff[k] = pp;
-    b.npad[k] = (int)((n + EX_TILE - 1) / EX_TILE * EX_TILE);
+    b.poff[k] = padded ? pp : b.off[k];
+    b.npad[k] = padded ? (int)((n + EX_TILE - 1) / EX_TILE * EX_TILE) : (int)n;
     pp += b.npad[k];
   }
   b.N = b.off[S];
-  b.Ppad = pp;
   if (b.N > (int64_t(1) << 30)) return fail(c, GS_ERR_INVALID_ARG, "offsets[S] must be <= 2^30");
+  b.Ppad = padded ? pp : (b.N + EX_TILE - 1) / EX_TILE * EX_TILE;
+  b.items.clear();
+  b.groups.clear();
+  if (!padded) {
+    for (int k = 0; k < S; k++)
+      for (int64_t f = b.off[k]; f < b.off[k + 1]; f += 32)
+        b.groups.push_back(make_int4((int)f, (int)std::min<int64_t>(32, b.off[k + 1] - f),
+                                     (int)b.off[k], (int)b.off[k + 1]));
+    return GS_OK;
+  }
   std::vector<int> order(S);
   for (int k = 0; k < S; k++) order[k] = k;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b2) { return b.npad[a] > b.npad[b2]; });
-  b.items.clear();
   for (int k : order)
     for (int t = 0; t < b.npad[k] / EX_NT; t++) b.items.push_back(make_int2(k, t));
   return GS_OK;
@@ -311,7 +327,8 @@ gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
   const size_t S = (size_t)b.S;
   const size_t o_off = 0, o_poff = o_off + up(8 * (S + 1)), o_cen = o_poff + up(8 * S),
                o_E = o_cen + up(24 * S), o_npad = o_E + up(24 * S),
-               o_items = o_npad + up(4 * S), o_q = o_items + up(8 * b.items.size()),
+               o_items = o_npad + up(4 * S), o_grp = o_items + up(8 * b.items.size()),
+               o_sbox = o_grp + up(16 * b.groups.size()), o_q = o_sbox + up(24 * S),
                total = o_q + up(4 * (size_t)n_queues);
   CK(c->bmeta.ensure(total), "workspace");
   char* base = c->bmeta.as<char>();
@@ -320,6 +337,7 @@ gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
   memcpy(h.data() + o_poff, b.poff.data(), 8 * S);
   memcpy(h.data() + o_npad, b.npad.data(), 4 * S);
   memcpy(h.data() + o_items, b.items.data(), 8 * b.items.size());
+  memcpy(h.data() + o_grp, b.groups.data(), 16 * b.groups.size());
   // synchronous copy: `h` is freed on return
   CK(cudaStreamSynchronize(st), "stream synchronize");
   CK(cudaMemcpy(base, h.data(), o_q, cudaMemcpyHostToDevice), "layout upload");
@@ -332,6 +350,8 @@ gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
   b.dev.centers = reinterpret_cast<const double*>(base + o_cen);
   b.dev.queue = nullptr;
   b.E = reinterpret_cast<double*>(base + o_E);
+  b.dgroups = b.groups.empty() ? nullptr : reinterpret_cast<const int4*>(base + o_grp);
+  b.sbox = reinterpret_cast<float*>(base + o_sbox);
   b.queues = reinterpret_cast<int*>(base + o_q);
   b.n_queues = n_queues;
   b.next_queue = 0;
@@ -434,8 +454,10 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     CK(c->abpacks.ensure(ab), "workspace");
     if ((ps = pad_packs(S, c->abpacks.as<float4>(), 2)) != GS_OK) return ps;
   }
-  if (batch) {
-    if (S.mode != GS_EXACT) return fail(c, GS_ERR_INVALID_ARG, "internal: batched layout needs GS_EXACT");
+  if (batch && batch->padded != (S.mode == GS_EXACT))
+    return fail(c, GS_ERR_INVALID_ARG, "internal: batch layout does not match the mode");
+  if (S.mode == GS_EXACT && batch) {
+    // persistent kernels: no split partials
   } else if (S.mode == GS_EXACT) {
     int J = std::max(S.gf.J, S.ga.J);
     CK(c->part.ensure((size_t)J * 15 * S.Npad * sizeof(float2)), "workspace");
@@ -446,7 +468,8 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     }
     CK(cudaMemsetAsync(c->tickets.p, 0, tn * sizeof(unsigned), st), "memset");
   } else {
-    gs_status s = tree_reserve(c->tree, N, tree_slots, st);
+    gs_status s =
+        tree_reserve(c->tree, N, tree_slots, st, batch ? (int64_t)batch->groups.size() : 0);
     if (s != GS_OK) return fail(c, s, "Barnes-Hut workspace allocation failed");
   }
   return GS_OK;
@@ -460,7 +483,8 @@ gs_status solver_pack(Solver& S, int slot) {
   if (S.batch) {
     const Batch& b = *S.batch;
     CK(launch_batch_pack(c->q.as<double>(), c->p.as<double>(), S.N, b.dev.off, b.dev.poff, b.S,
-                         b.dev.centers, S.s, S.pack(slot), S.st),
+                         b.dev.centers, S.s, S.pack(slot),
+                         S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
        "pack");
     return GS_OK;
   }
@@ -484,6 +508,21 @@ gs_status solver_load(Solver& S, const double* q0, const double* p0, int slot) {
   return solver_pack(S, slot);
 }
 
+// The forest of a Barnes-Hut batch (S = 0: one point set).
+BHForest bh_forest(const Solver& S) {
+  BHForest f;
+  if (S.batch) {
+    const Batch& b = *S.batch;
+    f.S = b.S;
+    f.off = b.dev.off;
+    f.groups = b.dgroups;
+    f.G = (int)b.groups.size();
+    f.sbox = b.sbox;
+    f.centers = b.dev.centers;
+  }
+  return f;
+}
+
 FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
   FwdEpi e{};
   e.q = S.c->q.as<double>();
@@ -502,7 +541,7 @@ FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
 // (Barnes-Hut: tree and interaction lists built in tree slot `tslot`).
 gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int tslot = 0) {
   gs_ctx* c = S.c;
-  if (S.batch) {
+  if (S.batch && S.mode == GS_EXACT) {
     Batch& bt = *const_cast<Batch*>(S.batch);
     BatchInfo bi;
     gs_status qs = batch_take_queue(c, bt, &bi);
@@ -523,7 +562,7 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S)};
   gs_status s;
   {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -561,7 +600,7 @@ AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) 
 gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* counts,
                       int tslot = 0, bool reuse = false) {
   gs_ctx* c = S.c;
-  if (S.batch) {
+  if (S.batch && S.mode == GS_EXACT) {
     Batch& bt = *const_cast<Batch*>(S.batch);
     BatchInfo bi;
     gs_status qs = batch_take_queue(c, bt, &bi);
@@ -582,7 +621,7 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S)};
   gs_status s;
   if (reuse) {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -891,7 +930,7 @@ gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const d
   gs_status s;
   if ((s = check_params(c, prm, true))) return s;
   Batch b;
-  if ((s = batch_plan(c, S, offsets, b))) return s;
+  if ((s = batch_plan(c, S, offsets, prm->mode == GS_EXACT, b))) return s;
   const int64_t N = b.N;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -908,23 +947,9 @@ gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const d
   if ((s = batch_upload(c, b, prm->mode == GS_EXACT ? 3 * T + 2 : 0, st))) return s;
   CK(c->bout.ensure(b3), "workspace");
   double* dgrad = c->bout.as<double>();
-  if (prm->mode == GS_EXACT) {
-    if ((s = run_grad(c, N, dq0, dp0, dX, prm, &b, b.E, dgrad, nullptr, st))) return s;
-  } else {
-    // Barnes-Hut: one subject after another (largest first, so that the
-    // workspace is sized once), each with its own tree per step
-    std::vector<int> order(S);
-    for (int k = 0; k < S; k++) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      return b.off[x + 1] - b.off[x] > b.off[y + 1] - b.off[y];
-    });
-    for (int k : order) {
-      const int64_t o = b.off[k], n = b.off[k + 1] - o;
-      if ((s = run_grad(c, n, dq0 + 3 * o, dp0 + 3 * o, dX + 3 * o, prm, nullptr, b.E + 3 * k,
-                        dgrad + 3 * o, nullptr, st)))
-        return s;
-    }
-  }
+  // exact: persistent launches over (subject, tile) items; Barnes-Hut: one
+  // forest of all subjects per step
+  if ((s = run_grad(c, N, dq0, dp0, dX, prm, &b, b.E, dgrad, nullptr, st))) return s;
   CK(launch_check_finite(b.E, 3 * (int64_t)S, c->d_status, st), "check");
   CK(launch_check_finite(dgrad, N * 3, c->d_status, st), "check");
   if ((s = copy_out(c, E, b.E, 3 * (size_t)S * sizeof(double), st))) return s;

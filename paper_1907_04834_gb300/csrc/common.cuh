@@ -135,6 +135,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// Subject of row i in a set of subjects with offsets off[0..S]: the last s
+// with off[s] <= i.
+__device__ __forceinline__ int subject_of(const int64_t* off, int S, int64_t i) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---------------------------------------------------------------- packing
 // Pair layout of the per-step source arrays ("packs"): point pair m = j/2
 // occupies 3 float4 = {x0,x1,y0,y1}, {z0,z1,u0,u1}, {v0,v1,w0,w1}, where

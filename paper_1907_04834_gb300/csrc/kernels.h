@@ -57,10 +57,11 @@ cudaError_t launch_batched_adj(const float4* pk, const float4* ab, const BatchIn
 // centers[s] = bounding-box centre of subject s (one block per subject)
 cudaError_t launch_batch_centers(const double* q, const int64_t* off, int S, double* centers,
                                  cudaStream_t st);
-// pack entries of every subject (and zero padding in `slots` consecutive packs)
+// pack entries of every subject (raw: NULL or FP32 positions at the same
+// entries)
 cudaError_t launch_batch_pack(const double* q, const double* p, int64_t N, const int64_t* off,
                               const int64_t* poff, int S, const double* centers, double s,
-                              float4* pack, cudaStream_t st);
+                              float4* pack, float4* raw, cudaStream_t st);
 cudaError_t launch_batch_pad_zero(float4* base, size_t slot_f4, int slots, const int64_t* off,
                                   const int64_t* poff, const int* npad, int S, cudaStream_t st);
 // alpha = 2 lambda (q - X), beta = 0, adjoint pack; r2[i] = |q_i - X_i|^2

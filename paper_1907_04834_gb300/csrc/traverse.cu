@@ -50,11 +50,12 @@ struct Own {
   float4 m0, m1, m2, m3;  // record: xs, p, a, b
 };
 
-__device__ __forceinline__ Own load_own(const TreeArrays& t, int N, int g, int lane, bool adj) {
+__device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi, int lane,
+                                        bool adj) {
   Own w;
-  w.i = g * 32 + lane;
-  w.valid = w.i < N;
-  const int ii = w.valid ? w.i : N - 1;
+  w.i = gi.first + lane;
+  w.valid = lane < gi.count;
+  const int ii = w.valid ? w.i : gi.first;
   w.o = (int)t.perm[ii];
   const int leaf = ii + (int)t.offs[ii + 1];
   w.m0 = t.nrec[4 * leaf];
@@ -68,26 +69,23 @@ __device__ __forceinline__ Own load_own(const TreeArrays& t, int N, int g, int l
   return w;
 }
 
-// Slices of the node range for group g: [0, L-D), [L-D, L), [L, L+D),
-// [L+D, M) where L is the leaf of the group's middle point and
-// D = clamp(M / 32, 256, 4096).  Any cut points give the same interactions;
-// these spread a group's work over four warps.  D depends only on the
-// current tree, so results are reproducible.
-__device__ __forceinline__ int slice_start(const TreeArrays& t, const BHLists& L, int N, int g,
-                                           int k) {
-  if (k == 0) return 0;
-  const int i = min(g * 32 + 16, N - 1);
+// Slices of the group's node range [nb, ne): [nb, L-D), [L-D, L), [L, L+D),
+// [L+D, ne) (clamped to the range) where L is the leaf of the group's middle
+// point and D = clamp((ne - nb) / 32, 256, 4096).  Any cut points give the
+// same interactions; these spread a group's work over four warps.  D depends
+// only on the current tree, so results are reproducible.
+__device__ __forceinline__ int slice_start(const TreeArrays& t, const GroupInfo& gi, int k) {
+  if (k == 0) return gi.nb;
+  const int i = gi.first + min(16, gi.count - 1);
   const int mid = i + (int)t.offs[i + 1];
-  const int M = total_nodes(t, N);
-  const int D = min(max(M >> 5, 256), 4096);
-  if (k == 1) return max(0, mid - D);
+  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096);
+  if (k == 1) return max(gi.nb, mid - D);
   if (k == 2) return mid;
-  return min(M, mid + D);
+  return min(gi.ne, mid + D);
 }
 
-__device__ __forceinline__ int slice_end(const TreeArrays& t, const BHLists& L, int N, int g,
-                                         int k) {
-  return k == BH_SLICES - 1 ? total_nodes(t, N) : slice_start(t, L, N, g, k + 1);
+__device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& gi, int k) {
+  return k == BH_SLICES - 1 ? gi.ne : slice_start(t, gi, k + 1);
 }
 
 // Resume point of this lane at node s: test the ancestors of s from the root
@@ -378,21 +376,21 @@ struct ListSink {
 template <bool COUNT>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-              int64_t* counts) {
+              WalkGroups wg, int64_t* counts) {
   __shared__ float4 s_box[TR_WARPS][32][2];
   __shared__ int2 s_ent[TR_WARPS][BH_CHUNK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * TR_WARPS + w;
-  const int G = (N + 31) / 32;
-  if (l >= G * BH_SLICES) return;
+  if (l >= wg.G * BH_SLICES) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
-  const int i = g * 32 + lane;
-  const bool valid = i < N;
-  const float4 rr = raw[(int)t.perm[valid ? i : N - 1]];
-  int x = slice_start(t, L, N, g, k);
-  const int end = slice_end(t, L, N, g, k);
+  const GroupInfo gi = group_info(t, N, wg.groups, g);
+  const bool valid = lane < gi.count;
+  const float4 rr = raw[(int)t.perm[gi.first + (valid ? lane : 0)]];
+  int x = slice_start(t, gi, k);
+  const int end = slice_end(t, gi, k);
   int resume = valid ? 0 : INT_MAX;
-  if (k > 0 && valid) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
+  // (an empty slice may start at the node count: no node to test there)
+  if (k > 0 && valid && x < end) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
   bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
@@ -413,7 +411,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // One warp per list: partial sums of its entries, part[(l*NC + c)*32 + lane].
 template <bool ADJ>
 __global__ void __launch_bounds__(TR_WARPS * 32)
-    k_bh_eval(TreeArrays t, int N, BHLists L) {
+    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg) {
   constexpr int NR = ADJ ? 12 : 6;
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
@@ -421,10 +419,9 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * TR_WARPS + w;
-  const int G = (N + 31) / 32;
-  if (l >= G * BH_SLICES) return;
+  if (l >= wg.G * BH_SLICES) return;
   if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
-  const Own me = load_own(t, N, l / BH_SLICES, lane, ADJ);
+  const Own me = load_own(t, group_info(t, N, wg.groups, l / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
   A.zero();
   const int n = L.len[l];
@@ -490,7 +487,7 @@ struct EvalSink {
 template <bool ADJ, bool COUNT>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-                  int64_t* counts) {
+                  WalkGroups wg, int64_t* counts) {
   constexpr int NR = ADJ ? 12 : 6;
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ float4 s_box[TR_WARPS][32][2];
@@ -499,16 +496,16 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int l = blockIdx.x * TR_WARPS + w;
-  const int G = (N + 31) / 32;
-  if (l >= G * BH_SLICES) return;
+  if (l >= wg.G * BH_SLICES) return;
   if (L.ovf_x[l] < 0) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
-  const Own me = load_own(t, N, g, lane, ADJ);
+  const GroupInfo gi = group_info(t, N, wg.groups, g);
+  const Own me = load_own(t, gi, lane, ADJ);
   const float4 rr = raw[me.o];
-  int x = slice_start(t, L, N, g, k);
-  const int end = slice_end(t, L, N, g, k);
+  int x = slice_start(t, gi, k);
+  const int end = slice_end(t, gi, k);
   int resume = me.valid ? 0 : INT_MAX;
-  if (k > 0 && me.valid) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
+  if (k > 0 && me.valid && x < end) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane};
@@ -527,11 +524,15 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // Per point: the slices' partial sums (and resumed parts) in a fixed order,
 // then the epilogue.
 template <bool ADJ>
-__global__ void k_bh_combine(TreeArrays t, int N, BHLists L, FwdEpi fe, AdjEpi ae) {
+__global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdEpi fe,
+                             AdjEpi ae) {
   constexpr int NC = Acc<ADJ>::NC;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int g = i >> 5, lane = i & 31;
+  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = gl >> 5, lane = gl & 31;
+  if (g >= wg.G) return;
+  const GroupInfo gi = group_info(t, N, wg.groups, g);
+  if (lane >= gi.count) return;
+  const int i = gi.first + lane;
   double acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; c++) acc[c] = 0.0;
@@ -545,42 +546,51 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, FwdEpi fe, AdjEpi a
     }
   }
   const int o = (int)t.perm[i];
-  if constexpr (!ADJ) fwd_epilogue(o, acc, acc + 3, fe);
-  else adj_epilogue(o, acc, acc + 3, acc + 6, acc + 9, acc + 12, ae);
+  if constexpr (!ADJ) {
+    // a forest's subjects have their own recentring points
+    const double* c = wg.centers ? wg.centers + 3 * subject_of(wg.off, wg.S, o) : fe.center;
+    fwd_epilogue_at(o, o, c, acc, acc + 3, fe);
+  } else {
+    adj_epilogue(o, acc, acc + 3, acc + 6, acc + 9, acc + 12, ae);
+  }
 }
 
-inline unsigned list_blocks(int N) {
-  const int lists = (N + 31) / 32 * BH_SLICES;
+inline unsigned list_blocks(int G) {
+  const int lists = G * BH_SLICES;
   return (unsigned)((lists + TR_WARPS - 1) / TR_WARPS);
 }
 
 }  // namespace
 
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
-                           const BHLists& L, int64_t* counts, cudaStream_t st) {
-  if (counts) k_bh_walk<true><<<list_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
-  else k_bh_walk<false><<<list_blocks(N), TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
+                           const BHLists& L, const WalkGroups& wg, int64_t* counts,
+                           cudaStream_t st) {
+  const unsigned nb = list_blocks(wg.G);
+  if (counts) k_bh_walk<true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  else k_bh_walk<false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   note_launches(1);
   return cudaGetLastError();
 }
 
 template <bool ADJ>
 static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr,
-                        const BHLists& L, const FwdEpi& fe, const AdjEpi& ae, int64_t* counts,
-                        cudaStream_t st) {
-  const unsigned nb = list_blocks(N);
-  const unsigned nc = (unsigned)((N + 255) / 256);
-  if (counts) k_bh_fallback<ADJ, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
-  else k_bh_fallback<ADJ, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, counts);
-  k_bh_eval<ADJ><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L);
-  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, fe, ae);
+                        const BHLists& L, const WalkGroups& wg, const FwdEpi& fe,
+                        const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+  const unsigned nb = list_blocks(wg.G);
+  const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
+  if (counts)
+    k_bh_fallback<ADJ, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  else
+    k_bh_fallback<ADJ, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  k_bh_eval<ADJ><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg);
+  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae);
 }
 
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
-                           const BHLists& L, bool adj, const FwdEpi& fe, const AdjEpi& ae,
-                           int64_t* counts, cudaStream_t st) {
-  if (!adj) eval_launch<false>(t, N, raw, thr, L, fe, ae, counts, st);
-  else eval_launch<true>(t, N, raw, thr, L, fe, ae, counts, st);
+                           const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
+                           const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+  if (!adj) eval_launch<false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+  else eval_launch<true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
   note_launches(3);
   return cudaGetLastError();
 }

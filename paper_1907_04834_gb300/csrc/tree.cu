@@ -14,6 +14,12 @@
 // The paper inserts points one at a time into a pointer tree; the node set,
 // the members of every node and the depth-first order are the same here (the
 // tests compare them bit for bit with the oracle's insertion tree).
+//
+// A forest of independent point sets (subjects) is built in the same passes:
+// each subject is quantised in its own bounding box, the sort key is
+// (subject, code) (extra radix passes over the subject index), and two
+// sorted points of different subjects share no cell, so every subject's tree
+// is the one it would have alone, placed in a contiguous preorder range.
 #include <algorithm>
 #include <cstdio>
 #include <utility>
@@ -117,6 +123,84 @@ __global__ void k_morton(const float4* __restrict__ raw, int N, const float* __r
   key[i] = c;
   perm[i] = (uint32_t)i;
   codes[i] = c;
+}
+
+// Forest: one block per subject, its FP32 bounding box into sbox[6 s ..].
+__global__ void k_bbox_subjects(const float4* __restrict__ raw, const int64_t* __restrict__ off,
+                                float* sbox) {
+  __shared__ float sh[6][kBBoxThreads / 32];
+  const int s = blockIdx.x;
+  const int a = (int)off[s], b = (int)off[s + 1];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const float4 r = raw[i];
+    lo[0] = fminf(lo[0], r.x);
+    lo[1] = fminf(lo[1], r.y);
+    lo[2] = fminf(lo[2], r.z);
+    hi[0] = fmaxf(hi[0], r.x);
+    hi[1] = fmaxf(hi[1], r.y);
+    hi[2] = fmaxf(hi[2], r.z);
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int k = 0; k < 3; k++) {
+      lo[k] = fminf(lo[k], __shfl_down_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_down_sync(0xffffffffu, hi[k], o));
+    }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; k++) {
+      sh[k][w] = lo[k];
+      sh[3 + k][w] = hi[k];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    float v = sh[k][0];
+    for (int m = 1; m < kBBoxThreads / 32; m++) v = k < 3 ? fminf(v, sh[k][m]) : fmaxf(v, sh[k][m]);
+    sbox[6 * s + k] = v;
+  }
+}
+
+// Forest: Morton code of every point in its subject's box.
+__global__ void k_morton_subjects(const float4* __restrict__ raw, int N,
+                                  const int64_t* __restrict__ off, int S,
+                                  const float* __restrict__ sbox, uint32_t* key, uint32_t* perm,
+                                  uint32_t* codes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float* box = sbox + 6 * subject_of(off, S, i);
+  const float4 r = raw[i];
+  float ext[3], inv[3];
+  for (int a = 0; a < 3; a++) {
+    ext[a] = __fsub_rn(box[3 + a], box[a]);
+    inv[a] = ext[a] > 0.f ? __fdiv_rn(1024.0f, ext[a]) : 0.f;
+  }
+  const uint32_t kx = quantise(r.x, box[0], ext[0], inv[0]);
+  const uint32_t ky = quantise(r.y, box[1], ext[1], inv[1]);
+  const uint32_t kz = quantise(r.z, box[2], ext[2], inv[2]);
+  const uint32_t c = (spread10(kx) << 2) | (spread10(ky) << 1) | spread10(kz);
+  key[i] = c;
+  perm[i] = (uint32_t)i;
+  codes[i] = c;
+}
+
+// Forest: subject index of each sorted point, the key of the subject passes.
+__global__ void k_subject_keys(const uint32_t* __restrict__ perm, int N,
+                               const int64_t* __restrict__ off, int S, uint32_t* skey) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) skey[i] = (uint32_t)subject_of(off, S, perm[i]);
+}
+
+// Forest, after the subject passes: sorted subjects, permutation and codes.
+__global__ void k_forest_finish(const uint32_t* skey, const uint32_t* sperm, int N,
+                                const uint32_t* __restrict__ codes, uint32_t* key,
+                                uint32_t* perm, uint32_t* ssub) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t s = skey[i], v = sperm[i];
+  ssub[i] = s;
+  perm[i] = v;
+  key[i] = codes[v];
 }
 
 // ---------------------------------------------------------------- scans
@@ -268,19 +352,30 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ key, const uint32_t* _
 }
 
 // ---------------------------------------------------------------- node list
-__device__ __forceinline__ int delta_at(const uint32_t* sk, int i) {
+// ss: NULL for one point set, else the subject of every sorted position;
+// points of different subjects share no cell (split "above" the root).
+
+// depth of the deepest cell holding sorted points i and i+1 (10: same code;
+// -1: different subjects)
+__device__ __forceinline__ int delta_at(const uint32_t* sk, const uint32_t* ss, int i) {
+  if (ss && ss[i] != ss[i + 1]) return -1;
   const uint32_t x = sk[i] ^ sk[i + 1];
   return x == 0u ? 10 : (__clz(x) - 2) / 3;
 }
 
-// smallest j <= i with sk[j] >> sh == sk[i] >> sh
-__device__ int gallop_left(const uint32_t* sk, int i, int sh) {
-  const uint32_t pre = sk[i] >> sh;
+__device__ __forceinline__ bool same_cell(const uint32_t* sk, const uint32_t* ss, int j,
+                                          uint32_t pre, uint32_t sub, int sh) {
+  return (sk[j] >> sh) == pre && (!ss || ss[j] == sub);
+}
+
+// smallest j <= i in the cell of sorted point i at shift sh
+__device__ int gallop_left(const uint32_t* sk, const uint32_t* ss, int i, int sh) {
+  const uint32_t pre = sk[i] >> sh, sub = ss ? ss[i] : 0u;
   int good = i, bad = -1, step = 1;
   while (true) {
     const int j = good - step;
     if (j < 0) break;
-    if ((sk[j] >> sh) == pre) {
+    if (same_cell(sk, ss, j, pre, sub, sh)) {
       good = j;
       step <<= 1;
     } else {
@@ -291,20 +386,20 @@ __device__ int gallop_left(const uint32_t* sk, int i, int sh) {
   int L = bad + 1, R = good;
   while (L < R) {
     const int mid = (L + R) >> 1;
-    if ((sk[mid] >> sh) == pre) R = mid;
+    if (same_cell(sk, ss, mid, pre, sub, sh)) R = mid;
     else L = mid + 1;
   }
   return L;
 }
 
-// largest j >= i with sk[j] >> sh == sk[i] >> sh
-__device__ int gallop_right(const uint32_t* sk, int i, int N, int sh) {
-  const uint32_t pre = sk[i] >> sh;
+// largest j >= i in the cell of sorted point i at shift sh
+__device__ int gallop_right(const uint32_t* sk, const uint32_t* ss, int i, int N, int sh) {
+  const uint32_t pre = sk[i] >> sh, sub = ss ? ss[i] : 0u;
   int good = i, bad = N, step = 1;
   while (true) {
     const int j = good + step;
     if (j >= N) break;
-    if ((sk[j] >> sh) == pre) {
+    if (same_cell(sk, ss, j, pre, sub, sh)) {
       good = j;
       step <<= 1;
     } else {
@@ -315,27 +410,31 @@ __device__ int gallop_right(const uint32_t* sk, int i, int N, int sh) {
   int L = good, R = bad - 1;
   while (L < R) {
     const int mid = (L + R + 1) >> 1;
-    if ((sk[mid] >> sh) == pre) L = mid;
+    if (same_cell(sk, ss, mid, pre, sub, sh)) L = mid;
     else R = mid - 1;
   }
   return L;
 }
 
 // Boundary i (between sorted i and i+1) owns the internal node of depth
-// D = delta_i that it is the first depth-D split of.
-__global__ void k_owners(const uint32_t* __restrict__ sk, int N, uint32_t* mask, int32_t* own_a,
-                         int32_t* own_b) {
+// D = delta_i that it is the first depth-D split of (none between subjects).
+__global__ void k_owners(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ ss, int N,
+                         uint32_t* mask, int32_t* own_a, int32_t* own_b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N - 1) return;
-  const int D = delta_at(sk, i);
+  const int D = delta_at(sk, ss, i);
+  if (D < 0) {
+    own_a[i] = -1;
+    return;
+  }
   const int sh = 30 - 3 * D;
-  const int a = gallop_left(sk, i, sh);
+  const int a = gallop_left(sk, ss, i, sh);
   bool owner;
   if (D == 10) owner = (a == i);
   else owner = (sk[a] >> (sh - 3)) == (sk[i] >> (sh - 3));
   if (owner) {
     own_a[i] = a;
-    own_b[i] = gallop_right(sk, i + 1, N, sh);
+    own_b[i] = gallop_right(sk, ss, i + 1, N, sh);
     atomicOr(&mask[a], 1u << D);
   } else {
     own_a[i] = -1;
@@ -348,17 +447,18 @@ __device__ __forceinline__ int node_id(const uint32_t* offs, const uint32_t* mas
 
 // parent of a node spanning sorted [a, b]: the cell of depth
 // max(delta_{a-1}, delta_b) that contains it (-1 when there is none)
-__device__ int parent_of(const uint32_t* sk, const uint32_t* offs, const uint32_t* mask, int N,
-                         int a, int b) {
+__device__ int parent_of(const uint32_t* sk, const uint32_t* ss, const uint32_t* offs,
+                         const uint32_t* mask, int N, int a, int b) {
   int Dp = -1;
-  if (a > 0) Dp = delta_at(sk, a - 1);
-  if (b < N - 1) Dp = max(Dp, delta_at(sk, b));
+  if (a > 0) Dp = delta_at(sk, ss, a - 1);
+  if (b < N - 1) Dp = max(Dp, delta_at(sk, ss, b));
   if (Dp < 0) return -1;
-  const int pa = gallop_left(sk, a, 30 - 3 * Dp);
+  const int pa = gallop_left(sk, ss, a, 30 - 3 * Dp);
   return node_id(offs, mask, pa, Dp);
 }
 
-__global__ void k_write_nodes(const uint32_t* __restrict__ sk, int N,
+__global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ ss,
+                              int N,
                               const uint32_t* __restrict__ mask, const uint32_t* __restrict__ offs,
                               const int32_t* __restrict__ own_a, const int32_t* __restrict__ own_b,
                               int2* nsc, int2* ninfo, int32_t* nparent, int32_t* acnt) {
@@ -368,15 +468,15 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, int N,
   const int leaf = i + (int)offs[i + 1];
   nsc[leaf] = make_int2(leaf + 1, 1);
   ninfo[leaf] = make_int2(-1, i);
-  nparent[leaf] = parent_of(sk, offs, mask, N, i, i);
+  nparent[leaf] = parent_of(sk, ss, offs, mask, N, i, i);
   acnt[leaf] = 0;
   // the internal node owned by boundary i
   if (i < N - 1 && own_a[i] >= 0) {
-    const int a = own_a[i], b = own_b[i], D = delta_at(sk, i);
+    const int a = own_a[i], b = own_b[i], D = delta_at(sk, ss, i);
     const int id = node_id(offs, mask, a, D);
     nsc[id] = make_int2(b + 1 + (int)offs[b + 1], b - a + 1);
     ninfo[id] = make_int2(D, a);
-    nparent[id] = parent_of(sk, offs, mask, N, a, b);
+    nparent[id] = parent_of(sk, ss, offs, mask, N, a, b);
     acnt[id] = 0;
   }
 }
@@ -466,12 +566,12 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
 // ---------------------------------------------------------------- layout
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-size_t n_lists(int64_t n) { return (size_t)((n + 31) / 32) * BH_SLICES; }
+size_t n_lists(int64_t groups) { return (size_t)groups * BH_SLICES; }
 
-// Shared scratch of one workspace (capacity n points, 2n + 2 nodes); with
-// mem == NULL only the size is computed.
-size_t carve_shared(void* mem, int64_t n, TreeArrays* t, BHLists* L) {
-  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(n);
+// Shared scratch of one workspace (capacity n points, 2n + 2 nodes, `groups`
+// walk groups); with mem == NULL only the size is computed.
+size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists* L) {
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(groups);
   const size_t nb_rs = nblocks(n, RS_TILE), nb_bb = kMaxBBoxBlocks;
   const size_t hist_n = 256 * nb_rs + 1;
   const size_t bsum_n = nblocks((int64_t)std::max<size_t>(hist_n, N1), SCAN_TILE) + 1;
@@ -482,7 +582,8 @@ size_t carve_shared(void* mem, int64_t n, TreeArrays* t, BHLists* L) {
     return at;
   };
   const size_t o_key = take(4 * N1), o_key2 = take(4 * N1), o_perm2 = take(4 * N1),
-               o_codes = take(4 * N1), o_mask = take(4 * N1), o_oa = take(4 * N1),
+               o_codes = take(4 * N1), o_ssub = take(4 * N1), o_mask = take(4 * N1),
+               o_oa = take(4 * N1),
                o_ob = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
                o_nrec = take(64 * M), o_ninfo = take(8 * M), o_acnt = take(4 * M),
@@ -495,6 +596,7 @@ size_t carve_shared(void* mem, int64_t n, TreeArrays* t, BHLists* L) {
     t->key_alt = (uint32_t*)(b + o_key2);
     t->perm_alt = (uint32_t*)(b + o_perm2);
     t->codes = (uint32_t*)(b + o_codes);
+    t->ssub = (uint32_t*)(b + o_ssub);
     t->mask = (uint32_t*)(b + o_mask);
     t->own_a = (int32_t*)(b + o_oa);
     t->own_b = (int32_t*)(b + o_ob);
@@ -515,8 +617,9 @@ size_t carve_shared(void* mem, int64_t n, TreeArrays* t, BHLists* L) {
 }
 
 // One step's tree and interaction lists (kept for the backward stage).
-size_t carve_slot(void* mem, int64_t n, int64_t chunks, TreeArrays* t, BHLists* L) {
-  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(n);
+size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArrays* t,
+                  BHLists* L) {
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(groups);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -552,33 +655,57 @@ size_t carve_slot(void* mem, int64_t n, int64_t chunks, TreeArrays* t, BHLists* 
     if (e_ != cudaSuccess) return e_;      \
   } while (0)
 
-// Steps 1-5 for one state.  abpack = NULL for the forward stage.
+// Steps 1-5 for one state (one point set, or the forest f).  abpack = NULL
+// for the forward stage.
 cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* pack,
-                  const float4* abpack, cudaStream_t st) {
-  const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
-  k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
-  k_morton<<<nblocks(N, 256), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb, t.key, t.perm,
-                                            t.codes, t.bbox);
+                  const float4* abpack, const BHForest& f, cudaStream_t st) {
+  int launches = 0;
+  if (f.S > 0) {
+    k_bbox_subjects<<<f.S, kBBoxThreads, 0, st>>>(raw, f.off, f.sbox);
+    k_morton_subjects<<<nblocks(N, 256), 256, 0, st>>>(raw, N, f.off, f.S, f.sbox, t.key, t.perm,
+                                                       t.codes);
+  } else {
+    const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
+    k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
+    k_morton<<<nblocks(N, 256), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb, t.key, t.perm,
+                                              t.codes, t.bbox);
+  }
+  launches += 2;
   TRY(cudaGetLastError());
   // radix sort, 4 passes of 8 bits (the 30-bit codes end in key/perm)
   const int nb = (int)nblocks(N, RS_TILE);
   uint32_t *k0 = t.key, *v0 = t.perm, *k1 = t.key_alt, *v1 = t.perm_alt;
-  for (int pass = 0; pass < 4; pass++) {
-    k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, N, 8 * pass, t.hist);
+  auto pass = [&](int shift) -> cudaError_t {
+    k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, N, shift, t.hist);
     TRY(scan(t.hist, 256 * nb, t.bsum, t.hscan, Ident(), st));
-    k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, N, 8 * pass, t.hscan, k1, v1);
-    TRY(cudaGetLastError());
+    k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, N, shift, t.hscan, k1, v1);
     std::swap(k0, k1);
     std::swap(v0, v1);
+    launches += 5;
+    return cudaGetLastError();
+  };
+  for (int p = 0; p < 4; p++) TRY(pass(8 * p));
+  // forest: stable passes over the subject index (most significant digits)
+  const uint32_t* ss = nullptr;
+  if (f.S > 1) {
+    k_subject_keys<<<nblocks(N, 256), 256, 0, st>>>(v0, N, f.off, f.S, k0);
+    launches++;
+    for (int shift = 0; ((uint32_t)(f.S - 1) >> shift) != 0u; shift += 8) TRY(pass(shift));
+    k_forest_finish<<<nblocks(N, 256), 256, 0, st>>>(k0, v0, N, t.codes, t.key, t.perm, t.ssub);
+    launches++;
+    ss = t.ssub;
   }
   // node list
   TRY(cudaMemsetAsync(t.mask, 0, sizeof(uint32_t) * (size_t)N, st));
-  if (N > 1) k_owners<<<nblocks(N - 1, 256), 256, 0, st>>>(t.key, N, t.mask, t.own_a, t.own_b);
+  if (N > 1) {
+    k_owners<<<nblocks(N - 1, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.own_a, t.own_b);
+    launches++;
+  }
   TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
-  k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, N, t.mask, t.offs, t.own_a, t.own_b,
+  k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.offs, t.own_a, t.own_b,
                                                  t.nsc, t.ninfo, t.nparent, t.acnt);
   k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack, true);
-  note_launches(2 + 4 * 5 + (N > 1 ? 1 : 0) + 3 + 2);
+  note_launches(launches + 3 + 2);
   return cudaGetLastError();
 }
 
@@ -594,8 +721,24 @@ constexpr int64_t kEntriesPerPoint = 512;  // pool per slot: entries per point a
 void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
   *t = TreeArrays{};
   *L = BHLists{};
-  carve_shared(w.mem, w.cap_n, t, L);
-  carve_slot(static_cast<char*>(w.smem) + (size_t)slot * w.slot_bytes, w.cap_n, w.lcap, t, L);
+  carve_shared(w.mem, w.cap_n, w.cap_groups, t, L);
+  carve_slot(static_cast<char*>(w.smem) + (size_t)slot * w.slot_bytes, w.cap_n, w.cap_groups,
+             w.lcap, t, L);
+}
+
+// Walk groups of a step: the forest's table, or 32-point groups of one set.
+WalkGroups walk_groups(const BHStep& b) {
+  WalkGroups g{};
+  if (b.f.S > 0) {
+    g.groups = b.f.groups;
+    g.G = b.f.G;
+    g.off = b.f.off;
+    g.S = b.f.S;
+    g.centers = b.f.centers;
+  } else {
+    g.G = (int)((b.N + 31) / 32);
+  }
+  return g;
 }
 }  // namespace
 
@@ -607,8 +750,8 @@ cudaError_t tree_setup() { return cudaSuccess; }
 // at least kMinChunksPerList chunks per list.
 // The pool size only decides how many slices take the slower re-walk path,
 // never the results.
-static int64_t pool_chunks(const TreeWork& w, int64_t N, int slots) {
-  const int64_t nl = (int64_t)n_lists(N);
+static int64_t pool_chunks(const TreeWork& w, int64_t N, int64_t groups, int slots) {
+  const int64_t nl = (int64_t)n_lists(groups);
   if (w.lcap_req > 0) return std::max<int64_t>(1, nl * w.lcap_req / BH_CHUNK);
   size_t budget = kListBudget;
   size_t fr = 0, tot = 0;
@@ -620,19 +763,23 @@ static int64_t pool_chunks(const TreeWork& w, int64_t N, int slots) {
   return std::max(per_slot, nl * kMinChunksPerList);
 }
 
-gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st) {
+gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st, int64_t groups) {
   (void)st;
   if (N > (int64_t(1) << 30)) return GS_ERR_INVALID_ARG;
   slots = std::max(slots, 1);
-  if (w.mem && w.cap_n >= N && w.nslots >= slots && w.lcap_req == w.lcap_from_req) return GS_OK;
+  groups = std::max(groups, (N + 31) / 32);
+  if (w.mem && w.cap_n >= N && w.cap_groups >= groups && w.nslots >= slots &&
+      w.lcap_req == w.lcap_from_req)
+    return GS_OK;
   N = std::max<int64_t>(N, w.cap_n);
+  groups = std::max<int64_t>(groups, w.cap_groups);
   slots = std::max(slots, w.nslots);
   tree_release(w);
-  const int64_t cap = pool_chunks(w, N, slots);
+  const int64_t cap = pool_chunks(w, N, groups, slots);
   TreeArrays t;
   BHLists L;
-  const size_t sb = carve_shared(nullptr, N, &t, &L);
-  const size_t slb = carve_slot(nullptr, N, cap, &t, &L);
+  const size_t sb = carve_shared(nullptr, N, groups, &t, &L);
+  const size_t slb = carve_slot(nullptr, N, groups, cap, &t, &L);
   if (cudaMalloc(&w.mem, sb) != cudaSuccess ||
       cudaMalloc(&w.smem, slb * (size_t)slots) != cudaSuccess) {
     cudaGetLastError();
@@ -643,6 +790,7 @@ gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st) {
   w.slot_bytes = slb;
   w.nslots = slots;
   w.cap_n = N;
+  w.cap_groups = groups;
   w.lcap = cap;
   w.lcap_from_req = w.lcap_req;
   views(w, 0, &t, &L);
@@ -656,6 +804,7 @@ void tree_release(TreeWork& w) {
   w.mem = nullptr;
   w.smem = nullptr;
   w.cap_n = 0;
+  w.cap_groups = 0;
   w.nslots = 0;
   w.d_counts = nullptr;
 }
@@ -676,7 +825,8 @@ gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero
   cudaError_t err;
   if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
     return cuda_err(err);
-  if ((err = build(t, (int)b.N, b.raw, b.pack, abpack, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = build(t, (int)b.N, b.raw, b.pack, abpack, b.f, st)) != cudaSuccess)
+    return cuda_err(err);
   return GS_OK;
 }
 
@@ -703,7 +853,8 @@ gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st) {
   views(w, b.slot, &t, &L);
   cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
   if (err == cudaSuccess)
-    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, counts ? t.counts : nullptr, st);
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), counts ? t.counts : nullptr,
+                         st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -712,8 +863,8 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, false, e, AdjEpi{},
-                                   counts ? t.counts : nullptr, st);
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), false, e,
+                                   AdjEpi{}, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -722,8 +873,8 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, true, FwdEpi{}, e,
-                                   counts ? t.counts : nullptr, st);
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), true, FwdEpi{},
+                                   e, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -758,7 +909,8 @@ gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_
   BHLists L;
   views(w, 0, &t, &L);
   cudaError_t err;
-  if ((err = build(t, (int)N, raw, pack, nullptr, st)) != cudaSuccess) return cuda_err(err);
+  if ((err = build(t, (int)N, raw, pack, nullptr, BHForest{}, st)) != cudaSuccess)
+    return cuda_err(err);
   uint32_t nint = 0;
   if ((err = cudaMemcpyAsync(&nint, t.offs + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) !=
           cudaSuccess ||

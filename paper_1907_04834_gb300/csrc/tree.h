@@ -19,14 +19,31 @@ struct TreeWork {
   size_t slot_bytes = 0;
   int nslots = 0;
   int64_t cap_n = 0;     // points it was sized for
+  int64_t cap_groups = 0; // walk groups it was sized for
   int64_t* d_counts = nullptr;  // interaction counters {point, node}
   int64_t lcap = 0;      // chunks in each slot's interaction-list pool
   int lcap_req = 0;      // requested entries per list (0 = budget-based pool)
   int lcap_from_req = 0; // the request the current allocation was made for
 };
 
+// Many independent point sets ("subjects") in one forest.  Subject s owns
+// points [off[s], off[s+1]) in the input order and, after the sort (by
+// subject, then Morton code), the same range of sorted positions; its own
+// octree (quantised in its own bounding box) is a contiguous preorder range,
+// and no node spans two subjects.  Walk groups hold up to 32 sorted points of
+// one subject: {first sorted position, count, off[s], off[s+1]}.
+struct BHForest {
+  int S = 0;                        // 0: one point set (no forest)
+  const int64_t* off = nullptr;     // S + 1 offsets (device)
+  const int4* groups = nullptr;     // G walk groups (device)
+  int G = 0;
+  float* sbox = nullptr;            // 6 S floats: per-subject bounding boxes
+  const double* centers = nullptr;  // S x 3 recentring points of the packs
+};
+
 // Inputs of one tree step: pack = scaled recentred FP32 positions and
-// momenta (pair layout), raw = FP32 positions {x, y, z, 0}.
+// momenta (pair layout, entry = input index), raw = FP32 positions
+// {x, y, z, 0}.
 struct BHStep {
   int slot;       // tree slot of this step
   int64_t N, Npad;
@@ -34,10 +51,12 @@ struct BHStep {
   float thr;      // far threshold r*r (FP32)
   const float4* pack;
   const float4* raw;
+  BHForest f;
 };
 
 cudaError_t tree_setup();
-gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st);
+// groups: walk groups to provide for (0: ceil(N / 32), one point set)
+gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st, int64_t groups = 0);
 void tree_release(TreeWork& w);
 // Builds the tree of one state (abpack = NULL in the forward stage).
 gs_status bh_build(TreeWork& w, const BHStep& b, const float4* abpack, bool zero_counts,

@@ -27,6 +27,7 @@ struct TreeArrays {
   uint32_t* key_alt;
   uint32_t* perm_alt;
   uint32_t* codes;  // Morton code per original index (before the sort)
+  uint32_t* ssub;   // forest: subject of each sorted position
   uint32_t* mask;   // bit D set: an internal node of depth D starts here
   uint32_t* offs;   // N + 1: exclusive prefix count of internal nodes
   int32_t* own_a;   // per boundary i (between sorted i, i+1): node start or -1
@@ -69,6 +70,30 @@ __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
   return N + (int)t.offs[N];
 }
 
+// A walk group: up to 32 consecutive sorted points of one point set, and the
+// preorder node range [nb, ne) of that set's tree.  groups == NULL: one point
+// set, group g = sorted points [32 g, 32 g + 32).
+struct GroupInfo {
+  int first, count, nb, ne;
+};
+__device__ __forceinline__ GroupInfo group_info(const TreeArrays& t, int N, const int4* groups,
+                                                int g) {
+  GroupInfo gi;
+  if (!groups) {
+    gi.first = g * 32;
+    gi.count = min(32, N - gi.first);
+    gi.nb = 0;
+    gi.ne = total_nodes(t, N);
+  } else {
+    const int4 v = groups[g];
+    gi.first = v.x;
+    gi.count = v.y;
+    gi.nb = v.z + (int)t.offs[v.z];
+    gi.ne = v.w + (int)t.offs[v.w];
+  }
+  return gi;
+}
+
 // FP32 distance-squared from a point to an axis-aligned box, no contraction:
 // dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4& lo,
@@ -79,12 +104,23 @@ __device__ __forceinline__ float box_dist2(float x, float y, float z, const floa
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+// Walk groups and, for a forest, the per-subject recentring points used by
+// the forward epilogue.
+struct WalkGroups {
+  const int4* groups;      // NULL: one point set
+  int G;                   // number of groups
+  const int64_t* off;      // forest: S + 1 offsets
+  int S;
+  const double* centers;   // forest: S x 3
+};
+
 // counts: NULL or 2 int64 accumulating {point, node} interactions
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
-                           const BHLists& L, int64_t* counts, cudaStream_t st);
+                           const BHLists& L, const WalkGroups& wg, int64_t* counts,
+                           cudaStream_t st);
 // fallback for overflowed lists, evaluation, fixed-order combine + epilogue
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
-                           const BHLists& L, bool adj, const FwdEpi& fe, const AdjEpi& ae,
-                           int64_t* counts, cudaStream_t st);
+                           const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
+                           const AdjEpi& ae, int64_t* counts, cudaStream_t st);
 
 }  // namespace gs

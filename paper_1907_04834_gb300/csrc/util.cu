@@ -129,17 +129,6 @@ __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* sta
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
-// subject of row i: the last s with off[s] <= i
-__device__ __forceinline__ int subject_of(const int64_t* off, int S, int64_t i) {
-  int lo = 0, hi = S - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= i) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // one block per subject: centre of its bounding box
 __global__ void k_batch_centers(const double* __restrict__ q, const int64_t* __restrict__ off,
                                 double* centers) {
@@ -178,12 +167,15 @@ __global__ void k_batch_centers(const double* __restrict__ q, const int64_t* __r
 __global__ void k_batch_pack(const double* __restrict__ q, const double* __restrict__ p,
                              int64_t N, const int64_t* __restrict__ off,
                              const int64_t* __restrict__ poff, int S,
-                             const double* __restrict__ centers, double sc, float4* pack) {
+                             const double* __restrict__ centers, double sc, float4* pack,
+                             float4* raw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int s = subject_of(off, S, i);
   const PackScale ps{centers[3 * s], centers[3 * s + 1], centers[3 * s + 2], sc};
-  pack_state(pack, poff[s] + (i - off[s]), q + 3 * i, p + 3 * i, ps);
+  const int64_t e = poff[s] + (i - off[s]);
+  pack_state(pack, e, q + 3 * i, p + 3 * i, ps);
+  if (raw) raw[e] = make_float4((float)q[3 * i], (float)q[3 * i + 1], (float)q[3 * i + 2], 0.f);
 }
 
 // one block per (subject, pack slot): zero the subject's padding entries
@@ -253,8 +245,8 @@ cudaError_t launch_batch_centers(const double* q, const int64_t* off, int S, dou
 
 cudaError_t launch_batch_pack(const double* q, const double* p, int64_t N, const int64_t* off,
                               const int64_t* poff, int S, const double* centers, double s,
-                              float4* pack, cudaStream_t st) {
-  k_batch_pack<<<blocks_for(N, 256), 256, 0, st>>>(q, p, N, off, poff, S, centers, s, pack);
+                              float4* pack, float4* raw, cudaStream_t st) {
+  k_batch_pack<<<blocks_for(N, 256), 256, 0, st>>>(q, p, N, off, poff, S, centers, s, pack, raw);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -3,7 +3,9 @@ subject's objective and gradient against the FP64 oracle run on that subject
 alone (points interact only within their subject), through the C ABI.
 
 The exact path runs one persistent launch per step over (subject, target
-tile) work items; the Barnes-Hut path runs the subjects one after another.
+tile) work items; the Barnes-Hut path builds one forest of all subjects per
+step, in which every subject's tree, decisions and sums are those it would
+have alone (checked bit for bit against single-set calls).
 Tolerances as for one point set: gradient relative L2 <= 1e-4, E to 1e-6."""
 import numpy as np
 import pytest
@@ -90,6 +92,34 @@ def test_batched_bh_equals_single_subject_calls():
     for k, w in enumerate(ws):
         Ek, gk, _ = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), 2.0, 4, w.lam, mode="bh")
         assert torch.equal(E[k], Ek) and torch.equal(g[off[k]:off[k + 1]], gk), k
+
+
+def test_batched_bh_forest_overlapping_subjects():
+    """Subjects that overlap in space (same region, different clouds) still
+    interact only within themselves: forest result == single-set calls."""
+    ws = [inputs.make("blobs", n, 50 + n, T=3) for n in (1200, 900, 1)]
+    q0, p0, X, off = _stack(ws)
+    E, g = gs.shoot_batched(dt(q0), dt(p0), dt(X), off, ws[0].sigma, 3, 1.0, mode="bh")
+    for k, w in enumerate(ws):
+        Ek, gk, _ = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), w.sigma, 3, 1.0, mode="bh")
+        assert torch.equal(E[k], Ek) and torch.equal(g[off[k]:off[k + 1]], gk), k
+
+
+@pytest.mark.parametrize("mode", ["exact", "bh"])
+def test_batched_many_small_subjects(oracle, mode):
+    """300 subjects of 1-60 points (the forest's sort takes two subject
+    passes), against the oracle subject by subject."""
+    rng = np.random.default_rng(77)
+    ws = [inputs.make("slab", int(n), 1000 + k, T=2, sigma=2.0)
+          for k, n in enumerate(rng.integers(1, 61, size=300))]
+    q0, p0, X, off = _stack(ws)
+    E, g = gs.shoot_batched(dt(q0), dt(p0), dt(X), off, 2.0, 2, 1.0, mode=mode)
+    E, g = npy(E), npy(g)
+    om = oracle.BH if mode == "bh" else oracle.EXACT
+    for k, w in enumerate(ws):
+        Eo, go, _ = oracle.shoot_grad(w.q0, w.p0, w.X, 2.0, 2, 1.0, mode=om)
+        assert rel_l2(g[off[k]:off[k + 1]], go) <= 1e-4, k
+        np.testing.assert_allclose(E[k], Eo, rtol=1e-6, err_msg=f"subject {k}")
 
 
 def test_batched_exact_close_to_single_subject_calls():
