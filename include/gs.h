@@ -126,6 +126,20 @@ gs_status gs_shoot_batched(gs_ctx *ctx, int32_t S, const int64_t *offsets,
                            const double *X, const gs_params *prm, double *E,
                            double *grad, void *stream);
 
+/*
+ * Fixed-step gradient descent on the initial momenta of S independent
+ * registrations (the batched driver; the paper optimises each subject with
+ * L-BFGS, Sec. 2.1): `iters` times, (E, grad) as gs_shoot_batched, then
+ * p0 <- p0 - step * grad.  p0 (offsets[S] x 3) is read and overwritten with
+ * the final momenta.  E_hist: NULL or iters x S x 3 doubles, the energies
+ * of each iteration before its update.  The per-iteration step loop is
+ * replayed from one captured CUDA graph (see gs_set_option "graphs").
+ */
+gs_status gs_descend_batched(gs_ctx *ctx, int32_t S, const int64_t *offsets,
+                             const double *q0, double *p0, const double *X,
+                             const gs_params *prm, double step, int32_t iters,
+                             double *E_hist, void *stream);
+
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
 
 /* One forward right-hand side at state (q, p): F, Phi as in Eq. 1 (GS_BH:
@@ -168,7 +182,13 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
  *   kept step); 0 = default (a budget of up to 24 GB, at most a quarter of
  *   the free memory, shared by the kept steps).  Slices whose lists do not
  *   fit are evaluated by a slower fused walk-and-evaluate pass that gives
- *   bit-identical results. */
+ *   bit-identical results.
+ *   "graphs": 1 (default) = gs_shoot, gs_shoot_grad, gs_shoot_batched and
+ *   gs_descend_batched capture their step loop (every launch between the
+ *   input staging and the result copies) into a CUDA graph the first time
+ *   they see a set of sizes, parameters and device addresses, and replay it
+ *   while those stay the same; 0 = launch kernel by kernel.  Graphs are not
+ *   used while gs_timing is on.  Results are identical either way. */
 gs_status gs_set_option(gs_ctx *ctx, const char *name, int64_t value);
 
 /* Kernel classes timed by gs_timing. */

@@ -150,6 +150,28 @@ def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.
     return E, grad
 
 
+def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, mode="exact",
+                    thresh=3.0, ckpt_every=0, stream=None):
+    """Fixed-step gradient descent on the subjects' initial momenta
+    (gs_descend_batched): ``iters`` times p0 <- p0 - step * dE/dp0.
+    Returns (p0 after the last update (N, 3), E history (iters, S, 3))."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
+    off = torch.as_tensor(offsets, dtype=torch.int64).cpu().contiguous()
+    S = off.numel() - 1
+    if S < 1 or int(off[-1]) != n:
+        raise ValueError("offsets must have S+1 entries ending at N")
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every)
+    p = p0.clone()
+    Eh = _like(q0, (int(iters), S, 3))
+    c.check(c.lib.gs_descend_batched(c.handle, S, _ptr(off), _ptr(q0), _ptr(p), _ptr(X),
+                                     ctypes.byref(prm), float(step), int(iters), _ptr(Eh),
+                                     _stream_ptr(c.device, stream)))
+    return p, Eh
+
+
 def rhs(q, p, sigma, mode="exact", thresh=3.0, stream=None):
     """One forward right-hand side: (F, Phi, (point pairs, node pairs))."""
     q = _pts(q, "q")

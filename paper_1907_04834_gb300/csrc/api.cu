@@ -66,7 +66,17 @@ struct gs_ctx {
   DevMem part, tickets;
   size_t tickets_n = 0;
   // many-subject calls: per-subject layout, queues, energies and gradients
-  DevMem bmeta, bout;
+  DevMem bmeta, bout, gd_p, gd_E;
+  std::vector<int64_t> bmeta_key;  // layout currently held by bmeta
+  // CUDA graphs of the step loops (one cached executable per entry point)
+  struct GraphCache {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;  // kernels per replay
+  };
+  GraphCache g_shoot, g_grad, g_batch;
+  cudaStream_t cap = nullptr;  // capture stream
+  bool graphs = true;
   TreeWork tree;  // Barnes-Hut workspace (tree.h)
 };
 
@@ -141,6 +151,69 @@ struct DeviceGuard {
     if (prev >= 0) cudaSetDevice(prev);
   }
 };
+
+// Identity of a captured step loop: sizes, parameters and every device
+// address the captured launches use.  A graph is replayed only for an equal
+// key; anything else is captured again.
+struct Key {
+  std::vector<unsigned char> b;
+  template <class T>
+  void add(const T& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    b.insert(b.end(), p, p + sizeof(T));
+  }
+  void params(const gs_params* prm) {
+    add(prm->sigma), add(prm->lambda), add(prm->thresh_sigmas);
+    add(prm->T), add(prm->mode), add(prm->ckpt_every), add(prm->flags);
+  }
+  void workspace(const gs_ctx* c) {
+    for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
+                            &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
+                            &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
+                            &c->gd_p})
+      add(m->p), add(m->bytes);
+    add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
+    add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
+  }
+};
+
+// Runs work(stream): directly, or (graphs on, timing off) as a CUDA graph
+// captured on the context's capture stream the first time a key is seen and
+// replayed on `st` afterwards.  Work must only enqueue (no allocation, no
+// synchronisation).
+template <class F>
+gs_status run_graphed(gs_ctx* c, gs_ctx::GraphCache& gc, const Key& k, cudaStream_t st, F&& work) {
+  if (!c->graphs || c->timing) return work(st);
+  if (!(gc.exec && gc.key == k.b)) {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+    gc.key.clear();
+    if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "stream create");
+    const long long l0 = launches_total();
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+    gs_status s = work(c->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    const int n = (int)(launches_total() - l0);
+    note_launches(-n);  // captured, not run
+    if (s != GS_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return s != GS_OK ? s : cuda_fail(c, e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      gc.exec = nullptr;
+      return cuda_fail(c, e, "graph instantiate");
+    }
+    gc.key = k.b;
+    gc.launches = n;
+  }
+  CK(cudaGraphLaunch(gc.exec, st), "graph launch");
+  note_launches(gc.launches);
+  return GS_OK;
+}
 
 gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
   if (!prm) return fail(c, GS_ERR_INVALID_ARG, "params is NULL");
@@ -321,7 +394,8 @@ gs_status batch_plan(gs_ctx* c, int32_t S, const int64_t* offsets, bool padded, 
   return GS_OK;
 }
 
-// Device copy of the layout, the energies and `n_queues` zeroed queue heads.
+// Device copy of the layout, the energies and `n_queues` queue heads (zeroed
+// by batch_zero_queues).  The copy is skipped when bmeta already holds it.
 gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t S = (size_t)b.S;
@@ -330,18 +404,25 @@ gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
                o_items = o_npad + up(4 * S), o_grp = o_items + up(8 * b.items.size()),
                o_sbox = o_grp + up(16 * b.groups.size()), o_q = o_sbox + up(24 * S),
                total = o_q + up(4 * (size_t)n_queues);
+  std::vector<int64_t> key(b.off);
+  key.push_back(b.padded);
+  key.push_back(n_queues);
+  key.push_back(c->num_sms);
+  const void* before = c->bmeta.p;
   CK(c->bmeta.ensure(total), "workspace");
   char* base = c->bmeta.as<char>();
-  std::vector<char> h(o_q);
-  memcpy(h.data() + o_off, b.off.data(), 8 * (S + 1));
-  memcpy(h.data() + o_poff, b.poff.data(), 8 * S);
-  memcpy(h.data() + o_npad, b.npad.data(), 4 * S);
-  memcpy(h.data() + o_items, b.items.data(), 8 * b.items.size());
-  memcpy(h.data() + o_grp, b.groups.data(), 16 * b.groups.size());
-  // synchronous copy: `h` is freed on return
-  CK(cudaStreamSynchronize(st), "stream synchronize");
-  CK(cudaMemcpy(base, h.data(), o_q, cudaMemcpyHostToDevice), "layout upload");
-  CK(cudaMemsetAsync(base + o_q, 0, 4 * (size_t)n_queues, st), "memset");
+  if (c->bmeta.p != before || key != c->bmeta_key) {
+    std::vector<char> h(o_q);
+    memcpy(h.data() + o_off, b.off.data(), 8 * (S + 1));
+    memcpy(h.data() + o_poff, b.poff.data(), 8 * S);
+    memcpy(h.data() + o_npad, b.npad.data(), 4 * S);
+    memcpy(h.data() + o_items, b.items.data(), 8 * b.items.size());
+    memcpy(h.data() + o_grp, b.groups.data(), 16 * b.groups.size());
+    // synchronous copy: `h` is freed on return
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    CK(cudaMemcpy(base, h.data(), o_q, cudaMemcpyHostToDevice), "layout upload");
+    c->bmeta_key = key;
+  }
   b.dev.items = reinterpret_cast<const int2*>(base + o_items);
   b.dev.n_items = (int)b.items.size();
   b.dev.off = reinterpret_cast<const int64_t*>(base + o_off);
@@ -357,6 +438,13 @@ gs_status batch_upload(gs_ctx* c, Batch& b, int n_queues, cudaStream_t st) {
   b.next_queue = 0;
   b.fwd_blocks = std::max(1, std::min(b.dev.n_items, c->num_sms * batched_resident_blocks(false)));
   b.adj_blocks = std::max(1, std::min(b.dev.n_items, c->num_sms * batched_resident_blocks(true)));
+  return GS_OK;
+}
+
+gs_status batch_zero_queues(gs_ctx* c, Batch& b, cudaStream_t st) {
+  b.next_queue = 0;
+  if (b.n_queues > 0)
+    CK(cudaMemsetAsync(b.queues, 0, sizeof(int) * (size_t)b.n_queues, st), "memset");
   return GS_OK;
 }
 
@@ -645,25 +733,48 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
 }
 
 // Objective and gradient (Eq. 2 and the discrete adjoint) of one point set
-// of N rows (batch NULL) or of every subject of `batch`.  Inputs are device
+// of N rows (batch NULL) or of every subject of `batch`: grad_setup sizes
+// the workspace (allocations, never captured), grad_enqueue enqueues the
+// whole forward and backward pass on `st` (capturable).  Inputs are device
 // arrays; E receives 3 doubles per subject, grad N x 3, q1 (optional) q(1).
-gs_status run_grad(gs_ctx* c, int64_t N, const double* dq0, const double* dp0, const double* dX,
-                   const gs_params* prm, Batch* batch, double* E, double* grad, double* q1,
-                   cudaStream_t st) {
-  gs_status s;
-  const int T = prm->T;
-  const int ck = prm->ckpt_every > 0 && prm->ckpt_every < T ? prm->ckpt_every : 0;
-  // pack slots: every step (store-all) or one segment (checkpointing)
-  const int slots = ck ? ck + 1 : T + 1;
+struct GradRun {
   Solver S;
+  Batch* batch = nullptr;
+  int T = 0, ck = 0, nck = 0;
+  double* ckq = nullptr;
+};
+
+gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, cudaStream_t st,
+                     GradRun& R) {
+  gs_status s;
+  R.batch = batch;
+  R.T = prm->T;
+  R.ck = prm->ckpt_every > 0 && prm->ckpt_every < R.T ? prm->ckpt_every : 0;
+  // pack slots: every step (store-all) or one segment (checkpointing)
+  const int slots = R.ck ? R.ck + 1 : R.T + 1;
   // Barnes-Hut: one tree slot per step kept for the backward stage (a
   // segment's steps with checkpointing)
-  const int tslots = prm->mode == GS_BH ? (ck ? ck : T) : 1;
-  if ((s = solver_init(c, S, N, prm, slots, true, st, tslots, batch))) return s;
+  const int tslots = prm->mode == GS_BH ? (R.ck ? R.ck : R.T) : 1;
+  if ((s = solver_init(c, R.S, N, prm, slots, true, st, tslots, batch))) return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  R.nck = R.ck ? (R.T + R.ck - 1) / R.ck : 0;
+  if (R.ck) CK(c->ckpt.ensure((size_t)R.nck * 2 * b3), "checkpoint allocation");
+  R.ckq = R.ck ? c->ckpt.as<double>() : nullptr;
+  return GS_OK;
+}
+
+gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const double* dX,
+                       double* E, double* grad, double* q1, cudaStream_t st) {
+  gs_status s;
+  Solver& S = R.S;
+  S.st = st;
+  gs_ctx* c = S.c;
+  Batch* batch = R.batch;
+  const int64_t N = S.N;
+  const int T = R.T, ck = R.ck, nck = R.nck;
+  double* ckq = R.ckq;
   const size_t n3 = (size_t)N * 3, b3 = n3 * sizeof(double);
-  const int nck = ck ? (T + ck - 1) / ck : 0;
-  if (ck) CK(c->ckpt.ensure((size_t)nck * 2 * b3), "checkpoint allocation");
-  double* ckq = ck ? c->ckpt.as<double>() : nullptr;
+  if (batch && (s = batch_zero_queues(c, *batch, st))) return s;
   if ((s = solver_load(S, dq0, dp0, 0))) return s;
 
   // ---- forward pass
@@ -733,6 +844,45 @@ gs_status run_grad(gs_ctx* c, int64_t N, const double* dq0, const double* dp0, c
   return GS_OK;
 }
 
+// Objective and gradient of every subject of b (layout uploaded): energies
+// into b.E, gradients into dgrad.
+gs_status batched_grad(gs_ctx* c, Batch& b, const double* dq0, const double* dp0,
+                       const double* dX, const gs_params* prm, double* dgrad, cudaStream_t st) {
+  gs_status s;
+  GradRun R;
+  if ((s = grad_setup(c, b.N, prm, &b, st, R))) return s;
+  Key k;
+  k.add(b.N), k.params(prm), k.add(dq0), k.add(dp0), k.add(dX), k.add(dgrad), k.workspace(c);
+  for (int64_t v : c->bmeta_key) k.add(v);
+  return run_graphed(c, c->g_batch, k, st, [&](cudaStream_t s2) {
+    return grad_enqueue(R, dq0, dp0, dX, b.E, dgrad, nullptr, s2);
+  });
+}
+
+// Forward shooting of one point set: state left in c->q, c->p; with H,
+// H(q0, p0) and H(q1, p1) in scal[SC_H0], scal[SC_H1] (capturable).
+gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
+                        cudaStream_t st) {
+  gs_status s;
+  gs_ctx* c = S.c;
+  S.st = st;
+  const int64_t N = S.N;
+  if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  for (int k = 0; k < S.T; k++) {
+    FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
+    if (k == 0 && H) e.pf_part = c->pf.as<double>();
+    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+    if (k == 0 && H) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+  }
+  if (H) {
+    FwdEpi e = fwd_epi(S, -1, 0.0);
+    e.pf_part = c->pf.as<double>();
+    if ((s = forward_rhs(S, S.T & 1, e, nullptr))) return s;
+    CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H1), st), "sum");
+  }
+  return GS_OK;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -774,8 +924,12 @@ void gs_destroy(gs_ctx* c) {
     cudaDeviceSynchronize();
     for (DevMem* m : {&c->in_q, &c->in_p, &c->in_a, &c->in_b, &c->in_X, &c->out_a, &c->out_b,
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
-                      &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout})
+                      &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
+                      &c->gd_p, &c->gd_E})
       m->release();
+    for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch})
+      if (gc->exec) cudaGraphExecDestroy(gc->exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
     tree_release(c->tree);
     for (auto& t : c->pending) {
       cudaEventDestroy(t.a);
@@ -795,6 +949,11 @@ gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
     if (value < 0 || value > (int64_t(1) << 24))
       return fail(c, GS_ERR_INVALID_ARG, "bh_list_cap must be in [0, 2^24]");
     c->tree.lcap_req = (int)value;
+    return GS_OK;
+  }
+  if (strcmp(name, "graphs") == 0) {
+    if (value != 0 && value != 1) return fail(c, GS_ERR_INVALID_ARG, "graphs must be 0 or 1");
+    c->graphs = value != 0;
     return GS_OK;
   }
   return fail(c, GS_ERR_INVALID_ARG, "unknown option '%s'", name);
@@ -858,18 +1017,14 @@ gs_status gs_shoot(gs_ctx* c, const double* q0, const double* p0, int64_t N,
     return s;
   Solver S;
   if ((s = solver_init(c, S, N, prm, 2, false, st))) return s;
-  if ((s = solver_load(S, dq0, dp0, 0))) return s;
-  for (int k = 0; k < S.T; k++) {
-    FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
-    if (k == 0 && H) e.pf_part = c->pf.as<double>();
-    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
-    if (k == 0 && H) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+  {
+    Key k;
+    k.add(N), k.params(prm), k.add(dq0), k.add(dp0), k.add(H != nullptr), k.workspace(c);
+    s = run_graphed(c, c->g_shoot, k, st,
+                    [&](cudaStream_t s2) { return shoot_enqueue(S, dq0, dp0, H != nullptr, s2); });
+    if (s) return s;
   }
   if (H) {
-    FwdEpi e = fwd_epi(S, -1, 0.0);
-    e.pf_part = c->pf.as<double>();
-    if ((s = forward_rhs(S, S.T & 1, e, nullptr))) return s;
-    CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H1), st), "sum");
     CK(launch_check_finite(S.scal(SC_H0), 2, c->d_status, st), "check");
     if ((s = copy_out(c, H, S.scal(SC_H0), 2 * sizeof(double), st))) return s;
   }
@@ -909,9 +1064,16 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
   CK(c->out_b.ensure(b3), "workspace");
   CK(c->scal.ensure(SC_N * 8), "workspace");
   double* dE = c->scal.as<double>() + SC_E;
-  if ((s = run_grad(c, N, dq0, dp0, dX, prm, nullptr, dE, c->out_a.as<double>(),
-                    q1 ? c->out_b.as<double>() : nullptr, st)))
-    return s;
+  GradRun R;
+  if ((s = grad_setup(c, N, prm, nullptr, st, R))) return s;
+  double* dgrad = c->out_a.as<double>();
+  double* dq1 = q1 ? c->out_b.as<double>() : nullptr;
+  Key k;
+  k.add(N), k.params(prm), k.add(dq0), k.add(dp0), k.add(dX), k.add(dq1), k.workspace(c);
+  s = run_graphed(c, c->g_grad, k, st, [&](cudaStream_t s2) {
+    return grad_enqueue(R, dq0, dp0, dX, dE, dgrad, dq1, s2);
+  });
+  if (s) return s;
   CK(launch_check_finite(dE, 3, c->d_status, st), "check");
   CK(launch_check_finite(c->out_a.as<double>(), N * 3, c->d_status, st), "check");
   if ((s = copy_out(c, E, dE, 3 * sizeof(double), st))) return s;
@@ -949,12 +1111,57 @@ gs_status gs_shoot_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const d
   double* dgrad = c->bout.as<double>();
   // exact: persistent launches over (subject, tile) items; Barnes-Hut: one
   // forest of all subjects per step
-  if ((s = run_grad(c, N, dq0, dp0, dX, prm, &b, b.E, dgrad, nullptr, st))) return s;
+  if ((s = batched_grad(c, b, dq0, dp0, dX, prm, dgrad, st))) return s;
   CK(launch_check_finite(b.E, 3 * (int64_t)S, c->d_status, st), "check");
   CK(launch_check_finite(dgrad, N * 3, c->d_status, st), "check");
   if ((s = copy_out(c, E, b.E, 3 * (size_t)S * sizeof(double), st))) return s;
   if ((s = copy_out(c, grad, dgrad, b3, st))) return s;
   if (hE || hg) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_descend_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const double* q0,
+                             double* p0, const double* X, const gs_params* prm, double step,
+                             int32_t iters, double* E_hist, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_params(c, prm, true))) return s;
+  if (!std::isfinite(step)) return fail(c, GS_ERR_INVALID_ARG, "step must be finite");
+  if (iters < 0 || iters > 1000000)
+    return fail(c, GS_ERR_INVALID_ARG, "iters must be in [0, 1e6] (got %d)", iters);
+  Batch b;
+  if ((s = batch_plan(c, S, offsets, prm->mode == GS_EXACT, b))) return s;
+  const int64_t N = b.N;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hp = false, hE = false;
+  if ((s = output(c, p0, "p0", &hp))) return s;
+  if (E_hist && (s = output(c, E_hist, "E_hist", &hE))) return s;
+  const double *dq0, *dX;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, X, (size_t)N * 3, "X", c->in_X, st, &dX)))
+    return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double), eb = 3 * (size_t)S * sizeof(double);
+  CK(c->gd_p.ensure(b3), "workspace");
+  CK(c->gd_E.ensure(std::max<size_t>(eb * (size_t)iters, 8)), "workspace");
+  CK(c->bout.ensure(b3), "workspace");
+  CK(cudaMemcpyAsync(c->gd_p.p, p0, b3, cudaMemcpyDefault, st), "p0 copy");
+  if ((s = batch_upload(c, b, prm->mode == GS_EXACT ? 3 * prm->T + 2 : 0, st))) return s;
+  double* dp = c->gd_p.as<double>();
+  double* dgrad = c->bout.as<double>();
+  for (int it = 0; it < iters; it++) {
+    if ((s = batched_grad(c, b, dq0, dp, dX, prm, dgrad, st))) return s;
+    CK(cudaMemcpyAsync(c->gd_E.as<char>() + eb * it, b.E, eb, cudaMemcpyDeviceToDevice, st),
+       "energy copy");
+    CK(launch_axpy(dp, dgrad, -step, N * 3, st), "update");
+  }
+  if (iters > 0) CK(launch_check_finite(c->gd_E.as<double>(), 3 * (int64_t)S * iters, c->d_status, st), "check");
+  CK(launch_check_finite(dp, N * 3, c->d_status, st), "check");
+  if ((s = copy_out(c, p0, dp, b3, st))) return s;
+  if (E_hist && iters > 0 && (s = copy_out(c, E_hist, c->gd_E.p, eb * iters, st))) return s;
+  if (hp || hE) return read_status(c, st);
   CK(cudaGetLastError(), "launch");
   return GS_OK;
 }

@@ -72,6 +72,8 @@ cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t 
 // out[s * stride] = scale * Sum over rows of subject s of x (fixed order)
 cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
                                double* out, int stride, cudaStream_t st);
+// y += a x (product rounded, then the sum: no fused multiply-add)
+cudaError_t launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 // E[s] = {H[s] + D[s], H[s], D[s]} from E[s*3+1] = H, E[s*3+2] = D
 cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st);
 

@@ -222,6 +222,11 @@ __global__ void k_segment_sum(const double* __restrict__ x, const int64_t* __res
   if (threadIdx.x == 0) out[(size_t)s * stride] = scale * v;
 }
 
+__global__ void k_axpy(double* y, const double* __restrict__ x, double a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __dadd_rn(y[i], __dmul_rn(a, x[i]));  // rounded product, then sum
+}
+
 __global__ void k_batch_energy(double* E, int S) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < S) E[3 * s] = E[3 * s + 1] + E[3 * s + 2];
@@ -272,6 +277,12 @@ cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t 
 cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
                                double* out, int stride, cudaStream_t st) {
   k_segment_sum<<<S, kRedThreads, 0, st>>>(x, off, scale, out, stride);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st) {
+  k_axpy<<<blocks_for(n, 256), 256, 0, st>>>(y, x, a, n);
   note_launches(1);
   return cudaGetLastError();
 }
