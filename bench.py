@@ -10,6 +10,12 @@ Barnes-Hut ms per gradient (the paper's method); the plain exact figure, the
 speed-up and pair-interaction rates ride along.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --batched [--steps K] [--warmup W]
+
+--batched measures the many-subject workload instead (64 bent-slab subjects,
+N log-uniform in [5000, 40000], sigma = 2 mm, T = 20): ms per gradient of all
+subjects for the batched exact and batched Barnes-Hut calls against plain
+per-subject exact calls, one JSON line.
 
 With --gpus N > 1 (launched by torch.distributed.run, one rank per GPU) each
 rank computes its own replica of the workload (the shooting of one point set
@@ -54,6 +60,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="measure the 64-subject batched workload (separate JSON line)")
     ap.add_argument("--probe", choices=["bh", "exact"],
                     help="for profiler captures: two rounds of one forward and one adjoint "
                          "right-hand side at the workload's initial state, then exit")
@@ -381,10 +389,66 @@ def run_probe(args):
     return 0
 
 
+def run_batched(args):
+    """64 slab subjects: batched exact, batched Barnes-Hut and plain
+    per-subject exact gradients, CUDA events around each call."""
+    import numpy as np
+    import torch
+    from paper_1907_04834_gb300 import native, inputs
+    native.build()
+    import paper_1907_04834_gb300 as gs
+    ws, off = inputs.batch()
+    dev = torch.device("cuda", 0)
+    cat = lambda k: torch.as_tensor(np.concatenate([getattr(w, k) for w in ws]), device=dev)
+    q0, p0, X = cat("q0"), cat("p0"), cat("X")
+    sig, T, lam = ws[0].sigma, ws[0].T, ws[0].lam
+    ns = np.diff(off)
+
+    def plain():
+        for k in range(len(ws)):
+            sl = slice(int(off[k]), int(off[k + 1]))
+            gs.shoot_grad(q0[sl], p0[sl], X[sl], sig, T, lam, mode="exact")
+
+    runs = {"batched_exact": lambda: gs.shoot_batched(q0, p0, X, off, sig, T, lam, mode="exact"),
+            "batched_bh": lambda: gs.shoot_batched(q0, p0, X, off, sig, T, lam, mode="bh",
+                                                   thresh=THRESH),
+            "plain_per_subject_exact": plain}
+    res = {}
+    for name, fn in runs.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        res[name] = statistics.median(ts)
+    Eb, gb = runs["batched_bh"]()
+    Ee, ge = runs["batched_exact"]()
+    line = {"mode": "batched", "unit": "ms per gradient of all subjects", "steps": args.steps,
+            "warmup": args.warmup, "ms": res,
+            "speedup_batched_bh_vs_plain": res["plain_per_subject_exact"] / res["batched_bh"],
+            "speedup_batched_exact_vs_plain": res["plain_per_subject_exact"] / res["batched_exact"],
+            "bh_vs_exact_grad_rel_l2": float(torch.linalg.norm(gb - ge) / torch.linalg.norm(ge)),
+            "exact_pairs_per_s_batched": 2 * T * float(np.sum(ns.astype(float) ** 2))
+            / (res["batched_exact"] * 1e-3),
+            "config": {"workload": f"{len(ws)} bent-slab subjects, N log-uniform in [5000, 40000] "
+                                   f"(total {int(off[-1])}), sigma={sig} mm, T={T}, lambda={lam}",
+                       "dtype": "f32 pair sums, f64 state"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.probe:
         return run_probe(args)
+    if args.batched:
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
