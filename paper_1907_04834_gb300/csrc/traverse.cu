@@ -69,19 +69,23 @@ __device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi
   return w;
 }
 
-// Slices of the group's node range [nb, ne): [nb, L-D), [L-D, L), [L, L+D),
-// [L+D, ne) (clamped to the range) where L is the leaf of the group's middle
-// point and D = clamp((ne - nb) / 32, 256, 4096).  Any cut points give the
-// same interactions; these spread a group's work over four warps.  D depends
-// only on the current tree, so results are reproducible.
+// Slices of the group's node range [nb, ne): with K = BH_SLICES, h = K/2 and
+// L the leaf of the group's middle point, the cuts are L - D 2^(h-1-k) for
+// k = 1 .. h-1, L, and L + D 2^(k-h-1) for k = h+1 .. K-1 (clamped to the
+// range), D = clamp((ne - nb) / 32, 256, 4096) >> GS_BH_DSHIFT; four slices:
+// [nb, L-D), [L-D, L), [L, L+D), [L+D, ne).  Any cut points give the same
+// interactions; these spread a group's work over K warps, narrow slices near
+// the group where the walk opens most nodes.  The cuts depend only on the
+// current tree, so results are reproducible.
 __device__ __forceinline__ int slice_start(const TreeArrays& t, const GroupInfo& gi, int k) {
+  constexpr int h = BH_SLICES / 2;
   if (k == 0) return gi.nb;
   const int i = gi.first + min(16, gi.count - 1);
   const int mid = i + (int)t.offs[i + 1];
-  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096);
-  if (k == 1) return max(gi.nb, mid - D);
-  if (k == 2) return mid;
-  return min(gi.ne, mid + D);
+  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096) >> GS_BH_DSHIFT;
+  if (k < h) return max(gi.nb, mid - (D << (h - 1 - k)));
+  if (k == h) return mid;
+  return min(gi.ne, mid + (D << (k - h - 1)));
 }
 
 __device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& gi, int k) {
@@ -409,8 +413,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 
 // ------------------------------------------------------------------ evaluate
 // One warp per list: partial sums of its entries, part[(l*NC + c)*32 + lane].
+// The adjoint variant is held to 128 registers (4 blocks per SM, a few
+// spilled values): measured faster than 3 blocks at 168 registers.
 template <bool ADJ>
-__global__ void __launch_bounds__(TR_WARPS * 32)
+__global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg) {
   constexpr int NR = ADJ ? 12 : 6;
   constexpr int NC = Acc<ADJ>::NC;

@@ -52,7 +52,14 @@ struct TreeArrays {
 // Interaction lists of one traversal: BH_SLICES per group of 32 points.
 // Entries live in a pool of chunks of BH_CHUNK entries; a list is the chain
 // of chunks starting at head[l] (next[c] links them in order).
-constexpr int BH_SLICES = 4;
+#ifndef GS_BH_SLICES
+#define GS_BH_SLICES 4
+#endif
+#ifndef GS_BH_DSHIFT
+#define GS_BH_DSHIFT 0
+#endif
+constexpr int BH_SLICES = GS_BH_SLICES;  // even
+static_assert(BH_SLICES >= 2 && BH_SLICES % 2 == 0, "slices come in pairs around the group");
 constexpr int BH_CHUNK = 64;
 struct BHLists {
   int2* ent;      // pool: n_chunks x BH_CHUNK entries {node, lane mask}
