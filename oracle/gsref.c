@@ -611,6 +611,57 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Dense velocity field (Eq. 3) and points carried by it.                     */
+/* ------------------------------------------------------------------------ */
+
+/* Velocity of Eq. 3 at M points x of the domain (mesh vertices, grid nodes):
+ * v(x) = sum_i G(|x - q_i|) p_i, all N particles, exact sums. */
+void gsref_velocity(int64_t N, const double *q, const double *p, int64_t M,
+                    const double *x, double sigma, double *v) {
+  double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+#pragma omp parallel for schedule(static)
+  for (int64_t m = 0; m < M; m++) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = 0; i < N; i++) {
+      double e0 = x[3 * m] - q[3 * i];
+      double e1 = x[3 * m + 1] - q[3 * i + 1];
+      double e2 = x[3 * m + 2] - q[3 * i + 2];
+      double G = exp(-(e0 * e0 + e1 * e1 + e2 * e2) * inv2s2);
+      for (int a = 0; a < 3; a++) acc[a] += G * p[3 * i + a];
+    }
+    for (int a = 0; a < 3; a++) v[3 * m + a] = acc[a];
+  }
+}
+
+/* Shooting (exact, Eq. 1) with M tracer points x carried by the velocity
+ * field of Eq. 3.  The tracers do not act on the particles; they take the
+ * same explicit Euler steps (reading R4), from the particles' state at the
+ * start of each step:  x^{k+1} = x^k + h v(x^k; q^k, p^k). */
+void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
+                const double *x0, double sigma, int T, double *q1, double *p1,
+                double *x1) {
+  double *F = (double *)malloc((size_t)N * 3 * sizeof(double));
+  double *Phi = (double *)malloc((size_t)N * 3 * sizeof(double));
+  double *v = (double *)malloc((size_t)(M > 0 ? M : 1) * 3 * sizeof(double));
+  double h = 1.0 / (double)T;
+  memcpy(q1, q0, (size_t)N * 3 * sizeof(double));
+  memcpy(p1, p0, (size_t)N * 3 * sizeof(double));
+  memcpy(x1, x0, (size_t)M * 3 * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    gsref_velocity(N, q1, p1, M, x1, sigma, v);
+    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, F, Phi, NULL);
+    for (int64_t i = 0; i < 3 * M; i++) x1[i] += h * v[i];
+    for (int64_t i = 0; i < 3 * N; i++) {
+      q1[i] += h * F[i];
+      p1[i] += h * Phi[i];
+    }
+  }
+  free(F);
+  free(Phi);
+  free(v);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Tree inspection for tests.                                                 */
 /* ------------------------------------------------------------------------ */
 
