@@ -140,7 +140,28 @@ gs_status gs_descend_batched(gs_ctx *ctx, int32_t S, const int64_t *offsets,
                              const gs_params *prm, double step, int32_t iters,
                              double *E_hist, void *stream);
 
+/*
+ * Shooting that also carries M tracer points (mesh vertices, grid nodes)
+ * through the dense velocity field of Eq. 3, v(x, t) = sum_i G(|x - q_i(t)|)
+ * p_i(t), as the paper does to deform meshes and label maps with the
+ * registration.  The tracers take the particles' explicit Euler steps from
+ * each step's particle state: x^{k+1} = x^k + h v(x^k; q^k, p^k); they do
+ * not act on the particles.  x0, x1: M x 3 (M >= 0; x0, x1 may be NULL when
+ * M = 0); q1, p1: NULL or N x 3 particle results.  Exact sums only: GS_BH
+ * returns GS_ERR_UNSUPPORTED.
+ */
+gs_status gs_flow(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
+                  const double *x0, int64_t M, const gs_params *prm,
+                  double *q1, double *p1, double *x1, void *stream);
+
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
+
+/* Velocity field of Eq. 3 at M >= 1 points x (M x 3): v = sum_i G(|x - q_i|)
+ * p_i over all N particles (exact sums, FP32 pairs with compensated sums as
+ * in gs_rhs).  v: M x 3. */
+gs_status gs_velocity(gs_ctx *ctx, const double *q, const double *p, int64_t N,
+                      const double *x, int64_t M, double sigma, double *v,
+                      void *stream);
 
 /* One forward right-hand side at state (q, p): F, Phi as in Eq. 1 (GS_BH:
  * Sec. 2.2 summaries).  counts: NULL or 2 int64 {point-point interactions,

@@ -172,6 +172,36 @@ def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, m
     return p, Eh
 
 
+def flow(q0, p0, x0, sigma, T, stream=None):
+    """Exact shooting that carries tracer points x0 (M, 3) through the
+    velocity field of Eq. 3 (gs_flow).  Returns (q1, p1, x1)."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0 = _pts(p0, "p0", n)
+    x0 = _pts(x0, "x0")
+    m = x0.shape[0]
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, "exact")
+    q1, p1, x1 = _like(q0), _like(q0), _like(x0)
+    c.check(c.lib.gs_flow(c.handle, _ptr(q0), _ptr(p0), n, _ptr(x0) if m else None, m,
+                          ctypes.byref(prm), _ptr(q1), _ptr(p1), _ptr(x1) if m else None,
+                          _stream_ptr(c.device, stream)))
+    return q1, p1, x1
+
+
+def velocity(q, p, x, sigma, stream=None):
+    """Velocity field of Eq. 3 at points x (M, 3): v = sum_i G(|x - q_i|) p_i."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    p = _pts(p, "p", n)
+    x = _pts(x, "x")
+    c = _ctx_for(q)
+    v = _like(x)
+    c.check(c.lib.gs_velocity(c.handle, _ptr(q), _ptr(p), n, _ptr(x), x.shape[0], float(sigma),
+                              _ptr(v), _stream_ptr(c.device, stream)))
+    return v
+
+
 def rhs(q, p, sigma, mode="exact", thresh=3.0, stream=None):
     """One forward right-hand side: (F, Phi, (point pairs, node pairs))."""
     q = _pts(q, "q")

@@ -74,7 +74,10 @@ struct gs_ctx {
     cudaGraphExec_t exec = nullptr;
     int launches = 0;  // kernels per replay
   };
-  GraphCache g_shoot, g_grad, g_batch;
+  GraphCache g_shoot, g_grad, g_batch, g_flow;
+  // tracer points of the velocity field (gs_flow, gs_velocity)
+  DevMem in_x, xs, xpks, xpart, xtickets;
+  size_t xtickets_n = 0;
   cudaStream_t cap = nullptr;  // capture stream
   bool graphs = true;
   TreeWork tree;  // Barnes-Hut workspace (tree.h)
@@ -170,7 +173,7 @@ struct Key {
     for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
                             &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
                             &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
-                            &c->gd_p})
+                            &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets})
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
@@ -883,6 +886,75 @@ gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
   return GS_OK;
 }
 
+// Tracer points (Eq. 3) moving with the particles of solver S: workspace
+// for M points (tracer_setup, never captured) and one step of them
+// (tracer_step: targets = tracer records of slot k & 1, sources = the
+// particles' pack slot k & 1, next records into slot (k + 1) & 1).
+struct Tracers {
+  int64_t M = 0;
+  TracerGeom tg{};
+  float4* xpk(const gs_ctx* c, int k) const { return c->xpks.as<float4>() + (size_t)k * tg.Mpad; }
+};
+
+gs_status tracer_setup(gs_ctx* c, const Solver& S, int64_t M, cudaStream_t st, Tracers& X) {
+  X.M = M;
+  X.tg.M = M;
+  X.tg.n_itiles = (int)((std::max<int64_t>(M, 1) + EX_NT - 1) / EX_NT);
+  X.tg.Mpad = (int64_t)X.tg.n_itiles * EX_NT;
+  X.tg.J = choose_J(X.tg.n_itiles, S.gf.n_jtiles, 3 * c->num_sms);
+  CK(c->xs.ensure((size_t)std::max<int64_t>(M, 1) * 24), "workspace");
+  CK(c->xpks.ensure(2 * (size_t)X.tg.Mpad * sizeof(float4)), "workspace");
+  CK(c->xpart.ensure((size_t)X.tg.J * 3 * X.tg.Mpad * sizeof(float2)), "workspace");
+  const size_t tn = (size_t)X.tg.n_itiles;
+  if (c->xtickets_n < tn) {
+    CK(c->xtickets.ensure(tn * sizeof(unsigned)), "workspace");
+    c->xtickets_n = tn;
+  }
+  CK(cudaMemsetAsync(c->xtickets.p, 0, tn * sizeof(unsigned), st), "memset");
+  return GS_OK;
+}
+
+gs_status tracer_step(const Solver& S, const Tracers& X, int k, double h, double* v_out,
+                      cudaStream_t st) {
+  gs_ctx* c = S.c;
+  if (X.M == 0) return GS_OK;
+  TracerEpi e{};
+  e.x = c->xs.as<double>();
+  e.xpk_next = h != 0.0 ? X.xpk(c, (k + 1) & 1) : nullptr;
+  e.v_out = v_out;
+  e.center = S.scal(SC_CENTER);
+  e.s = S.s;
+  e.h = h;
+  e.M = X.M;
+  KTimer tm(c, GS_K_EXACT_FWD, st);
+  CK(launch_tracer(S.pack(k & 1), S.gf, X.xpk(c, k & 1), X.tg, c->xpart.as<float2>(),
+                   c->xtickets.as<unsigned>(), e, c->d_status, st),
+     "tracer kernel");
+  return GS_OK;
+}
+
+// Shooting with tracers (capturable): particles as shoot_enqueue without H,
+// tracers x0 carried along; final tracer positions left in c->xs.
+gs_status flow_enqueue(Solver& S, const Tracers& X, const double* dq0, const double* dp0,
+                       const double* dx0, cudaStream_t st) {
+  gs_status s;
+  gs_ctx* c = S.c;
+  S.st = st;
+  if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  if (X.M > 0) {
+    CK(cudaMemcpyAsync(c->xs.p, dx0, (size_t)X.M * 24, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(launch_pack_points(c->xs.as<double>(), X.M, S.scal(SC_CENTER), S.s, X.xpk(c, 0), st),
+       "pack");
+  }
+  for (int k = 0; k < S.T; k++) {
+    // both read step k's particle pack; the particle step writes slot k+1
+    if ((s = tracer_step(S, X, k, S.h, nullptr, st))) return s;
+    FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
+    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+  }
+  return GS_OK;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -925,9 +997,9 @@ void gs_destroy(gs_ctx* c) {
     for (DevMem* m : {&c->in_q, &c->in_p, &c->in_a, &c->in_b, &c->in_X, &c->out_a, &c->out_b,
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
-                      &c->gd_p, &c->gd_E})
+                      &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets})
       m->release();
-    for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch})
+    for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch, &c->g_flow})
       if (gc->exec) cudaGraphExecDestroy(gc->exec);
     if (c->cap) cudaStreamDestroy(c->cap);
     tree_release(c->tree);
@@ -1162,6 +1234,90 @@ gs_status gs_descend_batched(gs_ctx* c, int32_t S, const int64_t* offsets, const
   if ((s = copy_out(c, p0, dp, b3, st))) return s;
   if (E_hist && iters > 0 && (s = copy_out(c, E_hist, c->gd_E.p, eb * iters, st))) return s;
   if (hp || hE) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_flow(gs_ctx* c, const double* q0, const double* p0, int64_t N, const double* x0,
+                  int64_t M, const gs_params* prm, double* q1, double* p1, double* x1,
+                  void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if (M < 0 || M > (int64_t(1) << 30))
+    return fail(c, GS_ERR_INVALID_ARG, "M must be in [0, 2^30] (got %lld)", (long long)M);
+  if (prm->mode != GS_EXACT)
+    return fail(c, GS_ERR_UNSUPPORTED, "tracer points: exact mode only");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hq = false, hp = false, hx = false;
+  if (q1 && (s = output(c, q1, "q1", &hq))) return s;
+  if (p1 && (s = output(c, p1, "p1", &hp))) return s;
+  if (M > 0 && (s = output(c, x1, "x1", &hx))) return s;
+  const double *dq0, *dp0, *dx0 = nullptr;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)))
+    return s;
+  if (M > 0 && (s = input(c, x0, (size_t)M * 3, "x0", c->in_x, st, &dx0))) return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 2, false, st))) return s;
+  Tracers X;
+  if ((s = tracer_setup(c, S, M, st, X))) return s;
+  {
+    Key k;
+    k.add(N), k.add(M), k.params(prm), k.add(dq0), k.add(dp0), k.add(dx0), k.workspace(c);
+    s = run_graphed(c, c->g_flow, k, st,
+                    [&](cudaStream_t s2) { return flow_enqueue(S, X, dq0, dp0, dx0, s2); });
+    if (s) return s;
+  }
+  const size_t b = (size_t)N * 3 * sizeof(double);
+  if (q1) {
+    CK(launch_check_finite(c->q.as<double>(), N * 3, c->d_status, st), "check");
+    if ((s = copy_out(c, q1, c->q.p, b, st))) return s;
+  }
+  if (p1) {
+    CK(launch_check_finite(c->p.as<double>(), N * 3, c->d_status, st), "check");
+    if ((s = copy_out(c, p1, c->p.p, b, st))) return s;
+  }
+  if (M > 0) {
+    CK(launch_check_finite(c->xs.as<double>(), M * 3, c->d_status, st), "check");
+    if ((s = copy_out(c, x1, c->xs.p, (size_t)M * 24, st))) return s;
+  }
+  if (hq || hp || hx) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, const double* x,
+                      int64_t M, double sigma, double* v, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0};
+  if ((s = check_n(c, N)) || (s = check_params(c, &prm, false))) return s;
+  if (M < 1 || M > (int64_t(1) << 30))
+    return fail(c, GS_ERR_INVALID_ARG, "M must be in [1, 2^30] (got %lld)", (long long)M);
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hv = false;
+  if ((s = output(c, v, "v", &hv))) return s;
+  const double *dq, *dp, *dx;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)) ||
+      (s = input(c, x, (size_t)M * 3, "x", c->in_x, st, &dx)))
+    return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
+  if ((s = solver_load(S, dq, dp, 0))) return s;
+  Tracers X;
+  if ((s = tracer_setup(c, S, M, st, X))) return s;
+  CK(c->out_a.ensure((size_t)M * 24), "workspace");
+  CK(cudaMemcpyAsync(c->xs.p, dx, (size_t)M * 24, cudaMemcpyDeviceToDevice, st), "copy");
+  CK(launch_pack_points(c->xs.as<double>(), M, S.scal(SC_CENTER), S.s, X.xpk(c, 0), st), "pack");
+  if ((s = tracer_step(S, X, 0, 0.0, c->out_a.as<double>(), st))) return s;
+  if ((s = copy_out(c, v, c->out_a.p, (size_t)M * 24, st))) return s;
+  if (hv) return read_status(c, st);
   CK(cudaGetLastError(), "launch");
   return GS_OK;
 }

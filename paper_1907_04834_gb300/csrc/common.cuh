@@ -241,6 +241,35 @@ __device__ __forceinline__ void fwd_epilogue(int64_t i, const double F[3], const
   fwd_epilogue_at(i, i, e.center, F, Sraw, e);
 }
 
+// Tracer points carried by the velocity field of Eq. 3: with v = Sum_j g p_j
+// finished, x += h v (FP64) and the next step's tracer record
+// {(x - c) s, 0} is written.
+struct TracerEpi {
+  double* x;                // M x 3 tracer positions (updated when h != 0)
+  float4* xpk_next;         // next step's tracer records (NULL = none)
+  double* v_out;            // M x 3 velocity (NULL = none)
+  const double* center;     // recentring point (the particles')
+  double s;                 // coordinate scale
+  double h;
+  int64_t M;
+};
+
+__device__ __forceinline__ void tracer_epilogue(int64_t i, const double v[3], const TracerEpi& e) {
+  if (e.v_out)
+    for (int a = 0; a < 3; a++) e.v_out[3 * i + a] = v[a];
+  if (e.h != 0.0) {
+    double xn[3];
+    for (int a = 0; a < 3; a++) {
+      xn[a] = e.x[3 * i + a] + e.h * v[a];
+      e.x[3 * i + a] = xn[a];
+    }
+    if (e.xpk_next)
+      e.xpk_next[i] = make_float4((float)((xn[0] - e.center[0]) * e.s),
+                                  (float)((xn[1] - e.center[1]) * e.s),
+                                  (float)((xn[2] - e.center[2]) * e.s), 0.f);
+  }
+}
+
 // Adjoint: finished sums A1 = Sum g (a_i.p_j + a_j.p_i) d_s, A2 = Sum c g w,
 // A3 = Sum c g (w.d_s) d_s, B1 = Sum g a_j, B2 = Sum g (w.d_s) p_j; the
 // backward step is alpha += h dA, beta += h dB with

@@ -139,6 +139,39 @@ struct FwdTarget {
   }
 };
 
+// Velocity of Eq. 3 at one tracer point over one staged tile:
+//   v = Sum_j g(x - q_j) p_j  (the tracer is not a source).
+constexpr int kVelComps = 3;
+struct VelTarget {
+  f2 xi, yi, zi;
+  Kahan K[kVelComps];
+  __device__ __forceinline__ void load(const float4* xpk, int64_t i, int64_t M) {
+    const float4 r = i < M ? xpk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    xi = f2_dup(r.x), yi = f2_dup(r.y), zi = f2_dup(r.z);
+#pragma unroll
+    for (int c = 0; c < kVelComps; c++) K[c].zero();
+  }
+  __device__ __forceinline__ void tile(const float4* stage) {
+    const ulonglong2* tb = reinterpret_cast<const ulonglong2*>(stage);
+    f2 fx = 0, fy = 0, fz = 0;
+#pragma unroll 4
+    for (int m = 0; m < EX_TILE / 2; m++) {
+      const ulonglong2 v0 = tb[3 * m + 0], v1 = tb[3 * m + 1], v2 = tb[3 * m + 2];
+      const f2 dx = f2_sub(xi, v0.x), dy = f2_sub(yi, v0.y), dz = f2_sub(zi, v1.x);
+      f2 r = f2_mul(dx, dx);
+      r = f2_fma(dy, dy, r);
+      r = f2_fma(dz, dz, r);
+      const f2 g = gauss2(r);
+      fx = f2_fma(g, v1.y, fx);
+      fy = f2_fma(g, v2.x, fy);
+      fz = f2_fma(g, v2.y, fz);
+    }
+    K[0].add(f2_sum(fx));
+    K[1].add(f2_sum(fy));
+    K[2].add(f2_sum(fz));
+  }
+};
+
 // Adjoint sums of one target over one staged tile (a = alpha^{k+1},
 // b = beta^{k+1}, w = b_i - b_j, d = d_s):
 //   A1 = Sum g (a_i.p_j + a_j.p_i) d,  A2 = Sum c g w,  A3 = Sum c g (w.d) d,
@@ -319,6 +352,44 @@ __global__ void __launch_bounds__(EX_NT, 2)
 }
 
 // ---------------------------------------------------------------------------
+// Tracer points (Eq. 3): targets are the tracers, sources the particles'
+// pack; split over J source ranges like k_exact_fwd.  tg.M tracers in
+// tg.n_itiles tiles of EX_NT.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(EX_NT, 3)
+    k_tracer(const float4* __restrict__ pk, ExactGeom geo, const float4* __restrict__ xpk,
+             TracerGeom tg, float2* __restrict__ part, unsigned* __restrict__ tickets,
+             TracerEpi epi, int* status) {
+  extern __shared__ __align__(128) float4 sbuf[];
+  __shared__ uint64_t bars[EX_STAGES];
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  const int64_t i = (int64_t)bi * EX_NT + threadIdx.x;
+  const TileRange tr = tile_range(bj, tg.J, geo.n_jtiles);
+  VelTarget vt;
+  vt.load(xpk, i, tg.M);
+  init_barriers(bars);
+  const float4* srcs[1] = {pk};
+  unsigned done = 0;
+  stream_tiles<1>(sbuf, bars, srcs, tr.t0, tr.nt, done, status,
+                  [&](const float4* st) { vt.tile(st); });
+#pragma unroll
+  for (int c = 0; c < kVelComps; c++)
+    part[((size_t)bj * kVelComps + c) * tg.Mpad + i] = vt.K[c].out();
+  if (!last_block(tickets, bi, tg.J)) return;
+  if (i >= tg.M) return;
+  double v[kVelComps];
+#pragma unroll
+  for (int c = 0; c < kVelComps; c++) v[c] = 0.0;
+  for (int b = 0; b < tg.J; b++)
+#pragma unroll
+    for (int c = 0; c < kVelComps; c++) {
+      const float2 u = __ldcg(&part[((size_t)b * kVelComps + c) * tg.Mpad + i]);
+      v[c] += (double)u.x + (double)u.y;
+    }
+  tracer_epilogue(i, v, epi);
+}
+
+// ---------------------------------------------------------------------------
 // Many point sets: persistent blocks over (subject, target tile) items.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(EX_NT, 3)
@@ -398,6 +469,9 @@ cudaError_t exact_setup() {
     e = cudaFuncSetAttribute(k_batched_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)exact_fwd_smem());
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tracer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)exact_fwd_smem());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_batched_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)exact_adj_smem());
   return e;
@@ -415,6 +489,15 @@ cudaError_t launch_exact_adj(const float4* pk, const float4* ab, const ExactGeom
                              unsigned* tickets, const AdjEpi& e, int* status, cudaStream_t st) {
   dim3 grid(g.n_itiles, g.J);
   k_exact_adj<<<grid, EX_NT, exact_adj_smem(), st>>>(pk, ab, g, part, tickets, e, status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tracer(const float4* pk, const ExactGeom& g, const float4* xpk,
+                          const TracerGeom& tg, float2* part, unsigned* tickets,
+                          const TracerEpi& e, int* status, cudaStream_t st) {
+  dim3 grid(tg.n_itiles, tg.J);
+  k_tracer<<<grid, EX_NT, exact_fwd_smem(), st>>>(pk, g, xpk, tg, part, tickets, e, status);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -46,6 +46,17 @@ cudaError_t launch_exact_fwd(const float4* pk, const ExactGeom& g, float2* part,
 cudaError_t launch_exact_adj(const float4* pk, const float4* ab, const ExactGeom& g, float2* part,
                              unsigned* tickets, const AdjEpi& e, int* status, cudaStream_t st);
 
+// Tracer points of the velocity field (Eq. 3): M targets in n_itiles tiles
+// of EX_NT (Mpad = n_itiles * EX_NT), J splits of the particle source tiles.
+struct TracerGeom {
+  int64_t M, Mpad;
+  int n_itiles, J;
+};
+// part: J x 3 x Mpad float2; tickets: n_itiles (zero, reset by the kernel)
+cudaError_t launch_tracer(const float4* pk, const ExactGeom& g, const float4* xpk,
+                          const TracerGeom& tg, float2* part, unsigned* tickets,
+                          const TracerEpi& e, int* status, cudaStream_t st);
+
 // resident blocks per SM of the persistent batched kernels
 int batched_resident_blocks(bool adjoint);
 cudaError_t launch_batched_fwd(const float4* pk, const BatchInfo& b, const FwdEpi& e, int* status,
@@ -72,6 +83,9 @@ cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t 
 // out[s * stride] = scale * Sum over rows of subject s of x (fixed order)
 cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
                                double* out, int stride, cudaStream_t st);
+// tracer records {(x - c) s, 0} of M points
+cudaError_t launch_pack_points(const double* x, int64_t M, const double* center, double s,
+                               float4* xpk, cudaStream_t st);
 // y += a x (product rounded, then the sum: no fused multiply-add)
 cudaError_t launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 // E[s] = {H[s] + D[s], H[s], D[s]} from E[s*3+1] = H, E[s*3+2] = D

@@ -222,6 +222,14 @@ __global__ void k_segment_sum(const double* __restrict__ x, const int64_t* __res
   if (threadIdx.x == 0) out[(size_t)s * stride] = scale * v;
 }
 
+__global__ void k_pack_points(const double* __restrict__ x, int64_t M,
+                              const double* __restrict__ c, double s, float4* xpk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M)
+    xpk[i] = make_float4((float)((x[3 * i] - c[0]) * s), (float)((x[3 * i + 1] - c[1]) * s),
+                         (float)((x[3 * i + 2] - c[2]) * s), 0.f);
+}
+
 __global__ void k_axpy(double* y, const double* __restrict__ x, double a, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = __dadd_rn(y[i], __dmul_rn(a, x[i]));  // rounded product, then sum
@@ -278,6 +286,15 @@ cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, doubl
                                double* out, int stride, cudaStream_t st) {
   k_segment_sum<<<S, kRedThreads, 0, st>>>(x, off, scale, out, stride);
   note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_points(const double* x, int64_t M, const double* center, double s,
+                               float4* xpk, cudaStream_t st) {
+  if (M > 0) {
+    k_pack_points<<<blocks_for(M, 256), 256, 0, st>>>(x, M, center, s, xpk);
+    note_launches(1);
+  }
   return cudaGetLastError();
 }
 
