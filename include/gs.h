@@ -154,6 +154,25 @@ gs_status gs_flow(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
                   const double *x0, int64_t M, const gs_params *prm,
                   double *q1, double *p1, double *x1, void *stream);
 
+/*
+ * L-BFGS on the initial momenta of one registration (Sec. 2.1: the paper
+ * minimises Eq. 2 with the L-BFGS of the VNL library): limited-memory BFGS
+ * with the m most recent curvature pairs (two-loop recursion), a
+ * backtracking line search from the unit step (Armijo condition, constant
+ * 1e-4, halving up to 50 times; the first direction is -grad / |grad|), and
+ * pairs with s.y <= 1e-12 |s| |y| skipped.  Stops after `iters` iterations,
+ * when |grad| <= gtol * max(1, |grad(p0 initial)|), or when the line search
+ * fails.  Each objective and gradient is gs_shoot_grad's (prm: mode,
+ * checkpointing and all).  p0 (N x 3) is read and overwritten with the last
+ * iterate; E_hist: NULL or iters + 1 doubles, E of the initial point and of
+ * each accepted iterate (NaN after the last); n_done: NULL or the
+ * iterations done.  The vector algebra runs on the device (FP64, fixed-order
+ * dot products); the host reads back scalars.  Synchronises the stream.
+ */
+gs_status gs_lbfgs(gs_ctx *ctx, const double *q0, double *p0, const double *X,
+                   int64_t N, const gs_params *prm, int32_t m, int32_t iters,
+                   double gtol, double *E_hist, int32_t *n_done, void *stream);
+
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
 
 /* Velocity field of Eq. 3 at M >= 1 points x (M x 3): v = sum_i G(|x - q_i|)

@@ -57,6 +57,8 @@ _SIGS = {
                                         _vp, _vp, _vp]),
     "gs_descend_batched": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(Params),
                                           ctypes.c_double, _i32, _vp, _vp]),
+    "gs_lbfgs": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _i32, _i32,
+                                ctypes.c_double, _vp, _vp, _vp]),
     "gs_flow": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp, _vp,
                                _vp, _vp]),
     "gs_velocity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _vp]),

@@ -172,6 +172,25 @@ def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, m
     return p, Eh
 
 
+def lbfgs(q0, p0, X, sigma, T, lam=1.0, m=8, iters=50, gtol=1e-6, mode="exact", thresh=3.0,
+          ckpt_every=0, stream=None):
+    """L-BFGS on the initial momenta (gs_lbfgs).  Returns (p0 after the last
+    iterate, E history of the initial point and each accepted iterate,
+    iterations done)."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every)
+    p = p0.clone()
+    Eh = torch.empty(int(iters) + 1, dtype=torch.float64)
+    done = ctypes.c_int32(0)
+    c.check(c.lib.gs_lbfgs(c.handle, _ptr(q0), _ptr(p), _ptr(X), n, ctypes.byref(prm), int(m),
+                           int(iters), float(gtol), _ptr(Eh), ctypes.byref(done),
+                           _stream_ptr(c.device, stream)))
+    return p, Eh[: done.value + 1], done.value
+
+
 def flow(q0, p0, x0, sigma, T, stream=None):
     """Exact shooting that carries tracer points x0 (M, 3) through the
     velocity field of Eq. 3 (gs_flow).  Returns (q1, p1, x1)."""

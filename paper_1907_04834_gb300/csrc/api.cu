@@ -77,6 +77,7 @@ struct gs_ctx {
   GraphCache g_shoot, g_grad, g_batch, g_flow;
   // tracer points of the velocity field (gs_flow, gs_velocity)
   DevMem in_x, xs, xpks, xpart, xtickets;
+  DevMem lb;  // L-BFGS vectors
   size_t xtickets_n = 0;
   cudaStream_t cap = nullptr;  // capture stream
   bool graphs = true;
@@ -173,7 +174,8 @@ struct Key {
     for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
                             &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
                             &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
-                            &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets})
+                            &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
+                            &c->lb})
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
@@ -997,7 +999,8 @@ void gs_destroy(gs_ctx* c) {
     for (DevMem* m : {&c->in_q, &c->in_p, &c->in_a, &c->in_b, &c->in_X, &c->out_a, &c->out_b,
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
-                      &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets})
+                      &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
+                      &c->lb})
       m->release();
     for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch, &c->g_flow})
       if (gc->exec) cudaGraphExecDestroy(gc->exec);
@@ -1320,6 +1323,158 @@ gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, co
   if (hv) return read_status(c, st);
   CK(cudaGetLastError(), "launch");
   return GS_OK;
+}
+
+gs_status gs_lbfgs(gs_ctx* c, const double* q0, double* p0, const double* X, int64_t N,
+                   const gs_params* prm, int32_t m, int32_t iters, double gtol, double* E_hist,
+                   int32_t* n_done, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, true))) return s;
+  if (m < 1 || m > 64) return fail(c, GS_ERR_INVALID_ARG, "m must be in [1, 64] (got %d)", m);
+  if (iters < 0 || iters > 100000)
+    return fail(c, GS_ERR_INVALID_ARG, "iters must be in [0, 1e5] (got %d)", iters);
+  if (!(gtol >= 0.0) || !std::isfinite(gtol))
+    return fail(c, GS_ERR_INVALID_ARG, "gtol must be finite and >= 0");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hp = false, hE = false;
+  if ((s = output(c, p0, "p0", &hp))) return s;
+  if (E_hist && (s = output(c, E_hist, "E_hist", &hE))) return s;
+  const double *dq0, *dX;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, X, (size_t)N * 3, "X", c->in_X, st, &dX)))
+    return s;
+  const int64_t n3 = N * 3;
+  const size_t b3 = (size_t)n3 * sizeof(double);
+  // iterate x, gradient g, direction d, trial point xt and its gradient gt,
+  // the m most recent pairs s = x_{k+1} - x_k, y = g_{k+1} - g_k, a scalar
+  CK(c->lb.ensure((size_t)(5 + 2 * m) * b3 + 64), "workspace");
+  double* x = c->lb.as<double>();
+  double *gv = x + n3, *d = gv + n3, *xt = d + n3, *gt = xt + n3, *Sv = gt + n3,
+         *Yv = Sv + (size_t)m * n3, *sc = Yv + (size_t)m * n3;
+  CK(c->scal.ensure(SC_N * 8), "workspace");
+  double* dE = c->scal.as<double>() + SC_E;
+  CK(cudaMemcpyAsync(x, p0, b3, cudaMemcpyDefault, st), "p0 copy");
+  GradRun R;
+  if ((s = grad_setup(c, N, prm, nullptr, st, R))) return s;
+
+  // E and gradient at xt (into gt): the gradient graph, replayed
+  auto evaluate = [&](double* E) -> gs_status {
+    Key k;
+    k.add(N), k.params(prm), k.add(dq0), k.add((const double*)xt), k.add(dX), k.add(gt);
+    k.workspace(c);
+    gs_status r = run_graphed(c, c->g_grad, k, st, [&](cudaStream_t s2) {
+      return grad_enqueue(R, dq0, xt, dX, dE, gt, nullptr, s2);
+    });
+    if (r) return r;
+    CK(cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, st), "energy read");
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    return GS_OK;
+  };
+  auto dot = [&](const double* a, const double* b, double* out) -> gs_status {
+    CK(launch_dot(a, b, n3, sc, st), "dot");
+    CK(cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st), "dot read");
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    return GS_OK;
+  };
+  auto copy = [&](double* dst, const double* src) -> gs_status {
+    CK(cudaMemcpyAsync(dst, src, b3, cudaMemcpyDeviceToDevice, st), "copy");
+    return GS_OK;
+  };
+#define LB(call)          \
+  do {                    \
+    if ((s = (call))) return s; \
+  } while (0)
+  double E = 0.0, gg = 0.0;
+  LB(copy(xt, x));
+  LB(evaluate(&E));
+  LB(copy(gv, gt));
+  LB(dot(gv, gv, &gg));
+  std::vector<double> Eh{E}, rho(m), alpha(m);
+  const double g0 = std::sqrt(gg);
+  int stored = 0, head = 0, it = 0;
+  for (; it < iters; it++) {
+    if (!(std::sqrt(gg) > gtol * std::max(1.0, g0))) break;
+    // two-loop recursion: d = -H g with H from the stored pairs
+    LB(copy(d, gv));
+    for (int j = 0; j < stored; j++) {  // newest to oldest
+      const int i = (head - 1 - j + m) % m;
+      double sq = 0.0;
+      LB(dot(Sv + (size_t)i * n3, d, &sq));
+      alpha[i] = rho[i] * sq;
+      CK(launch_axpy(d, Yv + (size_t)i * n3, -alpha[i], n3, st), "axpy");
+    }
+    double gamma = 1.0 / std::max(std::sqrt(gg), 1e-300);
+    if (stored > 0) {
+      const int i = (head - 1 + m) % m;
+      double yy = 0.0;
+      LB(dot(Yv + (size_t)i * n3, Yv + (size_t)i * n3, &yy));
+      gamma = 1.0 / (rho[i] * yy);  // s.y / y.y
+    }
+    CK(launch_scale(d, d, gamma, n3, st), "scale");
+    for (int j = stored - 1; j >= 0; j--) {  // oldest to newest
+      const int i = (head - 1 - j + m) % m;
+      double yr = 0.0;
+      LB(dot(Yv + (size_t)i * n3, d, &yr));
+      CK(launch_axpy(d, Sv + (size_t)i * n3, alpha[i] - rho[i] * yr, n3, st), "axpy");
+    }
+    CK(launch_scale(d, d, -1.0, n3, st), "scale");
+    double gd = 0.0;
+    LB(dot(gv, d, &gd));
+    if (!(gd < 0.0)) {  // not a descent direction: restart from -g / |g|
+      stored = 0;
+      CK(launch_scale(d, gv, -1.0 / std::sqrt(gg), n3, st), "scale");
+      gd = -std::sqrt(gg);
+    }
+    // backtracking line search (Armijo, c1 = 1e-4), unit step first
+    double t = 1.0, Et = 0.0;
+    bool ok = false;
+    for (int ls = 0; ls < 50; ls++) {
+      LB(copy(xt, x));
+      CK(launch_axpy(xt, d, t, n3, st), "axpy");
+      LB(evaluate(&Et));
+      if (std::isfinite(Et) && Et <= E + 1e-4 * t * gd) {
+        ok = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!ok) break;
+    // new pair s = t d, y = gt - g
+    double* Si = Sv + (size_t)head * n3;
+    double* Yi = Yv + (size_t)head * n3;
+    CK(launch_scale(Si, d, t, n3, st), "scale");
+    LB(copy(Yi, gt));
+    CK(launch_axpy(Yi, gv, -1.0, n3, st), "axpy");
+    double sy = 0.0, ss = 0.0, yy = 0.0;
+    LB(dot(Si, Yi, &sy));
+    LB(dot(Si, Si, &ss));
+    LB(dot(Yi, Yi, &yy));
+    LB(copy(x, xt));
+    LB(copy(gv, gt));
+    E = Et;
+    Eh.push_back(E);
+    LB(dot(gv, gv, &gg));
+    if (sy > 1e-12 * std::sqrt(ss * yy)) {  // curvature condition: keep the pair
+      rho[head] = 1.0 / sy;
+      head = (head + 1) % m;
+      stored = std::min(stored + 1, m);
+    }
+  }
+#undef LB
+  if (n_done) *n_done = it;
+  CK(launch_check_finite(x, n3, c->d_status, st), "check");
+  if ((s = copy_out(c, p0, x, b3, st))) return s;
+  if (E_hist) {
+    std::vector<double> out((size_t)iters + 1, std::nan(""));
+    std::copy(Eh.begin(), Eh.end(), out.begin());
+    CK(cudaMemcpyAsync(E_hist, out.data(), out.size() * sizeof(double), cudaMemcpyDefault, st),
+       "E_hist copy");
+    CK(cudaStreamSynchronize(st), "stream synchronize");  // `out` is freed on return
+  }
+  return read_status(c, st);
 }
 
 gs_status gs_rhs(gs_ctx* c, const double* q, const double* p, int64_t N, const gs_params* prm,

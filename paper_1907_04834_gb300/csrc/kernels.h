@@ -86,6 +86,10 @@ cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, doubl
 // tracer records {(x - c) s, 0} of M points
 cudaError_t launch_pack_points(const double* x, int64_t M, const double* center, double s,
                                float4* xpk, cudaStream_t st);
+// *out = a . b (FP64, fixed order)
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out, cudaStream_t st);
+// y = a x (y may be x)
+cudaError_t launch_scale(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 // y += a x (product rounded, then the sum: no fused multiply-add)
 cudaError_t launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 // E[s] = {H[s] + D[s], H[s], D[s]} from E[s*3+1] = H, E[s*3+2] = D

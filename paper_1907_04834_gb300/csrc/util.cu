@@ -230,6 +230,24 @@ __global__ void k_pack_points(const double* __restrict__ x, int64_t M,
                          (float)((x[3 * i + 2] - c[2]) * s), 0.f);
 }
 
+// a . b over n values: each thread sums a contiguous chunk in order, then a
+// fixed tree (deterministic)
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                      double* out) {
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t c0 = (int64_t)threadIdx.x * chunk;
+  const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  double v = 0.0;
+  for (int64_t i = c0; i < c1; i++) v += a[i] * b[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_scale(double* y, const double* __restrict__ x, double a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i];
+}
+
 __global__ void k_axpy(double* y, const double* __restrict__ x, double a, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = __dadd_rn(y[i], __dmul_rn(a, x[i]));  // rounded product, then sum
@@ -295,6 +313,19 @@ cudaError_t launch_pack_points(const double* x, int64_t M, const double* center,
     k_pack_points<<<blocks_for(M, 256), 256, 0, st>>>(x, M, center, s, xpk);
     note_launches(1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
+                       cudaStream_t st) {
+  k_dot<<<1, kRedThreads, 0, st>>>(a, b, n, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* y, const double* x, double a, int64_t n, cudaStream_t st) {
+  k_scale<<<blocks_for(n, 256), 256, 0, st>>>(y, x, a, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 
