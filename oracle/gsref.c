@@ -10,17 +10,17 @@
  * points across threads; each target's sum keeps its sequential order).
  *
  * Notation (Sec. 2.1): q_i, p_i in R^3, i = 0..N-1; d_ij = q_i - q_j;
- * g_ij = G(|d_ij|) = exp(-|d_ij|^2 / (2 sigma^2)) (reading R1: unnormalised
- * Gaussian, G(0) = 1); c_ij = p_i . p_j.
- * Hamiltonian (Sec. 2.1, with the 1/2 of reading R2):
+ * g_ij = G(|d_ij|) = exp(-|d_ij|^2 / (2 sigma^2)) (the paper names a Gaussian
+ * kernel without a formula: taken unnormalised, G(0) = 1); c_ij = p_i . p_j.
+ * Hamiltonian (Sec. 2.1, with a factor 1/2 so that Eq. 1 gives dq/dt = K p):
  *     H(q,p) = 1/2 sum_i sum_j g_ij c_ij.
  * Hamilton's equations (Eq. 1):
- *     dq_i/dt =  dH/dp_i = F_i   = sum_j g_ij p_j                (j = i included, R3)
+ *     dq_i/dt =  dH/dp_i = F_i   = sum_j g_ij p_j                (j = i included)
  *     dp_i/dt = -dH/dq_i = Phi_i = sigma^-2 sum_j c_ij g_ij d_ij
- * Time discretisation (Sec. 2.1, "discretized in time"; reading R4):
+ * Time discretisation (Sec. 2.1 says only "discretized in time"; taken as):
  *     explicit Euler, h = 1/T, q^{k+1} = q^k + h F^k, p^{k+1} = p^k + h Phi^k.
- * Objective (Eq. 2, reading R5):  E(p0) = H(q0,p0) + lambda sum_i |q_i^T - X_i|^2.
- * Backward stage (Sec. 2.2, reading R6): discrete adjoint of the Euler map,
+ * Objective (Eq. 2, p0* = argmin E):  E(p0) = H(q0,p0) + lambda sum_i |q_i^T - X_i|^2.
+ * Backward stage (Sec. 2.2; taken as the discrete adjoint of the Euler map),
  *     alpha = dE/dq, beta = dE/dp; alpha^T = 2 lambda (q^T - X), beta^T = 0,
  *     alpha^k = alpha^{k+1} + h [ (dF/dq)^T alpha^{k+1} + (dPhi/dq)^T beta^{k+1} ]
  *     beta^k  = beta^{k+1}  + h [ (dF/dp)^T alpha^{k+1} + (dPhi/dp)^T beta^{k+1} ]
@@ -31,27 +31,27 @@
  *     (dF/dp)^T a   |_i =  sum_j g_ij a_j
  *     (dPhi/dp)^T b |_i =  sigma^-2 sum_j g_ij (w_ij.d_ij) p_j
  *
- * Barnes-Hut (Sec. 2.2), rebuilt at every forward and backward step (R13):
+ * Barnes-Hut (Sec. 2.2), rebuilt at every forward and backward step:
  *   - root cell = FP32 bounding box of the FP32-rounded positions; cells are
  *     per-axis bisections; a point's child octant at depth d is bit (9-d) of its
- *     10-bit quantised coordinates (reading R7: ext = hi-lo; inv = 1024/ext;
+ *     10-bit quantised coordinates (quantisation taken as: ext = hi-lo; inv = 1024/ext;
  *     u = (x-lo)*inv; k = min((uint32)u, 1023); k = 0 when ext == 0; all FP32,
  *     round to nearest, no contraction); octant = (kx_b << 2) | (ky_b << 1) | kz_b.
  *   - points are inserted one by one in index order with the three-case rule
  *     (internal -> descend; empty leaf -> store; occupied leaf -> split into
  *     eight and pass both points down); depth 10 cannot split and keeps a list.
  *   - node statistics updated as each point is passed to a node: n, total
- *     momentum P = sum p, position sum (centroid = sum q / n, reading R8), the
+ *     momentum P = sum p, position sum (centroid = sum q / n, the plain mean), the
  *     FP32 "actual range" [lo, hi]; the backward stage adds A = sum alpha and
  *     B = sum beta.
  *   - traversal for a target point m (three cases of Sec. 2.2): a node with
  *     n >= 2 whose actual range lies farther than the threshold from q_m is one
  *     interaction with its summary; a leaf is computed exactly point by point;
- *     any other node is opened.  "Farther than the threshold" (reading R9) is
+ *     any other node is opened.  "Farther than the threshold" is taken as
  *     dist^2(q32_m, [lo,hi]) > r*r in FP32, with r = (float)(thresh * sigma),
  *     dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
  *   - summary interaction (Eq. 4 and the replacement rules after it, with the
- *     n_k multiplicity of readings R10/R11): the node acts as one source point
+ *     n_k members each counted, so the node acts as one source point
  *     at the centroid with momentum P, position derivative A and momentum
  *     derivative B/n.
  */
@@ -257,7 +257,7 @@ static void insert(otree *t, int64_t k, int64_t i) {
   }
 }
 
-/* Quantised coordinates of reading R7 from the FP32 positions. */
+/* Quantised coordinates (rule in the header) from the FP32 positions. */
 static void quantise(int64_t N, const float *q32, float lo[3], float hi[3],
                      uint32_t *kq) {
   for (int a = 0; a < 3; a++) {
@@ -308,13 +308,13 @@ static void tree_free(otree *t) {
   free(t->q32);
 }
 
-/* Threshold r*r of reading R9, in FP32. */
+/* Threshold r*r of the far test, in FP32. */
 static float far_threshold(double thresh, double sigma) {
   float r = (float)(thresh * sigma);
   return r * r;
 }
 
-/* Reading R9: is the node's actual range farther than the threshold? */
+/* Is the node's actual range farther than the threshold (rule in the header)? */
 static int is_far(const float *x, const onode *nd, float thr) {
   float dd[3];
   for (int a = 0; a < 3; a++) {
@@ -343,6 +343,7 @@ typedef struct {
   double sigma;
   float thr;
   int adjoint;
+  int64_t leaf; /* leaf-size variant: near nodes of <= leaf points taken exactly */
   int64_t m;
   double acc0[3], acc1[3];
   int64_t n_point, n_node;
@@ -390,6 +391,19 @@ static void node_source(visit_ctx *v, int64_t k) {
   record(v, 1, k);
 }
 
+/* Every point of node k, exactly (children in octant order). */
+static void all_points(visit_ctx *v, int64_t k) {
+  const otree *t = v->t;
+  const onode *nd = &t->nodes[k];
+  if (nd->n == 0) return;
+  if (nd->leaf) {
+    for (int64_t s = nd->head; s >= 0; s = t->next[s]) point_source(v, s);
+    return;
+  }
+  for (int c = 0; c < 8; c++)
+    if (nd->child[c] >= 0) all_points(v, nd->child[c]);
+}
+
 static void visit(visit_ctx *v, int64_t k) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
@@ -402,18 +416,23 @@ static void visit(visit_ctx *v, int64_t k) {
     for (int64_t s = nd->head; s >= 0; s = t->next[s]) point_source(v, s);
     return;
   }
+  if (nd->n <= v->leaf) { /* leaf-size variant: a near node of <= leaf points, exactly */
+    all_points(v, k);
+    return;
+  }
   for (int c = 0; c < 8; c++) /* case 3: open the node */
     if (nd->child[c] >= 0) visit(v, nd->child[c]);
 }
 
-static void bh_target(const otree *t, double sigma, float thr, int adjoint,
-                      int64_t m, double *o0, double *o1, int64_t *np,
-                      int64_t *nn, ilist *list) {
+static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
+                      int adjoint, int64_t m, double *o0, double *o1,
+                      int64_t *np, int64_t *nn, ilist *list) {
   visit_ctx v;
   memset(&v, 0, sizeof(v));
   v.t = t;
   v.sigma = sigma;
   v.thr = thr;
+  v.leaf = leaf;
   v.adjoint = adjoint;
   v.m = m;
   v.list = list;
@@ -434,7 +453,7 @@ static void bh_target(const otree *t, double sigma, float thr, int adjoint,
  * all pairs (Sec. 2.1); mode 1 = Barnes-Hut (Sec. 2.2).  counts (optional,
  * 2 entries) receives the number of point-point and point-node interactions. */
 void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
-               int mode, double thresh, double *F, double *Phi,
+               int mode, double thresh, int leaf, double *F, double *Phi,
                int64_t *counts) {
   int64_t np_tot = 0, nn_tot = 0;
   if (mode == GSREF_EXACT) {
@@ -449,7 +468,7 @@ void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
     for (int64_t i = 0; i < N; i++) {
       int64_t a, b;
-      bh_target(&t, sigma, thr, 0, i, F + 3 * i, Phi + 3 * i, &a, &b, NULL);
+      bh_target(&t, sigma, thr, leaf, 0, i, F + 3 * i, Phi + 3 * i, &a, &b, NULL);
       for (int c = 0; c < 3; c++) Phi[3 * i + c] /= sigma * sigma;
       np_tot += a;
       nn_tot += b;
@@ -475,7 +494,8 @@ void gsref_rhs_rows(int64_t N, const double *q, const double *p, double sigma,
  * beta^k = b + h dB (a = alpha^{k+1}, b = beta^{k+1}). */
 void gsref_adj_rhs(int64_t N, const double *q, const double *p,
                    const double *al, const double *be, double sigma, int mode,
-                   double thresh, double *dA, double *dB, int64_t *counts) {
+                   double thresh, int leaf, double *dA, double *dB,
+                   int64_t *counts) {
   int64_t np_tot = 0, nn_tot = 0;
   if (mode == GSREF_EXACT) {
 #pragma omp parallel for schedule(static)
@@ -489,7 +509,7 @@ void gsref_adj_rhs(int64_t N, const double *q, const double *p,
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
     for (int64_t i = 0; i < N; i++) {
       int64_t a, b;
-      bh_target(&t, sigma, thr, 1, i, dA + 3 * i, dB + 3 * i, &a, &b, NULL);
+      bh_target(&t, sigma, thr, leaf, 1, i, dA + 3 * i, dB + 3 * i, &a, &b, NULL);
       np_tot += a;
       nn_tot += b;
     }
@@ -523,15 +543,15 @@ static double half_p_dot_F(int64_t N, const double *p, const double *F) {
 /* Geodesic shooting (Eq. 1, Euler, h = 1/T).  H (optional, 2 entries) gets
  * H(q^0,p^0) and H(q^T,p^T) = 1/2 sum_i p_i . F_i in the same mode. */
 void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
-                 int T, int mode, double thresh, double *q1, double *p1,
-                 double *H) {
+                 int T, int mode, double thresh, int leaf, double *q1,
+                 double *p1, double *H) {
   double *F = (double *)malloc((size_t)N * 3 * sizeof(double));
   double *Phi = (double *)malloc((size_t)N * 3 * sizeof(double));
   double h = 1.0 / (double)T;
   memcpy(q1, q0, (size_t)N * 3 * sizeof(double));
   memcpy(p1, p0, (size_t)N * 3 * sizeof(double));
   for (int k = 0; k < T; k++) {
-    gsref_rhs(N, q1, p1, sigma, mode, thresh, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, F, Phi, NULL);
     if (k == 0 && H) H[0] = half_p_dot_F(N, p1, F);
     for (int64_t i = 0; i < 3 * N; i++) {
       q1[i] += h * F[i];
@@ -539,7 +559,7 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
     }
   }
   if (H) {
-    gsref_rhs(N, q1, p1, sigma, mode, thresh, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, F, Phi, NULL);
     H[1] = half_p_dot_F(N, p1, F);
   }
   free(F);
@@ -551,8 +571,8 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
  * gets q^T.  The whole trajectory is stored (plain, no checkpointing). */
 void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
                       const double *X, double sigma, int T, double lambda,
-                      int mode, double thresh, double *E, double *grad,
-                      double *q1) {
+                      int mode, double thresh, int leaf, double *E,
+                      double *grad, double *q1) {
   size_t sz = (size_t)N * 3;
   double *qs = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
   double *ps = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
@@ -568,7 +588,7 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
   memcpy(ps, p0, sz * sizeof(double));
   for (int k = 0; k < T; k++) {
     double *qk = qs + (size_t)k * sz, *pk = ps + (size_t)k * sz;
-    gsref_rhs(N, qk, pk, sigma, mode, thresh, F, Phi, NULL);
+    gsref_rhs(N, qk, pk, sigma, mode, thresh, leaf, F, Phi, NULL);
     if (k == 0) memcpy(F0, F, sz * sizeof(double));
     for (size_t i = 0; i < sz; i++) {
       qk[sz + i] = qk[i] + h * F[i];
@@ -591,7 +611,7 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
   }
   for (int k = T - 1; k >= 0; k--) {
     gsref_adj_rhs(N, qs + (size_t)k * sz, ps + (size_t)k * sz, al, be, sigma,
-                  mode, thresh, dA, dB, NULL);
+                  mode, thresh, leaf, dA, dB, NULL);
     for (size_t i = 0; i < sz; i++) {
       al[i] += h * dA[i];
       be[i] += h * dB[i];
@@ -635,7 +655,7 @@ void gsref_velocity(int64_t N, const double *q, const double *p, int64_t M,
 
 /* Shooting (exact, Eq. 1) with M tracer points x carried by the velocity
  * field of Eq. 3.  The tracers do not act on the particles; they take the
- * same explicit Euler steps (reading R4), from the particles' state at the
+ * same explicit Euler steps, from the particles' state at the
  * start of each step:  x^{k+1} = x^k + h v(x^k; q^k, p^k). */
 void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
                 const double *x0, double sigma, int T, double *q1, double *p1,
@@ -649,7 +669,7 @@ void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
   memcpy(x1, x0, (size_t)M * 3 * sizeof(double));
   for (int k = 0; k < T; k++) {
     gsref_velocity(N, q1, p1, M, x1, sigma, v);
-    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, 1, F, Phi, NULL);
     for (int64_t i = 0; i < 3 * M; i++) x1[i] += h * v[i];
     for (int64_t i = 0; i < 3 * N; i++) {
       q1[i] += h * F[i];
@@ -665,7 +685,7 @@ void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
 /* Tree inspection for tests.                                                 */
 /* ------------------------------------------------------------------------ */
 
-/* Per-point quantised coordinates and the 30-bit Morton code of reading R7
+/* Per-point quantised coordinates and the 30-bit Morton code of the rule in the header
  * (bit 3b+2 = x bit b, 3b+1 = y bit b, 3b = z bit b). */
 void gsref_morton(int64_t N, const double *q, uint32_t *kq, uint32_t *code) {
   float *q32 = (float *)malloc((size_t)N * 3 * sizeof(float));
@@ -783,8 +803,8 @@ int64_t gsref_tree(int64_t N, const double *q, const double *p,
  * point index) or 1 (node summary, id = preorder node id as exported by
  * gsref_tree).  Returns the list length (entries beyond cap are dropped). */
 int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
-                      double sigma, double thresh, int64_t m, int64_t cap,
-                      int64_t *kind, int64_t *id) {
+                      double sigma, double thresh, int leaf, int64_t m,
+                      int64_t cap, int64_t *kind, int64_t *id) {
   otree t;
   tree_build(&t, N, q, p, NULL, NULL);
   dfs_ctx c;
@@ -802,7 +822,8 @@ int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
   L.cap = cap;
   double o0[3], o1[3];
   int64_t a, b;
-  bh_target(&t, sigma, far_threshold(thresh, sigma), 0, m, o0, o1, &a, &b, &L);
+  bh_target(&t, sigma, far_threshold(thresh, sigma), leaf, 0, m, o0, o1, &a, &b,
+            &L);
   for (int64_t r = 0; r < L.len && r < cap; r++)
     if (kind[r] == 1) id[r] = c.remap[id[r]];
   free(order);

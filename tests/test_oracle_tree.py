@@ -9,7 +9,7 @@ from paper_1907_04834_gb300 import inputs
 
 
 def _quantise_f32(q):
-    """Reading R7 written directly in numpy float32 (each op rounds to FP32)."""
+    """The quantisation rule written directly in numpy float32 (each op rounds to FP32)."""
     q32 = q.astype(np.float32)
     lo, hi = q32.min(axis=0), q32.max(axis=0)
     ext = hi - lo
@@ -218,3 +218,59 @@ def test_bh_error_shrinks_with_threshold(oracle):
         errs.append(np.abs(Fb - F).max() / np.abs(F).max())
     assert errs[0] > errs[1] > errs[2] > errs[3]
     assert errs[1] < 1e-2
+
+
+@pytest.mark.parametrize("leaf", [4, 16])
+def test_leaf_size_variant_lists(oracle, leaf):
+    """Leaf-size variant: a near node of at most `leaf` points is taken
+    exactly instead of opened.  Sources still partition all points; a
+    summarised node is far, and every ancestor is near and holds more than
+    `leaf` points; the summaries are a subset of the paper's (leaf = 1)."""
+    n = 260
+    w = inputs.make("blobs", n, 23)
+    q, p = w.q0, w.p0
+    sigma = w.sigma * 0.6
+    t = oracle.tree(q, p)
+    r = np.float32(3.0 * sigma)
+    thr = np.float32(r * r)
+    q32 = q.astype(np.float32)
+    fewer = 0
+    for m in range(0, n, 5):
+        kind, ids = oracle.bh_list(q, p, sigma, m, 3.0, leaf=leaf)
+        kind1, ids1 = oracle.bh_list(q, p, sigma, m, 3.0)
+        seen = np.zeros(n, np.int64)
+        for kd, i in zip(kind, ids):
+            if kd == 1:
+                assert _far(q32[m], t["lo"][i], t["hi"][i], thr)
+                a = t["parent"][i]
+                while a >= 0:
+                    assert not _far(q32[m], t["lo"][a], t["hi"][a], thr)
+                    assert t["n"][a] > leaf
+                    a = t["parent"][a]
+                seen[t["order"][t["first"][i]:t["first"][i] + t["n"][i]]] += 1
+            else:
+                seen[i] += 1
+        assert np.all(seen == 1)
+        far_l = set(ids[kind == 1].tolist())
+        far_1 = set(ids1[kind1 == 1].tolist())
+        assert far_l <= far_1
+        fewer += len(far_1) - len(far_l)
+    assert fewer > 0  # the variant changes something here
+
+
+def test_leaf_size_limits(oracle):
+    """leaf = 1 is the paper's rule, bit for bit; leaf >= N takes every pair
+    exactly (the root holds the target, so it is never far)."""
+    w = inputs.make("blobs", 300, 29, T=3)
+    F1, P1, c1 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1)
+    Fl, Pl, cl = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=1)
+    assert np.array_equal(F1, Fl) and np.array_equal(P1, Pl) and np.array_equal(c1, cl)
+    Fe, Pe, _ = oracle.rhs(w.q0, w.p0, w.sigma)
+    FN, PN, cN = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=300)
+    assert cN[0] == 300 * 300 and cN[1] == 0
+    np.testing.assert_allclose(FN, Fe, rtol=1e-12, atol=1e-15 * np.abs(Fe).max())
+    np.testing.assert_allclose(PN, Pe, rtol=1e-12, atol=1e-13 * np.abs(Pe).max())
+    # interactions move from node summaries to exact pairs as leaf grows
+    c4 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=4)[2]
+    c16 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=16)[2]
+    assert c1[1] >= c4[1] >= c16[1] and c1[0] <= c4[0] <= c16[0]
