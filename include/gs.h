@@ -74,6 +74,12 @@ typedef struct gs_params {
                             backward pass; k > 0 = keep every k-th state and
                             recompute the others (memory (T/k + k) x N) */
   uint32_t flags;        /* reserved, must be 0 */
+  int32_t leaf_size;     /* GS_BH: 0 or 1 = the paper's rule (a leaf is one
+                            point, every near node is opened); L in [2, 32] =
+                            leaf-size variant: a node of at most L points that
+                            is not far is taken exactly, all its points, instead
+                            of being opened (far nodes are still summarised).
+                            Changes results; gs_autotune picks L by timing */
 } gs_params;
 
 typedef struct gs_ctx gs_ctx;
@@ -172,6 +178,21 @@ gs_status gs_flow(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
 gs_status gs_lbfgs(gs_ctx *ctx, const double *q0, double *p0, const double *X,
                    int64_t N, const gs_params *prm, int32_t m, int32_t iters,
                    double gtol, double *E_hist, int32_t *n_done, void *stream);
+
+/*
+ * Autotuner of the Barnes-Hut leaf size (gs_params.leaf_size) for a state
+ * (q, p) of N points (prm: GS_BH, its sigma and thresh_sigmas): times one
+ * forward and one adjoint right-hand side (tree build, walk, evaluations, as
+ * in a gradient step) for each candidate leaf size with CUDA events on the
+ * stream (best of three after a warm-up) and writes the fastest to *best.
+ * cand: n_cand candidates in [1, 32], or NULL for {1, 2, 4, 8, 16, 32};
+ * ms: NULL or n_cand times in milliseconds.  Leaf sizes above 1 change the
+ * approximation (more pairs exact), so the result is a choice for the
+ * caller, not applied by the library.  Synchronises the stream.
+ */
+gs_status gs_autotune(gs_ctx *ctx, const double *q, const double *p, int64_t N,
+                      const gs_params *prm, const int32_t *cand, int32_t n_cand,
+                      int32_t *best, double *ms, void *stream);
 
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
 

@@ -33,14 +33,15 @@ class Params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("thresh_sigmas", ctypes.c_double), ("T", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("leaf_size", ctypes.c_int32)]
 
 
-def make_params(sigma, T, mode=GS_EXACT, lam=1.0, thresh=3.0, ckpt_every=0, flags=0) -> Params:
+def make_params(sigma, T, mode=GS_EXACT, lam=1.0, thresh=3.0, ckpt_every=0, flags=0,
+                leaf_size=1) -> Params:
     if isinstance(mode, str):
         mode = {"exact": GS_EXACT, "bh": GS_BH}[mode.lower()]
     return Params(float(sigma), float(lam), float(thresh), int(T), int(mode), int(ckpt_every),
-                  int(flags))
+                  int(flags), int(leaf_size))
 
 
 _lib = None
@@ -59,6 +60,8 @@ _SIGS = {
                                           ctypes.c_double, _i32, _vp, _vp]),
     "gs_lbfgs": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _i32, _i32,
                                 ctypes.c_double, _vp, _vp, _vp]),
+    "gs_autotune": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _i32, _vp,
+                                   _vp, _vp]),
     "gs_flow": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp, _vp,
                                _vp, _vp]),
     "gs_velocity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _vp]),

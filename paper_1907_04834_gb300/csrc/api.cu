@@ -168,7 +168,7 @@ struct Key {
   }
   void params(const gs_params* prm) {
     add(prm->sigma), add(prm->lambda), add(prm->thresh_sigmas);
-    add(prm->T), add(prm->mode), add(prm->ckpt_every), add(prm->flags);
+    add(prm->T), add(prm->mode), add(prm->ckpt_every), add(prm->flags), add(prm->leaf_size);
   }
   void workspace(const gs_ctx* c) {
     for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
@@ -235,6 +235,8 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
   if (prm->ckpt_every < 0)
     return fail(c, GS_ERR_INVALID_ARG, "ckpt_every must be >= 0 (got %d)", prm->ckpt_every);
   if (prm->flags != 0) return fail(c, GS_ERR_INVALID_ARG, "flags must be 0");
+  if (prm->leaf_size < 0 || prm->leaf_size > 32)
+    return fail(c, GS_ERR_INVALID_ARG, "leaf_size must be in [0, 32] (got %d)", prm->leaf_size);
   return GS_OK;
 }
 
@@ -319,6 +321,7 @@ struct Solver {
   int T, mode;
   double sigma, s, h, lambda;
   float thr;  // Barnes-Hut threshold (r*r, FP32)
+  int leaf;   // Barnes-Hut leaf size (1 = the paper's rule)
   ExactGeom gf, ga;
   size_t pack_f4;  // float4 per pack slot
   int slots;       // pack slots allocated
@@ -513,6 +516,7 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     float r = (float)(prm->thresh_sigmas * prm->sigma);
     S.thr = r * r;
   }
+  S.leaf = std::max(1, (int)prm->leaf_size);
   S.pack_f4 = (size_t)(S.Npad / 2) * 3;
   S.slots = slots;
   ExactGeom g;
@@ -655,7 +659,7 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf};
   gs_status s;
   {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -714,7 +718,7 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S)};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf};
   gs_status s;
   if (reuse) {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -1297,7 +1301,7 @@ gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, co
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
-  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0};
+  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0, 0};
   if ((s = check_n(c, N)) || (s = check_params(c, &prm, false))) return s;
   if (M < 1 || M > (int64_t(1) << 30))
     return fail(c, GS_ERR_INVALID_ARG, "M must be in [1, 2^30] (got %lld)", (long long)M);
@@ -1477,6 +1481,85 @@ gs_status gs_lbfgs(gs_ctx* c, const double* q0, double* p0, const double* X, int
   return read_status(c, st);
 }
 
+gs_status gs_autotune(gs_ctx* c, const double* q, const double* p, int64_t N,
+                      const gs_params* prm, const int32_t* cand, int32_t n_cand, int32_t* best,
+                      double* ms, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if (prm->mode != GS_BH) return fail(c, GS_ERR_INVALID_ARG, "gs_autotune tunes GS_BH only");
+  static const int32_t kDefault[] = {1, 2, 4, 8, 16, 32};
+  if (!cand) {
+    cand = kDefault;
+    n_cand = 6;
+  }
+  if (n_cand < 1 || n_cand > 32) return fail(c, GS_ERR_INVALID_ARG, "n_cand must be in [1, 32]");
+  for (int k = 0; k < n_cand; k++)
+    if (cand[k] < 1 || cand[k] > 32)
+      return fail(c, GS_ERR_INVALID_ARG, "candidate leaf sizes must be in [1, 32]");
+  if (!best) return fail(c, GS_ERR_INVALID_ARG, "best is NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double *dq, *dp;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)))
+    return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0), "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, GS_ERR_CUDA, "event create failed");
+  }
+  double best_ms = 0.0;
+  int32_t best_l = cand[0];
+  gs_status rc = GS_OK;
+  const bool was_timing = c->timing;
+  c->timing = false;
+  for (int k = 0; k < n_cand && rc == GS_OK; k++) {
+    gs_params pk = *prm;
+    pk.leaf_size = cand[k];
+    Solver S;
+    if ((rc = solver_init(c, S, N, &pk, 1, true, st))) break;
+    if ((rc = solver_load(S, dq, dp, 0))) break;
+    // one forward and one adjoint right-hand side on (q, p), adjoint
+    // variables zero (their values do not change the work)
+    if (cudaMemsetAsync(c->al.p, 0, (size_t)N * 24, st) != cudaSuccess ||
+        cudaMemsetAsync(c->be.p, 0, (size_t)N * 24, st) != cudaSuccess ||
+        launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, S.abpack(0), st) !=
+            cudaSuccess) {
+      rc = cuda_fail(c, cudaGetLastError(), "autotune setup");
+      break;
+    }
+    float best_k = 0.f;
+    for (int rep = 0; rep < 4 && rc == GS_OK; rep++) {  // first run is a warm-up
+      cudaEventRecord(e0, st);
+      if ((rc = forward_rhs(S, 0, fwd_epi(S, -1, 0.0), nullptr, 0))) break;
+      if ((rc = adjoint_rhs(S, 0, 0, adj_epi(S, -1, 0.0, false, nullptr), nullptr, 0, true)))
+        break;
+      cudaEventRecord(e1, st);
+      float t = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+        rc = cuda_fail(c, cudaGetLastError(), "autotune timing");
+        break;
+      }
+      if (rep == 1 || (rep > 1 && t < best_k)) best_k = t;
+    }
+    if (rc != GS_OK) break;
+    if (ms) ms[k] = best_k;
+    if (k == 0 || best_k < best_ms) {
+      best_ms = best_k;
+      best_l = cand[k];
+    }
+  }
+  c->timing = was_timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GS_OK) return rc;
+  *best = best_l;
+  return read_status(c, st);
+}
+
 gs_status gs_rhs(gs_ctx* c, const double* q, const double* p, int64_t N, const gs_params* prm,
                  double* F, double* Phi, int64_t* counts, void* stream) {
   if (!c) return GS_ERR_INVALID_ARG;
@@ -1574,7 +1657,7 @@ gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_
   cudaStream_t st = (cudaStream_t)stream;
   const double* dq;
   if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
-  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0};
+  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0};
   Solver S;
   if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
   if ((s = solver_load(S, dq, dq, 0))) return s;

@@ -13,6 +13,12 @@
 // stepping into a node when any lane opens it and jumping to skip otherwise.
 // A lane's interactions are exactly those of its own recursive traversal.
 //
+// Leaf-size variant (leaf > 1): a node holding at most `leaf` points that a
+// lane does not find far is taken exactly, all of its points at once,
+// instead of being opened; its points are emitted as point entries (~i for
+// sorted point i) that the evaluation maps to their leaf records.  leaf = 1
+// is the paper's rule.
+//
 // Two phases:
 //   walk     -- decisions only, few registers.  The node range is cut in two
 //               slices at the group's middle point; the second slice starts
@@ -93,9 +99,11 @@ __device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& g
 }
 
 // Resume point of this lane at node s: test the ancestors of s from the root
-// down; the first one this lane finds far makes it skip past s.
+// down; the first one this lane finds far, or (leaf-size variant) near but
+// of at most `leaf` points -- taken whole by the slice that visits it --
+// makes it skip past s.
 __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float rz, float thr,
-                         int resume) {
+                         int leaf, int resume) {
   int path[12];
   int n = 0;
   for (int a = t.nparent[s]; a >= 0 && n < 12; a = t.nparent[a]) path[n++] = a;
@@ -103,7 +111,8 @@ __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float r
     const int a = path[k];
     if (resume > a) continue;
     const float4 lo = t.nbox[2 * a], hi = t.nbox[2 * a + 1];
-    if (box_dist2(rx, ry, rz, lo, hi) > thr) resume = __float_as_int(lo.w);
+    if (box_dist2(rx, ry, rz, lo, hi) > thr || __float_as_int(hi.w) <= leaf)
+      resume = __float_as_int(lo.w);
   }
   return resume;
 }
@@ -229,7 +238,8 @@ template <bool ADJ>
 __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nodes,
                                              unsigned* mask, float* soa, int n, int lane) {
   for (int e = lane; e < n; e += 32) {
-    const int nd = nodes[e];
+    int nd = nodes[e];
+    if (nd < 0) nd = ~nd + (int)t.offs[~nd + 1];  // point entry -> its leaf
     const float4 r0 = t.nrec[4 * nd], r1 = t.nrec[4 * nd + 1];
     soa[0 * TR_CAP + e] = r0.x, soa[1 * TR_CAP + e] = r0.y, soa[2 * TR_CAP + e] = r0.z;
     soa[3 * TR_CAP + e] = r1.x, soa[4 * TR_CAP + e] = r1.y, soa[5 * TR_CAP + e] = r1.z;
@@ -256,8 +266,9 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
 // (x and resume are then the state to resume from).  Returns false if stopped.
 template <bool COUNT, class Sink>
 __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
-                                           int end, const float4& rr, float thr, int& resume,
-                                           Sink& sink, int lane, long long& np, long long& nn) {
+                                           int end, const float4& rr, float thr, int leaf,
+                                           int& resume, Sink& sink, int lane, long long& np,
+                                           long long& nn) {
   int base = INT_MIN / 2;
   // window bit masks (bit j = node base + j): leaf, "all children leaves"
   unsigned leafmask = 0u, botmask = 0u;
@@ -292,7 +303,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       const unsigned mk = __ballot_sync(FULL, resume <= x);
       if (mk) {
         if (!sink.fits(r)) return false;
-        sink.add(x, r, mk);
+        sink.add(x, r, mk, false);
         if (COUNT) np += (long long)__popc(mk) * r;
       }
       x += r;
@@ -303,18 +314,22 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const bool active = x >= resume;
     const bool far = active && box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr;
     const unsigned mt = __ballot_sync(FULL, far), mo = __ballot_sync(FULL, active && !far);
-    // an opened node whose children are all leaves: take them at once
+    // an opened node whose children are all leaves: take them at once; a
+    // node of at most `leaf` points (leaf-size variant): take its points
+    const int ncount = __float_as_int(bh.w);
     const bool bottom = mo && ((botmask >> off) & 1u);
-    if (mt | (bottom ? 1u : 0u)) {
-      const int cn = bottom ? __float_as_int(bh.w) : 0;
+    const bool bucket = mo && !bottom && ncount <= leaf;
+    if (mt | ((bottom || bucket) ? 1u : 0u)) {
+      const int cn = (bottom || bucket) ? ncount : 0;
       // stop before x (state unchanged) when the sink is full
       if (!sink.fits((mt ? 1 : 0) + cn)) return false;
-      if (mt) sink.add(x, 1, mt);
-      if (bottom) sink.add(x + 1, cn, mo);
+      if (mt) sink.add(x, 1, mt, false);
+      if (bottom) sink.add(x + 1, cn, mo, false);
+      if (bucket) sink.add(t.ninfo[x].y, cn, mo, true);
       if (COUNT) nn += __popc(mt), np += (long long)__popc(mo) * cn;
     }
     if (far) resume = skip;
-    x = (mo && !bottom) ? x + 1 : skip;
+    x = (mo && !bottom && !bucket) ? x + 1 : skip;
   }
   return true;
 }
@@ -352,12 +367,13 @@ struct ListSink {
     tail = c;
     written += n;
   }
-  // n <= 32 entries (a leaf run, a node's children or one node), so at most
-  // one chunk fills per call
-  __device__ __forceinline__ void add(int node0, int n, unsigned mask) {
+  // n <= 32 entries (a leaf run, a node's children or points, or one node),
+  // so at most one chunk fills per call; points: entries ~(node0 + k)
+  __device__ __forceinline__ void add(int node0, int n, unsigned mask, bool points) {
     if (ovf) return;
     const int c2 = cnt + n;
-    if (lane < n && cnt + lane < BH_CHUNK) buf[cnt + lane] = make_int2(node0 + lane, (int)mask);
+    auto enc = [&](int k) { return points ? ~(node0 + k) : node0 + k; };
+    if (lane < n && cnt + lane < BH_CHUNK) buf[cnt + lane] = make_int2(enc(lane), (int)mask);
     if (c2 < BH_CHUNK) {
       cnt = c2;
       return;
@@ -366,7 +382,7 @@ struct ListSink {
     put_chunk(BH_CHUNK);
     __syncwarp();
     const int rest = c2 - BH_CHUNK;
-    if (lane < rest) buf[lane] = make_int2(node0 + (n - rest) + lane, (int)mask);
+    if (lane < rest) buf[lane] = make_int2(enc((n - rest) + lane), (int)mask);
     cnt = rest;
   }
   __device__ __forceinline__ void finish() {
@@ -394,10 +410,12 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int end = slice_end(t, gi, k);
   int resume = valid ? 0 : INT_MAX;
   // (an empty slice may start at the node count: no node to test there)
-  if (k > 0 && valid && x < end) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
+  if (k > 0 && valid && x < end)
+    resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
+  bool done =
+      walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, resume, sink, lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -473,11 +491,11 @@ struct EvalSink {
     __syncwarp();
     cnt = 0;
   }
-  __device__ __forceinline__ void add(int node0, int n, unsigned mk) {
+  __device__ __forceinline__ void add(int node0, int n, unsigned mk, bool points) {
     while (n > 0) {
       const int take = min(n, BH_CHUNK - cnt);
       if (lane < take) {
-        node[cnt + lane] = node0 + lane;
+        node[cnt + lane] = points ? ~(node0 + lane) : node0 + lane;
         mask[cnt + lane] = mk;
       }
       cnt += take;
@@ -511,12 +529,13 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   int x = slice_start(t, gi, k);
   const int end = slice_end(t, gi, k);
   int resume = me.valid ? 0 : INT_MAX;
-  if (k > 0 && me.valid && x < end) resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, resume);
+  if (k > 0 && me.valid && x < end)
+    resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane};
   long long np = 0, nn = 0;
-  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, resume, sink, lane, np, nn);
+  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, resume, sink, lane, np, nn);
   if (sink.cnt) sink.flush();
 #pragma unroll
   for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();

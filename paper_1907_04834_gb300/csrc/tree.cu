@@ -586,7 +586,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_oa = take(4 * N1),
                o_ob = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
-               o_nrec = take(64 * M), o_ninfo = take(8 * M), o_acnt = take(4 * M),
+               o_nrec = take(64 * M), o_acnt = take(4 * M),
                o_isum = take(96 * M), o_cnt = take(16),
                o_part = take(nl * 15 * 32 * sizeof(float2)),
                o_fb = take(nl * 15 * 32 * sizeof(float2));
@@ -606,7 +606,6 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     t->bbox_part = (float*)(b + o_bbp);
     t->bbox = (float*)(b + o_bb);
     t->nrec = (float4*)(b + o_nrec);
-    t->ninfo = (int2*)(b + o_ninfo);
     t->acnt = (int32_t*)(b + o_acnt);
     t->isum = (double*)(b + o_isum);
     t->counts = (int64_t*)(b + o_cnt);
@@ -627,7 +626,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     return at;
   };
   const size_t o_perm = take(4 * N1), o_offs = take(4 * (N1 + 1)), o_npar = take(4 * M),
-               o_nsc = take(8 * M), o_nbox = take(32 * M),
+               o_nsc = take(8 * M), o_ninfo = take(8 * M), o_nbox = take(32 * M),
                o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
                o_next = take(4 * (size_t)chunks), o_head = take(4 * nl), o_len = take(4 * nl),
                o_ovx = take(4 * nl), o_used = take(4);
@@ -637,6 +636,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     t->offs = (uint32_t*)(b + o_offs);
     t->nparent = (int32_t*)(b + o_npar);
     t->nsc = (int2*)(b + o_nsc);
+    t->ninfo = (int2*)(b + o_ninfo);
     t->nbox = (float4*)(b + o_nbox);
     L->ent = (int2*)(b + o_ent);
     L->next = (int*)(b + o_next);
@@ -729,6 +729,7 @@ void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
 // Walk groups of a step: the forest's table, or 32-point groups of one set.
 WalkGroups walk_groups(const BHStep& b) {
   WalkGroups g{};
+  g.leaf = b.leaf;
   if (b.f.S > 0) {
     g.groups = b.f.groups;
     g.G = b.f.G;

@@ -52,6 +52,7 @@ struct BHStep {
   const float4* pack;
   const float4* raw;
   BHForest f;
+  int leaf = 1;   // leaf-size variant (1 = the paper's rule)
 };
 
 cudaError_t tree_setup();

@@ -42,7 +42,8 @@ struct TreeArrays {
   float4* nbox;     // 2 per node: {lo.xyz, skip (int bits)}, {hi.xyz, count (int bits)}
   float4* nrec;     // 4 per node: source record {xs}, {P}, {A}, {B / n}
   int2* nsc;        // {skip, count} written at build time
-  int2* ninfo;      // {depth (-1 = leaf), first sorted position}
+  int2* ninfo;      // {depth (-1 = leaf), first sorted position} (kept per step: the
+                    // leaf-size variant's walk reads it, also when re-walking a kept tree)
   int32_t* nparent; // preorder id of the parent, -1 for the root
   int32_t* acnt;    // arrival counters of the bottom-up pass
   double* isum;     // 12 per node: sums of xs, p, a, b over members
@@ -119,6 +120,7 @@ struct WalkGroups {
   const int64_t* off;      // forest: S + 1 offsets
   int S;
   const double* centers;   // forest: S x 3
+  int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
 };
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions

@@ -2,10 +2,13 @@
 and exports every entry point declared in include/gs.h, and argument errors
 are rejected before any CUDA work."""
 import ctypes
+import os
 
 import pytest
 
 from paper_1907_04834_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -39,9 +42,27 @@ def test_create_rejects_bad_device(lib):
     assert lib.gs_create(0, None) == _lib.GS_ERR_INVALID_ARG
 
 
-def test_params_layout_matches_header():
-    # sigma, lambda, thresh (3 doubles) + T, mode, ckpt_every, flags (4 x 32 bit)
-    assert ctypes.sizeof(_lib.Params) == 40
+def test_params_layout_matches_header(tmp_path):
+    """The ctypes mirror of gs_params has the header's size and field
+    offsets (a C program compiled against include/gs.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = ["sigma", "lambda", "thresh_sigmas", "T", "mode", "ckpt_every", "flags", "leaf_size"]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"gs.h\"\n"
+                   "int main(void) { printf(\"%zu\", sizeof(gs_params));"
+                   + "".join(f' printf(" %zu", offsetof(gs_params, {n}));' for n in names)
+                   + " return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    fields = ["sigma", "lambda_", "thresh_sigmas", "T", "mode", "ckpt_every", "flags", "leaf_size"]
+    assert vals[0] == ctypes.sizeof(_lib.Params)
+    assert vals[1:] == [getattr(_lib.Params, f).offset for f in fields]
     p = _lib.make_params(2.0, 7, "bh", 0.5, 3.0, 2)
     assert (p.sigma, p.lambda_, p.thresh_sigmas, p.T, p.mode, p.ckpt_every) == (
         2.0, 0.5, 3.0, 7, 1, 2)
