@@ -24,6 +24,7 @@ _LIB = os.path.join(_HERE, "libgsref.so")
 
 EXACT = 0
 BH = 1
+TRUNC = 2
 
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")

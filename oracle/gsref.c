@@ -70,6 +70,7 @@
 
 #define GSREF_EXACT 0
 #define GSREF_BH 1
+#define GSREF_TRUNC 2 /* pure truncation: only pairs within the threshold */
 #define MAX_DEPTH 10
 
 /* ------------------------------------------------------------------------ */
@@ -130,6 +131,39 @@ static void rhs_exact_row(int64_t N, const double *q, const double *p,
   }
 }
 
+/* Pure 3-sigma truncation (a variant of the method, not the paper's
+ * approximation): the sums of Eq. 1 and of the adjoint over the pairs whose
+ * FP32-rounded positions lie within the threshold r = (float)(thresh *
+ * sigma): dx = x32_m - x32_j per axis, d2 = (dx*dx + dy*dy) + dz*dz in FP32
+ * (each operation rounded, no contraction), pair taken iff d2 <= r*r.  The
+ * relation is symmetric, and a point is always within its own threshold. */
+static int within_cut(const float *a, const float *b, float thr) {
+  float dx = a[0] - b[0];
+  float dy = a[1] - b[1];
+  float dz = a[2] - b[2];
+  float d2 = dx * dx;
+  d2 = d2 + dy * dy;
+  d2 = d2 + dz * dz;
+  return d2 <= thr;
+}
+
+static int64_t rhs_trunc_row(int64_t N, const double *q, const double *p,
+                             const float *q32, float thr, double sigma,
+                             int64_t i, double *F, double *Phi) {
+  double f[3] = {0, 0, 0}, ph[3] = {0, 0, 0};
+  int64_t n = 0;
+  for (int64_t j = 0; j < N; j++)
+    if (within_cut(q32 + 3 * i, q32 + 3 * j, thr)) {
+      fwd_pair(q + 3 * i, p + 3 * i, q + 3 * j, p + 3 * j, sigma, f, ph);
+      n++;
+    }
+  for (int a = 0; a < 3; a++) {
+    F[a] = f[a];
+    Phi[a] = ph[a] / (sigma * sigma);
+  }
+  return n;
+}
+
 static void adj_exact_row(int64_t N, const double *q, const double *p,
                           const double *al, const double *be, double sigma,
                           int64_t i, double *dA, double *dB) {
@@ -141,6 +175,31 @@ static void adj_exact_row(int64_t N, const double *q, const double *p,
     dA[a] = da[a];
     dB[a] = db[a];
   }
+}
+
+static int64_t adj_trunc_row(int64_t N, const double *q, const double *p,
+                             const double *al, const double *be,
+                             const float *q32, float thr, double sigma,
+                             int64_t i, double *dA, double *dB) {
+  double da[3] = {0, 0, 0}, db[3] = {0, 0, 0};
+  int64_t n = 0;
+  for (int64_t j = 0; j < N; j++)
+    if (within_cut(q32 + 3 * i, q32 + 3 * j, thr)) {
+      adj_pair(q + 3 * i, p + 3 * i, al + 3 * i, be + 3 * i, q + 3 * j,
+               p + 3 * j, al + 3 * j, be + 3 * j, sigma, da, db);
+      n++;
+    }
+  for (int a = 0; a < 3; a++) {
+    dA[a] = da[a];
+    dB[a] = db[a];
+  }
+  return n;
+}
+
+static float *round_positions(int64_t N, const double *q) {
+  float *q32 = (float *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(float));
+  for (int64_t i = 0; i < 3 * N; i++) q32[i] = (float)q[i];
+  return q32;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -450,7 +509,8 @@ static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
 /* ------------------------------------------------------------------------ */
 
 /* Forward right-hand side (F, Phi) of Eq. 1 for every point.  mode 0 = exact
- * all pairs (Sec. 2.1); mode 1 = Barnes-Hut (Sec. 2.2).  counts (optional,
+ * all pairs (Sec. 2.1); mode 1 = Barnes-Hut (Sec. 2.2); mode 2 = pure
+ * truncation (pairs within the threshold only; counts[0] = those pairs).  counts (optional,
  * 2 entries) receives the number of point-point and point-node interactions. */
 void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
                int mode, double thresh, int leaf, double *F, double *Phi,
@@ -461,6 +521,13 @@ void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
     for (int64_t i = 0; i < N; i++)
       rhs_exact_row(N, q, p, sigma, i, F + 3 * i, Phi + 3 * i);
     np_tot = N * N;
+  } else if (mode == GSREF_TRUNC) {
+    float *q32 = round_positions(N, q);
+    float thr = far_threshold(thresh, sigma);
+#pragma omp parallel for schedule(static) reduction(+ : np_tot)
+    for (int64_t i = 0; i < N; i++)
+      np_tot += rhs_trunc_row(N, q, p, q32, thr, sigma, i, F + 3 * i, Phi + 3 * i);
+    free(q32);
   } else {
     otree t;
     tree_build(&t, N, q, p, NULL, NULL);
@@ -502,6 +569,13 @@ void gsref_adj_rhs(int64_t N, const double *q, const double *p,
     for (int64_t i = 0; i < N; i++)
       adj_exact_row(N, q, p, al, be, sigma, i, dA + 3 * i, dB + 3 * i);
     np_tot = N * N;
+  } else if (mode == GSREF_TRUNC) {
+    float *q32 = round_positions(N, q);
+    float thr = far_threshold(thresh, sigma);
+#pragma omp parallel for schedule(static) reduction(+ : np_tot)
+    for (int64_t i = 0; i < N; i++)
+      np_tot += adj_trunc_row(N, q, p, al, be, q32, thr, sigma, i, dA + 3 * i, dB + 3 * i);
+    free(q32);
   } else {
     otree t;
     tree_build(&t, N, q, p, al, be);
