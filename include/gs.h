@@ -60,7 +60,13 @@ typedef enum gs_status {
 
 typedef enum gs_mode {
   GS_EXACT = 0, /* all pairs, O(N^2) per step (Sec. 2.1) */
-  GS_BH = 1     /* octree / threshold approximation (Sec. 2.2) */
+  GS_BH = 1,    /* octree / threshold approximation (Sec. 2.2) */
+  GS_TRUNC = 2  /* variant, not the paper's approximation: pure truncation --
+                   only pairs whose FP32 positions lie within thresh_sigmas *
+                   sigma (dx = x_i - x_j per axis, (dx*dx + dy*dy) + dz*dz <=
+                   r*r, each operation rounded), the same cut in the adjoint;
+                   far nodes are dropped instead of summarised.  rhs counts:
+                   {pairs kept, 0} */
 } gs_mode;
 
 typedef struct gs_params {

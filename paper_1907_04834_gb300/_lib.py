@@ -18,7 +18,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_NONFINITE, GS_ERR_TIM
     GS_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
                 4: "GS_ERR_NONFINITE", 5: "GS_ERR_TIMEOUT", 6: "GS_ERR_UNSUPPORTED"}
-GS_EXACT, GS_BH = 0, 1
+GS_EXACT, GS_BH, GS_TRUNC = 0, 1, 2
 RHS_NOALLOC_MAX_N = 16384  # GS_RHS_NOALLOC_MAX_N in include/gs.h
 KERNEL_CLASSES = ("exact_fwd", "exact_adj", "tree_build", "bh_fwd", "bh_adj", "bh_walk")
 
@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
 def make_params(sigma, T, mode=GS_EXACT, lam=1.0, thresh=3.0, ckpt_every=0, flags=0,
                 leaf_size=1) -> Params:
     if isinstance(mode, str):
-        mode = {"exact": GS_EXACT, "bh": GS_BH}[mode.lower()]
+        mode = {"exact": GS_EXACT, "bh": GS_BH, "trunc": GS_TRUNC}[mode.lower()]
     return Params(float(sigma), float(lam), float(thresh), int(T), int(mode), int(ckpt_every),
                   int(flags), int(leaf_size))
 

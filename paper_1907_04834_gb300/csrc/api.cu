@@ -226,9 +226,10 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
     return fail(c, GS_ERR_INVALID_ARG, "sigma must be finite and > 0 (got %g)", prm->sigma);
   if (prm->T < 1 || prm->T > 1000000)
     return fail(c, GS_ERR_INVALID_ARG, "T must be in [1, 1e6] (got %d)", prm->T);
-  if (prm->mode != GS_EXACT && prm->mode != GS_BH)
-    return fail(c, GS_ERR_INVALID_ARG, "mode must be GS_EXACT or GS_BH (got %d)", prm->mode);
-  if (prm->mode == GS_BH && (!(prm->thresh_sigmas > 0.0) || std::isnan(prm->thresh_sigmas)))
+  if (prm->mode != GS_EXACT && prm->mode != GS_BH && prm->mode != GS_TRUNC)
+    return fail(c, GS_ERR_INVALID_ARG, "mode must be GS_EXACT, GS_BH or GS_TRUNC (got %d)",
+                prm->mode);
+  if (prm->mode != GS_EXACT && (!(prm->thresh_sigmas > 0.0) || std::isnan(prm->thresh_sigmas)))
     return fail(c, GS_ERR_INVALID_ARG, "thresh_sigmas must be > 0 (got %g)", prm->thresh_sigmas);
   if (need_lambda && (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda)))
     return fail(c, GS_ERR_INVALID_ARG, "lambda must be finite and >= 0 (got %g)", prm->lambda);
@@ -539,7 +540,7 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
   CK(c->packs.ensure(pbytes), "workspace");
   gs_status ps = pad_packs(S, c->packs.as<float4>(), slots);
   if (ps != GS_OK) return ps;
-  if (S.mode == GS_BH) {
+  if (S.mode != GS_EXACT) {
     size_t rb = (size_t)slots * S.Npad * sizeof(float4);
     CK(c->raws.ensure(rb), "workspace");
   }
@@ -581,12 +582,12 @@ gs_status solver_pack(Solver& S, int slot) {
     const Batch& b = *S.batch;
     CK(launch_batch_pack(c->q.as<double>(), c->p.as<double>(), S.N, b.dev.off, b.dev.poff, b.S,
                          b.dev.centers, S.s, S.pack(slot),
-                         S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
+                         S.mode != GS_EXACT ? S.raw(slot) : nullptr, S.st),
        "pack");
     return GS_OK;
   }
   CK(launch_pack(c->q.as<double>(), c->p.as<double>(), S.N, S.scal(SC_CENTER), S.s, S.pack(slot),
-                 S.mode == GS_BH ? S.raw(slot) : nullptr, S.st),
+                 S.mode != GS_EXACT ? S.raw(slot) : nullptr, S.st),
      "pack");
   return GS_OK;
 }
@@ -625,7 +626,7 @@ FwdEpi fwd_epi(const Solver& S, int next_slot, double h) {
   e.q = S.c->q.as<double>();
   e.p = S.c->p.as<double>();
   e.pack_next = next_slot >= 0 ? S.pack(next_slot) : nullptr;
-  e.raw_next = (next_slot >= 0 && S.mode == GS_BH) ? S.raw(next_slot) : nullptr;
+  e.raw_next = (next_slot >= 0 && S.mode != GS_EXACT) ? S.raw(next_slot) : nullptr;
   e.center = S.scal(SC_CENTER);
   e.s = S.s;
   e.phi_scale = 1.0 / (S.sigma * S.sigma * S.s);
@@ -659,7 +660,8 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
+           S.mode == GS_TRUNC};
   gs_status s;
   {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -718,7 +720,8 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     }
     return GS_OK;
   }
-  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf};
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
+           S.mode == GS_TRUNC};
   gs_status s;
   if (reuse) {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -763,7 +766,7 @@ gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, c
   const int slots = R.ck ? R.ck + 1 : R.T + 1;
   // Barnes-Hut: one tree slot per step kept for the backward stage (a
   // segment's steps with checkpointing)
-  const int tslots = prm->mode == GS_BH ? (R.ck ? R.ck : R.T) : 1;
+  const int tslots = prm->mode != GS_EXACT ? (R.ck ? R.ck : R.T) : 1;
   if ((s = solver_init(c, R.S, N, prm, slots, true, st, tslots, batch))) return s;
   const size_t b3 = (size_t)N * 3 * sizeof(double);
   R.nck = R.ck ? (R.T + R.ck - 1) / R.ck : 0;
@@ -841,7 +844,7 @@ gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const d
       for (int k = k0; k < k1; k++) {
         // the last step of the segment only builds its tree and lists
         // (its state update is not needed): the adjoint reuses them
-        if (S.mode == GS_BH || k < k1 - 1) {
+        if (S.mode != GS_EXACT || k < k1 - 1) {
           FwdEpi e = fwd_epi(S, k < k1 - 1 ? k - k0 + 1 : -1, k < k1 - 1 ? S.h : 0.0);
           if ((s = forward_rhs(S, k - k0, e, nullptr, k - k0))) return s;
         }
@@ -1488,7 +1491,8 @@ gs_status gs_autotune(gs_ctx* c, const double* q, const double* p, int64_t N,
   c->err.clear();
   gs_status s;
   if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
-  if (prm->mode != GS_BH) return fail(c, GS_ERR_INVALID_ARG, "gs_autotune tunes GS_BH only");
+  if (prm->mode == GS_EXACT)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_autotune tunes the tree modes (GS_BH, GS_TRUNC)");
   static const int32_t kDefault[] = {1, 2, 4, 8, 16, 32};
   if (!cand) {
     cand = kDefault;
@@ -1589,7 +1593,7 @@ gs_status gs_rhs(gs_ctx* c, const double* q, const double* p, int64_t N, const g
     return s;
   if (counts) {
     CK(cudaStreamSynchronize(st), "stream synchronize");
-    if (S.mode == GS_BH) bh_counts(c->tree, cnt);
+    if (S.mode != GS_EXACT) bh_counts(c->tree, cnt);
     counts[0] = cnt[0];
     counts[1] = cnt[1];
   }
@@ -1633,7 +1637,7 @@ gs_status gs_adj_rhs(gs_ctx* c, const double* q, const double* p, const double* 
     return s;
   if (counts) {
     CK(cudaStreamSynchronize(st), "stream synchronize");
-    if (S.mode == GS_BH) bh_counts(c->tree, cnt);
+    if (S.mode != GS_EXACT) bh_counts(c->tree, cnt);
     counts[0] = cnt[0];
     counts[1] = cnt[1];
   }

@@ -13,6 +13,12 @@
 // stepping into a node when any lane opens it and jumping to skip otherwise.
 // A lane's interactions are exactly those of its own recursive traversal.
 //
+// Pure truncation (a variant, not the paper's approximation): far boxes are
+// dropped instead of summarised, and the evaluation keeps only the pairs
+// whose FP32 raw positions pass the same test as the far rule applied to
+// the two points (d2 <= r*r); a point's distance to its leaf's box is never
+// below the box distance in FP32, so dropping far boxes loses no such pair.
+//
 // Leaf-size variant (leaf > 1): a node holding at most `leaf` points that a
 // lane does not find far is taken exactly, all of its points at once,
 // instead of being opened; its points are emitted as point entries (~i for
@@ -54,6 +60,7 @@ struct Own {
   int i, o;  // sorted position, original index
   bool valid;
   float4 m0, m1, m2, m3;  // record: xs, p, a, b
+  float rx, ry, rz;       // FP32 raw position (truncation test)
 };
 
 __device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi, int lane,
@@ -72,7 +79,17 @@ __device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi
     w.m2 = t.nrec[4 * leaf + 2];
     w.m3 = t.nrec[4 * leaf + 3];
   }
+  const float4 rb = t.nbox[2 * leaf];  // a leaf's box is its point
+  w.rx = rb.x, w.ry = rb.y, w.rz = rb.z;
   return w;
+}
+
+// Truncation test of a pair in FP32: (dx*dx + dy*dy) + dz*dz <= thr, each
+// operation rounded, no contraction.
+__device__ __forceinline__ bool within(float ax, float ay, float az, float bx, float by, float bz,
+                                       float thr) {
+  const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <= thr;
 }
 
 // Slices of the group's node range [nb, ne): with K = BH_SLICES, h = K/2 and
@@ -130,9 +147,22 @@ struct Acc {
 
 // Evaluates sources e in [0, n) (n even) whose records are staged in soa
 // (component-major, stride TR_CAP) and whose lane masks are in mask[].
-template <bool ADJ>
+// TRUNC: the raw positions follow the record components in soa; a pair is
+// also dropped unless it passes the truncation test, and npair counts the
+// pairs kept.
+template <bool ADJ, bool TRUNC>
 __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const unsigned* mask,
-                                           int n, int lane, const Own& me) {
+                                           int n, int lane, const Own& me, float thr,
+                                           int& npair) {
+  constexpr int NR = ADJ ? 12 : 6;
+  auto keep = [&](int e, bool b) {
+    if constexpr (TRUNC) {
+      b = b && within(me.rx, me.ry, me.rz, soa[NR * TR_CAP + e], soa[(NR + 1) * TR_CAP + e],
+                      soa[(NR + 2) * TR_CAP + e], thr);
+      npair += b ? 1 : 0;
+    }
+    return b;
+  };
   const f2 X = f2_dup(me.m0.x), Y = f2_dup(me.m0.y), Z = f2_dup(me.m0.z);
   const f2 U = f2_dup(me.m1.x), V = f2_dup(me.m1.y), W = f2_dup(me.m1.z);
   auto ld = [&](int c, int e) { return *reinterpret_cast<const f2*>(soa + c * TR_CAP + e); };
@@ -140,7 +170,7 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
     f2 fx = 0, fy = 0, fz = 0, hx = 0, hy = 0, hz = 0;
 #pragma unroll 2
     for (int e = 0; e < n; e += 2) {
-      const bool b0 = (mask[e] >> lane) & 1u, b1 = (mask[e + 1] >> lane) & 1u;
+      const bool b0 = keep(e, (mask[e] >> lane) & 1u), b1 = keep(e + 1, (mask[e + 1] >> lane) & 1u);
       const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
       f2 r = f2_mul(dx, dx);
       r = f2_fma(dy, dy, r);
@@ -172,7 +202,7 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
     f2 a1x = 0, a1y = 0, a1z = 0, a2x = 0, a2y = 0, a2z = 0, a3x = 0, a3y = 0, a3z = 0;
     f2 b1x = 0, b1y = 0, b1z = 0, b2x = 0, b2y = 0, b2z = 0;
     for (int e = 0; e < n; e += 2) {
-      const bool b0 = (mask[e] >> lane) & 1u, b1 = (mask[e + 1] >> lane) & 1u;
+      const bool b0 = keep(e, (mask[e] >> lane) & 1u), b1 = keep(e + 1, (mask[e + 1] >> lane) & 1u);
       const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
       f2 r = f2_mul(dx, dx);
       r = f2_fma(dy, dy, r);
@@ -233,10 +263,12 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
   }
 }
 
-// Stages the records of queued nodes[0, n) into soa (padding n to even).
-template <bool ADJ>
+// Stages the records of queued nodes[0, n) into soa (padding n to even);
+// TRUNC: also their FP32 raw positions (entries are leaves then).
+template <bool ADJ, bool TRUNC>
 __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nodes,
                                              unsigned* mask, float* soa, int n, int lane) {
+  constexpr int NR = ADJ ? 12 : 6;
   for (int e = lane; e < n; e += 32) {
     int nd = nodes[e];
     if (nd < 0) nd = ~nd + (int)t.offs[~nd + 1];  // point entry -> its leaf
@@ -248,10 +280,15 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
       soa[6 * TR_CAP + e] = r2.x, soa[7 * TR_CAP + e] = r2.y, soa[8 * TR_CAP + e] = r2.z;
       soa[9 * TR_CAP + e] = r3.x, soa[10 * TR_CAP + e] = r3.y, soa[11 * TR_CAP + e] = r3.z;
     }
+    if constexpr (TRUNC) {
+      const float4 rb = t.nbox[2 * nd];
+      soa[NR * TR_CAP + e] = rb.x, soa[(NR + 1) * TR_CAP + e] = rb.y;
+      soa[(NR + 2) * TR_CAP + e] = rb.z;
+    }
   }
   if (n & 1) {
     if (lane == 0) mask[n] = 0u;
-    if (lane < (ADJ ? 12 : 6)) soa[lane * TR_CAP + n] = 0.f;
+    if (lane < NR + (TRUNC ? 3 : 0)) soa[lane * TR_CAP + n] = 0.f;
     n++;
   }
   return n;
@@ -267,8 +304,8 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
 template <bool COUNT, class Sink>
 __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
                                            int end, const float4& rr, float thr, int leaf,
-                                           int& resume, Sink& sink, int lane, long long& np,
-                                           long long& nn) {
+                                           bool trunc, int& resume, Sink& sink, int lane,
+                                           long long& np, long long& nn) {
   int base = INT_MIN / 2;
   // window bit masks (bit j = node base + j): leaf, "all children leaves"
   unsigned leafmask = 0u, botmask = 0u;
@@ -304,7 +341,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       if (mk) {
         if (!sink.fits(r)) return false;
         sink.add(x, r, mk, false);
-        if (COUNT) np += (long long)__popc(mk) * r;
+        if (COUNT && !trunc) np += (long long)__popc(mk) * r;
       }
       x += r;
       continue;
@@ -319,14 +356,16 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const int ncount = __float_as_int(bh.w);
     const bool bottom = mo && ((botmask >> off) & 1u);
     const bool bucket = mo && !bottom && ncount <= leaf;
-    if (mt | ((bottom || bucket) ? 1u : 0u)) {
+    // (truncation: a far node is dropped, not summarised)
+    const unsigned ms = trunc ? 0u : mt;
+    if (ms | ((bottom || bucket) ? 1u : 0u)) {
       const int cn = (bottom || bucket) ? ncount : 0;
       // stop before x (state unchanged) when the sink is full
-      if (!sink.fits((mt ? 1 : 0) + cn)) return false;
-      if (mt) sink.add(x, 1, mt, false);
+      if (!sink.fits((ms ? 1 : 0) + cn)) return false;
+      if (ms) sink.add(x, 1, ms, false);
       if (bottom) sink.add(x + 1, cn, mo, false);
       if (bucket) sink.add(t.ninfo[x].y, cn, mo, true);
-      if (COUNT) nn += __popc(mt), np += (long long)__popc(mo) * cn;
+      if (COUNT && !trunc) nn += __popc(mt), np += (long long)__popc(mo) * cn;
     }
     if (far) resume = skip;
     x = (mo && !bottom && !bucket) ? x + 1 : skip;
@@ -414,8 +453,8 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  bool done =
-      walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, resume, sink, lane, np, nn);
+  bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, resume, sink,
+                                lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -433,10 +472,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // One warp per list: partial sums of its entries, part[(l*NC + c)*32 + lane].
 // The adjoint variant is held to 128 registers (4 blocks per SM, a few
 // spilled values): measured faster than 3 blocks at 168 registers.
-template <bool ADJ>
+template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
-    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg) {
-  constexpr int NR = ADJ ? 12 : 6;
+    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts) {
+  constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
   __shared__ int s_node[TR_WARPS][TR_CAP];
@@ -448,6 +487,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
   const Own me = load_own(t, group_info(t, N, wg.groups, l / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
   A.zero();
+  int npair = 0;
   const int n = L.len[l];
   int chunk = L.head[l];
   for (int c0 = 0; c0 < n; c0 += BH_CHUNK) {
@@ -461,19 +501,24 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     }
     if (c0 + BH_CHUNK < n) chunk = L.next[chunk];
     __syncwarp();
-    const int ce = stage_records<ADJ>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
+    const int ce = stage_records<ADJ, TRUNC>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
     __syncwarp();
-    eval_batch<ADJ>(A, s_soa[w], s_mask[w], ce, lane, me);
+    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, npair);
   }
 #pragma unroll
   for (int c = 0; c < NC; c++) L.part[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
+  if (TRUNC && counts) {
+    const int tot = __reduce_add_sync(FULL, (unsigned)npair);
+    if (lane == 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)tot);
+  }
 }
 
 // ------------------------------------------------------------------ fallback
 // Sink that evaluates queued entries in place, in chunks of BH_CHUNK entries
 // aligned exactly like the list evaluation's chunks, so a slice gives the
 // same sums whichever path evaluates it.
-template <bool ADJ>
+template <bool ADJ, bool TRUNC>
 struct EvalSink {
   const TreeArrays* t;
   int* node;
@@ -482,12 +527,14 @@ struct EvalSink {
   Acc<ADJ>* A;
   const Own* me;
   int cnt, lane;
+  float thr;
+  int npair;
   __device__ __forceinline__ bool fits(int) const { return true; }
   __device__ __forceinline__ void flush() {
     __syncwarp();
-    const int ce = stage_records<ADJ>(*t, node, mask, soa, cnt, lane);
+    const int ce = stage_records<ADJ, TRUNC>(*t, node, mask, soa, cnt, lane);
     __syncwarp();
-    eval_batch<ADJ>(*A, soa, mask, ce, lane, *me);
+    eval_batch<ADJ, TRUNC>(*A, soa, mask, ce, lane, *me, thr, npair);
     __syncwarp();
     cnt = 0;
   }
@@ -508,11 +555,11 @@ struct EvalSink {
 
 // Evaluates a slice whose list overflowed: walks it again from its start and
 // evaluates in place; partial sums go to L.fb[(l*NC + c)*32 + lane].
-template <bool ADJ, bool COUNT>
+template <bool ADJ, bool COUNT, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
                   WalkGroups wg, int64_t* counts) {
-  constexpr int NR = ADJ ? 12 : 6;
+  constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ float4 s_box[TR_WARPS][32][2];
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
@@ -533,13 +580,17 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   Acc<ADJ> A;
   A.zero();
-  EvalSink<ADJ> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane};
+  EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, 0};
   long long np = 0, nn = 0;
-  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, resume, sink, lane, np, nn);
+  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, resume, sink, lane, np, nn);
   if (sink.cnt) sink.flush();
 #pragma unroll
   for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
-  if (COUNT && lane == 0) {
+  if (COUNT && TRUNC) {  // pairs kept by the truncation test
+    const int tot = __reduce_add_sync(FULL, (unsigned)sink.npair);
+    if (lane == 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)tot);
+  } else if (COUNT && lane == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
   }
@@ -597,25 +648,30 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
   return cudaGetLastError();
 }
 
-template <bool ADJ>
+template <bool ADJ, bool TRUNC>
 static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr,
                         const BHLists& L, const WalkGroups& wg, const FwdEpi& fe,
                         const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
   if (counts)
-    k_bh_fallback<ADJ, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+    k_bh_fallback<ADJ, true, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   else
-    k_bh_fallback<ADJ, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
-  k_bh_eval<ADJ><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg);
+    k_bh_fallback<ADJ, false, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts);
   k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae);
 }
 
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
                            const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
-  if (!adj) eval_launch<false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
-  else eval_launch<true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+  if (wg.trunc) {
+    if (!adj) eval_launch<false, true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+    else eval_launch<true, true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+  } else {
+    if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+    else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+  }
   note_launches(3);
   return cudaGetLastError();
 }

@@ -730,6 +730,7 @@ void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
 WalkGroups walk_groups(const BHStep& b) {
   WalkGroups g{};
   g.leaf = b.leaf;
+  g.trunc = b.trunc;
   if (b.f.S > 0) {
     g.groups = b.f.groups;
     g.G = b.f.G;

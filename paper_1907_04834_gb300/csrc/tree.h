@@ -53,6 +53,7 @@ struct BHStep {
   const float4* raw;
   BHForest f;
   int leaf = 1;   // leaf-size variant (1 = the paper's rule)
+  bool trunc = false;  // pure truncation variant (far nodes dropped, pairs cut)
 };
 
 cudaError_t tree_setup();

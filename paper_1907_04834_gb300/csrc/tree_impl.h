@@ -121,6 +121,7 @@ struct WalkGroups {
   int S;
   const double* centers;   // forest: S x 3
   int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
+  bool trunc;              // pure truncation: far nodes dropped, pairs cut at the threshold
 };
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions
