@@ -119,6 +119,7 @@ __device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& g
 // down; the first one this lane finds far, or (leaf-size variant) near but
 // of at most `leaf` points -- taken whole by the slice that visits it --
 // makes it skip past s.
+template <bool VAR>
 __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float rz, float thr,
                          int leaf, int resume) {
   int path[12];
@@ -128,7 +129,7 @@ __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float r
     const int a = path[k];
     if (resume > a) continue;
     const float4 lo = t.nbox[2 * a], hi = t.nbox[2 * a + 1];
-    if (box_dist2(rx, ry, rz, lo, hi) > thr || __float_as_int(hi.w) <= leaf)
+    if (box_dist2(rx, ry, rz, lo, hi) > thr || (VAR && __float_as_int(hi.w) <= leaf))
       resume = __float_as_int(lo.w);
   }
   return resume;
@@ -301,7 +302,8 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
 // consecutive leaves, or -- when an opened node's children are all leaves --
 // those children at once.  sink.fits(n) false stops the walk before node x
 // (x and resume are then the state to resume from).  Returns false if stopped.
-template <bool COUNT, class Sink>
+// VAR = false compiles the paper's rule only (leaf and trunc ignored).
+template <bool COUNT, bool VAR, class Sink>
 __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
                                            int end, const float4& rr, float thr, int leaf,
                                            bool trunc, int& resume, Sink& sink, int lane,
@@ -341,7 +343,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       if (mk) {
         if (!sink.fits(r)) return false;
         sink.add(x, r, mk, false);
-        if (COUNT && !trunc) np += (long long)__popc(mk) * r;
+        if (COUNT && !(VAR && trunc)) np += (long long)__popc(mk) * r;
       }
       x += r;
       continue;
@@ -355,9 +357,9 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     // node of at most `leaf` points (leaf-size variant): take its points
     const int ncount = __float_as_int(bh.w);
     const bool bottom = mo && ((botmask >> off) & 1u);
-    const bool bucket = mo && !bottom && ncount <= leaf;
+    const bool bucket = VAR && mo && !bottom && ncount <= leaf;
     // (truncation: a far node is dropped, not summarised)
-    const unsigned ms = trunc ? 0u : mt;
+    const unsigned ms = (VAR && trunc) ? 0u : mt;
     if (ms | ((bottom || bucket) ? 1u : 0u)) {
       const int cn = (bottom || bucket) ? ncount : 0;
       // stop before x (state unchanged) when the sink is full
@@ -365,7 +367,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       if (ms) sink.add(x, 1, ms, false);
       if (bottom) sink.add(x + 1, cn, mo, false);
       if (bucket) sink.add(t.ninfo[x].y, cn, mo, true);
-      if (COUNT && !trunc) nn += __popc(mt), np += (long long)__popc(mo) * cn;
+      if (COUNT && !(VAR && trunc)) nn += __popc(mt), np += (long long)__popc(mo) * cn;
     }
     if (far) resume = skip;
     x = (mo && !bottom && !bucket) ? x + 1 : skip;
@@ -432,7 +434,7 @@ struct ListSink {
 };
 
 // One warp per (group, slice): emits the ordered interaction list.
-template <bool COUNT>
+template <bool COUNT, bool VAR>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
               WalkGroups wg, int64_t* counts) {
@@ -450,11 +452,11 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   int resume = valid ? 0 : INT_MAX;
   // (an empty slice may start at the node count: no node to test there)
   if (k > 0 && valid && x < end)
-    resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
+    resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  bool done = walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, resume, sink,
-                                lane, np, nn);
+  bool done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, resume,
+                                     sink, lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -577,12 +579,13 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int end = slice_end(t, gi, k);
   int resume = me.valid ? 0 : INT_MAX;
   if (k > 0 && me.valid && x < end)
-    resume = resume_at(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
+    resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, 0};
   long long np = 0, nn = 0;
-  walk_nodes<COUNT>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, resume, sink, lane, np, nn);
+  walk_nodes<COUNT, true>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, resume, sink, lane, np,
+                          nn);
   if (sink.cnt) sink.flush();
 #pragma unroll
   for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
@@ -642,8 +645,15 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
-  if (counts) k_bh_walk<true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
-  else k_bh_walk<false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  const bool var = wg.leaf > 1 || wg.trunc;  // the paper's rule runs the lean walk
+  if (counts && var)
+    k_bh_walk<true, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  else if (counts)
+    k_bh_walk<true, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  else if (var)
+    k_bh_walk<false, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  else
+    k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   note_launches(1);
   return cudaGetLastError();
 }
