@@ -64,6 +64,9 @@ def parse_args():
                     help="skip the leaf-size and truncation variant lines (launch-list captures)")
     ap.add_argument("--batched", action="store_true",
                     help="measure the 64-subject batched workload (separate JSON line)")
+    ap.add_argument("--sphere", action="store_true",
+                    help="measure the 1M-point sphere workload: Barnes-Hut gradient, T = 40, "
+                         "checkpoint every 6 steps (separate JSON line)")
     ap.add_argument("--probe", choices=["bh", "exact", "batched"],
                     help="for profiler captures: two rounds of one forward and one adjoint "
                          "right-hand side at the workload's initial state (batched: one "
@@ -497,12 +500,54 @@ def run_batched(args):
     return 0
 
 
+def run_sphere(args):
+    """N = 1,000,000 points on a bumpy 50 mm sphere, sigma = 1 mm, T = 40:
+    Barnes-Hut gradient with the trajectory checkpointed every 6 steps (the
+    paper's rule and the autotuned leaf size), CUDA events around each call."""
+    import torch
+    from paper_1907_04834_gb300 import native, inputs
+    native.build()
+    import paper_1907_04834_gb300 as gs
+    w = inputs.config("sphere1m")
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    q0, p0, X = t(w.q0), t(w.p0), t(w.X)
+    _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
+    best, _ = gs.autotune(q0, p0, w.sigma, thresh=THRESH)
+    res = {}
+    for name, leaf in (("bh", 1), (f"bh_leaf{best}", best)):
+        fn = lambda: gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH,
+                                   ckpt_every=6, leaf_size=leaf)
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_ev.record()
+            fn()
+            b_ev.record()
+            torch.cuda.synchronize()
+            ts.append(a_ev.elapsed_time(b_ev))
+        res[name] = statistics.median(ts)
+    line = {"mode": "sphere", "unit": "ms per gradient", "steps": args.steps,
+            "warmup": args.warmup, "ms": res,
+            "bh_interactions_per_point_step": (cnt[0] + cnt[1]) / w.N,
+            "config": {"workload": f"sphere1m: N={w.N} points on a 50 mm sphere with 32 radial "
+                                   f"bumps, sigma={w.sigma} mm, T={w.T}, lambda={w.lam}, "
+                                   "checkpoint every 6 steps, Barnes-Hut threshold 3 sigma"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.probe:
         return run_probe(args)
     if args.batched:
         return run_batched(args)
+    if args.sphere:
+        return run_sphere(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -53,23 +53,25 @@ def _load():
     build()
     lib = ctypes.CDLL(_LIB)
     i64, dbl, cint = ctypes.c_int64, ctypes.c_double, ctypes.c_int
-    lib.gsref_rhs.argtypes = [i64, _f64p, _f64p, dbl, cint, dbl, cint, _f64p, _f64p, _i64p]
+    lib.gsref_rhs.argtypes = [i64, _f64p, _f64p, dbl, cint, dbl, cint, cint, _f64p, _f64p,
+                              _i64p]
     lib.gsref_rhs_rows.argtypes = [i64, _f64p, _f64p, dbl, i64, _i64p, _f64p, _f64p]
-    lib.gsref_adj_rhs.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, dbl, cint, dbl, cint,
+    lib.gsref_adj_rhs.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, dbl, cint, dbl, cint, cint,
                                   _f64p, _f64p, _i64p]
     lib.gsref_adj_rhs_rows.argtypes = [i64, _f64p, _f64p, _f64p, _f64p, dbl, i64, _i64p,
                                        _f64p, _f64p]
-    lib.gsref_shoot.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, _f64p, _f64p,
-                                _f64p]
+    lib.gsref_shoot.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, cint, _f64p,
+                                _f64p, _f64p]
     lib.gsref_shoot_grad.argtypes = [i64, _f64p, _f64p, _f64p, dbl, cint, dbl, cint, dbl, cint,
-                                     _f64p, _f64p, _f64p]
+                                     cint, _f64p, _f64p, _f64p]
     lib.gsref_morton.argtypes = [i64, _f64p, _u32p, _u32p]
     lib.gsref_velocity.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, _f64p]
     lib.gsref_flow.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, cint, _f64p, _f64p, _f64p]
     lib.gsref_tree.argtypes = [i64, _f64p, _f64p, ctypes.c_void_p, ctypes.c_void_p, _i64p, i64,
                                _i64p, _f64p, _f32p]
     lib.gsref_tree.restype = i64
-    lib.gsref_bh_list.argtypes = [i64, _f64p, _f64p, dbl, dbl, cint, i64, i64, _i64p, _i64p]
+    lib.gsref_bh_list.argtypes = [i64, _f64p, _f64p, dbl, dbl, cint, cint, i64, i64, _i64p,
+                                  _i64p]
     lib.gsref_bh_list.restype = i64
     lib.gsref_num_threads.restype = cint
     _lib = lib
@@ -84,15 +86,17 @@ def num_threads() -> int:
     return int(_load().gsref_num_threads())
 
 
-def rhs(q, p, sigma, mode=EXACT, thresh=3.0, leaf=1):
+def rhs(q, p, sigma, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     """Forward right-hand side (F, Phi) of Eq. 1, plus interaction counts
     (point-point, point-node).  leaf > 1: Barnes-Hut leaf-size variant (a
-    near node of at most `leaf` points is taken exactly)."""
+    near node of at most `leaf` points is taken exactly); crit = 1:
+    opening-angle variant of the far test with theta = thresh."""
     q, p = _c(q), _c(p)
     n = q.shape[0]
     F, Phi = np.empty_like(q), np.empty_like(q)
     cnt = np.zeros(2, np.int64)
-    _load().gsref_rhs(n, q, p, float(sigma), int(mode), float(thresh), int(leaf), F, Phi, cnt)
+    _load().gsref_rhs(n, q, p, float(sigma), int(mode), float(thresh), int(leaf), int(crit), F,
+                      Phi, cnt)
     return F, Phi, cnt
 
 
@@ -123,13 +127,13 @@ def rhs_rows(q, p, sigma, rows):
     return F, Phi
 
 
-def adj_rhs(q, p, al, be, sigma, mode=EXACT, thresh=3.0, leaf=1):
+def adj_rhs(q, p, al, be, sigma, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     """Adjoint right-hand side: alpha^k = a + h dA, beta^k = b + h dB."""
     q, p, al, be = _c(q), _c(p), _c(al), _c(be)
     dA, dB = np.empty_like(q), np.empty_like(q)
     cnt = np.zeros(2, np.int64)
     _load().gsref_adj_rhs(q.shape[0], q, p, al, be, float(sigma), int(mode), float(thresh),
-                          int(leaf), dA, dB, cnt)
+                          int(leaf), int(crit), dA, dB, cnt)
     return dA, dB, cnt
 
 
@@ -142,24 +146,24 @@ def adj_rhs_rows(q, p, al, be, sigma, rows):
     return dA, dB
 
 
-def shoot(q0, p0, sigma, T, mode=EXACT, thresh=3.0, leaf=1):
+def shoot(q0, p0, sigma, T, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     """Geodesic shooting: returns q(1), p(1), [H(0), H(1)]."""
     q0, p0 = _c(q0), _c(p0)
     q1, p1 = np.empty_like(q0), np.empty_like(q0)
     H = np.zeros(2)
     _load().gsref_shoot(q0.shape[0], q0, p0, float(sigma), int(T), int(mode), float(thresh),
-                        int(leaf), q1, p1, H)
+                        int(leaf), int(crit), q1, p1, H)
     return q1, p1, H
 
 
-def shoot_grad(q0, p0, X, sigma, T, lam, mode=EXACT, thresh=3.0, leaf=1):
+def shoot_grad(q0, p0, X, sigma, T, lam, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     """Objective E = [total, H0, data] (Eq. 2) and dE/dp0 by the discrete
     adjoint; also returns q(1)."""
     q0, p0, X = _c(q0), _c(p0), _c(X)
     E = np.zeros(3)
     grad, q1 = np.empty_like(q0), np.empty_like(q0)
     _load().gsref_shoot_grad(q0.shape[0], q0, p0, X, float(sigma), int(T), float(lam),
-                             int(mode), float(thresh), int(leaf), E, grad, q1)
+                             int(mode), float(thresh), int(leaf), int(crit), E, grad, q1)
     return E, grad, q1
 
 
@@ -197,13 +201,13 @@ def tree(q, p, al=None, be=None):
                 sa=stat[:, 6:9], sb=stat[:, 9:12], lo=rng[:, 0:3], hi=rng[:, 3:6])
 
 
-def bh_list(q, p, sigma, m, thresh=3.0, leaf=1):
+def bh_list(q, p, sigma, m, thresh=3.0, leaf=1, crit=0):
     """Interaction list of target ``m``: arrays (kind, id); kind 0 = point
     (id = point index), kind 1 = node summary (id = preorder node id)."""
     q, p = _c(q), _c(p)
     cap = q.shape[0] * 2 + 16
     kind = np.zeros(cap, np.int64)
     ids = np.zeros(cap, np.int64)
-    L = _load().gsref_bh_list(q.shape[0], q, p, float(sigma), float(thresh), int(leaf), int(m),
-                              cap, kind, ids)
+    L = _load().gsref_bh_list(q.shape[0], q, p, float(sigma), float(thresh), int(leaf),
+                              int(crit), int(m), cap, kind, ids)
     return kind[:L], ids[:L]

@@ -390,6 +390,39 @@ static int is_far(const float *x, const onode *nd, float thr) {
   return d2 > thr;
 }
 
+/* Opening-angle variant (classic Barnes-Hut form, not the paper's rule): with
+ * s the largest side of the node's FP32 actual range and c its centre,
+ * c = (lo + hi) * 0.5, the node is summarised iff s*s < theta^2 * d2, where
+ * d2 = (dx*dx + dy*dy) + dz*dz, dx = x - c per axis, and thr = theta32 *
+ * theta32 (theta32 = (float)theta); all FP32, each operation rounded. */
+static int is_far_angle(const float *x, const onode *nd, float thr) {
+  float s = nd->hi[0] - nd->lo[0];
+  float sy = nd->hi[1] - nd->lo[1];
+  float sz = nd->hi[2] - nd->lo[2];
+  if (sy > s) s = sy;
+  if (sz > s) s = sz;
+  float d[3];
+  for (int a = 0; a < 3; a++) {
+    float c = (nd->lo[a] + nd->hi[a]) * 0.5f;
+    d[a] = x[a] - c;
+  }
+  float d2 = d[0] * d[0];
+  d2 = d2 + d[1] * d[1];
+  d2 = d2 + d[2] * d[2];
+  float ss = s * s;
+  float td = thr * d2;
+  return ss < td;
+}
+
+static float angle_threshold(double theta) {
+  float t = (float)theta;
+  return t * t;
+}
+
+static float rule_threshold(int crit, double thresh, double sigma) {
+  return crit ? angle_threshold(thresh) : far_threshold(thresh, sigma);
+}
+
 /* Interaction lists are produced by the same traversal, so tests can check
  * which sources each target took (kind 0 = point, 1 = node summary). */
 typedef struct {
@@ -403,6 +436,7 @@ typedef struct {
   float thr;
   int adjoint;
   int64_t leaf; /* leaf-size variant: near nodes of <= leaf points taken exactly */
+  int crit;     /* 0: the paper's distance rule; 1: opening-angle variant */
   int64_t m;
   double acc0[3], acc1[3];
   int64_t n_point, n_node;
@@ -467,7 +501,8 @@ static void visit(visit_ctx *v, int64_t k) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
   if (nd->n == 0) return;
-  if (nd->n >= 2 && is_far(t->q32 + 3 * v->m, nd, v->thr)) {
+  const float *x = t->q32 + 3 * v->m;
+  if (nd->n >= 2 && (v->crit ? is_far_angle(x, nd, v->thr) : is_far(x, nd, v->thr))) {
     node_source(v, k); /* case 2: summarised far node */
     return;
   }
@@ -484,7 +519,7 @@ static void visit(visit_ctx *v, int64_t k) {
 }
 
 static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
-                      int adjoint, int64_t m, double *o0, double *o1,
+                      int crit, int adjoint, int64_t m, double *o0, double *o1,
                       int64_t *np, int64_t *nn, ilist *list) {
   visit_ctx v;
   memset(&v, 0, sizeof(v));
@@ -492,6 +527,7 @@ static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
   v.sigma = sigma;
   v.thr = thr;
   v.leaf = leaf;
+  v.crit = crit;
   v.adjoint = adjoint;
   v.m = m;
   v.list = list;
@@ -513,8 +549,8 @@ static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
  * truncation (pairs within the threshold only; counts[0] = those pairs).  counts (optional,
  * 2 entries) receives the number of point-point and point-node interactions. */
 void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
-               int mode, double thresh, int leaf, double *F, double *Phi,
-               int64_t *counts) {
+               int mode, double thresh, int leaf, int crit, double *F,
+               double *Phi, int64_t *counts) {
   int64_t np_tot = 0, nn_tot = 0;
   if (mode == GSREF_EXACT) {
 #pragma omp parallel for schedule(static)
@@ -531,11 +567,11 @@ void gsref_rhs(int64_t N, const double *q, const double *p, double sigma,
   } else {
     otree t;
     tree_build(&t, N, q, p, NULL, NULL);
-    float thr = far_threshold(thresh, sigma);
+    float thr = rule_threshold(crit, thresh, sigma);
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
     for (int64_t i = 0; i < N; i++) {
       int64_t a, b;
-      bh_target(&t, sigma, thr, leaf, 0, i, F + 3 * i, Phi + 3 * i, &a, &b, NULL);
+      bh_target(&t, sigma, thr, leaf, crit, 0, i, F + 3 * i, Phi + 3 * i, &a, &b, NULL);
       for (int c = 0; c < 3; c++) Phi[3 * i + c] /= sigma * sigma;
       np_tot += a;
       nn_tot += b;
@@ -561,7 +597,7 @@ void gsref_rhs_rows(int64_t N, const double *q, const double *p, double sigma,
  * beta^k = b + h dB (a = alpha^{k+1}, b = beta^{k+1}). */
 void gsref_adj_rhs(int64_t N, const double *q, const double *p,
                    const double *al, const double *be, double sigma, int mode,
-                   double thresh, int leaf, double *dA, double *dB,
+                   double thresh, int leaf, int crit, double *dA, double *dB,
                    int64_t *counts) {
   int64_t np_tot = 0, nn_tot = 0;
   if (mode == GSREF_EXACT) {
@@ -579,11 +615,11 @@ void gsref_adj_rhs(int64_t N, const double *q, const double *p,
   } else {
     otree t;
     tree_build(&t, N, q, p, al, be);
-    float thr = far_threshold(thresh, sigma);
+    float thr = rule_threshold(crit, thresh, sigma);
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : np_tot, nn_tot)
     for (int64_t i = 0; i < N; i++) {
       int64_t a, b;
-      bh_target(&t, sigma, thr, leaf, 1, i, dA + 3 * i, dB + 3 * i, &a, &b, NULL);
+      bh_target(&t, sigma, thr, leaf, crit, 1, i, dA + 3 * i, dB + 3 * i, &a, &b, NULL);
       np_tot += a;
       nn_tot += b;
     }
@@ -617,15 +653,15 @@ static double half_p_dot_F(int64_t N, const double *p, const double *F) {
 /* Geodesic shooting (Eq. 1, Euler, h = 1/T).  H (optional, 2 entries) gets
  * H(q^0,p^0) and H(q^T,p^T) = 1/2 sum_i p_i . F_i in the same mode. */
 void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
-                 int T, int mode, double thresh, int leaf, double *q1,
-                 double *p1, double *H) {
+                 int T, int mode, double thresh, int leaf, int crit,
+                 double *q1, double *p1, double *H) {
   double *F = (double *)malloc((size_t)N * 3 * sizeof(double));
   double *Phi = (double *)malloc((size_t)N * 3 * sizeof(double));
   double h = 1.0 / (double)T;
   memcpy(q1, q0, (size_t)N * 3 * sizeof(double));
   memcpy(p1, p0, (size_t)N * 3 * sizeof(double));
   for (int k = 0; k < T; k++) {
-    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
     if (k == 0 && H) H[0] = half_p_dot_F(N, p1, F);
     for (int64_t i = 0; i < 3 * N; i++) {
       q1[i] += h * F[i];
@@ -633,7 +669,7 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
     }
   }
   if (H) {
-    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
     H[1] = half_p_dot_F(N, p1, F);
   }
   free(F);
@@ -645,7 +681,7 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
  * gets q^T.  The whole trajectory is stored (plain, no checkpointing). */
 void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
                       const double *X, double sigma, int T, double lambda,
-                      int mode, double thresh, int leaf, double *E,
+                      int mode, double thresh, int leaf, int crit, double *E,
                       double *grad, double *q1) {
   size_t sz = (size_t)N * 3;
   double *qs = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
@@ -662,7 +698,7 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
   memcpy(ps, p0, sz * sizeof(double));
   for (int k = 0; k < T; k++) {
     double *qk = qs + (size_t)k * sz, *pk = ps + (size_t)k * sz;
-    gsref_rhs(N, qk, pk, sigma, mode, thresh, leaf, F, Phi, NULL);
+    gsref_rhs(N, qk, pk, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
     if (k == 0) memcpy(F0, F, sz * sizeof(double));
     for (size_t i = 0; i < sz; i++) {
       qk[sz + i] = qk[i] + h * F[i];
@@ -685,7 +721,7 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
   }
   for (int k = T - 1; k >= 0; k--) {
     gsref_adj_rhs(N, qs + (size_t)k * sz, ps + (size_t)k * sz, al, be, sigma,
-                  mode, thresh, leaf, dA, dB, NULL);
+                  mode, thresh, leaf, crit, dA, dB, NULL);
     for (size_t i = 0; i < sz; i++) {
       al[i] += h * dA[i];
       be[i] += h * dB[i];
@@ -743,7 +779,7 @@ void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
   memcpy(x1, x0, (size_t)M * 3 * sizeof(double));
   for (int k = 0; k < T; k++) {
     gsref_velocity(N, q1, p1, M, x1, sigma, v);
-    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, 1, F, Phi, NULL);
+    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, 1, 0, F, Phi, NULL);
     for (int64_t i = 0; i < 3 * M; i++) x1[i] += h * v[i];
     for (int64_t i = 0; i < 3 * N; i++) {
       q1[i] += h * F[i];
@@ -877,8 +913,8 @@ int64_t gsref_tree(int64_t N, const double *q, const double *p,
  * point index) or 1 (node summary, id = preorder node id as exported by
  * gsref_tree).  Returns the list length (entries beyond cap are dropped). */
 int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
-                      double sigma, double thresh, int leaf, int64_t m,
-                      int64_t cap, int64_t *kind, int64_t *id) {
+                      double sigma, double thresh, int leaf, int crit,
+                      int64_t m, int64_t cap, int64_t *kind, int64_t *id) {
   otree t;
   tree_build(&t, N, q, p, NULL, NULL);
   dfs_ctx c;
@@ -896,8 +932,8 @@ int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
   L.cap = cap;
   double o0[3], o1[3];
   int64_t a, b;
-  bh_target(&t, sigma, far_threshold(thresh, sigma), leaf, 0, m, o0, o1, &a, &b,
-            &L);
+  bh_target(&t, sigma, rule_threshold(crit, thresh, sigma), leaf, crit, 0, m, o0, o1,
+            &a, &b, &L);
   for (int64_t r = 0; r < L.len && r < cap; r++)
     if (kind[r] == 1) id[r] = c.remap[id[r]];
   free(order);

@@ -274,3 +274,61 @@ def test_leaf_size_limits(oracle):
     c4 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=4)[2]
     c16 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, leaf=16)[2]
     assert c1[1] >= c4[1] >= c16[1] and c1[0] <= c4[0] <= c16[0]
+
+
+def _far_angle(x32, lo, hi, thr):
+    s = np.float32(max(np.float32(hi[0] - lo[0]), np.float32(hi[1] - lo[1]),
+                       np.float32(hi[2] - lo[2])))
+    c = ((lo + hi).astype(np.float32) * np.float32(0.5)).astype(np.float32)
+    d = (x32 - c).astype(np.float32)
+    d2 = np.float32(d[0] * d[0])
+    d2 = np.float32(d2 + np.float32(d[1] * d[1]))
+    d2 = np.float32(d2 + np.float32(d[2] * d[2]))
+    return bool(np.float32(s * s) < np.float32(thr * d2))
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.7])
+def test_opening_angle_variant_lists(oracle, theta):
+    """Opening-angle variant (classic Barnes-Hut form): sources partition the
+    points; a summarised node passes the angle rule and none of its
+    ancestors does; no node holding the target itself is summarised (a
+    point inside a box has d <= sqrt(3)/2 s, so s^2 > theta^2 d^2 for theta <= 1)."""
+    n = 300
+    w = inputs.make("blobs", n, 31)
+    q, p = w.q0, w.p0
+    t = oracle.tree(q, p)
+    t32 = np.float32(theta)
+    thr = np.float32(t32 * t32)
+    q32 = q.astype(np.float32)
+    nfar = 0
+    for m in range(0, n, 7):
+        kind, ids = oracle.bh_list(q, p, w.sigma, m, theta, crit=1)
+        seen = np.zeros(n, np.int64)
+        for kd, i in zip(kind, ids):
+            if kd == 1:
+                nfar += 1
+                assert _far_angle(q32[m], t["lo"][i], t["hi"][i], thr)
+                members = t["order"][t["first"][i]:t["first"][i] + t["n"][i]]
+                assert m not in members
+                a = t["parent"][i]
+                while a >= 0:
+                    assert not _far_angle(q32[m], t["lo"][a], t["hi"][a], thr)
+                    a = t["parent"][a]
+                seen[members] += 1
+            else:
+                seen[i] += 1
+        assert np.all(seen == 1)
+    assert nfar > 0
+
+
+def test_opening_angle_limits_and_error(oracle):
+    w = inputs.make("blobs", 400, 37)
+    Fe, Pe, _ = oracle.rhs(w.q0, w.p0, w.sigma)
+    F0, P0, c0 = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, thresh=1e-30, crit=1)
+    assert c0[1] == 0 and c0[0] == 400 * 400
+    np.testing.assert_allclose(F0, Fe, rtol=1e-12, atol=1e-15 * np.abs(Fe).max())
+    errs = []
+    for theta in (0.9, 0.5, 0.25):
+        F, _, _ = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, thresh=theta, crit=1)
+        errs.append(np.abs(F - Fe).max())
+    assert errs[0] > errs[1] > errs[2]
