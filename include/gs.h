@@ -86,6 +86,13 @@ typedef struct gs_params {
                             is not far is taken exactly, all its points, instead
                             of being opened (far nodes are still summarised).
                             Changes results; gs_autotune picks L by timing */
+  int32_t criterion;     /* GS_BH far test: 0 = the paper's rule (the node's
+                            FP32 actual range farther than thresh_sigmas *
+                            sigma); 1 = opening-angle variant (classic
+                            Barnes-Hut form): summarised iff s*s < theta^2 *
+                            d2, s the largest side of the range, d2 the FP32
+                            squared distance to its centre (lo + hi) * 0.5,
+                            theta = thresh_sigmas in (0, 1] (dimensionless) */
 } gs_params;
 
 typedef struct gs_ctx gs_ctx;

@@ -98,13 +98,14 @@ def _ctx_for(t: torch.Tensor) -> Context:
     return context(d if d is not None else None)
 
 
-def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, leaf_size=1, stream=None):
+def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, leaf_size=1, criterion=0,
+          stream=None):
     """Geodesic shooting (Eq. 1, Euler).  Returns (q1, p1, H) with H = None or
     the tensor [H(q0,p0), H(q1,p1)]."""
     q0 = _pts(q0, "q0")
     p0 = _pts(p0, "p0", q0.shape[0])
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size)
+    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
     q1, p1 = _like(q0), _like(q0)
     H = _like(q0, (2,)) if with_H else None
     c.check(c.lib.gs_shoot(c.handle, _ptr(q0), _ptr(p0), q0.shape[0], ctypes.byref(prm), _ptr(q1),
@@ -113,14 +114,14 @@ def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, leaf_size=1,
 
 
 def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_every=0,
-               leaf_size=1, stream=None):
+               leaf_size=1, criterion=0, stream=None):
     """Objective of Eq. 2 and dE/dp0.  Returns (E, grad, q1) with
     E = [E, H(q0,p0), lambda |q1 - X|^2]."""
     q0 = _pts(q0, "q0")
     n = q0.shape[0]
     p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size, criterion=criterion)
     E = _like(q0, (3,))
     grad, q1 = _like(q0), _like(q0)
     c.check(c.lib.gs_shoot_grad(c.handle, _ptr(q0), _ptr(p0), _ptr(X), n, ctypes.byref(prm),
@@ -129,7 +130,7 @@ def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_ever
 
 
 def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.0,
-                  ckpt_every=0, leaf_size=1, stream=None):
+                  ckpt_every=0, leaf_size=1, criterion=0, stream=None):
     """Independent registrations of the subjects delimited by ``offsets``
     (S+1 increasing ints, rows of q0/p0/X).  Returns (E (S, 3), grad (N, 3)),
     E[s] = [E, H(q0,p0), lambda |q1 - X|^2] of subject s."""
@@ -141,7 +142,7 @@ def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.
     if S < 1 or int(off[-1]) != n:
         raise ValueError("offsets must have S+1 entries ending at N")
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size, criterion=criterion)
     E = _like(q0, (S, 3))
     grad = _like(q0)
     c.check(c.lib.gs_shoot_batched(c.handle, S, _ptr(off), _ptr(q0), _ptr(p0), _ptr(X),
@@ -151,7 +152,7 @@ def shoot_batched(q0, p0, X, offsets, sigma, T, lam=1.0, mode="exact", thresh=3.
 
 
 def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, mode="exact",
-                    thresh=3.0, ckpt_every=0, leaf_size=1, stream=None):
+                    thresh=3.0, ckpt_every=0, leaf_size=1, criterion=0, stream=None):
     """Fixed-step gradient descent on the subjects' initial momenta
     (gs_descend_batched): ``iters`` times p0 <- p0 - step * dE/dp0.
     Returns (p0 after the last update (N, 3), E history (iters, S, 3))."""
@@ -163,7 +164,7 @@ def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, m
     if S < 1 or int(off[-1]) != n:
         raise ValueError("offsets must have S+1 entries ending at N")
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size, criterion=criterion)
     p = p0.clone()
     Eh = _like(q0, (int(iters), S, 3))
     c.check(c.lib.gs_descend_batched(c.handle, S, _ptr(off), _ptr(q0), _ptr(p), _ptr(X),
@@ -173,7 +174,7 @@ def descend_batched(q0, p0, X, offsets, sigma, T, lam=1.0, step=0.1, iters=50, m
 
 
 def lbfgs(q0, p0, X, sigma, T, lam=1.0, m=8, iters=50, gtol=1e-6, mode="exact", thresh=3.0,
-          ckpt_every=0, leaf_size=1, stream=None):
+          ckpt_every=0, leaf_size=1, criterion=0, stream=None):
     """L-BFGS on the initial momenta (gs_lbfgs).  Returns (p0 after the last
     iterate, E history of the initial point and each accepted iterate,
     iterations done)."""
@@ -181,7 +182,7 @@ def lbfgs(q0, p0, X, sigma, T, lam=1.0, m=8, iters=50, gtol=1e-6, mode="exact", 
     n = q0.shape[0]
     p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size, criterion=criterion)
     p = p0.clone()
     Eh = torch.empty(int(iters) + 1, dtype=torch.float64)
     done = ctypes.c_int32(0)
@@ -238,12 +239,12 @@ def velocity(q, p, x, sigma, stream=None):
     return v
 
 
-def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, stream=None):
+def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=None):
     """One forward right-hand side: (F, Phi, (point pairs, node pairs))."""
     q = _pts(q, "q")
     p = _pts(p, "p", q.shape[0])
     c = _ctx_for(q)
-    prm = make_params(sigma, 1, mode, 0.0, thresh, leaf_size=leaf_size)
+    prm = make_params(sigma, 1, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
     F, Phi = torch.empty_like(q), torch.empty_like(q)
     cnt = (ctypes.c_int64 * 2)()
     c.check(c.lib.gs_rhs(c.handle, _ptr(q), _ptr(p), q.shape[0], ctypes.byref(prm), _ptr(F),
@@ -251,13 +252,13 @@ def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, stream=None):
     return F, Phi, (cnt[0], cnt[1])
 
 
-def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, leaf_size=1, stream=None):
+def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=None):
     """One adjoint right-hand side: (dA, dB, counts)."""
     q = _pts(q, "q")
     n = q.shape[0]
     p, al, be = _pts(p, "p", n), _pts(al, "al", n), _pts(be, "be", n)
     c = _ctx_for(q)
-    prm = make_params(sigma, 1, mode, 0.0, thresh, leaf_size=leaf_size)
+    prm = make_params(sigma, 1, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
     dA, dB = torch.empty_like(q), torch.empty_like(q)
     cnt = (ctypes.c_int64 * 2)()
     c.check(c.lib.gs_adj_rhs(c.handle, _ptr(q), _ptr(p), _ptr(al), _ptr(be), n,

@@ -169,6 +169,7 @@ struct Key {
   void params(const gs_params* prm) {
     add(prm->sigma), add(prm->lambda), add(prm->thresh_sigmas);
     add(prm->T), add(prm->mode), add(prm->ckpt_every), add(prm->flags), add(prm->leaf_size);
+    add(prm->criterion);
   }
   void workspace(const gs_ctx* c) {
     for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
@@ -238,6 +239,11 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
   if (prm->flags != 0) return fail(c, GS_ERR_INVALID_ARG, "flags must be 0");
   if (prm->leaf_size < 0 || prm->leaf_size > 32)
     return fail(c, GS_ERR_INVALID_ARG, "leaf_size must be in [0, 32] (got %d)", prm->leaf_size);
+  if (prm->criterion != 0 && prm->criterion != 1)
+    return fail(c, GS_ERR_INVALID_ARG, "criterion must be 0 or 1 (got %d)", prm->criterion);
+  if (prm->criterion == 1 && (prm->mode != GS_BH || !(prm->thresh_sigmas <= 1.0)))
+    return fail(c, GS_ERR_INVALID_ARG,
+                "criterion 1 (opening angle) needs GS_BH and theta = thresh_sigmas in (0, 1]");
   return GS_OK;
 }
 
@@ -323,6 +329,7 @@ struct Solver {
   double sigma, s, h, lambda;
   float thr;  // Barnes-Hut threshold (r*r, FP32)
   int leaf;   // Barnes-Hut leaf size (1 = the paper's rule)
+  int crit;   // far test: 0 the paper's distance rule, 1 opening angle
   ExactGeom gf, ga;
   size_t pack_f4;  // float4 per pack slot
   int slots;       // pack slots allocated
@@ -513,7 +520,11 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
   S.s = std::sqrt(kLog2e / (2.0 * prm->sigma * prm->sigma));
   S.h = 1.0 / (double)prm->T;
   S.lambda = prm->lambda;
-  {
+  S.crit = prm->criterion;
+  if (S.crit == 1) {  // opening angle: theta^2
+    float th = (float)prm->thresh_sigmas;
+    S.thr = th * th;
+  } else {
     float r = (float)(prm->thresh_sigmas * prm->sigma);
     S.thr = r * r;
   }
@@ -661,7 +672,7 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     return GS_OK;
   }
   BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
-           S.mode == GS_TRUNC};
+           S.mode == GS_TRUNC, S.crit};
   gs_status s;
   {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -721,7 +732,7 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
     return GS_OK;
   }
   BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
-           S.mode == GS_TRUNC};
+           S.mode == GS_TRUNC, S.crit};
   gs_status s;
   if (reuse) {
     KTimer tm(c, GS_K_TREE_BUILD, S.st);
@@ -1304,7 +1315,7 @@ gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, co
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
-  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0, 0};
+  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0, 0, 0};
   if ((s = check_n(c, N)) || (s = check_params(c, &prm, false))) return s;
   if (M < 1 || M > (int64_t(1) << 30))
     return fail(c, GS_ERR_INVALID_ARG, "M must be in [1, 2^30] (got %lld)", (long long)M);
@@ -1661,7 +1672,7 @@ gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_
   cudaStream_t st = (cudaStream_t)stream;
   const double* dq;
   if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
-  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0};
+  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0, 0};
   Solver S;
   if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
   if ((s = solver_load(S, dq, dq, 0))) return s;

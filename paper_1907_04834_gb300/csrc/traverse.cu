@@ -84,6 +84,23 @@ __device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi
   return w;
 }
 
+// Far test of a node for point (x, y, z).  crit 0 (the paper's rule): the
+// FP32 distance to the actual range exceeds r (thr = r*r).  crit 1
+// (opening-angle variant): s*s < theta^2 * d2 with s the largest side of the
+// range, d2 the squared FP32 distance to its centre (lo + hi) * 0.5 and
+// thr = theta^2, each operation rounded.
+__device__ __forceinline__ bool far_test(float x, float y, float z, const float4& lo,
+                                         const float4& hi, float thr, int crit) {
+  if (crit == 0) return box_dist2(x, y, z, lo, hi) > thr;
+  const float s = fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)),
+                        __fsub_rn(hi.z, lo.z));
+  const float dx = __fsub_rn(x, __fmul_rn(__fadd_rn(lo.x, hi.x), 0.5f));
+  const float dy = __fsub_rn(y, __fmul_rn(__fadd_rn(lo.y, hi.y), 0.5f));
+  const float dz = __fsub_rn(z, __fmul_rn(__fadd_rn(lo.z, hi.z), 0.5f));
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  return __fmul_rn(s, s) < __fmul_rn(thr, d2);
+}
+
 // Truncation test of a pair in FP32: (dx*dx + dy*dy) + dz*dz <= thr, each
 // operation rounded, no contraction.
 __device__ __forceinline__ bool within(float ax, float ay, float az, float bx, float by, float bz,
@@ -121,7 +138,7 @@ __device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& g
 // makes it skip past s.
 template <bool VAR>
 __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float rz, float thr,
-                         int leaf, int resume) {
+                         int leaf, int crit, int resume) {
   int path[12];
   int n = 0;
   for (int a = t.nparent[s]; a >= 0 && n < 12; a = t.nparent[a]) path[n++] = a;
@@ -129,7 +146,9 @@ __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float r
     const int a = path[k];
     if (resume > a) continue;
     const float4 lo = t.nbox[2 * a], hi = t.nbox[2 * a + 1];
-    if (box_dist2(rx, ry, rz, lo, hi) > thr || (VAR && __float_as_int(hi.w) <= leaf))
+    const bool far = VAR ? far_test(rx, ry, rz, lo, hi, thr, crit)
+                         : box_dist2(rx, ry, rz, lo, hi) > thr;
+    if (far || (VAR && __float_as_int(hi.w) <= leaf))
       resume = __float_as_int(lo.w);
   }
   return resume;
@@ -306,8 +325,8 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
 template <bool COUNT, bool VAR, class Sink>
 __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
                                            int end, const float4& rr, float thr, int leaf,
-                                           bool trunc, int& resume, Sink& sink, int lane,
-                                           long long& np, long long& nn) {
+                                           bool trunc, int crit, int& resume, Sink& sink,
+                                           int lane, long long& np, long long& nn) {
   int base = INT_MIN / 2;
   // window bit masks (bit j = node base + j): leaf, "all children leaves"
   unsigned leafmask = 0u, botmask = 0u;
@@ -351,7 +370,8 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const float4 bl = sbox[off][0], bh = sbox[off][1];
     const int skip = __float_as_int(bl.w);
     const bool active = x >= resume;
-    const bool far = active && box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr;
+    const bool far = active && (VAR ? far_test(rr.x, rr.y, rr.z, bl, bh, thr, crit)
+                                    : box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr);
     const unsigned mt = __ballot_sync(FULL, far), mo = __ballot_sync(FULL, active && !far);
     // an opened node whose children are all leaves: take them at once; a
     // node of at most `leaf` points (leaf-size variant): take its points
@@ -452,11 +472,11 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   int resume = valid ? 0 : INT_MAX;
   // (an empty slice may start at the node count: no node to test there)
   if (k > 0 && valid && x < end)
-    resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
+    resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  bool done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, resume,
-                                     sink, lane, np, nn);
+  bool done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, wg.crit,
+                                     resume, sink, lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -579,13 +599,13 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int end = slice_end(t, gi, k);
   int resume = me.valid ? 0 : INT_MAX;
   if (k > 0 && me.valid && x < end)
-    resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, resume);
+    resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, 0};
   long long np = 0, nn = 0;
-  walk_nodes<COUNT, true>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, resume, sink, lane, np,
-                          nn);
+  walk_nodes<COUNT, true>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, wg.crit, resume, sink,
+                          lane, np, nn);
   if (sink.cnt) sink.flush();
 #pragma unroll
   for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
@@ -645,7 +665,7 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
-  const bool var = wg.leaf > 1 || wg.trunc;  // the paper's rule runs the lean walk
+  const bool var = wg.leaf > 1 || wg.trunc || wg.crit != 0;  // the paper's rule: lean walk
   if (counts && var)
     k_bh_walk<true, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   else if (counts)

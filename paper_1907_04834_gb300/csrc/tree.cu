@@ -731,6 +731,7 @@ WalkGroups walk_groups(const BHStep& b) {
   WalkGroups g{};
   g.leaf = b.leaf;
   g.trunc = b.trunc;
+  g.crit = b.crit;
   if (b.f.S > 0) {
     g.groups = b.f.groups;
     g.G = b.f.G;

@@ -54,6 +54,7 @@ struct BHStep {
   BHForest f;
   int leaf = 1;   // leaf-size variant (1 = the paper's rule)
   bool trunc = false;  // pure truncation variant (far nodes dropped, pairs cut)
+  int crit = 0;        // far test: 0 the paper's distance rule, 1 opening angle
 };
 
 cudaError_t tree_setup();

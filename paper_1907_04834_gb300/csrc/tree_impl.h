@@ -122,6 +122,7 @@ struct WalkGroups {
   const double* centers;   // forest: S x 3
   int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
   bool trunc;              // pure truncation: far nodes dropped, pairs cut at the threshold
+  int crit;                // far test: 0 the paper's distance rule, 1 opening angle
 };
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions

@@ -88,3 +88,51 @@ def test_autotune_picks_a_candidate():
     print("\nleaf-size autotune, blobs N=20000:", best, {k: round(v, 3) for k, v in ms.items()})
     with pytest.raises(gs.GSError):
         gs.autotune(dt(w.q0), dt(w.p0), w.sigma, candidates=(0, 4))
+
+
+@pytest.mark.parametrize("geom,n,seed,theta,leaf", [("blobs", 3000, 21, 0.5, 1),
+                                                    ("sphere", 4000, 22, 0.8, 1),
+                                                    ("slab", 2500, 23, 0.6, 8)])
+def test_opening_angle_matches_oracle(oracle, geom, n, seed, theta, leaf):
+    """Opening-angle variant (criterion 1): decisions equal the oracle's
+    (interaction counts exact), values within FP32 rounding."""
+    w = inputs.make(geom, n, seed)
+    q, p = w.q0, w.p0
+    F, Phi, cnt = gs.rhs(dt(q), dt(p), w.sigma, mode="bh", thresh=theta, leaf_size=leaf,
+                         criterion=1)
+    Fo, Phio, cnto = oracle.rhs(q, p, w.sigma, mode=1, thresh=theta, leaf=leaf, crit=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto) and cnto[1] > 0
+    assert max_rel(npy(F), Fo) <= 1e-5
+    assert max_rel(npy(Phi), Phio, phi_floor(p, w.sigma)) <= 1e-5
+    rng = np.random.default_rng(seed)
+    al, be = rng.normal(size=q.shape), rng.normal(scale=0.1, size=q.shape)
+    dA, dB, cnt = gs.adj_rhs(dt(q), dt(p), dt(al), dt(be), w.sigma, mode="bh", thresh=theta,
+                             leaf_size=leaf, criterion=1)
+    dAo, dBo, cnto = oracle.adj_rhs(q, p, al, be, w.sigma, mode=1, thresh=theta, leaf=leaf, crit=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(dA), dAo, 1e-12 * np.abs(al).max() * np.abs(p).max() / w.sigma) <= 1e-5
+    assert max_rel(npy(dB), dBo) <= 1e-5
+
+
+def test_opening_angle_gradient_and_overflow(oracle):
+    w = inputs.make("blobs", 2000, 24, T=5)
+    args = (dt(w.q0), dt(w.p0), dt(w.X), w.sigma, w.T, w.lam)
+    E, g, q1 = gs.shoot_grad(*args, mode="bh", thresh=0.5, criterion=1)
+    Eo, go, q1o = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, w.T, w.lam, mode=1, thresh=0.5,
+                                    crit=1)
+    assert rel_l2(npy(g), go) <= 1e-4
+    np.testing.assert_allclose(npy(E), Eo, rtol=1e-6)
+    gs.set_option("bh_list_cap", 2)
+    try:
+        E2, g2, q2 = gs.shoot_grad(*args, mode="bh", thresh=0.5, criterion=1)
+    finally:
+        gs.set_option("bh_list_cap", 0)
+    assert torch.equal(E, E2) and torch.equal(g, g2) and torch.equal(q1, q2)
+
+
+def test_opening_angle_argument_checks():
+    w = inputs.make("blobs", 50, 25)
+    with pytest.raises(gs.GSError):
+        gs.rhs(dt(w.q0), dt(w.p0), w.sigma, mode="bh", thresh=3.0, criterion=1)  # theta > 1
+    with pytest.raises(gs.GSError):
+        gs.rhs(dt(w.q0), dt(w.p0), w.sigma, mode="trunc", thresh=0.5, criterion=1)
