@@ -66,7 +66,9 @@ def _load():
                                      cint, _f64p, _f64p, _f64p]
     lib.gsref_morton.argtypes = [i64, _f64p, _u32p, _u32p]
     lib.gsref_velocity.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, _f64p]
-    lib.gsref_flow.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, cint, _f64p, _f64p, _f64p]
+    lib.gsref_velocity_bh.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, dbl, cint, cint, _f64p]
+    lib.gsref_flow.argtypes = [i64, _f64p, _f64p, i64, _f64p, dbl, cint, cint, dbl, cint, cint,
+                               _f64p, _f64p, _f64p]
     lib.gsref_tree.argtypes = [i64, _f64p, _f64p, ctypes.c_void_p, ctypes.c_void_p, _i64p, i64,
                                _i64p, _f64p, _f32p]
     lib.gsref_tree.restype = i64
@@ -100,20 +102,26 @@ def rhs(q, p, sigma, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     return F, Phi, cnt
 
 
-def velocity(q, p, x, sigma):
-    """Velocity field of Eq. 3 at points x: v(x) = sum_i G(|x - q_i|) p_i."""
+def velocity(q, p, x, sigma, mode=EXACT, thresh=3.0, leaf=1, crit=0):
+    """Velocity field of Eq. 3 at points x: v(x) = sum_i G(|x - q_i|) p_i
+    (mode BH: Barnes-Hut over the particles' tree)."""
     q, p, x = _c(q), _c(p), _c(x)
     v = np.empty_like(x)
-    _load().gsref_velocity(q.shape[0], q, p, x.shape[0], x, float(sigma), v)
+    if mode == BH:
+        _load().gsref_velocity_bh(q.shape[0], q, p, x.shape[0], x, float(sigma), float(thresh),
+                                  int(leaf), int(crit), v)
+    else:
+        _load().gsref_velocity(q.shape[0], q, p, x.shape[0], x, float(sigma), v)
     return v
 
 
-def flow(q0, p0, x0, sigma, T):
-    """Exact shooting with tracer points x carried by Eq. 3's field (Euler
-    steps in lockstep): returns q(1), p(1), x(1)."""
+def flow(q0, p0, x0, sigma, T, mode=EXACT, thresh=3.0, leaf=1, crit=0):
+    """Shooting with tracer points x carried by Eq. 3's field (Euler steps in
+    lockstep; mode EXACT or BH for both): returns q(1), p(1), x(1)."""
     q0, p0, x0 = _c(q0), _c(p0), _c(x0)
     q1, p1, x1 = np.empty_like(q0), np.empty_like(q0), np.empty_like(x0)
-    _load().gsref_flow(q0.shape[0], q0, p0, x0.shape[0], x0, float(sigma), int(T), q1, p1, x1)
+    _load().gsref_flow(q0.shape[0], q0, p0, x0.shape[0], x0, float(sigma), int(T), int(mode),
+                       float(thresh), int(leaf), int(crit), q1, p1, x1)
     return q1, p1, x1
 
 

@@ -438,6 +438,9 @@ typedef struct {
   int64_t leaf; /* leaf-size variant: near nodes of <= leaf points taken exactly */
   int crit;     /* 0: the paper's distance rule; 1: opening-angle variant */
   int64_t m;
+  /* the target: point m of the tree, or an outside point (tracer) */
+  const double *tq, *tp, *ta, *tb;
+  const float *tq32;
   double acc0[3], acc1[3];
   int64_t n_point, n_node;
   ilist *list;
@@ -454,12 +457,10 @@ static void record(visit_ctx *v, int64_t kind, int64_t id) {
 
 static void point_source(visit_ctx *v, int64_t s) {
   const otree *t = v->t;
-  int64_t m = v->m;
   if (!v->adjoint)
-    fwd_pair(t->q + 3 * m, t->p + 3 * m, t->q + 3 * s, t->p + 3 * s, v->sigma,
-             v->acc0, v->acc1);
+    fwd_pair(v->tq, v->tp, t->q + 3 * s, t->p + 3 * s, v->sigma, v->acc0, v->acc1);
   else
-    adj_pair(t->q + 3 * m, t->p + 3 * m, t->al + 3 * m, t->be + 3 * m,
+    adj_pair(v->tq, v->tp, v->ta, v->tb,
              t->q + 3 * s, t->p + 3 * s, t->al + 3 * s, t->be + 3 * s,
              v->sigma, v->acc0, v->acc1);
   v->n_point++;
@@ -469,15 +470,13 @@ static void point_source(visit_ctx *v, int64_t s) {
 static void node_source(visit_ctx *v, int64_t k) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
-  int64_t m = v->m;
   double n = (double)nd->n;
   double qc[3] = {nd->sq[0] / n, nd->sq[1] / n, nd->sq[2] / n};
   if (!v->adjoint) {
-    fwd_pair(t->q + 3 * m, t->p + 3 * m, qc, nd->sp, v->sigma, v->acc0,
-             v->acc1);
+    fwd_pair(v->tq, v->tp, qc, nd->sp, v->sigma, v->acc0, v->acc1);
   } else {
     double bavg[3] = {nd->sb[0] / n, nd->sb[1] / n, nd->sb[2] / n};
-    adj_pair(t->q + 3 * m, t->p + 3 * m, t->al + 3 * m, t->be + 3 * m, qc,
+    adj_pair(v->tq, v->tp, v->ta, v->tb, qc,
              nd->sp, nd->sa, bavg, v->sigma, v->acc0, v->acc1);
   }
   v->n_node++;
@@ -501,7 +500,7 @@ static void visit(visit_ctx *v, int64_t k) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
   if (nd->n == 0) return;
-  const float *x = t->q32 + 3 * v->m;
+  const float *x = v->tq32;
   if (nd->n >= 2 && (v->crit ? is_far_angle(x, nd, v->thr) : is_far(x, nd, v->thr))) {
     node_source(v, k); /* case 2: summarised far node */
     return;
@@ -528,6 +527,11 @@ static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
   v.thr = thr;
   v.leaf = leaf;
   v.crit = crit;
+  v.tq = t->q + 3 * m;
+  v.tp = t->p + 3 * m;
+  v.ta = adjoint ? t->al + 3 * m : NULL;
+  v.tb = adjoint ? t->be + 3 * m : NULL;
+  v.tq32 = t->q32 + 3 * m;
   v.adjoint = adjoint;
   v.m = m;
   v.list = list;
@@ -763,13 +767,45 @@ void gsref_velocity(int64_t N, const double *q, const double *p, int64_t M,
   }
 }
 
-/* Shooting (exact, Eq. 1) with M tracer points x carried by the velocity
- * field of Eq. 3.  The tracers do not act on the particles; they take the
- * same explicit Euler steps, from the particles' state at the
- * start of each step:  x^{k+1} = x^k + h v(x^k; q^k, p^k). */
+/* Velocity of Eq. 3 at M outside points with the Barnes-Hut approximation
+ * of Sec. 2.2 over the particles' tree: each point is a target of the
+ * three-case traversal (its FP32 position decides), with no momentum of its
+ * own, so only the velocity sums are formed.  leaf, crit as in gsref_rhs. */
+void gsref_velocity_bh(int64_t N, const double *q, const double *p, int64_t M,
+                       const double *x, double sigma, double thresh, int leaf,
+                       int crit, double *v) {
+  otree t;
+  tree_build(&t, N, q, p, NULL, NULL);
+  float thr = rule_threshold(crit, thresh, sigma);
+  float *x32 = round_positions(M, x);
+  static const double zero[3] = {0.0, 0.0, 0.0};
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t m = 0; m < M; m++) {
+    visit_ctx vc;
+    memset(&vc, 0, sizeof(vc));
+    vc.t = &t;
+    vc.sigma = sigma;
+    vc.thr = thr;
+    vc.leaf = leaf;
+    vc.crit = crit;
+    vc.tq = x + 3 * m;
+    vc.tp = zero;
+    vc.tq32 = x32 + 3 * m;
+    visit(&vc, 0);
+    for (int a = 0; a < 3; a++) v[3 * m + a] = vc.acc0[a];
+  }
+  free(x32);
+  tree_free(&t);
+}
+
+/* Shooting (Eq. 1; mode 0 exact, 1 Barnes-Hut) with M tracer points x
+ * carried by the velocity field of Eq. 3 (same mode).  The tracers do not
+ * act on the particles; they take the same explicit Euler steps, from the
+ * particles' state at the start of each step:
+ * x^{k+1} = x^k + h v(x^k; q^k, p^k). */
 void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
-                const double *x0, double sigma, int T, double *q1, double *p1,
-                double *x1) {
+                const double *x0, double sigma, int T, int mode, double thresh,
+                int leaf, int crit, double *q1, double *p1, double *x1) {
   double *F = (double *)malloc((size_t)N * 3 * sizeof(double));
   double *Phi = (double *)malloc((size_t)N * 3 * sizeof(double));
   double *v = (double *)malloc((size_t)(M > 0 ? M : 1) * 3 * sizeof(double));
@@ -778,8 +814,12 @@ void gsref_flow(int64_t N, const double *q0, const double *p0, int64_t M,
   memcpy(p1, p0, (size_t)N * 3 * sizeof(double));
   memcpy(x1, x0, (size_t)M * 3 * sizeof(double));
   for (int k = 0; k < T; k++) {
-    gsref_velocity(N, q1, p1, M, x1, sigma, v);
-    gsref_rhs(N, q1, p1, sigma, GSREF_EXACT, 0.0, 1, 0, F, Phi, NULL);
+    if (mode == GSREF_BH)
+      gsref_velocity_bh(N, q1, p1, M, x1, sigma, thresh, leaf, crit, v);
+    else
+      gsref_velocity(N, q1, p1, M, x1, sigma, v);
+    gsref_rhs(N, q1, p1, sigma, mode == GSREF_BH ? GSREF_BH : GSREF_EXACT, thresh, leaf,
+              crit, F, Phi, NULL);
     for (int64_t i = 0; i < 3 * M; i++) x1[i] += h * v[i];
     for (int64_t i = 0; i < 3 * N; i++) {
       q1[i] += h * F[i];

@@ -100,3 +100,31 @@ def test_tracers_translation_equivariant(oracle):
     _, _, x1 = oracle.flow(q, p, x0, 1.7, 8)
     _, _, x1c = oracle.flow(q + c, p, x0 + c, 1.7, 8)
     np.testing.assert_allclose(x1c - c, x1, rtol=0, atol=1e-12)
+
+
+def test_bh_field_at_particles_is_their_bh_velocity(oracle):
+    """A tracer at a particle's position takes that particle's Barnes-Hut
+    decisions (same FP32 position) and sums: v_BH(q_i) = F_BH,i exactly;
+    Barnes-Hut tracers on particles follow them."""
+    from paper_1907_04834_gb300 import inputs
+    w = inputs.make("blobs", 600, 41)
+    v = oracle.velocity(w.q0, w.p0, w.q0, w.sigma, mode=oracle.BH)
+    F, _, _ = oracle.rhs(w.q0, w.p0, w.sigma, mode=oracle.BH)
+    assert np.array_equal(v, F)
+    x0 = w.q0[::4].copy()
+    q1, _, x1 = oracle.flow(w.q0, w.p0, x0, w.sigma, 6, mode=oracle.BH)
+    assert np.array_equal(x1, q1[::4])
+
+
+def test_bh_field_limits_and_linearity(oracle):
+    from paper_1907_04834_gb300 import inputs
+    w = inputs.make("blobs", 500, 42)
+    rng = np.random.default_rng(3)
+    x = w.q0[rng.choice(500, 40)] + rng.normal(scale=2.0, size=(40, 3))
+    ve = oracle.velocity(w.q0, w.p0, x, w.sigma)
+    vinf = oracle.velocity(w.q0, w.p0, x, w.sigma, mode=oracle.BH, thresh=1e30)
+    np.testing.assert_allclose(vinf, ve, rtol=1e-12, atol=1e-15 * np.abs(ve).max())
+    v1 = oracle.velocity(w.q0, w.p0, x, w.sigma, mode=oracle.BH)
+    v2 = oracle.velocity(w.q0, 2.0 * w.p0, x, w.sigma, mode=oracle.BH)
+    assert np.array_equal(v2, 2.0 * v1)
+    assert np.abs(v1 - ve).max() <= 0.05 * np.abs(ve).max()  # approximation, not garbage
