@@ -166,8 +166,10 @@ gs_status gs_descend_batched(gs_ctx *ctx, int32_t S, const int64_t *offsets,
  * registration.  The tracers take the particles' explicit Euler steps from
  * each step's particle state: x^{k+1} = x^k + h v(x^k; q^k, p^k); they do
  * not act on the particles.  x0, x1: M x 3 (M >= 0; x0, x1 may be NULL when
- * M = 0); q1, p1: NULL or N x 3 particle results.  Exact sums only: GS_BH
- * returns GS_ERR_UNSUPPORTED.
+ * M = 0); q1, p1: NULL or N x 3 particle results.  GS_EXACT: exact sums;
+ * GS_BH: the tracers are targets of the Sec. 2.2 traversal of the
+ * particles' tree of each step (their FP32 positions decide; leaf_size and
+ * criterion apply); GS_TRUNC returns GS_ERR_UNSUPPORTED.
  */
 gs_status gs_flow(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
                   const double *x0, int64_t M, const gs_params *prm,
@@ -210,10 +212,11 @@ gs_status gs_autotune(gs_ctx *ctx, const double *q, const double *p, int64_t N,
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
 
 /* Velocity field of Eq. 3 at M >= 1 points x (M x 3): v = sum_i G(|x - q_i|)
- * p_i over all N particles (exact sums, FP32 pairs with compensated sums as
- * in gs_rhs).  v: M x 3. */
+ * p_i over the N particles; prm: sigma and mode (GS_EXACT: all pairs;
+ * GS_BH: Barnes-Hut over the particles' tree as in gs_flow), FP32 pairs with
+ * compensated sums as in gs_rhs.  v: M x 3. */
 gs_status gs_velocity(gs_ctx *ctx, const double *q, const double *p, int64_t N,
-                      const double *x, int64_t M, double sigma, double *v,
+                      const double *x, int64_t M, const gs_params *prm, double *v,
                       void *stream);
 
 /* One forward right-hand side at state (q, p): F, Phi as in Eq. 1 (GS_BH:

@@ -65,7 +65,8 @@ _SIGS = {
                                    _vp, _vp]),
     "gs_flow": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp, _vp,
                                _vp, _vp]),
-    "gs_velocity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, _vp]),
+    "gs_velocity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp,
+                                   _vp]),
     "gs_rhs": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp, _vp]),
     "gs_adj_rhs": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp,
                                   _vp, _vp, _vp]),

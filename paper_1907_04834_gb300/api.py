@@ -209,16 +209,17 @@ def autotune(q, p, sigma, thresh=3.0, candidates=(1, 2, 4, 8, 16, 32), stream=No
     return best.value, {int(v): ms[k] for k, v in enumerate(candidates)}
 
 
-def flow(q0, p0, x0, sigma, T, stream=None):
-    """Exact shooting that carries tracer points x0 (M, 3) through the
-    velocity field of Eq. 3 (gs_flow).  Returns (q1, p1, x1)."""
+def flow(q0, p0, x0, sigma, T, mode="exact", thresh=3.0, leaf_size=1, criterion=0,
+         stream=None):
+    """Shooting that carries tracer points x0 (M, 3) through the velocity
+    field of Eq. 3 (gs_flow; mode "exact" or "bh").  Returns (q1, p1, x1)."""
     q0 = _pts(q0, "q0")
     n = q0.shape[0]
     p0 = _pts(p0, "p0", n)
     x0 = _pts(x0, "x0")
     m = x0.shape[0]
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, "exact")
+    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
     q1, p1, x1 = _like(q0), _like(q0), _like(x0)
     c.check(c.lib.gs_flow(c.handle, _ptr(q0), _ptr(p0), n, _ptr(x0) if m else None, m,
                           ctypes.byref(prm), _ptr(q1), _ptr(p1), _ptr(x1) if m else None,
@@ -226,16 +227,18 @@ def flow(q0, p0, x0, sigma, T, stream=None):
     return q1, p1, x1
 
 
-def velocity(q, p, x, sigma, stream=None):
-    """Velocity field of Eq. 3 at points x (M, 3): v = sum_i G(|x - q_i|) p_i."""
+def velocity(q, p, x, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=None):
+    """Velocity field of Eq. 3 at points x (M, 3): v = sum_i G(|x - q_i|) p_i
+    (mode "bh": Barnes-Hut over the particles' tree)."""
     q = _pts(q, "q")
     n = q.shape[0]
     p = _pts(p, "p", n)
     x = _pts(x, "x")
     c = _ctx_for(q)
     v = _like(x)
-    c.check(c.lib.gs_velocity(c.handle, _ptr(q), _ptr(p), n, _ptr(x), x.shape[0], float(sigma),
-                              _ptr(v), _stream_ptr(c.device, stream)))
+    prm = make_params(sigma, 1, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
+    c.check(c.lib.gs_velocity(c.handle, _ptr(q), _ptr(p), n, _ptr(x), x.shape[0],
+                              ctypes.byref(prm), _ptr(v), _stream_ptr(c.device, stream)))
     return v
 
 

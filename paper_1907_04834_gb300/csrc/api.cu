@@ -76,7 +76,7 @@ struct gs_ctx {
   };
   GraphCache g_shoot, g_grad, g_batch, g_flow;
   // tracer points of the velocity field (gs_flow, gs_velocity)
-  DevMem in_x, xs, xpks, xpart, xtickets;
+  DevMem in_x, xs, xpks, xpart, xtickets, xraws, xsort;
   DevMem lb;  // L-BFGS vectors
   size_t xtickets_n = 0;
   cudaStream_t cap = nullptr;  // capture stream
@@ -176,7 +176,7 @@ struct Key {
                             &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
                             &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                             &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                            &c->lb})
+                            &c->lb, &c->xraws, &c->xsort})
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
@@ -913,7 +913,11 @@ gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
 struct Tracers {
   int64_t M = 0;
   TracerGeom tg{};
+  bool tree = false;  // Barnes-Hut: tracers walk the particles' tree
   float4* xpk(const gs_ctx* c, int k) const { return c->xpks.as<float4>() + (size_t)k * tg.Mpad; }
+  float4* xraw(const gs_ctx* c, int k) const {
+    return c->xraws.as<float4>() + (size_t)k * tg.Mpad;
+  }
 };
 
 gs_status tracer_setup(gs_ctx* c, const Solver& S, int64_t M, cudaStream_t st, Tracers& X) {
@@ -931,6 +935,51 @@ gs_status tracer_setup(gs_ctx* c, const Solver& S, int64_t M, cudaStream_t st, T
     c->xtickets_n = tn;
   }
   CK(cudaMemsetAsync(c->xtickets.p, 0, tn * sizeof(unsigned), st), "memset");
+  X.tree = S.mode == GS_BH;
+  if (X.tree) {
+    // FP32 tracer positions, the tracer sort's scratch, list room for the
+    // tracer groups
+    CK(c->xraws.ensure(2 * (size_t)X.tg.Mpad * sizeof(float4)), "workspace");
+    CK(c->xsort.ensure(tracer_scratch_bytes(M)), "workspace");
+    gs_status s = tree_reserve(c->tree, S.N, 1, st, (M + 31) / 32);
+    if (s != GS_OK) return fail(c, s, "Barnes-Hut workspace allocation failed");
+  }
+  return GS_OK;
+}
+
+// Barnes-Hut tracer step k on the particles' tree of state k (tree slot 0,
+// built by the particle step that precedes it).
+gs_status tracer_bh_step(const Solver& S, const Tracers& X, int k, double h, double* v_out,
+                         cudaStream_t st) {
+  gs_ctx* c = S.c;
+  if (X.M == 0) return GS_OK;
+  BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(k & 1), S.raw(k & 1), BHForest{}, S.leaf, false,
+           S.crit};
+  BHTargets x;
+  gs_status s;
+  {
+    KTimer tm(c, GS_K_TREE_BUILD, st);
+    s = tracer_order(c->tree, b, X.xraw(c, k & 1), X.M, c->xsort.p, &x, st);
+  }
+  x.xrec = X.xpk(c, k & 1);
+  if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_WALK, st);
+    s = bh_walk_targets(c->tree, b, x, st);
+  }
+  if (s == GS_OK) {
+    TracerEpi e{};
+    e.x = c->xs.as<double>();
+    e.xpk_next = h != 0.0 ? X.xpk(c, (k + 1) & 1) : nullptr;
+    e.xraw_next = h != 0.0 ? X.xraw(c, (k + 1) & 1) : nullptr;
+    e.v_out = v_out;
+    e.center = S.scal(SC_CENTER);
+    e.s = S.s;
+    e.h = h;
+    e.M = X.M;
+    KTimer tm(c, GS_K_BH_FWD, st);
+    s = bh_eval_targets(c->tree, b, x, e, st);
+  }
+  if (s != GS_OK) return fail(c, s, "Barnes-Hut tracer step failed: %s", bh_last_error());
   return GS_OK;
 }
 
@@ -963,14 +1012,21 @@ gs_status flow_enqueue(Solver& S, const Tracers& X, const double* dq0, const dou
   if ((s = solver_load(S, dq0, dp0, 0))) return s;
   if (X.M > 0) {
     CK(cudaMemcpyAsync(c->xs.p, dx0, (size_t)X.M * 24, cudaMemcpyDeviceToDevice, st), "copy");
-    CK(launch_pack_points(c->xs.as<double>(), X.M, S.scal(SC_CENTER), S.s, X.xpk(c, 0), st),
+    CK(launch_pack_points(c->xs.as<double>(), X.M, S.scal(SC_CENTER), S.s, X.xpk(c, 0),
+                          X.tree ? X.xraw(c, 0) : nullptr, st),
        "pack");
   }
   for (int k = 0; k < S.T; k++) {
-    // both read step k's particle pack; the particle step writes slot k+1
-    if ((s = tracer_step(S, X, k, S.h, nullptr, st))) return s;
     FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
-    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+    if (X.tree) {
+      // the particle step builds state k's tree; the tracers walk it after
+      if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+      if ((s = tracer_bh_step(S, X, k, S.h, nullptr, st))) return s;
+    } else {
+      // both read step k's particle pack; the particle step writes slot k+1
+      if ((s = tracer_step(S, X, k, S.h, nullptr, st))) return s;
+      if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
+    }
   }
   return GS_OK;
 }
@@ -1018,7 +1074,7 @@ void gs_destroy(gs_ctx* c) {
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                       &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                      &c->lb})
+                      &c->lb, &c->xraws, &c->xsort})
       m->release();
     for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch, &c->g_flow})
       if (gc->exec) cudaGraphExecDestroy(gc->exec);
@@ -1268,8 +1324,8 @@ gs_status gs_flow(gs_ctx* c, const double* q0, const double* p0, int64_t N, cons
   if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
   if (M < 0 || M > (int64_t(1) << 30))
     return fail(c, GS_ERR_INVALID_ARG, "M must be in [0, 2^30] (got %lld)", (long long)M);
-  if (prm->mode != GS_EXACT)
-    return fail(c, GS_ERR_UNSUPPORTED, "tracer points: exact mode only");
+  if (prm->mode == GS_TRUNC)
+    return fail(c, GS_ERR_UNSUPPORTED, "tracer points: GS_EXACT or GS_BH");
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   bool hq = false, hp = false, hx = false;
@@ -1311,12 +1367,13 @@ gs_status gs_flow(gs_ctx* c, const double* q0, const double* p0, int64_t N, cons
 }
 
 gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, const double* x,
-                      int64_t M, double sigma, double* v, void* stream) {
+                      int64_t M, const gs_params* prm, double* v, void* stream) {
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
-  const gs_params prm{sigma, 0.0, 3.0, 1, GS_EXACT, 0, 0, 0, 0};
-  if ((s = check_n(c, N)) || (s = check_params(c, &prm, false))) return s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if (prm->mode == GS_TRUNC)
+    return fail(c, GS_ERR_UNSUPPORTED, "velocity field: GS_EXACT or GS_BH");
   if (M < 1 || M > (int64_t(1) << 30))
     return fail(c, GS_ERR_INVALID_ARG, "M must be in [1, 2^30] (got %lld)", (long long)M);
   DeviceGuard g(c->device);
@@ -1329,14 +1386,27 @@ gs_status gs_velocity(gs_ctx* c, const double* q, const double* p, int64_t N, co
       (s = input(c, x, (size_t)M * 3, "x", c->in_x, st, &dx)))
     return s;
   Solver S;
-  if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
+  if ((s = solver_init(c, S, N, prm, 1, false, st))) return s;
   if ((s = solver_load(S, dq, dp, 0))) return s;
   Tracers X;
   if ((s = tracer_setup(c, S, M, st, X))) return s;
   CK(c->out_a.ensure((size_t)M * 24), "workspace");
   CK(cudaMemcpyAsync(c->xs.p, dx, (size_t)M * 24, cudaMemcpyDeviceToDevice, st), "copy");
-  CK(launch_pack_points(c->xs.as<double>(), M, S.scal(SC_CENTER), S.s, X.xpk(c, 0), st), "pack");
-  if ((s = tracer_step(S, X, 0, 0.0, c->out_a.as<double>(), st))) return s;
+  CK(launch_pack_points(c->xs.as<double>(), M, S.scal(SC_CENTER), S.s, X.xpk(c, 0),
+                        X.tree ? X.xraw(c, 0) : nullptr, st),
+     "pack");
+  if (X.tree) {
+    // the particles' tree of (q, p), then the tracers walk it
+    BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(0), S.raw(0), BHForest{}, S.leaf, false, S.crit};
+    {
+      KTimer tm(c, GS_K_TREE_BUILD, st);
+      if ((s = bh_build(c->tree, b, nullptr, false, st)))
+        return fail(c, s, "Barnes-Hut build failed: %s", bh_last_error());
+    }
+    if ((s = tracer_bh_step(S, X, 0, 0.0, c->out_a.as<double>(), st))) return s;
+  } else if ((s = tracer_step(S, X, 0, 0.0, c->out_a.as<double>(), st))) {
+    return s;
+  }
   if ((s = copy_out(c, v, c->out_a.p, (size_t)M * 24, st))) return s;
   if (hv) return read_status(c, st);
   CK(cudaGetLastError(), "launch");

@@ -247,6 +247,7 @@ __device__ __forceinline__ void fwd_epilogue(int64_t i, const double F[3], const
 struct TracerEpi {
   double* x;                // M x 3 tracer positions (updated when h != 0)
   float4* xpk_next;         // next step's tracer records (NULL = none)
+  float4* xraw_next;        // next step's FP32 tracer positions (NULL = none)
   double* v_out;            // M x 3 velocity (NULL = none)
   const double* center;     // recentring point (the particles')
   double s;                 // coordinate scale
@@ -267,6 +268,7 @@ __device__ __forceinline__ void tracer_epilogue(int64_t i, const double v[3], co
       e.xpk_next[i] = make_float4((float)((xn[0] - e.center[0]) * e.s),
                                   (float)((xn[1] - e.center[1]) * e.s),
                                   (float)((xn[2] - e.center[2]) * e.s), 0.f);
+    if (e.xraw_next) e.xraw_next[i] = make_float4((float)xn[0], (float)xn[1], (float)xn[2], 0.f);
   }
 }
 

@@ -83,9 +83,9 @@ cudaError_t launch_batch_adjoint_init(const double* q, const double* X, int64_t 
 // out[s * stride] = scale * Sum over rows of subject s of x (fixed order)
 cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, double scale,
                                double* out, int stride, cudaStream_t st);
-// tracer records {(x - c) s, 0} of M points
+// tracer records {(x - c) s, 0} of M points (xraw: NULL or FP32 positions)
 cudaError_t launch_pack_points(const double* x, int64_t M, const double* center, double s,
-                               float4* xpk, cudaStream_t st);
+                               float4* xpk, float4* xraw, cudaStream_t st);
 // *out = a . b (FP64, fixed order)
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out, cudaStream_t st);
 // y = a x (y may be x)

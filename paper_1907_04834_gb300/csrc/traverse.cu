@@ -63,12 +63,22 @@ struct Own {
   float rx, ry, rz;       // FP32 raw position (truncation test)
 };
 
-__device__ __forceinline__ Own load_own(const TreeArrays& t, const GroupInfo& gi, int lane,
-                                        bool adj) {
+__device__ __forceinline__ Own load_own(const TreeArrays& t, const WalkGroups& wg,
+                                        const GroupInfo& gi, int lane, bool adj) {
   Own w;
   w.i = gi.first + lane;
   w.valid = lane < gi.count;
   const int ii = w.valid ? w.i : gi.first;
+  if (wg.xperm) {  // an outside target: its record, no momentum
+    w.o = (int)wg.xperm[ii];
+    w.m0 = wg.xrec[w.o];
+    w.m1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.m2 = w.m1;
+    w.m3 = w.m1;
+    const float4 r = wg.xraw[w.o];
+    w.rx = r.x, w.ry = r.y, w.rz = r.z;
+    return w;
+  }
   w.o = (int)t.perm[ii];
   const int leaf = ii + (int)t.offs[ii + 1];
   w.m0 = t.nrec[4 * leaf];
@@ -120,8 +130,7 @@ __device__ __forceinline__ bool within(float ax, float ay, float az, float bx, f
 __device__ __forceinline__ int slice_start(const TreeArrays& t, const GroupInfo& gi, int k) {
   constexpr int h = BH_SLICES / 2;
   if (k == 0) return gi.nb;
-  const int i = gi.first + min(16, gi.count - 1);
-  const int mid = i + (int)t.offs[i + 1];
+  const int mid = gi.mid;
   const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096) >> GS_BH_DSHIFT;
   if (k < h) return max(gi.nb, mid - (D << (h - 1 - k)));
   if (k == h) return mid;
@@ -464,9 +473,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   const int l = blockIdx.x * TR_WARPS + w;
   if (l >= wg.G * BH_SLICES) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
-  const GroupInfo gi = group_info(t, N, wg.groups, g);
+  const GroupInfo gi = target_group(t, N, wg, g);
   const bool valid = lane < gi.count;
-  const float4 rr = raw[(int)t.perm[gi.first + (valid ? lane : 0)]];
+  const int ti = gi.first + (valid ? lane : 0);
+  const float4 rr = wg.xperm ? wg.xraw[wg.xperm[ti]] : raw[(int)t.perm[ti]];
   int x = slice_start(t, gi, k);
   const int end = slice_end(t, gi, k);
   int resume = valid ? 0 : INT_MAX;
@@ -506,7 +516,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
   const int l = blockIdx.x * TR_WARPS + w;
   if (l >= wg.G * BH_SLICES) return;
   if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
-  const Own me = load_own(t, group_info(t, N, wg.groups, l / BH_SLICES), lane, ADJ);
+  const Own me = load_own(t, wg, target_group(t, N, wg, l / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
   A.zero();
   int npair = 0;
@@ -592,9 +602,9 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   if (l >= wg.G * BH_SLICES) return;
   if (L.ovf_x[l] < 0) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
-  const GroupInfo gi = group_info(t, N, wg.groups, g);
-  const Own me = load_own(t, gi, lane, ADJ);
-  const float4 rr = raw[me.o];
+  const GroupInfo gi = target_group(t, N, wg, g);
+  const Own me = load_own(t, wg, gi, lane, ADJ);
+  const float4 rr = wg.xperm ? make_float4(me.rx, me.ry, me.rz, 0.f) : raw[me.o];
   int x = slice_start(t, gi, k);
   const int end = slice_end(t, gi, k);
   int resume = me.valid ? 0 : INT_MAX;
@@ -624,12 +634,12 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // then the epilogue.
 template <bool ADJ>
 __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdEpi fe,
-                             AdjEpi ae) {
+                             AdjEpi ae, TracerEpi te) {
   constexpr int NC = Acc<ADJ>::NC;
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = gl >> 5, lane = gl & 31;
   if (g >= wg.G) return;
-  const GroupInfo gi = group_info(t, N, wg.groups, g);
+  const GroupInfo gi = target_group(t, N, wg, g);
   if (lane >= gi.count) return;
   const int i = gi.first + lane;
   double acc[NC];
@@ -643,6 +653,10 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
       const float2 v = src[((size_t)l * NC + c) * 32 + lane];
       acc[c] += (double)v.x + (double)v.y;
     }
+  }
+  if (wg.xperm) {  // tracer targets: the velocity of Eq. 3 is the F part
+    if constexpr (!ADJ) tracer_epilogue(wg.xperm[i], acc, te);
+    return;
   }
   const int o = (int)t.perm[i];
   if constexpr (!ADJ) {
@@ -681,7 +695,8 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
 template <bool ADJ, bool TRUNC>
 static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr,
                         const BHLists& L, const WalkGroups& wg, const FwdEpi& fe,
-                        const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+                        const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
+                        cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
   if (counts)
@@ -689,18 +704,19 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
   else
     k_bh_fallback<ADJ, false, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts);
-  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae);
+  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae, te);
 }
 
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
-                           const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+                           const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
+                           cudaStream_t st) {
   if (wg.trunc) {
-    if (!adj) eval_launch<false, true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
-    else eval_launch<true, true>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+    if (!adj) eval_launch<false, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
+    else eval_launch<true, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
   } else {
-    if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
-    else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, counts, st);
+    if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
+    else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
   }
   note_launches(3);
   return cudaGetLastError();

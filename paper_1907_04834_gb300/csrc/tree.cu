@@ -203,6 +203,42 @@ __global__ void k_forest_finish(const uint32_t* skey, const uint32_t* sperm, int
   key[i] = codes[v];
 }
 
+// Tracers walking a tree: Morton codes in the tree's root box (points
+// outside it clamp to the boundary cells), keyed with their index.
+__global__ void k_tracer_codes(const float4* __restrict__ xraw, int M,
+                               const float* __restrict__ bbox, uint32_t* key, uint32_t* perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const float4 r = xraw[i];
+  float ext[3], inv[3];
+  for (int a = 0; a < 3; a++) {
+    ext[a] = __fsub_rn(bbox[3 + a], bbox[a]);
+    inv[a] = ext[a] > 0.f ? __fdiv_rn(1024.0f, ext[a]) : 0.f;
+  }
+  const uint32_t kx = quantise(r.x, bbox[0], ext[0], inv[0]);
+  const uint32_t ky = quantise(r.y, bbox[1], ext[1], inv[1]);
+  const uint32_t kz = quantise(r.z, bbox[2], ext[2], inv[2]);
+  key[i] = (spread10(kx) << 2) | (spread10(ky) << 1) | spread10(kz);
+  perm[i] = (uint32_t)i;
+}
+
+// Per tracer group: the tree leaf nearest in Morton order to its middle
+// tracer (first sorted point with a code >= the tracer's), where the
+// group's slices are cut.
+__global__ void k_tracer_mid(const uint32_t* __restrict__ tkey, int M, const uint32_t* __restrict__ sk,
+                             const uint32_t* __restrict__ offs, int N, int* mid) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g * 32 >= M) return;
+  const uint32_t c = tkey[g * 32 + min(16, M - g * 32 - 1)];
+  int lo = 0, hi = N - 1;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (sk[m] < c) lo = m + 1;
+    else hi = m;
+  }
+  mid[g] = lo + (int)offs[lo + 1];
+}
+
 // ---------------------------------------------------------------- scans
 struct Ident {
   __device__ uint32_t operator()(uint32_t v) const { return v; }
@@ -867,7 +903,7 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
   BHLists L;
   views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), false, e,
-                                   AdjEpi{}, counts ? t.counts : nullptr, st);
+                                   AdjEpi{}, TracerEpi{}, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -877,7 +913,7 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   BHLists L;
   views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), true, FwdEpi{},
-                                   e, counts ? t.counts : nullptr, st);
+                                   e, TracerEpi{}, counts ? t.counts : nullptr, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -945,6 +981,115 @@ gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_
     if (err != cudaSuccess) return cuda_err(err);
   }
   return GS_OK;
+}
+
+// ---------------------------------------------------------------- tracers
+namespace {
+struct TracerScratch {
+  uint32_t *key, *key2, *perm2, *hist, *hscan, *bsum;
+};
+size_t carve_tracers(void* mem, int64_t M, TracerScratch* x, uint32_t** perm, int** mid) {
+  const size_t M1 = (size_t)M + 1, nb = nblocks(M, RS_TILE), hist_n = 256 * nb + 1;
+  const size_t bsum_n = nblocks((int64_t)hist_n, SCAN_TILE) + 1, G = (size_t)(M + 31) / 32;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t o_key = take(4 * M1), o_key2 = take(4 * M1), o_perm = take(4 * M1),
+               o_perm2 = take(4 * M1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
+               o_bsum = take(4 * bsum_n), o_mid = take(4 * G);
+  if (mem) {
+    char* b = static_cast<char*>(mem);
+    x->key = (uint32_t*)(b + o_key);
+    x->key2 = (uint32_t*)(b + o_key2);
+    x->perm2 = (uint32_t*)(b + o_perm2);
+    x->hist = (uint32_t*)(b + o_hist);
+    x->hscan = (uint32_t*)(b + o_hscan);
+    x->bsum = (uint32_t*)(b + o_bsum);
+    *perm = (uint32_t*)(b + o_perm);
+    *mid = (int*)(b + o_mid);
+  }
+  return o;
+}
+}  // namespace
+
+size_t tracer_scratch_bytes(int64_t M) {
+  TracerScratch x;
+  uint32_t* p;
+  int* m;
+  return carve_tracers(nullptr, std::max<int64_t>(M, 1), &x, &p, &m);
+}
+
+gs_status tracer_order(TreeWork& w, const BHStep& b, const float4* xraw, int64_t M,
+                       void* scratch, BHTargets* out, cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  TracerScratch x;
+  uint32_t* perm = nullptr;
+  int* mid = nullptr;
+  carve_tracers(scratch, M, &x, &perm, &mid);
+  const int Mi = (int)M;
+  k_tracer_codes<<<nblocks(M, 256), 256, 0, st>>>(xraw, Mi, t.bbox, x.key, perm);
+  // stable radix sort of the tracer codes, 4 passes of 8 bits
+  const int nb = (int)nblocks(M, RS_TILE);
+  uint32_t *k0 = x.key, *v0 = perm, *k1 = x.key2, *v1 = x.perm2;
+  cudaError_t err = cudaSuccess;
+  for (int pass = 0; pass < 4 && err == cudaSuccess; pass++) {
+    k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, Mi, 8 * pass, x.hist);
+    err = scan(x.hist, 256 * nb, x.bsum, x.hscan, Ident(), st);
+    k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, Mi, 8 * pass, x.hscan, k1, v1);
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  const int G = (int)((M + 31) / 32);
+  if (err == cudaSuccess)
+    k_tracer_mid<<<nblocks(G, 256), 256, 0, st>>>(k0, Mi, t.key, t.offs, (int)b.N, mid);
+  note_launches(3 + 4 * 5);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_err(err);
+  out->xraw = xraw;
+  out->xperm = v0;  // after an even number of passes: `perm`
+  out->xmid = mid;
+  out->M = M;
+  out->G = G;
+  return GS_OK;
+}
+
+namespace {
+WalkGroups target_groups(const BHStep& b, const BHTargets& x) {
+  WalkGroups g = walk_groups(b);
+  g.groups = nullptr;
+  g.G = x.G;
+  g.xraw = x.xraw;
+  g.xrec = x.xrec;
+  g.xperm = x.xperm;
+  g.xmid = x.xmid;
+  g.xM = (int)x.M;
+  return g;
+}
+}  // namespace
+
+gs_status bh_walk_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
+  if (err == cudaSuccess)
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), nullptr, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
+gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, const TracerEpi& e,
+                          cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), false,
+                                   FwdEpi{}, AdjEpi{}, e, nullptr, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
 }  // namespace gs

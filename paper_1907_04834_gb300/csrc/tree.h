@@ -78,6 +78,27 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
 gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
                       cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
+
+// Outside points (tracers, forward only) walking the tree of b.slot as
+// targets: positions xraw (FP32, by index), records xrec (scaled, by index);
+// tracer_order sorts them by Morton code in the tree's root box (scratch of
+// tracer_scratch_bytes(M)) and picks each 32-tracer group's slice cut.  The
+// tree's lists are overwritten.  The workspace must hold ceil(M/32) groups.
+struct BHTargets {
+  const float4* xraw = nullptr;
+  const float4* xrec = nullptr;
+  const uint32_t* xperm = nullptr;
+  const int* xmid = nullptr;
+  int64_t M = 0;
+  int G = 0;
+};
+size_t tracer_scratch_bytes(int64_t M);
+gs_status tracer_order(TreeWork& w, const BHStep& b, const float4* xraw, int64_t M,
+                       void* scratch, BHTargets* out, cudaStream_t st);
+gs_status bh_walk_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cudaStream_t st);
+// Evaluates the tracers' lists and applies the tracer epilogue.
+gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, const TracerEpi& e,
+                          cudaStream_t st);
 // Builds the tree on one state and exports it (see gs_tree in gs.h).
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
                       uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,

@@ -83,6 +83,7 @@ __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
 // set, group g = sorted points [32 g, 32 g + 32).
 struct GroupInfo {
   int first, count, nb, ne;
+  int mid;  // node at which the group's slices are cut (the leaf of its middle point)
 };
 __device__ __forceinline__ GroupInfo group_info(const TreeArrays& t, int N, const int4* groups,
                                                 int g) {
@@ -99,6 +100,8 @@ __device__ __forceinline__ GroupInfo group_info(const TreeArrays& t, int N, cons
     gi.nb = v.z + (int)t.offs[v.z];
     gi.ne = v.w + (int)t.offs[v.w];
   }
+  const int i = gi.first + min(16, gi.count - 1);
+  gi.mid = i + (int)t.offs[i + 1];
   return gi;
 }
 
@@ -123,7 +126,28 @@ struct WalkGroups {
   int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
   bool trunc;              // pure truncation: far nodes dropped, pairs cut at the threshold
   int crit;                // far test: 0 the paper's distance rule, 1 opening angle
+  // Outside targets (tracer points walking this tree, forward only); xperm
+  // NULL: the targets are the tree's own points.  Tracer groups are 32
+  // consecutive tracers in tracer-code order over the whole tree.
+  const float4* xraw;      // FP32 positions {x, y, z, 0} by tracer index
+  const float4* xrec;      // scaled records {xs, ys, zs, 0} by tracer index
+  const uint32_t* xperm;   // sorted tracer position -> tracer index
+  const int* xmid;         // per group: the node at which its slices are cut
+  int xM;                  // number of tracers
 };
+
+// Group g of the targets described by wg (tree points or outside tracers).
+__device__ __forceinline__ GroupInfo target_group(const TreeArrays& t, int N, const WalkGroups& wg,
+                                                  int g) {
+  if (!wg.xperm) return group_info(t, N, wg.groups, g);
+  GroupInfo gi;
+  gi.first = g * 32;
+  gi.count = min(32, wg.xM - gi.first);
+  gi.nb = 0;
+  gi.ne = total_nodes(t, N);
+  gi.mid = wg.xmid[g];
+  return gi;
+}
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
@@ -132,6 +156,7 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
 // fallback for overflowed lists, evaluation, fixed-order combine + epilogue
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
-                           const AdjEpi& ae, int64_t* counts, cudaStream_t st);
+                           const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
+                           cudaStream_t st);
 
 }  // namespace gs

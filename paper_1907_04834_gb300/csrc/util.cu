@@ -223,11 +223,12 @@ __global__ void k_segment_sum(const double* __restrict__ x, const int64_t* __res
 }
 
 __global__ void k_pack_points(const double* __restrict__ x, int64_t M,
-                              const double* __restrict__ c, double s, float4* xpk) {
+                              const double* __restrict__ c, double s, float4* xpk, float4* xraw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M)
-    xpk[i] = make_float4((float)((x[3 * i] - c[0]) * s), (float)((x[3 * i + 1] - c[1]) * s),
-                         (float)((x[3 * i + 2] - c[2]) * s), 0.f);
+  if (i >= M) return;
+  xpk[i] = make_float4((float)((x[3 * i] - c[0]) * s), (float)((x[3 * i + 1] - c[1]) * s),
+                       (float)((x[3 * i + 2] - c[2]) * s), 0.f);
+  if (xraw) xraw[i] = make_float4((float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2], 0.f);
 }
 
 // a . b over n values: each thread sums a contiguous chunk in order, then a
@@ -308,9 +309,9 @@ cudaError_t launch_segment_sum(const double* x, const int64_t* off, int S, doubl
 }
 
 cudaError_t launch_pack_points(const double* x, int64_t M, const double* center, double s,
-                               float4* xpk, cudaStream_t st) {
+                               float4* xpk, float4* xraw, cudaStream_t st) {
   if (M > 0) {
-    k_pack_points<<<blocks_for(M, 256), 256, 0, st>>>(x, M, center, s, xpk);
+    k_pack_points<<<blocks_for(M, 256), 256, 0, st>>>(x, M, center, s, xpk, xraw);
     note_launches(1);
   }
   return cudaGetLastError();
