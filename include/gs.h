@@ -73,7 +73,9 @@ typedef struct gs_params {
   double sigma;          /* Gaussian kernel width, > 0, same unit as q */
   double lambda;         /* data-term weight of Eq. 2, >= 0 */
   double thresh_sigmas;  /* GS_BH: a node is summarised when all its points
-                            lie farther than thresh_sigmas * sigma (paper: 3) */
+                            lie farther than thresh_sigmas * sigma (paper: 3);
+                            GS_TRUNC: the cutoff radius in sigmas; with
+                            criterion 1: the opening angle theta */
   int32_t T;             /* Euler steps over t in [0, 1], >= 1 */
   int32_t mode;          /* gs_mode */
   int32_t ckpt_every;    /* gs_shoot_grad: 0 = keep every step's state for the
