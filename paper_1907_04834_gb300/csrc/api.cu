@@ -569,7 +569,7 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     // persistent kernels: no split partials
   } else if (S.mode == GS_EXACT) {
     int J = std::max(S.gf.J, S.ga.J);
-    CK(c->part.ensure((size_t)J * 15 * S.Npad * sizeof(float2)), "workspace");
+    CK(c->part.ensure((size_t)J * 9 * S.Npad * sizeof(float2)), "workspace");
     size_t tn = (size_t)S.gf.n_itiles;
     if (c->tickets_n < tn) {
       CK(c->tickets.ensure(tn * sizeof(unsigned)), "workspace");

@@ -272,10 +272,21 @@ __device__ __forceinline__ void tracer_epilogue(int64_t i, const double v[3], co
   }
 }
 
-// Adjoint: finished sums A1 = Sum g (a_i.p_j + a_j.p_i) d_s, A2 = Sum c g w,
-// A3 = Sum c g (w.d_s) d_s, B1 = Sum g a_j, B2 = Sum g (w.d_s) p_j; the
-// backward step is alpha += h dA, beta += h dB with
-//   dA = sigma^-2 (-A1 / s + A2 - 2 ln2 A3),  dB = B1 + sigma^-2 B2 / s.
+// Adjoint.  With a = alpha^{k+1}, b = beta^{k+1}, w = b_i - b_j and the
+// scaled difference d_s, the backward step is alpha += h dA, beta += h dB,
+//   dA = sigma^-2 (-A1 / s + A2 - 2 ln2 A3),   dB = B1 + sigma^-2 B2 / s,
+// A1 = Sum g (a_i.p_j + a_j.p_i) d_s, A2 = Sum c g w, A3 = Sum c g (w.d_s) d_s,
+// B1 = Sum g a_j, B2 = Sum g (w.d_s) p_j.  The pair kernels accumulate the
+// three combinations that dA and dB need:
+//   A13 = Sum (-g (a_i.p_j + a_j.p_i) / s - 2 ln2 c g (w.d_s)) d_s,  A2,
+//   B   = Sum g (a_j + (sigma^-2 / s) (w.d_s) p_j),
+// so dA = sigma^-2 (A13 + A2) and dB = B.
+struct AdjConsts {
+  float c1;  // -1 / s
+  float c3;  // -2 ln 2
+  float kb;  // sigma^-2 / s
+};
+
 struct AdjEpi {
   double* al;           // N x 3 alpha (updated in place when h != 0)
   double* be;           // N x 3 beta
@@ -290,15 +301,17 @@ struct AdjEpi {
   int64_t N;
 };
 
-__device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const double A1[3],
-                                                const double A2[3], const double A3[3],
-                                                const double B1[3], const double B2[3],
+__host__ __device__ __forceinline__ AdjConsts adj_consts(const AdjEpi& e) {
+  return AdjConsts{(float)(-e.inv_s), -1.3862943611198906f, (float)(e.inv_s2 * e.inv_s)};
+}
+
+__device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const double A13[3],
+                                                const double A2[3], const double B[3],
                                                 const AdjEpi& e) {
-  const double two_ln2 = 1.3862943611198906;  // 2 ln 2 = 1 / (s^2 sigma^2)
   double dA[3], dB[3];
   for (int a = 0; a < 3; a++) {
-    dA[a] = e.inv_s2 * (-A1[a] * e.inv_s + A2[a] - two_ln2 * A3[a]);
-    dB[a] = B1[a] + e.inv_s2 * B2[a] * e.inv_s;
+    dA[a] = e.inv_s2 * (A13[a] + A2[a]);
+    dB[a] = B[a];
   }
   if (e.dA_out)
     for (int a = 0; a < 3; a++) e.dA_out[3 * i + a] = dA[a];
@@ -320,10 +333,9 @@ __device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const do
   }
 }
 
-__device__ __forceinline__ void adj_epilogue(int64_t i, const double A1[3], const double A2[3],
-                                             const double A3[3], const double B1[3],
-                                             const double B2[3], const AdjEpi& e) {
-  adj_epilogue_at(i, i, A1, A2, A3, B1, B2, e);
+__device__ __forceinline__ void adj_epilogue(int64_t i, const double A13[3], const double A2[3],
+                                             const double B[3], const AdjEpi& e) {
+  adj_epilogue_at(i, i, A13, A2, B, e);
 }
 
 }  // namespace gs

@@ -24,7 +24,7 @@ namespace gs {
 namespace {
 
 constexpr int kFwdComps = 6;
-constexpr int kAdjComps = 15;
+constexpr int kAdjComps = 9;
 constexpr int kTileF4 = EX_TILE / 2 * 3;  // float4 per tile of one pack
 
 struct TileRange {
@@ -173,13 +173,15 @@ struct VelTarget {
 };
 
 // Adjoint sums of one target over one staged tile (a = alpha^{k+1},
-// b = beta^{k+1}, w = b_i - b_j, d = d_s):
-//   A1 = Sum g (a_i.p_j + a_j.p_i) d,  A2 = Sum c g w,  A3 = Sum c g (w.d) d,
-//   B1 = Sum g a_j,                    B2 = Sum g (w.d) p_j.
+// b = beta^{k+1}, w = b_i - b_j, d = d_s; the combinations of AdjConsts):
+//   A13 = Sum (c1 g (a_i.p_j + a_j.p_i) + c3 c g (w.d)) d,  A2 = Sum c g w,
+//   B   = Sum g (a_j + kb (w.d) p_j).
 struct AdjTarget {
   f2 xi, yi, zi, ui, vi, wi, axi, ayi, azi, bxi, byi, bzi;
+  f2 c1, c3, kb;
   Kahan K[kAdjComps];
-  __device__ __forceinline__ void load(const float4* pk, const float4* ab, int64_t i) {
+  __device__ __forceinline__ void load(const float4* pk, const float4* ab, int64_t i,
+                                       const AdjConsts& k) {
     float qa[3], pa[3], aa[3], ba[3];
     pack_read(pk, i, qa, pa);
     pack_read(ab, i, aa, ba);
@@ -187,14 +189,14 @@ struct AdjTarget {
     ui = f2_dup(pa[0]), vi = f2_dup(pa[1]), wi = f2_dup(pa[2]);
     axi = f2_dup(aa[0]), ayi = f2_dup(aa[1]), azi = f2_dup(aa[2]);
     bxi = f2_dup(ba[0]), byi = f2_dup(ba[1]), bzi = f2_dup(ba[2]);
+    c1 = f2_dup(k.c1), c3 = f2_dup(k.c3), kb = f2_dup(k.kb);
 #pragma unroll
     for (int c = 0; c < kAdjComps; c++) K[c].zero();
   }
   __device__ __forceinline__ void tile(const float4* stage) {
     const ulonglong2* tq = reinterpret_cast<const ulonglong2*>(stage);
     const ulonglong2* ta = tq + kTileF4;
-    f2 a1x = 0, a1y = 0, a1z = 0, a2x = 0, a2y = 0, a2z = 0, a3x = 0, a3y = 0, a3z = 0;
-    f2 b1x = 0, b1y = 0, b1z = 0, b2x = 0, b2y = 0, b2z = 0;
+    f2 ax = 0, ay = 0, az = 0, a2x = 0, a2y = 0, a2z = 0, bx = 0, by = 0, bz = 0;
 #pragma unroll 2
     for (int m = 0; m < EX_TILE / 2; m++) {
       const ulonglong2 q0 = tq[3 * m + 0], q1 = tq[3 * m + 1], q2 = tq[3 * m + 2];
@@ -214,10 +216,6 @@ struct AdjTarget {
       sa = f2_fma(s0.x, ui, sa);  // + a_j . p_i
       sa = f2_fma(s0.y, vi, sa);
       sa = f2_fma(s1v.x, wi, sa);
-      const f2 gs = f2_mul(g, sa);
-      a1x = f2_fma(gs, dx, a1x);
-      a1y = f2_fma(gs, dy, a1y);
-      a1z = f2_fma(gs, dz, a1z);
       const f2 wx = f2_sub(bxi, s1v.y), wy = f2_sub(byi, s2.x), wz = f2_sub(bzi, s2.y);
       f2 wd = f2_mul(wx, dx);
       wd = f2_fma(wy, dy, wd);
@@ -226,33 +224,24 @@ struct AdjTarget {
       a2x = f2_fma(cg, wx, a2x);
       a2y = f2_fma(cg, wy, a2y);
       a2z = f2_fma(cg, wz, a2z);
-      const f2 cw = f2_mul(cg, wd);
-      a3x = f2_fma(cw, dx, a3x);
-      a3y = f2_fma(cw, dy, a3y);
-      a3z = f2_fma(cw, dz, a3z);
-      b1x = f2_fma(g, s0.x, b1x);
-      b1y = f2_fma(g, s0.y, b1y);
-      b1z = f2_fma(g, s1v.x, b1z);
-      const f2 gw = f2_mul(g, wd);
-      b2x = f2_fma(gw, q1.y, b2x);
-      b2y = f2_fma(gw, q2.x, b2y);
-      b2z = f2_fma(gw, q2.y, b2z);
+      const f2 kap = f2_fma(f2_mul(g, sa), c1, f2_mul(f2_mul(cg, wd), c3));
+      ax = f2_fma(kap, dx, ax);
+      ay = f2_fma(kap, dy, ay);
+      az = f2_fma(kap, dz, az);
+      const f2 t = f2_mul(wd, kb);
+      bx = f2_fma(g, f2_fma(t, q1.y, s0.x), bx);
+      by = f2_fma(g, f2_fma(t, q2.x, s0.y), by);
+      bz = f2_fma(g, f2_fma(t, q2.y, s1v.x), bz);
     }
-    K[0].add(f2_sum(a1x));
-    K[1].add(f2_sum(a1y));
-    K[2].add(f2_sum(a1z));
+    K[0].add(f2_sum(ax));
+    K[1].add(f2_sum(ay));
+    K[2].add(f2_sum(az));
     K[3].add(f2_sum(a2x));
     K[4].add(f2_sum(a2y));
     K[5].add(f2_sum(a2z));
-    K[6].add(f2_sum(a3x));
-    K[7].add(f2_sum(a3y));
-    K[8].add(f2_sum(a3z));
-    K[9].add(f2_sum(b1x));
-    K[10].add(f2_sum(b1y));
-    K[11].add(f2_sum(b1z));
-    K[12].add(f2_sum(b2x));
-    K[13].add(f2_sum(b2y));
-    K[14].add(f2_sum(b2z));
+    K[6].add(f2_sum(bx));
+    K[7].add(f2_sum(by));
+    K[8].add(f2_sum(bz));
   }
 };
 
@@ -328,7 +317,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
   const int64_t i = (int64_t)bi * EX_NT + threadIdx.x;
   const TileRange tr = tile_range(bj, geo.J, geo.n_jtiles);
   AdjTarget tg;
-  tg.load(pk, ab, i);
+  tg.load(pk, ab, i, adj_consts(epi));
   init_barriers(bars);
   const float4* srcs[2] = {pk, ab};
   unsigned done = 0;
@@ -348,7 +337,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
       const float2 v = __ldcg(&part[((size_t)b * kAdjComps + c) * geo.Npad + i]);
       acc[c] += (double)v.x + (double)v.y;
     }
-  adj_epilogue(i, acc, acc + 3, acc + 6, acc + 9, acc + 12, epi);
+  adj_epilogue(i, acc, acc + 3, acc + 6, epi);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +425,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
     const float4* sp = pk + (size_t)(pbase / 2) * 3;
     const float4* sa = ab + (size_t)(pbase / 2) * 3;
     AdjTarget tg;
-    tg.load(sp, sa, il);
+    tg.load(sp, sa, il, adj_consts(epi));
     const float4* srcs[2] = {sp, sa};
     if (!stream_tiles<2>(sbuf, bars, srcs, 0, bi.npad[w.x] / EX_TILE, done, status,
                          [&](const float4* st) { tg.tile(st); }))
@@ -448,7 +437,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
         const float2 v = tg.K[c].out();
         acc[c] = (double)v.x + (double)v.y;
       }
-      adj_epilogue_at(row0 + il, pbase + il, acc, acc + 3, acc + 6, acc + 9, acc + 12, epi);
+      adj_epilogue_at(row0 + il, pbase + il, acc, acc + 3, acc + 6, epi);
     }
   }
 }

@@ -166,7 +166,7 @@ __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float r
 // ------------------------------------------------------------------ evaluation
 template <bool ADJ>
 struct Acc {
-  static constexpr int NC = ADJ ? 15 : 6;
+  static constexpr int NC = ADJ ? 9 : 6;
   Kahan K[NC];
   __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -182,7 +182,7 @@ struct Acc {
 template <bool ADJ, bool TRUNC>
 __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const unsigned* mask,
                                            int n, int lane, const Own& me, float thr,
-                                           int& npair) {
+                                           const AdjConsts& ak, int& npair) {
   constexpr int NR = ADJ ? 12 : 6;
   auto keep = [&](int e, bool b) {
     if constexpr (TRUNC) {
@@ -226,10 +226,11 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
     A.K[4].add(f2_sum(hy));
     A.K[5].add(f2_sum(hz));
   } else {
+    // the three combined adjoint sums (see AdjConsts): A13, A2, B
     const f2 AX = f2_dup(me.m2.x), AY = f2_dup(me.m2.y), AZ = f2_dup(me.m2.z);
     const f2 BX = f2_dup(me.m3.x), BY = f2_dup(me.m3.y), BZ = f2_dup(me.m3.z);
-    f2 a1x = 0, a1y = 0, a1z = 0, a2x = 0, a2y = 0, a2z = 0, a3x = 0, a3y = 0, a3z = 0;
-    f2 b1x = 0, b1y = 0, b1z = 0, b2x = 0, b2y = 0, b2z = 0;
+    const f2 C1 = f2_dup(ak.c1), C3 = f2_dup(ak.c3), KB = f2_dup(ak.kb);
+    f2 ax = 0, ay = 0, az = 0, a2x = 0, a2y = 0, a2z = 0, bx = 0, by = 0, bz = 0;
     for (int e = 0; e < n; e += 2) {
       const bool b0 = keep(e, (mask[e] >> lane) & 1u), b1 = keep(e + 1, (mask[e + 1] >> lane) & 1u);
       const f2 dx = f2_sub(X, ld(0, e)), dy = f2_sub(Y, ld(1, e)), dz = f2_sub(Z, ld(2, e));
@@ -250,10 +251,6 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
       sa = f2_fma(QX, U, sa);  // + a_j . p_i
       sa = f2_fma(QY, V, sa);
       sa = f2_fma(QZ, W, sa);
-      const f2 gs = f2_mul(g, sa);
-      a1x = f2_fma(gs, dx, a1x);
-      a1y = f2_fma(gs, dy, a1y);
-      a1z = f2_fma(gs, dz, a1z);
       const f2 wx = f2_sub(BX, ld(9, e)), wy = f2_sub(BY, ld(10, e)), wz = f2_sub(BZ, ld(11, e));
       f2 wd = f2_mul(wx, dx);
       wd = f2_fma(wy, dy, wd);
@@ -262,33 +259,24 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
       a2x = f2_fma(cg, wx, a2x);
       a2y = f2_fma(cg, wy, a2y);
       a2z = f2_fma(cg, wz, a2z);
-      const f2 cw = f2_mul(cg, wd);
-      a3x = f2_fma(cw, dx, a3x);
-      a3y = f2_fma(cw, dy, a3y);
-      a3z = f2_fma(cw, dz, a3z);
-      b1x = f2_fma(g, QX, b1x);
-      b1y = f2_fma(g, QY, b1y);
-      b1z = f2_fma(g, QZ, b1z);
-      const f2 gw = f2_mul(g, wd);
-      b2x = f2_fma(gw, PX, b2x);
-      b2y = f2_fma(gw, PY, b2y);
-      b2z = f2_fma(gw, PZ, b2z);
+      const f2 kap = f2_fma(f2_mul(g, sa), C1, f2_mul(f2_mul(cg, wd), C3));
+      ax = f2_fma(kap, dx, ax);
+      ay = f2_fma(kap, dy, ay);
+      az = f2_fma(kap, dz, az);
+      const f2 t = f2_mul(wd, KB);
+      bx = f2_fma(g, f2_fma(t, PX, QX), bx);
+      by = f2_fma(g, f2_fma(t, PY, QY), by);
+      bz = f2_fma(g, f2_fma(t, PZ, QZ), bz);
     }
-    A.K[0].add(f2_sum(a1x));
-    A.K[1].add(f2_sum(a1y));
-    A.K[2].add(f2_sum(a1z));
+    A.K[0].add(f2_sum(ax));
+    A.K[1].add(f2_sum(ay));
+    A.K[2].add(f2_sum(az));
     A.K[3].add(f2_sum(a2x));
     A.K[4].add(f2_sum(a2y));
     A.K[5].add(f2_sum(a2z));
-    A.K[6].add(f2_sum(a3x));
-    A.K[7].add(f2_sum(a3y));
-    A.K[8].add(f2_sum(a3z));
-    A.K[9].add(f2_sum(b1x));
-    A.K[10].add(f2_sum(b1y));
-    A.K[11].add(f2_sum(b1z));
-    A.K[12].add(f2_sum(b2x));
-    A.K[13].add(f2_sum(b2y));
-    A.K[14].add(f2_sum(b2z));
+    A.K[6].add(f2_sum(bx));
+    A.K[7].add(f2_sum(by));
+    A.K[8].add(f2_sum(bz));
   }
 }
 
@@ -506,7 +494,8 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // spilled values): measured faster than 3 blocks at 168 registers.
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
-    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts) {
+    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, AdjConsts ak,
+              int64_t* counts) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
@@ -535,7 +524,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
     __syncwarp();
-    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, npair);
+    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, ak, npair);
   }
 #pragma unroll
   for (int c = 0; c < NC; c++) L.part[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
@@ -560,13 +549,14 @@ struct EvalSink {
   const Own* me;
   int cnt, lane;
   float thr;
+  AdjConsts ak;
   int npair;
   __device__ __forceinline__ bool fits(int) const { return true; }
   __device__ __forceinline__ void flush() {
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(*t, node, mask, soa, cnt, lane);
     __syncwarp();
-    eval_batch<ADJ, TRUNC>(*A, soa, mask, ce, lane, *me, thr, npair);
+    eval_batch<ADJ, TRUNC>(*A, soa, mask, ce, lane, *me, thr, ak, npair);
     __syncwarp();
     cnt = 0;
   }
@@ -590,7 +580,7 @@ struct EvalSink {
 template <bool ADJ, bool COUNT, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-                  WalkGroups wg, int64_t* counts) {
+                  WalkGroups wg, AdjConsts ak, int64_t* counts) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ float4 s_box[TR_WARPS][32][2];
@@ -612,7 +602,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   Acc<ADJ> A;
   A.zero();
-  EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, 0};
+  EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, ak, 0};
   long long np = 0, nn = 0;
   walk_nodes<COUNT, true>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, wg.crit, resume, sink,
                           lane, np, nn);
@@ -664,7 +654,7 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
     const double* c = wg.centers ? wg.centers + 3 * subject_of(wg.off, wg.S, o) : fe.center;
     fwd_epilogue_at(o, o, c, acc, acc + 3, fe);
   } else {
-    adj_epilogue(o, acc, acc + 3, acc + 6, acc + 9, acc + 12, ae);
+    adj_epilogue(o, acc, acc + 3, acc + 6, ae);
   }
 }
 
@@ -699,11 +689,14 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
                         cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
+  const AdjConsts ak = adj_consts(ae);
   if (counts)
-    k_bh_fallback<ADJ, true, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+    k_bh_fallback<ADJ, true, TRUNC>
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, ak, counts);
   else
-    k_bh_fallback<ADJ, false, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
-  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts);
+    k_bh_fallback<ADJ, false, TRUNC>
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, ak, counts);
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, ak, counts);
   k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae, te);
 }
 

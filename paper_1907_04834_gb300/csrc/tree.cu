@@ -624,8 +624,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
                o_nrec = take(64 * M), o_acnt = take(4 * M),
                o_isum = take(96 * M), o_cnt = take(16),
-               o_part = take(nl * 15 * 32 * sizeof(float2)),
-               o_fb = take(nl * 15 * 32 * sizeof(float2));
+               o_part = take(nl * 9 * 32 * sizeof(float2)),
+               o_fb = take(nl * 9 * 32 * sizeof(float2));
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->key = (uint32_t*)(b + o_key);

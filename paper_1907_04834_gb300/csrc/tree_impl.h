@@ -70,8 +70,8 @@ struct BHLists {
   int* ovf_x;     // per list: >= 0 if the pool ran out (slice re-walked)
   int* used;      // chunks taken from the pool (reset before each walk)
   int n_chunks;   // pool size
-  float2* part;   // per list x 15 x 32: partial sums of the list
-  float2* fb;     // per list x 15 x 32: partial sums of a re-walked slice
+  float2* part;   // per list x 9 x 32: partial sums of the list (at most 9 components)
+  float2* fb;     // per list x 9 x 32: partial sums of a re-walked slice
 };
 
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
