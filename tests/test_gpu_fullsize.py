@@ -1,7 +1,10 @@
 """Full-size checks at the benchmark's N = 100,000 blob workload (sigma =
 1.5, T = 20), in the configuration the benchmark times: sampled rows of one
 exact right-hand side and one adjoint right-hand side against the oracle,
-and properties of the full gradient that hold at any size."""
+the Barnes-Hut right-hand sides at full size (interaction counts exact) and
+a Barnes-Hut gradient over T = 4 steps against the oracle, and properties
+of the full gradient that hold at any size.  Each test prints the measured
+error beside its tolerance (pytest -s)."""
 import numpy as np
 import pytest
 import torch
@@ -31,8 +34,11 @@ def test_sampled_rows_rhs(oracle, w):
     be = rng.normal(scale=0.1, size=w.q0.shape)
     dA, dB, _ = gs.adj_rhs(dt(w.q0), dt(w.p0), dt(al), dt(be), w.sigma)
     dAo, dBo = oracle.adj_rhs_rows(w.q0, w.p0, al, be, w.sigma, rows)
-    assert np.abs(npy(dA)[rows] - dAo).max() <= 1e-5 * np.abs(dAo).max()
-    assert np.abs(npy(dB)[rows] - dBo).max() <= 1e-5 * np.abs(dBo).max()
+    eF = np.abs(F - Fo).max() / np.abs(Fo).max()
+    eA = np.abs(npy(dA)[rows] - dAo).max() / np.abs(dAo).max()
+    eB = np.abs(npy(dB)[rows] - dBo).max() / np.abs(dBo).max()
+    print(f"\nexact RHS at N=100k, 200 rows: F {eF:.2e}, dA {eA:.2e}, dB {eB:.2e} (tol 1e-5)")
+    assert eA <= 1e-5 and eB <= 1e-5
 
 
 def test_full_gradient_properties(w):
@@ -48,3 +54,53 @@ def test_full_gradient_properties(w):
     _, p1, _ = gs.shoot(dt(w.q0), dt(w.p0), w.sigma, w.T)
     s0, s1 = w.p0.sum(axis=0), npy(p1).sum(axis=0)
     assert np.abs(s1 - s0).max() <= 1e-6 * np.abs(w.p0).sum()
+
+
+def test_bh_rhs_full_size(oracle, w):
+    """Barnes-Hut forward and adjoint right-hand sides at N = 100,000 against
+    the oracle's pointer-tree traversal: the same decisions (interaction
+    counts equal) and values to FP32 rounding."""
+    F, Phi, cnt = gs.rhs(dt(w.q0), dt(w.p0), w.sigma, mode="bh")
+    Fo, Phio, cnto = oracle.rhs(w.q0, w.p0, w.sigma, mode=oracle.BH)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    eF = np.abs(npy(F) - Fo).max() / np.abs(Fo).max()
+    eP = np.abs(npy(Phi) - Phio).max() / np.abs(Phio).max()
+    rng = np.random.default_rng(1)
+    al, be = rng.normal(size=w.q0.shape), rng.normal(scale=0.1, size=w.q0.shape)
+    dA, dB, cnta = gs.adj_rhs(dt(w.q0), dt(w.p0), dt(al), dt(be), w.sigma, mode="bh")
+    dAo, dBo, cntao = oracle.adj_rhs(w.q0, w.p0, al, be, w.sigma, mode=oracle.BH)
+    assert tuple(cnta) == tuple(int(c) for c in cntao)
+    eA = np.abs(npy(dA) - dAo).max() / np.abs(dAo).max()
+    eB = np.abs(npy(dB) - dBo).max() / np.abs(dBo).max()
+    print(f"\nBH RHS at N=100k: counts {tuple(cnt)}; F {eF:.2e}, Phi {eP:.2e}, dA {eA:.2e}, "
+          f"dB {eB:.2e} (tol 1e-5)")
+    assert max(eF, eP, eA, eB) <= 1e-5
+
+
+def test_bh_gradient_full_size(oracle, w):
+    """The whole Barnes-Hut shooting gradient at N = 100,000 (T = 4 steps to
+    keep the oracle's time short) against the oracle."""
+    T = 4
+    E, g, q1 = gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), w.sigma, T, w.lam, mode="bh")
+    Eo, go, q1o = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, T, w.lam, mode=oracle.BH)
+    dq = np.abs(npy(q1) - q1o).max() / w.sigma
+    eg = np.linalg.norm(npy(g) - go) / np.linalg.norm(go)
+    eE = abs(float(E[0]) - Eo[0]) / abs(Eo[0])
+    print(f"\nBH gradient at N=100k, T={T}: max|dq1|/sigma {dq:.2e} (tol 1e-5), grad rel L2 "
+          f"{eg:.2e} (tol 1e-4), E rel {eE:.2e}")
+    assert dq <= 1e-5 and eg <= 1e-4 and eE <= 1e-6
+
+
+def test_exact_gradient_slab20k(oracle):
+    """The exact shooting gradient on the 20,000-point slab (sigma = 2; T = 4
+    steps to keep the oracle's time short) against the FP64 oracle."""
+    v = inputs.config("slab20k")
+    T = 4
+    E, g, q1 = gs.shoot_grad(dt(v.q0), dt(v.p0), dt(v.X), v.sigma, T, v.lam)
+    Eo, go, q1o = oracle.shoot_grad(v.q0, v.p0, v.X, v.sigma, T, v.lam)
+    dq = np.abs(npy(q1) - q1o).max() / v.sigma
+    eg = np.linalg.norm(npy(g) - go) / np.linalg.norm(go)
+    eE = abs(float(E[0]) - Eo[0]) / abs(Eo[0])
+    print(f"\nexact gradient at N=20k, T={T}: max|dq1|/sigma {dq:.2e} (tol 1e-5), grad rel L2 "
+          f"{eg:.2e} (tol 1e-4), E rel {eE:.2e}")
+    assert dq <= 1e-5 and eg <= 1e-4 and eE <= 1e-6
