@@ -128,3 +128,38 @@ def test_list_overflow_is_bit_exact(cap):
     assert c1 == c0
     for a, b in zip(out, ref):
         assert torch.equal(a, b)
+
+
+def _degenerate(kind):
+    rng = np.random.default_rng(71)
+    if kind == "cluster":  # 300 coincident points (one depth-10 cell) among 400 others
+        q = np.vstack([np.repeat(rng.normal(size=(1, 3)), 300, axis=0),
+                       rng.normal(scale=4.0, size=(400, 3))])
+    elif kind == "flat":  # a zero-extent axis: every z equal
+        q = rng.normal(scale=5.0, size=(900, 3))
+        q[:, 2] = 1.25
+    elif kind == "line":  # collinear points
+        t = rng.uniform(-20, 20, size=(600, 1))
+        q = t * np.array([[0.6, -0.48, 0.64]]) + np.array([[1.0, 2.0, 3.0]])
+    else:  # every point at the same position
+        q = np.repeat(np.array([[3.0, -1.0, 2.0]]), 64, axis=0)
+    p = rng.normal(scale=0.1, size=q.shape)
+    return q, p
+
+
+@pytest.mark.parametrize("kind", ["cluster", "flat", "line", "all_same"])
+def test_bh_degenerate_clouds(oracle, kind):
+    q, p = _degenerate(kind)
+    sigma = 1.0
+    F, Phi, cnt = gs.rhs(dt(q), dt(p), sigma, mode="bh")
+    Fo, Phio, cnto = oracle.rhs(q, p, sigma, mode=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(F), Fo) <= 1e-5
+    assert max_rel(npy(Phi), Phio, phi_floor(p, sigma)) <= 1e-5
+    rng = np.random.default_rng(3)
+    al, be = rng.normal(size=q.shape), rng.normal(scale=0.1, size=q.shape)
+    dA, dB, cnt = gs.adj_rhs(dt(q), dt(p), dt(al), dt(be), sigma, mode="bh")
+    dAo, dBo, cnto = oracle.adj_rhs(q, p, al, be, sigma, mode=1)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    assert max_rel(npy(dA), dAo, 1e-12 * np.abs(al).max() * np.abs(p).max() / sigma) <= 1e-5
+    assert max_rel(npy(dB), dBo) <= 1e-5
