@@ -137,6 +137,15 @@ __device__ __forceinline__ int slice_start(const TreeArrays& t, const GroupInfo&
   return min(gi.ne, mid + (D << (k - h - 1)));
 }
 
+// List evaluated by warp `wl` of a launch over all (group, slice) lists:
+// the warps of one block take the same slice of consecutive groups (lists
+// of similar length), the last slices -- on average the longest -- first.
+// Measured faster than one group's slices per block for the evaluations;
+// the walk keeps one group per block.
+__device__ __forceinline__ int list_of_warp(int wl, int G) {
+  return (wl % G) * BH_SLICES + (BH_SLICES - 1 - wl / G);
+}
+
 __device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& gi, int k) {
   return k == BH_SLICES - 1 ? gi.ne : slice_start(t, gi, k + 1);
 }
@@ -502,8 +511,8 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
   __shared__ int s_node[TR_WARPS][TR_CAP];
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int l = blockIdx.x * TR_WARPS + w;
-  if (l >= wg.G * BH_SLICES) return;
+  if (blockIdx.x * TR_WARPS + w >= wg.G * BH_SLICES) return;
+  const int l = list_of_warp(blockIdx.x * TR_WARPS + w, wg.G);
   if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
   const Own me = load_own(t, wg, target_group(t, N, wg, l / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
@@ -588,8 +597,8 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   __shared__ int s_node[TR_WARPS][TR_CAP];
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int l = blockIdx.x * TR_WARPS + w;
-  if (l >= wg.G * BH_SLICES) return;
+  if (blockIdx.x * TR_WARPS + w >= wg.G * BH_SLICES) return;
+  const int l = list_of_warp(blockIdx.x * TR_WARPS + w, wg.G);
   if (L.ovf_x[l] < 0) return;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
   const GroupInfo gi = target_group(t, N, wg, g);
