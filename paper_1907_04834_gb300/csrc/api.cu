@@ -119,7 +119,8 @@ struct KTimer {
 };
 
 // scal slots (doubles)
-enum { SC_CENTER = 0, SC_H0 = 3, SC_H1 = 4, SC_DATA = 5, SC_E = 6, SC_N = 16 };
+enum { SC_CENTER = 0, SC_H0 = 3, SC_H1 = 4, SC_DATA = 5, SC_E = 6, SC_BOX = 16,
+       SC_N = SC_BOX + 6 * kBoxBlocks };
 
 constexpr double kLog2e = 1.4426950408889634;
 
@@ -613,7 +614,8 @@ gs_status solver_load(Solver& S, const double* q0, const double* p0, int slot) {
                             const_cast<double*>(S.batch->dev.centers), S.st),
        "center");
   else
-    CK(launch_bbox_center(c->q.as<double>(), S.N, S.scal(SC_CENTER), S.st), "center");
+    CK(launch_bbox_center(c->q.as<double>(), S.N, S.scal(SC_CENTER), S.scal(SC_BOX), S.st),
+       "center");
   return solver_pack(S, slot);
 }
 

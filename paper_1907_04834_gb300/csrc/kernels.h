@@ -96,7 +96,11 @@ cudaError_t launch_axpy(double* y, const double* x, double a, int64_t n, cudaStr
 cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st);
 
 // ---- small helpers (util.cu)
-cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st);
+// Centre of the bounding box of q [N][3]; part is scratch for 6 * kBoxBlocks
+// doubles.
+constexpr int kBoxBlocks = 304;
+cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, double* part,
+                               cudaStream_t st);
 cudaError_t launch_pack(const double* q, const double* p, int64_t N, const double* center,
                         double s, float4* pack, float4* raw, cudaStream_t st);
 // zero the padding points [N, Npad) of `slots` consecutive packs

@@ -6,9 +6,10 @@
 // allocations), and latency-critical loops in which an allocation's implicit
 // device synchronisation is not acceptable.  This entry point allocates
 // nothing: its scratch (recentring point, status word, tickets, the source
-// pack and the split partial sums) lives in one file-scope device array of
-// fixed size that every GPU loading the library holds until the process
-// exits.  Inputs and outputs are the caller's device buffers.
+// pack, the split partial sums and the bounding-box partials) lives in one
+// file-scope device array of fixed size that every GPU loading the library
+// holds until the process exits.  Inputs and outputs are the caller's device
+// buffers.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -26,7 +27,8 @@ constexpr size_t kOffStatus = 256;
 constexpr size_t kOffTickets = 512;
 constexpr size_t kOffPack = kOffTickets + 4 * (kMaxN / EX_NT) + 256;
 constexpr size_t kOffPart = kOffPack + sizeof(float4) * 3 * (kMaxN / 2);
-constexpr size_t kScratchBytes = kOffPart + sizeof(float2) * 6 * kMaxJ * kMaxN;
+constexpr size_t kOffBox = kOffPart + sizeof(float2) * 6 * kMaxJ * kMaxN;
+constexpr size_t kScratchBytes = kOffBox + sizeof(double) * 6 * kBoxBlocks;
 static_assert(kMaxN % EX_TILE == 0, "the maximum size must be a whole number of tiles");
 
 // The scratch itself.  Host code must not use this name as an address: the
@@ -110,13 +112,14 @@ extern "C" gs_status gs_rhs_exact_noalloc(const double* q, const double* p, int6
   unsigned* tickets = reinterpret_cast<unsigned*>(d->scratch + kOffTickets);
   float4* pack = reinterpret_cast<float4*>(d->scratch + kOffPack);
   float2* part = reinterpret_cast<float2*>(d->scratch + kOffPart);
+  double* box = reinterpret_cast<double*>(d->scratch + kOffBox);
   const double sc = std::sqrt(1.4426950408889634 / (2.0 * sigma * sigma));
 
   // The scratch keeps the previous call's contents: clear what must start at
   // zero (status, tickets, padding sources of the pack).
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned) * g.n_itiles, st);
-  if (e == cudaSuccess) e = launch_bbox_center(q, N, center, st);
+  if (e == cudaSuccess) e = launch_bbox_center(q, N, center, box, st);
   if (e == cudaSuccess) e = launch_pad_zero(pack, (size_t)(g.Npad / 2) * 3, 1, N, g.Npad, st);
   if (e == cudaSuccess) e = launch_pack(q, p, N, center, sc, pack, nullptr, st);
   if (e == cudaSuccess) {

@@ -463,12 +463,15 @@ struct ListSink {
 template <bool COUNT, bool VAR>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-              WalkGroups wg, int64_t* counts) {
+              WalkGroups wg, int64_t* counts, const int* __restrict__ word) {
+  // word: NULL, or an order of the lists that is used when *L.worder_n says
+  // it holds as many lists as this walk has
   __shared__ float4 s_box[TR_WARPS][32][2];
   __shared__ int2 s_ent[TR_WARPS][BH_CHUNK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int l = blockIdx.x * TR_WARPS + w;
-  if (l >= wg.G * BH_SLICES) return;
+  const int nl = wg.G * BH_SLICES, wl = blockIdx.x * TR_WARPS + w;
+  if (wl >= nl) return;
+  const int l = (word && *L.worder_n == nl) ? word[wl] : wl;
   const int g = l / BH_SLICES, k = l % BH_SLICES;
   const GroupInfo gi = target_group(t, N, wg, g);
   const bool valid = lane < gi.count;
@@ -504,15 +507,16 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, AdjConsts ak,
-              int64_t* counts) {
+              int64_t* counts, const int* __restrict__ order) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
   __shared__ int s_node[TR_WARPS][TR_CAP];
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (blockIdx.x * TR_WARPS + w >= wg.G * BH_SLICES) return;
-  const int l = list_of_warp(blockIdx.x * TR_WARPS + w, wg.G);
+  const int wl = blockIdx.x * TR_WARPS + w;
+  if (wl >= wg.G * BH_SLICES) return;
+  const int l = order ? order[wl] : list_of_warp(wl, wg.G);
   if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
   const Own me = load_own(t, wg, target_group(t, N, wg, l / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
@@ -667,6 +671,56 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
   }
 }
 
+// Longest-first order of n lists by their lengths: a counting sort on
+// kOrderBuckets length classes (len * (kOrderBuckets - 1) / max len), one
+// block.  Lists of one class land in any order; every list appears once.
+// Writes order[] and worder[], and *worder_n = n.
+constexpr int kOrderThreads = 1024, kOrderBuckets = 512;
+__global__ void __launch_bounds__(kOrderThreads)
+    k_list_order(const int* __restrict__ len, int n, int* order, int* worder, int* worder_n) {
+  __shared__ int s_cnt[kOrderBuckets];
+  __shared__ int s_max[kOrderThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int mx = 0;
+  for (int l = tid; l < n; l += kOrderThreads) mx = max(mx, len[l]);
+  mx = __reduce_max_sync(FULL, (unsigned)mx);
+  if (lane == 0) s_max[w] = mx;
+  for (int b = tid; b < kOrderBuckets; b += kOrderThreads) s_cnt[b] = 0;
+  __syncthreads();
+  mx = 1;
+  for (int k = 0; k < kOrderThreads / 32; k++) mx = max(mx, s_max[k]);
+  // class 0 = longest
+  auto cls = [&](int l) {
+    const int v = min(max(len[l], 0), mx);
+    return kOrderBuckets - 1 - (int)((long long)v * (kOrderBuckets - 1) / mx);
+  };
+  for (int l = tid; l < n; l += kOrderThreads) atomicAdd(&s_cnt[cls(l)], 1);
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the class counts, 16 per lane
+    constexpr int per = kOrderBuckets / 32;
+    int loc = 0;
+    for (int k = 0; k < per; k++) loc += s_cnt[lane * per + k];
+    int inc = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += v;
+    }
+    int run = inc - loc;
+    for (int k = 0; k < per; k++) {
+      const int c = s_cnt[lane * per + k];
+      s_cnt[lane * per + k] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int l = tid; l < n; l += kOrderThreads) {
+    const int at = atomicAdd(&s_cnt[cls(l)], 1);
+    order[at] = l;
+    worder[at] = l;
+  }
+  if (tid == 0) *worder_n = n;
+}
+
 inline unsigned list_blocks(int G) {
   const int lists = G * BH_SLICES;
   return (unsigned)((lists + TR_WARPS - 1) / TR_WARPS);
@@ -676,18 +730,23 @@ inline unsigned list_blocks(int G) {
 
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
-                           cudaStream_t st) {
+                           bool scheduled, cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
+  const int nl = wg.G * BH_SLICES;
   const bool var = wg.leaf > 1 || wg.trunc || wg.crit != 0;  // the paper's rule: lean walk
+  // the previous walk's order (taken if it covers as many lists)
+  const int* word = scheduled ? L.worder : nullptr;
   if (counts && var)
-    k_bh_walk<true, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+    k_bh_walk<true, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else if (counts)
-    k_bh_walk<true, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+    k_bh_walk<true, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else if (var)
-    k_bh_walk<false, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+    k_bh_walk<false, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else
-    k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
-  note_launches(1);
+    k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
+  if (scheduled)
+    k_list_order<<<1, kOrderThreads, 0, st>>>(L.len, nl, L.order, L.worder, L.worder_n);
+  note_launches(scheduled ? 2 : 1);
   return cudaGetLastError();
 }
 
@@ -695,7 +754,7 @@ template <bool ADJ, bool TRUNC>
 static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr,
                         const BHLists& L, const WalkGroups& wg, const FwdEpi& fe,
                         const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
-                        cudaStream_t st) {
+                        const int* order, cudaStream_t st) {
   const unsigned nb = list_blocks(wg.G);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
   const AdjConsts ak = adj_consts(ae);
@@ -705,20 +764,21 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
   else
     k_bh_fallback<ADJ, false, TRUNC>
         <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, ak, counts);
-  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, ak, counts);
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, ak, counts, order);
   k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae, te);
 }
 
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
                            const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
-                           cudaStream_t st) {
+                           bool scheduled, cudaStream_t st) {
+  const int* ord = scheduled ? L.order : nullptr;
   if (wg.trunc) {
-    if (!adj) eval_launch<false, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
-    else eval_launch<true, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
+    if (!adj) eval_launch<false, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
+    else eval_launch<true, true>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
   } else {
-    if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
-    else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, st);
+    if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
+    else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
   }
   note_launches(3);
   return cudaGetLastError();

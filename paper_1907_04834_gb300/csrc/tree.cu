@@ -625,7 +625,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_nrec = take(64 * M), o_acnt = take(4 * M),
                o_isum = take(96 * M), o_cnt = take(16),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
-               o_fb = take(nl * 9 * 32 * sizeof(float2));
+               o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * nl),
+               o_wordn = take(4);
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->key = (uint32_t*)(b + o_key);
@@ -647,6 +648,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     t->counts = (int64_t*)(b + o_cnt);
     L->part = (float2*)(b + o_part);
     L->fb = (float2*)(b + o_fb);
+    L->worder = (int*)(b + o_word);
+    L->worder_n = (int*)(b + o_wordn);
   }
   return o;
 }
@@ -665,7 +668,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
                o_nsc = take(8 * M), o_ninfo = take(8 * M), o_nbox = take(32 * M),
                o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
                o_next = take(4 * (size_t)chunks), o_head = take(4 * nl), o_len = take(4 * nl),
-               o_ovx = take(4 * nl), o_used = take(4);
+               o_ovx = take(4 * nl), o_used = take(4), o_order = take(4 * nl);
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->perm = (uint32_t*)(b + o_perm);
@@ -680,6 +683,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     L->len = (int*)(b + o_len);
     L->ovf_x = (int*)(b + o_ovx);
     L->used = (int*)(b + o_used);
+    L->order = (int*)(b + o_order);
     L->n_chunks = (int)chunks;
   }
   return o;
@@ -834,6 +838,12 @@ gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st, int64
   w.lcap_from_req = w.lcap_req;
   views(w, 0, &t, &L);
   w.d_counts = t.counts;
+  // no walk order yet: the first walk takes its lists in index order
+  if (cudaMemset(L.worder_n, 0xff, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    tree_release(w);
+    return GS_ERR_CUDA;
+  }
   return GS_OK;
 }
 
@@ -893,7 +903,7 @@ gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
   if (err == cudaSuccess)
     err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), counts ? t.counts : nullptr,
-                         st);
+                         true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -903,7 +913,7 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
   BHLists L;
   views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), false, e,
-                                   AdjEpi{}, TracerEpi{}, counts ? t.counts : nullptr, st);
+                                   AdjEpi{}, TracerEpi{}, counts ? t.counts : nullptr, true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -913,7 +923,7 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   BHLists L;
   views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), true, FwdEpi{},
-                                   e, TracerEpi{}, counts ? t.counts : nullptr, st);
+                                   e, TracerEpi{}, counts ? t.counts : nullptr, true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -1078,7 +1088,7 @@ gs_status bh_walk_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cuda
   views(w, b.slot, &t, &L);
   cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
   if (err == cudaSuccess)
-    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), nullptr, st);
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), nullptr, false, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -1088,7 +1098,7 @@ gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cons
   BHLists L;
   views(w, b.slot, &t, &L);
   cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), false,
-                                   FwdEpi{}, AdjEpi{}, e, nullptr, st);
+                                   FwdEpi{}, AdjEpi{}, e, nullptr, false, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 

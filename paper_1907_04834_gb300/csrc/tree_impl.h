@@ -72,6 +72,13 @@ struct BHLists {
   int n_chunks;   // pool size
   float2* part;   // per list x 9 x 32: partial sums of the list (at most 9 components)
   float2* fb;     // per list x 9 x 32: partial sums of a re-walked slice
+  // Scheduling (never the results): order[k] is the list the k-th warp of an
+  // evaluation takes, longest lists first; worder is the order of the last
+  // walk's lists, which the next walk of as many lists (*worder_n) takes as
+  // its estimate of their cost.
+  int* order;     // per list (this step)
+  int* worder;    // per list (shared by the steps)
+  int* worder_n;  // list count of worder; -1 when it holds none
 };
 
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
@@ -149,14 +156,19 @@ __device__ __forceinline__ GroupInfo target_group(const TreeArrays& t, int N, co
   return gi;
 }
 
-// counts: NULL or 2 int64 accumulating {point, node} interactions
+// counts: NULL or 2 int64 accumulating {point, node} interactions.
+// scheduled: take the lists in the previous walk's longest-first order (when
+// it has as many lists), then sort this walk's lists by length into L.order
+// and L.worder.  Only the order in which warps take lists changes, never a
+// result.
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
-                           cudaStream_t st);
-// fallback for overflowed lists, evaluation, fixed-order combine + epilogue
+                           bool scheduled, cudaStream_t st);
+// fallback for overflowed lists, evaluation, fixed-order combine + epilogue;
+// scheduled: evaluate in L.order (written by a scheduled walk of these lists)
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, bool adj, const FwdEpi& fe,
                            const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
-                           cudaStream_t st);
+                           bool scheduled, cudaStream_t st);
 
 }  // namespace gs

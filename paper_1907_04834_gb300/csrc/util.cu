@@ -11,6 +11,7 @@ namespace gs {
 namespace {
 
 constexpr int kRedThreads = 1024;
+constexpr int kBoxThreads = 256;
 
 // Block-wide sum with a fixed reduction tree (deterministic).
 __device__ double block_sum(double v) {
@@ -25,12 +26,18 @@ __device__ double block_sum(double v) {
   return v;
 }
 
-__global__ void k_bbox_center(const double* __restrict__ q, int64_t N, double* center) {
-  __shared__ double smin[3][32], smax[3][32];
+// Bounding-box centre of q [N][3] in two launches: k_bbox_part gives each of
+// G blocks the min and max of a grid-stride share of the points
+// (part[6b..6b+2] low corner, part[6b+3..6b+5] high corner), k_bbox_fin
+// folds the G partials.  Min and max are exact, so the centre does not
+// depend on the split.
+__global__ void k_bbox_part(const double* __restrict__ q, int64_t N, double* __restrict__ part) {
+  __shared__ double sh[6][kBoxThreads / 32];
   double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-  for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
     for (int a = 0; a < 3; a++) {
-      double x = q[3 * i + a];
+      const double x = q[3 * i + a];
       lo[a] = fmin(lo[a], x);
       hi[a] = fmax(hi[a], x);
     }
@@ -39,23 +46,33 @@ __global__ void k_bbox_center(const double* __restrict__ q, int64_t N, double* c
       lo[a] = fmin(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
       hi[a] = fmax(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
     }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0)
-    for (int a = 0; a < 3; a++) {
-      smin[a][w] = lo[a];
-      smax[a][w] = hi[a];
-    }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; a++) sh[a][w] = lo[a], sh[3 + a][w] = hi[a];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int a = 0; a < 3; a++) {
-      double mn = smin[a][0], mx = smax[a][0];
-      for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
-        mn = fmin(mn, smin[a][k]);
-        mx = fmax(mx, smax[a][k]);
-      }
-      center[a] = 0.5 * (mn + mx);
-    }
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    double v = sh[a][0];
+    for (int k = 1; k < kBoxThreads / 32; k++) v = a < 3 ? fmin(v, sh[a][k]) : fmax(v, sh[a][k]);
+    part[6 * blockIdx.x + a] = v;
   }
+}
+
+__global__ void k_bbox_fin(const double* __restrict__ part, int G, double* center) {
+  const int l = threadIdx.x;
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int b = l; b < G; b += 32)
+    for (int a = 0; a < 3; a++) {
+      lo[a] = fmin(lo[a], part[6 * b + a]);
+      hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
+    }
+  for (int a = 0; a < 3; a++)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fmin(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmax(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+  if (l == 0)
+    for (int a = 0; a < 3; a++) center[a] = 0.5 * (lo[a] + hi[a]);
 }
 
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ p, int64_t N,
@@ -342,9 +359,16 @@ cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, cudaStream_t st) {
-  k_bbox_center<<<1, kRedThreads, 0, st>>>(q, N, center);
-  note_launches(1);
+int bbox_blocks(int64_t N) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kBoxBlocks, (N + kBoxThreads - 1) / kBoxThreads));
+}
+
+cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, double* part,
+                               cudaStream_t st) {
+  const int G = bbox_blocks(N);
+  k_bbox_part<<<G, kBoxThreads, 0, st>>>(q, N, part);
+  k_bbox_fin<<<1, 32, 0, st>>>(part, G, center);
+  note_launches(2);
   return cudaGetLastError();
 }
 
