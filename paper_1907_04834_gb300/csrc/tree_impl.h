@@ -114,12 +114,28 @@ __device__ __forceinline__ GroupInfo group_info(const TreeArrays& t, int N, cons
 
 // FP32 distance-squared from a point to an axis-aligned box, no contraction:
 // dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
+// Three-input maximum (sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Per axis max(lo - x, 0, x - hi), then (dx*dx + dy*dy) + dz*dz, every
+// operation rounded to nearest and none contracted; the x and y axes take
+// packed f32x2 subtractions and one packed product (same roundings).
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4& lo,
                                            const float4& hi) {
-  float dx = fmaxf(fmaxf(__fsub_rn(lo.x, x), 0.f), __fsub_rn(x, hi.x));
-  float dy = fmaxf(fmaxf(__fsub_rn(lo.y, y), 0.f), __fsub_rn(y, hi.y));
-  float dz = fmaxf(fmaxf(__fsub_rn(lo.z, z), 0.f), __fsub_rn(z, hi.z));
-  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  const f2 p = f2_make(x, y);
+  float ax, ay, bx, by;
+  f2_split(f2_sub(f2_make(lo.x, lo.y), p), ax, ay);
+  f2_split(f2_sub(p, f2_make(hi.x, hi.y)), bx, by);
+  const float dx = fmax3(ax, 0.f, bx), dy = fmax3(ay, 0.f, by);
+  const float dz = fmax3(__fsub_rn(lo.z, z), 0.f, __fsub_rn(z, hi.z));
+  const f2 d = f2_make(dx, dy);
+  float sx, sy;
+  f2_split(f2_mul(d, d), sx, sy);
+  return __fadd_rn(__fadd_rn(sx, sy), __fmul_rn(dz, dz));
 }
 
 // Walk groups and, for a forest, the per-subject recentring points used by
