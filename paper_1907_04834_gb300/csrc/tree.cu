@@ -518,18 +518,60 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* _
 }
 
 // ---------------------------------------------------------------- aggregates
-// write_box = false: the boxes (and skips) of this tree are already stored;
-// only the sums and source records are recomputed (backward-stage reuse).
+// Member sums are carried as unevaluated FP32 pairs (hi + lo, hi the rounded
+// sum): each addition is Knuth's TwoSum, which returns the rounding error of
+// hi exactly, so a pair holds the sum with about twice FP32's precision at
+// FP32 speed (FP64 arithmetic is the slow path on this GPU).  The pairs are
+// added in the same fixed bottom-up order as the tree's preorder, so results
+// are deterministic.
+struct Pair {
+  float hi, lo;
+};
+__device__ __forceinline__ void pair_add(Pair& s, float x) {
+  const float t = __fadd_rn(s.hi, x);
+  const float bp = __fsub_rn(t, s.hi);
+  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, e);
+}
+__device__ __forceinline__ void pair_add(Pair& s, float2 v) {
+  pair_add(s, v.x);
+  s.lo = __fadd_rn(s.lo, v.y);
+}
+// hi + lo renormalised (|lo| <= ulp(hi) / 2), stored as (hi, lo)
+__device__ __forceinline__ float2 pair_store(const Pair& s) {
+  const float t = __fadd_rn(s.hi, s.lo);
+  return make_float2(t, __fsub_rn(s.lo, __fsub_rn(t, s.hi)));
+}
+// the pair's value rounded to FP32
+__device__ __forceinline__ float pair_value(const Pair& s) { return __fadd_rn(s.hi, s.lo); }
+// (hi + lo) / n rounded to FP32.  n < 2^24 (exact in FP32): q = hi / n, then
+// one correction by the remainder hi - q n (exact by FMA) plus lo.  Larger
+// counts (only the top nodes of trees beyond 2^24 points) divide in FP64.
+__device__ __forceinline__ float pair_mean(const Pair& s, int count) {
+  if (count >= (1 << 24)) return (float)(((double)s.hi + (double)s.lo) / (double)count);
+  const float n = (float)count;
+  const float q = __fdiv_rn(s.hi, n);
+  const float r = __fadd_rn(__fmaf_rn(-q, n, s.hi), s.lo);
+  return __fadd_rn(q, __fdiv_rn(r, n));
+}
+
+// One thread per sorted point writes its leaf's record (and box), then walks
+// up: the last child to arrive at a parent (arrival counter) sums the
+// parent's children in preorder and writes its record (and box).
+// BOX = false: the boxes (and skips) of this tree are already stored; only
+// the sums and source records are recomputed (backward-stage reuse).
+template <bool ADJ, bool BOX>
 __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
-                            const float4* __restrict__ pack, const float4* __restrict__ abpack,
-                            bool write_box) {
+                            const float4* __restrict__ pack, const float4* __restrict__ abpack) {
+  constexpr int NS = ADJ ? 12 : 6;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const bool adj = abpack != nullptr;
   const int o = (int)t.perm[i];
   int x = i + (int)t.offs[i + 1];
+  float2* isum = reinterpret_cast<float2*>(t.isum);
   {
-    if (write_box) {
+    if (BOX) {
       const float4 r = raw[o];
       t.nbox[2 * x] = make_float4(r.x, r.y, r.z, __int_as_float(x + 1));
       t.nbox[2 * x + 1] = make_float4(r.x, r.y, r.z, __int_as_float(1));
@@ -538,7 +580,7 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     pack_read(pack, o, a, b);
     t.nrec[4 * x] = make_float4(a[0], a[1], a[2], 0.f);
     t.nrec[4 * x + 1] = make_float4(b[0], b[1], b[2], 0.f);
-    if (adj) {
+    if (ADJ) {
       pack_read(abpack, o, a, b);
       t.nrec[4 * x + 2] = make_float4(a[0], a[1], a[2], 0.f);
       t.nrec[4 * x + 3] = make_float4(b[0], b[1], b[2], 0.f);
@@ -554,48 +596,69 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     if (old + nx != sc.y) break;
     __threadfence();
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double S[12];
-    for (int k = 0; k < 12; k++) S[k] = 0.0;
+    Pair S[NS];
+#pragma unroll
+    for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
     int c = par + 1;
     while (c < sc.x) {
       const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
       const int cskip = __float_as_int(bl.w);
-      lo[0] = fminf(lo[0], bl.x);
-      lo[1] = fminf(lo[1], bl.y);
-      lo[2] = fminf(lo[2], bl.z);
-      hi[0] = fmaxf(hi[0], bh.x);
-      hi[1] = fmaxf(hi[1], bh.y);
-      hi[2] = fmaxf(hi[2], bh.z);
+      if (BOX) {
+        lo[0] = fminf(lo[0], bl.x);
+        lo[1] = fminf(lo[1], bl.y);
+        lo[2] = fminf(lo[2], bl.z);
+        hi[0] = fmaxf(hi[0], bh.x);
+        hi[1] = fmaxf(hi[1], bh.y);
+        hi[2] = fmaxf(hi[2], bh.z);
+      }
       if (cskip == c + 1) {
-        const float4 r0 = __ldcg(&t.nrec[4 * c]), r1 = __ldcg(&t.nrec[4 * c + 1]);
-        S[0] += r0.x, S[1] += r0.y, S[2] += r0.z;
-        S[3] += r1.x, S[4] += r1.y, S[5] += r1.z;
-        if (adj) {
-          const float4 r2 = __ldcg(&t.nrec[4 * c + 2]), r3 = __ldcg(&t.nrec[4 * c + 3]);
-          S[6] += r2.x, S[7] += r2.y, S[8] += r2.z;
-          S[9] += r3.x, S[10] += r3.y, S[11] += r3.z;
+        float4 r[4];
+#pragma unroll
+        for (int q = 0; q < NS / 3; q++) r[q] = __ldcg(&t.nrec[4 * c + q]);
+#pragma unroll
+        for (int q = 0; q < NS / 3; q++) {
+          pair_add(S[3 * q], r[q].x);
+          pair_add(S[3 * q + 1], r[q].y);
+          pair_add(S[3 * q + 2], r[q].z);
         }
       } else {
-        const int ns = adj ? 12 : 6;
-        for (int k = 0; k < ns; k++) S[k] += __ldcg(&t.isum[12 * (size_t)c + k]);
+        float2 v[NS];
+#pragma unroll
+        for (int k = 0; k < NS; k++) v[k] = __ldcg(&isum[12 * (size_t)c + k]);
+#pragma unroll
+        for (int k = 0; k < NS; k++) pair_add(S[k], v[k]);
       }
       c = cskip;
     }
-    const double n = (double)sc.y;
-    for (int k = 0; k < 12; k++) t.isum[12 * (size_t)par + k] = S[k];
-    t.nrec[4 * par] = make_float4((float)(S[0] / n), (float)(S[1] / n), (float)(S[2] / n), 0.f);
-    t.nrec[4 * par + 1] = make_float4((float)S[3], (float)S[4], (float)S[5], 0.f);
-    if (adj) {
-      t.nrec[4 * par + 2] = make_float4((float)S[6], (float)S[7], (float)S[8], 0.f);
+    const int n = sc.y;
+#pragma unroll
+    for (int k = 0; k < NS; k++) isum[12 * (size_t)par + k] = pair_store(S[k]);
+    t.nrec[4 * par] = make_float4(pair_mean(S[0], n), pair_mean(S[1], n), pair_mean(S[2], n), 0.f);
+    t.nrec[4 * par + 1] = make_float4(pair_value(S[3]), pair_value(S[4]), pair_value(S[5]), 0.f);
+    if (ADJ) {
+      t.nrec[4 * par + 2] =
+          make_float4(pair_value(S[6]), pair_value(S[7]), pair_value(S[8]), 0.f);
       t.nrec[4 * par + 3] =
-          make_float4((float)(S[9] / n), (float)(S[10] / n), (float)(S[11] / n), 0.f);
+          make_float4(pair_mean(S[9], n), pair_mean(S[10], n), pair_mean(S[11], n), 0.f);
     }
-    if (write_box) {
+    if (BOX) {
       t.nbox[2 * par] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
       t.nbox[2 * par + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(sc.y));
     }
     x = par;
     nx = sc.y;
+  }
+}
+
+void launch_aggregate(const TreeArrays& t, int N, const float4* raw, const float4* pack,
+                      const float4* abpack, bool box, cudaStream_t st) {
+  const unsigned nb = nblocks(N, 256);
+  if (abpack) {
+    if (box) k_aggregate<true, true><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
+    else k_aggregate<true, false><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
+  } else {
+    if (box) k_aggregate<false, true><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
+    else k_aggregate<false, false><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
   }
 }
 
@@ -744,7 +807,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
   TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.offs, t.own_a, t.own_b,
                                                  t.nsc, t.ninfo, t.nparent, t.acnt);
-  k_aggregate<<<nblocks(N, 256), 256, 0, st>>>(t, N, raw, pack, abpack, true);
+  launch_aggregate(t, N, raw, pack, abpack, true, st);
   note_launches(launches + 3 + 2);
   return cudaGetLastError();
 }
@@ -890,7 +953,7 @@ gs_status bh_aggregate(TreeWork& w, const BHStep& b, const float4* abpack, bool 
   if ((err = cudaMemsetAsync(t.acnt, 0, sizeof(int32_t) * (2 * (size_t)b.N + 2), st)) !=
       cudaSuccess)
     return cuda_err(err);
-  k_aggregate<<<nblocks(b.N, 256), 256, 0, st>>>(t, (int)b.N, b.raw, b.pack, abpack, false);
+  launch_aggregate(t, (int)b.N, b.raw, b.pack, abpack, false, st);
   note_launches(1);
   err = cudaGetLastError();
   return err == cudaSuccess ? GS_OK : cuda_err(err);

@@ -46,7 +46,7 @@ struct TreeArrays {
                     // leaf-size variant's walk reads it, also when re-walking a kept tree)
   int32_t* nparent; // preorder id of the parent, -1 for the root
   int32_t* acnt;    // arrival counters of the bottom-up pass
-  double* isum;     // 12 per node: sums of xs, p, a, b over members
+  double* isum;     // 12 per node: sums of xs, p, a, b over members (FP32 pairs)
   int64_t* counts;  // {point interactions, node interactions}
 };
 
