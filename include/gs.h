@@ -257,11 +257,15 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
 
 /* Tuning options of a context:
  *   "bh_list_cap": interaction-list storage of the Barnes-Hut walk, in
- *   entries per list on average (four lists per 32 points, one pool per
- *   kept step); 0 = default (a budget of up to 24 GB, at most a quarter of
- *   the free memory, shared by the kept steps).  Slices whose lists do not
- *   fit are evaluated by a slower fused walk-and-evaluate pass that gives
- *   bit-identical results.
+ *   entries per walk list on average (up to eight walk lists per 32 points,
+ *   one pool per kept step); 0 = default (a budget of up to 24 GB, at most a
+ *   quarter of the free memory, shared by the kept steps).  Slices whose
+ *   lists do not fit are evaluated by a slower fused walk-and-evaluate pass
+ *   that gives bit-identical results.
+ *   "bh_walk_split": walk lists per slice of the Barnes-Hut walk (each group
+ *   of 32 points has four slices): 1 or 2, or 0 (default) = 2 for trees of
+ *   fewer than 48 x (SM count) groups, else 1.  Splitting spreads a small
+ *   tree's walk over more warps; results are bit-identical either way.
  *   "graphs": 1 (default) = gs_shoot, gs_shoot_grad, gs_shoot_batched and
  *   gs_descend_batched capture their step loop (every launch between the
  *   input staging and the result copies) into a CUDA graph the first time

@@ -181,6 +181,7 @@ struct Key {
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
+    add(c->tree.wsplit_req);
   }
 };
 
@@ -1100,6 +1101,12 @@ gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
     if (value < 0 || value > (int64_t(1) << 24))
       return fail(c, GS_ERR_INVALID_ARG, "bh_list_cap must be in [0, 2^24]");
     c->tree.lcap_req = (int)value;
+    return GS_OK;
+  }
+  if (strcmp(name, "bh_walk_split") == 0) {
+    if (value != 0 && value != 1 && value != 2)
+      return fail(c, GS_ERR_INVALID_ARG, "bh_walk_split must be 0, 1 or 2");
+    c->tree.wsplit_req = (int)value;
     return GS_OK;
   }
   if (strcmp(name, "graphs") == 0) {

@@ -26,21 +26,25 @@
 // is the paper's rule.
 //
 // Two phases:
-//   walk     -- decisions only, few registers.  The node range is cut in two
-//               slices at the group's middle point; the second slice starts
-//               by testing the ancestors of its first node, which gives every
-//               lane the state it would have there.  Each slice emits an
-//               ordered list of (node, lane mask) entries; runs of
-//               consecutive leaves are appended in one step (a lane changes
-//               activity only at its resume point, so a run is cut there).
-//   evaluate -- one warp per list streams its entries, stages the source
-//               records in shared memory and evaluates two sources per f32x2
-//               instruction (a far node acts as one source at its centroid
-//               with momentum P, derivative A and momentum derivative B/n).
-// A slice whose list outgrows its capacity is walked again by a fused
-// walk+evaluate kernel that batches entries exactly as the list evaluation
-// does, so results do not depend on the capacity.  Partial sums are combined
-// in a fixed order: results are deterministic.
+//   walk     -- decisions only, few registers.  A group's node range is cut
+//               into BH_SLICES slices around the group's own leaves, and each
+//               slice is walked by one or two warps (walk lists); a walk that
+//               starts inside the range first tests the ancestors of its
+//               first node, which gives every lane the state it would have
+//               there.  Each walk list is an ordered list of (node, lane mask)
+//               entries; runs of consecutive leaves are appended in one step
+//               (a lane changes activity only at its resume point, so a run is
+//               cut there).
+//   evaluate -- one warp per slice streams the entries of the slice's walk
+//               lists in batches of BH_CHUNK, stages the source records in
+//               shared memory and evaluates two sources per f32x2 instruction
+//               (a far node acts as one source at its centroid with momentum
+//               P, derivative A and momentum derivative B/n).
+// A slice one of whose walk lists outgrew its capacity is walked again by a
+// fused walk+evaluate kernel that batches entries exactly as the list
+// evaluation does, so results do not depend on the capacity, nor on how
+// many walk lists a slice was split into.  Partial sums are combined in a
+// fixed order: results are deterministic.
 #include <climits>
 
 #include "kernels.h"
@@ -119,35 +123,41 @@ __device__ __forceinline__ bool within(float ax, float ay, float az, float bx, f
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <= thr;
 }
 
-// Slices of the group's node range [nb, ne): with K = BH_SLICES, h = K/2 and
-// L the leaf of the group's middle point, the cuts are L - D 2^(h-1-k) for
-// k = 1 .. h-1, L, and L + D 2^(k-h-1) for k = h+1 .. K-1 (clamped to the
-// range), D = clamp((ne - nb) / 32, 256, 4096) >> GS_BH_DSHIFT; four slices:
-// [nb, L-D), [L-D, L), [L, L+D), [L+D, ne).  Any cut points give the same
-// interactions; these spread a group's work over K warps, narrow slices near
-// the group where the walk opens most nodes.  The cuts depend only on the
-// current tree, so results are reproducible.
-__device__ __forceinline__ int slice_start(const TreeArrays& t, const GroupInfo& gi, int k) {
-  constexpr int h = BH_SLICES / 2;
-  if (k == 0) return gi.nb;
-  const int mid = gi.mid;
-  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096) >> GS_BH_DSHIFT;
+// Cut k (0 <= k <= wk) of the group's node range [nb, ne) into wk = 4 or 8
+// walk slices: nb, then L - D 2^(h-1-k) for k = 1 .. h-1, L, and
+// L + D 2^(k-h-1) for k = h+1 .. wk-1 (clamped to the range), then ne, with
+// h = wk/2, L the leaf of the group's middle point and
+// D = clamp((ne - nb) / 32, 256, 4096) * 8 / wk.  For wk = 8 the cuts are
+// L -/+ D0, 2 D0, 4 D0; for wk = 4 they are L -/+ 2 D0: the even cuts of the
+// eight, so the evaluation's four slices [cut 0, cut 1) ... are the same
+// node ranges either way.  Any cut points give the same interactions; these
+// spread a group's work over several warps, narrow slices near the group
+// where the walk opens most nodes.  The cuts depend only on the current
+// tree, so results are reproducible.
+__device__ __forceinline__ int walk_cut(const GroupInfo& gi, int k, int wk) {
+  if (k <= 0) return gi.nb;
+  if (k >= wk) return gi.ne;
+  const int h = wk >> 1, mid = gi.mid;
+  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096) * (8 / wk);
   if (k < h) return max(gi.nb, mid - (D << (h - 1 - k)));
   if (k == h) return mid;
   return min(gi.ne, mid + (D << (k - h - 1)));
 }
 
-// List evaluated by warp `wl` of a launch over all (group, slice) lists:
-// the warps of one block take the same slice of consecutive groups (lists
-// of similar length), the last slices -- on average the longest -- first.
-// Measured faster than one group's slices per block for the evaluations;
-// the walk keeps one group per block.
+// Slice evaluated by warp `wl` of a launch over all G * BH_SLICES slices
+// when no longest-first order is given: the warps of one block take the same
+// slice of consecutive groups (lists of similar length), the last slices --
+// on average the longest -- first.
 __device__ __forceinline__ int list_of_warp(int wl, int G) {
   return (wl % G) * BH_SLICES + (BH_SLICES - 1 - wl / G);
 }
 
-__device__ __forceinline__ int slice_end(const TreeArrays& t, const GroupInfo& gi, int k) {
-  return k == BH_SLICES - 1 ? gi.ne : slice_start(t, gi, k + 1);
+// True if a walk list of slice e (walk lists e*wsplit .. +wsplit-1, walk
+// lists numbered g*wk + k) ran out of pool: the fallback evaluates it.
+__device__ __forceinline__ bool slice_overflowed(const BHLists& L, int e, int wsplit) {
+  bool o = false;
+  for (int j = 0; j < wsplit; j++) o = o || L.ovf_x[e * wsplit + j] >= 0;
+  return o;
 }
 
 // Resume point of this lane at node s: test the ancestors of s from the root
@@ -469,16 +479,17 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   __shared__ float4 s_box[TR_WARPS][32][2];
   __shared__ int2 s_ent[TR_WARPS][BH_CHUNK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nl = wg.G * BH_SLICES, wl = blockIdx.x * TR_WARPS + w;
+  const int wk = BH_SLICES * wg.wsplit;
+  const int nl = wg.G * wk, wl = blockIdx.x * TR_WARPS + w;
   if (wl >= nl) return;
   const int l = (word && *L.worder_n == nl) ? word[wl] : wl;
-  const int g = l / BH_SLICES, k = l % BH_SLICES;
+  const int g = l / wk, k = l % wk;
   const GroupInfo gi = target_group(t, N, wg, g);
   const bool valid = lane < gi.count;
   const int ti = gi.first + (valid ? lane : 0);
   const float4 rr = wg.xperm ? wg.xraw[wg.xperm[ti]] : raw[(int)t.perm[ti]];
-  int x = slice_start(t, gi, k);
-  const int end = slice_end(t, gi, k);
+  int x = walk_cut(gi, k, wk);
+  const int end = walk_cut(gi, k + 1, wk);
   int resume = valid ? 0 : INT_MAX;
   // (an empty slice may start at the node count: no node to test there)
   if (k > 0 && valid && x < end)
@@ -501,7 +512,9 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 }
 
 // ------------------------------------------------------------------ evaluate
-// One warp per list: partial sums of its entries, part[(l*NC + c)*32 + lane].
+// One warp per slice: partial sums of its entries, part[(e*NC + c)*32 + lane].
+// The entries of the slice's walk lists are read as one sequence, BH_CHUNK
+// at a time, so the batches (and the sums) are those of an unsplit walk.
 // The adjoint variant is held to 128 registers (4 blocks per SM, a few
 // spilled values): measured faster than 3 blocks at 168 registers.
 template <bool ADJ, bool TRUNC>
@@ -516,31 +529,49 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wl = blockIdx.x * TR_WARPS + w;
   if (wl >= wg.G * BH_SLICES) return;
-  const int l = order ? order[wl] : list_of_warp(wl, wg.G);
-  if (L.ovf_x[l] >= 0) return;  // evaluated whole by the fallback
-  const Own me = load_own(t, wg, target_group(t, N, wg, l / BH_SLICES), lane, ADJ);
+  const int e = order ? order[wl] : list_of_warp(wl, wg.G);
+  const int ws = wg.wsplit, l0 = e * ws;
+  if (slice_overflowed(L, e, ws)) return;  // evaluated whole by the fallback
+  const Own me = load_own(t, wg, target_group(t, N, wg, e / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
   A.zero();
   int npair = 0;
-  const int n = L.len[l];
-  int chunk = L.head[l];
+  int n = 0;
+  for (int j = 0; j < ws; j++) n += L.len[l0 + j];
+  // reader state: walk list j, its current chunk, offset there, entries left
+  int j = 0, chunk = L.head[l0], off = 0, left = L.len[l0];
   for (int c0 = 0; c0 < n; c0 += BH_CHUNK) {
     const int cn = min(BH_CHUNK, n - c0);
-    const int2* src = L.ent + (size_t)chunk * BH_CHUNK;
     __syncwarp();
-    for (int e = lane; e < cn; e += 32) {
-      const int2 v = src[e];
-      s_node[w][e] = v.x;
-      s_mask[w][e] = (unsigned)v.y;
+    for (int got = 0; got < cn;) {
+      while (left == 0) {  // next walk list of the slice (entries remain)
+        j++;
+        chunk = L.head[l0 + j];
+        off = 0;
+        left = L.len[l0 + j];
+      }
+      const int take = min(min(BH_CHUNK - off, left), cn - got);
+      const int2* src = L.ent + (size_t)chunk * BH_CHUNK + off;
+      for (int q = lane; q < take; q += 32) {
+        const int2 v = src[q];
+        s_node[w][got + q] = v.x;
+        s_mask[w][got + q] = (unsigned)v.y;
+      }
+      got += take;
+      off += take;
+      left -= take;
+      if (off == BH_CHUNK && left > 0) {
+        chunk = L.next[chunk];
+        off = 0;
+      }
     }
-    if (c0 + BH_CHUNK < n) chunk = L.next[chunk];
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
     __syncwarp();
     eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, ak, npair);
   }
 #pragma unroll
-  for (int c = 0; c < NC; c++) L.part[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
+  for (int c = 0; c < NC; c++) L.part[((size_t)e * NC + c) * 32 + lane] = A.K[c].out();
   if (TRUNC && counts) {
     const int tot = __reduce_add_sync(FULL, (unsigned)npair);
     if (lane == 0)
@@ -588,8 +619,12 @@ struct EvalSink {
   }
 };
 
-// Evaluates a slice whose list overflowed: walks it again from its start and
-// evaluates in place; partial sums go to L.fb[(l*NC + c)*32 + lane].
+// Evaluates a slice one of whose walk lists overflowed: walks the slice
+// again, its walk slices one after the other with the lanes' state carried
+// over (the same entries as one walk over the slice), and evaluates in
+// place; partial sums go to L.fb[(e*NC + c)*32 + lane].  COUNT: a walk
+// list's interactions are counted here only if that list overflowed (the
+// walk counted the others).
 template <bool ADJ, bool COUNT, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
@@ -602,26 +637,30 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (blockIdx.x * TR_WARPS + w >= wg.G * BH_SLICES) return;
-  const int l = list_of_warp(blockIdx.x * TR_WARPS + w, wg.G);
-  if (L.ovf_x[l] < 0) return;
-  const int g = l / BH_SLICES, k = l % BH_SLICES;
+  const int e = list_of_warp(blockIdx.x * TR_WARPS + w, wg.G);
+  const int ws = wg.wsplit, wk = BH_SLICES * ws;
+  if (!slice_overflowed(L, e, ws)) return;
+  const int g = e / BH_SLICES, k0 = (e % BH_SLICES) * ws;
   const GroupInfo gi = target_group(t, N, wg, g);
   const Own me = load_own(t, wg, gi, lane, ADJ);
   const float4 rr = wg.xperm ? make_float4(me.rx, me.ry, me.rz, 0.f) : raw[me.o];
-  int x = slice_start(t, gi, k);
-  const int end = slice_end(t, gi, k);
+  int x = walk_cut(gi, k0, wk);
   int resume = me.valid ? 0 : INT_MAX;
-  if (k > 0 && me.valid && x < end)
+  if (k0 > 0 && me.valid && x < walk_cut(gi, k0 + ws, wk))
     resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   Acc<ADJ> A;
   A.zero();
   EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, ak, 0};
   long long np = 0, nn = 0;
-  walk_nodes<COUNT, true>(t, s_box[w], x, end, rr, thr, wg.leaf, TRUNC, wg.crit, resume, sink,
-                          lane, np, nn);
+  for (int j = 0; j < ws; j++) {
+    long long pj = 0, qj = 0;
+    walk_nodes<COUNT, true>(t, s_box[w], x, walk_cut(gi, k0 + j + 1, wk), rr, thr, wg.leaf,
+                            TRUNC, wg.crit, resume, sink, lane, pj, qj);
+    if (L.ovf_x[e * ws + j] >= 0) np += pj, nn += qj;
+  }
   if (sink.cnt) sink.flush();
 #pragma unroll
-  for (int c = 0; c < NC; c++) L.fb[((size_t)l * NC + c) * 32 + lane] = A.K[c].out();
+  for (int c = 0; c < NC; c++) L.fb[((size_t)e * NC + c) * 32 + lane] = A.K[c].out();
   if (COUNT && TRUNC) {  // pairs kept by the truncation test
     const int tot = __reduce_add_sync(FULL, (unsigned)sink.npair);
     if (lane == 0)
@@ -650,7 +689,7 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
   for (int c = 0; c < NC; c++) acc[c] = 0.0;
   for (int k = 0; k < BH_SLICES; k++) {
     const int l = g * BH_SLICES + k;
-    const float2* src = L.ovf_x[l] >= 0 ? L.fb : L.part;
+    const float2* src = slice_overflowed(L, l, wg.wsplit) ? L.fb : L.part;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
       const float2 v = src[((size_t)l * NC + c) * 32 + lane];
@@ -671,27 +710,25 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
   }
 }
 
-// Longest-first order of n lists by their lengths: a counting sort on
-// kOrderBuckets length classes (len * (kOrderBuckets - 1) / max len), one
-// block.  Lists of one class land in any order; every list appears once.
-// Writes order[] and worder[], and *worder_n = n.
+// Longest-first orders by length, each a counting sort on kOrderBuckets
+// length classes (len * (kOrderBuckets - 1) / max len) in one block; items of
+// one class land in any order, every item appears once.  First the nw walk
+// lists (worder, and *worder_n = nw), then the nw / ws slices, a slice's
+// length being that of its ws walk lists together (order).
 constexpr int kOrderThreads = 1024, kOrderBuckets = 512;
-__global__ void __launch_bounds__(kOrderThreads)
-    k_list_order(const int* __restrict__ len, int n, int* order, int* worder, int* worder_n) {
-  __shared__ int s_cnt[kOrderBuckets];
-  __shared__ int s_max[kOrderThreads / 32];
+template <class Len>
+__device__ void order_by_length(Len len, int n, int* out, int* out2, int* s_cnt, int* s_max) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int mx = 0;
-  for (int l = tid; l < n; l += kOrderThreads) mx = max(mx, len[l]);
+  for (int l = tid; l < n; l += kOrderThreads) mx = max(mx, len(l));
   mx = __reduce_max_sync(FULL, (unsigned)mx);
   if (lane == 0) s_max[w] = mx;
   for (int b = tid; b < kOrderBuckets; b += kOrderThreads) s_cnt[b] = 0;
   __syncthreads();
   mx = 1;
   for (int k = 0; k < kOrderThreads / 32; k++) mx = max(mx, s_max[k]);
-  // class 0 = longest
-  auto cls = [&](int l) {
-    const int v = min(max(len[l], 0), mx);
+  auto cls = [&](int l) {  // class 0 = longest
+    const int v = min(max(len(l), 0), mx);
     return kOrderBuckets - 1 - (int)((long long)v * (kOrderBuckets - 1) / mx);
   };
   for (int l = tid; l < n; l += kOrderThreads) atomicAdd(&s_cnt[cls(l)], 1);
@@ -715,24 +752,36 @@ __global__ void __launch_bounds__(kOrderThreads)
   __syncthreads();
   for (int l = tid; l < n; l += kOrderThreads) {
     const int at = atomicAdd(&s_cnt[cls(l)], 1);
-    order[at] = l;
-    worder[at] = l;
+    out[at] = l;
+    if (out2) out2[at] = l;
   }
-  if (tid == 0) *worder_n = n;
+  __syncthreads();
 }
 
-inline unsigned list_blocks(int G) {
-  const int lists = G * BH_SLICES;
-  return (unsigned)((lists + TR_WARPS - 1) / TR_WARPS);
+__global__ void __launch_bounds__(kOrderThreads)
+    k_list_order(const int* __restrict__ len, int nw, int ws, int* order, int* worder,
+                 int* worder_n) {
+  __shared__ int s_cnt[kOrderBuckets];
+  __shared__ int s_max[kOrderThreads / 32];
+  order_by_length([&](int l) { return len[l]; }, nw, worder, nullptr, s_cnt, s_max);
+  auto slice_len = [&](int e) {
+    int v = 0;
+    for (int j = 0; j < ws; j++) v += len[e * ws + j];
+    return v;
+  };
+  order_by_length(slice_len, nw / ws, order, nullptr, s_cnt, s_max);
+  if (threadIdx.x == 0) *worder_n = nw;
 }
+
+inline unsigned warp_blocks(int64_t warps) { return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS); }
 
 }  // namespace
 
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            bool scheduled, cudaStream_t st) {
-  const unsigned nb = list_blocks(wg.G);
-  const int nl = wg.G * BH_SLICES;
+  const int nl = wg.G * BH_SLICES * wg.wsplit;
+  const unsigned nb = warp_blocks(nl);
   const bool var = wg.leaf > 1 || wg.trunc || wg.crit != 0;  // the paper's rule: lean walk
   // the previous walk's order (taken if it covers as many lists)
   const int* word = scheduled ? L.worder : nullptr;
@@ -745,7 +794,8 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
   else
     k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   if (scheduled)
-    k_list_order<<<1, kOrderThreads, 0, st>>>(L.len, nl, L.order, L.worder, L.worder_n);
+    k_list_order<<<1, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
+                                              L.worder_n);
   note_launches(scheduled ? 2 : 1);
   return cudaGetLastError();
 }
@@ -755,7 +805,7 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
                         const BHLists& L, const WalkGroups& wg, const FwdEpi& fe,
                         const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
                         const int* order, cudaStream_t st) {
-  const unsigned nb = list_blocks(wg.G);
+  const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
   const AdjConsts ak = adj_consts(ae);
   if (counts)

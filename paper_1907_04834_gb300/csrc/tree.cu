@@ -665,7 +665,8 @@ void launch_aggregate(const TreeArrays& t, int N, const float4* raw, const float
 // ---------------------------------------------------------------- layout
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-size_t n_lists(int64_t groups) { return (size_t)groups * BH_SLICES; }
+size_t n_lists(int64_t groups) { return (size_t)groups * BH_SLICES; }       // slices
+size_t n_walk_lists(int64_t groups) { return (size_t)groups * BH_MAX_WK; }  // at most
 
 // Shared scratch of one workspace (capacity n points, 2n + 2 nodes, `groups`
 // walk groups); with mem == NULL only the size is computed.
@@ -688,7 +689,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_nrec = take(64 * M), o_acnt = take(4 * M),
                o_isum = take(96 * M), o_cnt = take(16),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
-               o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * nl),
+               o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
                o_wordn = take(4);
   if (mem) {
     char* b = static_cast<char*>(mem);
@@ -720,7 +721,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
 // One step's tree and interaction lists (kept for the backward stage).
 size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArrays* t,
                   BHLists* L) {
-  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(groups);
+  const size_t N1 = (size_t)n + 1, M = 2 * (size_t)n + 2, nl = n_lists(groups),
+               nw = n_walk_lists(groups);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -730,8 +732,8 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
   const size_t o_perm = take(4 * N1), o_offs = take(4 * (N1 + 1)), o_npar = take(4 * M),
                o_nsc = take(8 * M), o_ninfo = take(8 * M), o_nbox = take(32 * M),
                o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
-               o_next = take(4 * (size_t)chunks), o_head = take(4 * nl), o_len = take(4 * nl),
-               o_ovx = take(4 * nl), o_used = take(4), o_order = take(4 * nl);
+               o_next = take(4 * (size_t)chunks), o_head = take(4 * nw), o_len = take(4 * nw),
+               o_ovx = take(4 * nw), o_used = take(4), o_order = take(4 * nl);
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->perm = (uint32_t*)(b + o_perm);
@@ -829,8 +831,23 @@ void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
              w.lcap, t, L);
 }
 
+// Walk lists per slice for G groups: the request, else two when one list
+// per slice would give fewer than about four waves of walk warps (48
+// resident per SM), so that a small tree's walk still fills the GPU.  The
+// sums do not depend on it.
+int walk_split(const TreeWork& w, int64_t G) {
+  if (w.wsplit_req) return w.wsplit_req;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return G * BH_SLICES < 4 * 48 * (int64_t)sms ? 2 : 1;
+}
+
 // Walk groups of a step: the forest's table, or 32-point groups of one set.
-WalkGroups walk_groups(const BHStep& b) {
+WalkGroups walk_groups(const TreeWork& w, const BHStep& b) {
   WalkGroups g{};
   g.leaf = b.leaf;
   g.trunc = b.trunc;
@@ -844,6 +861,7 @@ WalkGroups walk_groups(const BHStep& b) {
   } else {
     g.G = (int)((b.N + 31) / 32);
   }
+  g.wsplit = walk_split(w, g.G);
   return g;
 }
 }  // namespace
@@ -857,7 +875,7 @@ cudaError_t tree_setup() { return cudaSuccess; }
 // The pool size only decides how many slices take the slower re-walk path,
 // never the results.
 static int64_t pool_chunks(const TreeWork& w, int64_t N, int64_t groups, int slots) {
-  const int64_t nl = (int64_t)n_lists(groups);
+  const int64_t nl = (int64_t)n_walk_lists(groups);
   if (w.lcap_req > 0) return std::max<int64_t>(1, nl * w.lcap_req / BH_CHUNK);
   size_t budget = kListBudget;
   size_t fr = 0, tot = 0;
@@ -965,8 +983,8 @@ gs_status bh_walk(TreeWork& w, const BHStep& b, bool counts, cudaStream_t st) {
   views(w, b.slot, &t, &L);
   cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
   if (err == cudaSuccess)
-    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), counts ? t.counts : nullptr,
-                         true, st);
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, walk_groups(w, b),
+                         counts ? t.counts : nullptr, true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -975,7 +993,7 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), false, e,
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(w, b), false, e,
                                    AdjEpi{}, TracerEpi{}, counts ? t.counts : nullptr, true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
@@ -985,7 +1003,7 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(b), true, FwdEpi{},
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, walk_groups(w, b), true, FwdEpi{},
                                    e, TracerEpi{}, counts ? t.counts : nullptr, true, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
@@ -1132,10 +1150,11 @@ gs_status tracer_order(TreeWork& w, const BHStep& b, const float4* xraw, int64_t
 }
 
 namespace {
-WalkGroups target_groups(const BHStep& b, const BHTargets& x) {
-  WalkGroups g = walk_groups(b);
+WalkGroups target_groups(const TreeWork& w, const BHStep& b, const BHTargets& x) {
+  WalkGroups g = walk_groups(w, b);
   g.groups = nullptr;
   g.G = x.G;
+  g.wsplit = walk_split(w, g.G);
   g.xraw = x.xraw;
   g.xrec = x.xrec;
   g.xperm = x.xperm;
@@ -1151,7 +1170,8 @@ gs_status bh_walk_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cuda
   views(w, b.slot, &t, &L);
   cudaError_t err = cudaMemsetAsync(L.used, 0, sizeof(int), st);
   if (err == cudaSuccess)
-    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), nullptr, false, st);
+    err = launch_bh_walk(t, (int)b.N, b.raw, b.thr, L, target_groups(w, b, x), nullptr, false,
+                         st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
@@ -1160,7 +1180,7 @@ gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cons
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, target_groups(b, x), false,
+  cudaError_t err = launch_bh_eval(t, (int)b.N, b.raw, b.thr, L, target_groups(w, b, x), false,
                                    FwdEpi{}, AdjEpi{}, e, nullptr, false, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }

@@ -24,6 +24,7 @@ struct TreeWork {
   int64_t lcap = 0;      // chunks in each slot's interaction-list pool
   int lcap_req = 0;      // requested entries per list (0 = budget-based pool)
   int lcap_from_req = 0; // the request the current allocation was made for
+  int wsplit_req = 0;    // walk lists per slice: 0 = by tree size, else 1 or 2
 };
 
 // Many independent point sets ("subjects") in one forest.  Subject s owns

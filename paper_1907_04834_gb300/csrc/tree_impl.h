@@ -50,34 +50,33 @@ struct TreeArrays {
   int64_t* counts;  // {point interactions, node interactions}
 };
 
-// Interaction lists of one traversal: BH_SLICES per group of 32 points.
-// Entries live in a pool of chunks of BH_CHUNK entries; a list is the chain
-// of chunks starting at head[l] (next[c] links them in order).
-#ifndef GS_BH_SLICES
-#define GS_BH_SLICES 4
-#endif
-#ifndef GS_BH_DSHIFT
-#define GS_BH_DSHIFT 0
-#endif
-constexpr int BH_SLICES = GS_BH_SLICES;  // even
-static_assert(BH_SLICES >= 2 && BH_SLICES % 2 == 0, "slices come in pairs around the group");
+// Interaction lists of one traversal.  A group of 32 points has BH_SLICES
+// slices (node ranges) whose sums are kept apart and combined in a fixed
+// order; the walk may split each slice into `wsplit` walk lists (walk slices
+// per group wk = BH_SLICES * wsplit) to spread a small tree's walk over more
+// warps.  The evaluation reads a slice's walk lists as one entry sequence in
+// batches of BH_CHUNK, so the sums do not depend on the split.  Entries live
+// in a pool of chunks of BH_CHUNK entries; a walk list is the chain of chunks
+// starting at head[l] (next[c] links them in order).
+constexpr int BH_SLICES = 4;
+constexpr int BH_MAX_WK = 8;  // walk lists per group at most
 constexpr int BH_CHUNK = 64;
 struct BHLists {
   int2* ent;      // pool: n_chunks x BH_CHUNK entries {node, lane mask}
   int* next;      // per chunk: next chunk of the same list
-  int* head;      // per list: first chunk
-  int* len;       // per list: entries recorded
-  int* ovf_x;     // per list: >= 0 if the pool ran out (slice re-walked)
+  int* head;      // per walk list: first chunk
+  int* len;       // per walk list: entries recorded
+  int* ovf_x;     // per walk list: >= 0 if the pool ran out (its slice is re-walked)
   int* used;      // chunks taken from the pool (reset before each walk)
   int n_chunks;   // pool size
-  float2* part;   // per list x 9 x 32: partial sums of the list (at most 9 components)
-  float2* fb;     // per list x 9 x 32: partial sums of a re-walked slice
-  // Scheduling (never the results): order[k] is the list the k-th warp of an
-  // evaluation takes, longest lists first; worder is the order of the last
-  // walk's lists, which the next walk of as many lists (*worder_n) takes as
-  // its estimate of their cost.
-  int* order;     // per list (this step)
-  int* worder;    // per list (shared by the steps)
+  float2* part;   // per slice x 9 x 32: partial sums of the slice (at most 9 components)
+  float2* fb;     // per slice x 9 x 32: partial sums of a re-walked slice
+  // Scheduling (never the results): order[k] is the slice the k-th warp of an
+  // evaluation takes, longest first; worder is the longest-first order of the
+  // last walk's lists, which the next walk of as many lists (*worder_n) takes
+  // as its estimate of their cost.
+  int* order;     // per slice (this step)
+  int* worder;    // per walk list (shared by the steps)
   int* worder_n;  // list count of worder; -1 when it holds none
 };
 
@@ -112,8 +111,6 @@ __device__ __forceinline__ GroupInfo group_info(const TreeArrays& t, int N, cons
   return gi;
 }
 
-// FP32 distance-squared from a point to an axis-aligned box, no contraction:
-// dx = max(lo - x, 0, x - hi) per axis, d2 = (dx*dx + dy*dy) + dz*dz.
 // Three-input maximum (sm_100 and later).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
@@ -121,9 +118,10 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return d;
 }
 
-// Per axis max(lo - x, 0, x - hi), then (dx*dx + dy*dy) + dz*dz, every
-// operation rounded to nearest and none contracted; the x and y axes take
-// packed f32x2 subtractions and one packed product (same roundings).
+// FP32 distance-squared from a point to an axis-aligned box: per axis
+// max(lo - x, 0, x - hi), then (dx*dx + dy*dy) + dz*dz, every operation
+// rounded to nearest and none contracted; the x and y axes take packed f32x2
+// subtractions and one packed product (same roundings).
 __device__ __forceinline__ float box_dist2(float x, float y, float z, const float4& lo,
                                            const float4& hi) {
   const f2 p = f2_make(x, y);
@@ -149,6 +147,7 @@ struct WalkGroups {
   int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
   bool trunc;              // pure truncation: far nodes dropped, pairs cut at the threshold
   int crit;                // far test: 0 the paper's distance rule, 1 opening angle
+  int wsplit;              // walk lists per slice: 1 or 2 (a power of two)
   // Outside targets (tracer points walking this tree, forward only); xperm
   // NULL: the targets are the tree's own points.  Tracer groups are 32
   // consecutive tracers in tracer-code order over the whole tree.
