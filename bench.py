@@ -45,7 +45,13 @@ THRESH = 3.0
 # FP32 pipe: 128 lanes per SM per clock (one FADD/FMUL/FFMA lane-op each),
 # 152 SMs, maximum SM clock 2070 MHz.
 ALU_PEAK_OPS = 152 * 128 * 2.07e9
+# Algorithmic FP32 ops per pair: the formulas' counts (forward 16; adjoint
+# 40, the direct evaluation of its four sums).  The adjoint kernels issue 36:
+# with beta stored scaled by 2 ln2 s in the adjoint pack, the sums need no
+# constants (ISSUED_OPS_PER_PAIR, reported beside the roofline).
 OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 40, "bh_fwd": 16, "bh_adj": 40, "bh_walk": 16}
+ISSUED_OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 36, "bh_fwd": 16, "bh_adj": 36,
+                       "bh_walk": 16}
 # algorithmic bytes per point of one tree build (read FP32 positions + pack,
 # sort passes, node records written): see the design notes
 TREE_BYTES_PER_POINT = 250.0
@@ -327,7 +333,10 @@ def run_ours(args):
         units = w.N * w.N if dom.startswith("exact") else bh_inter_step
         alg = OPS_PER_PAIR[dom] * units
         roof = {"bound": "alu", "achieved": alg / per_launch_s / 1e12,
-                "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s"}
+                "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s",
+                "ops_per_pair": OPS_PER_PAIR[dom],
+                "issued_ops_per_pair": ISSUED_OPS_PER_PAIR[dom],
+                "issued_frac": ISSUED_OPS_PER_PAIR[dom] * units / per_launch_s / ALU_PEAK_OPS}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
     roof["launch_ms"] = per_launch_s * 1e3

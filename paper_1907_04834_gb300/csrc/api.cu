@@ -702,6 +702,7 @@ AdjEpi adj_epi(const Solver& S, int next_ab, double h, bool last, double* grad) 
   e.grad = grad;
   e.inv_s2 = 1.0 / (S.sigma * S.sigma);
   e.inv_s = 1.0 / S.s;
+  e.mu = adj_beta_scale(S.s);
   e.h = h;
   e.N = S.N;
   return e;
@@ -1620,7 +1621,8 @@ gs_status gs_autotune(gs_ctx* c, const double* q, const double* p, int64_t N,
     // variables zero (their values do not change the work)
     if (cudaMemsetAsync(c->al.p, 0, (size_t)N * 24, st) != cudaSuccess ||
         cudaMemsetAsync(c->be.p, 0, (size_t)N * 24, st) != cudaSuccess ||
-        launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, S.abpack(0), st) !=
+        launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, adj_beta_scale(S.s),
+                       S.abpack(0), st) !=
             cudaSuccess) {
       rc = cuda_fail(c, cudaGetLastError(), "autotune setup");
       break;
@@ -1714,8 +1716,10 @@ gs_status gs_adj_rhs(gs_ctx* c, const double* q, const double* p, const double* 
   const size_t b3 = (size_t)N * 3 * sizeof(double);
   CK(cudaMemcpyAsync(c->al.p, da, b3, cudaMemcpyDeviceToDevice, st), "copy");
   CK(cudaMemcpyAsync(c->be.p, db, b3, cudaMemcpyDeviceToDevice, st), "copy");
-  // adjoint pack: alpha and beta as FP32 (no recentring/scaling)
-  CK(launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, S.abpack(0), st), "pack");
+  // adjoint pack: alpha and the scaled beta as FP32
+  CK(launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, adj_beta_scale(S.s),
+                    S.abpack(0), st),
+     "pack");
   CK(c->out_a.ensure(b3), "workspace");
   CK(c->out_b.ensure(b3), "workspace");
   AdjEpi e = adj_epi(S, -1, 0.0, false, nullptr);

@@ -276,17 +276,13 @@ __device__ __forceinline__ void tracer_epilogue(int64_t i, const double v[3], co
 // scaled difference d_s, the backward step is alpha += h dA, beta += h dB,
 //   dA = sigma^-2 (-A1 / s + A2 - 2 ln2 A3),   dB = B1 + sigma^-2 B2 / s,
 // A1 = Sum g (a_i.p_j + a_j.p_i) d_s, A2 = Sum c g w, A3 = Sum c g (w.d_s) d_s,
-// B1 = Sum g a_j, B2 = Sum g (w.d_s) p_j.  The pair kernels accumulate the
-// three combinations that dA and dB need:
-//   A13 = Sum (-g (a_i.p_j + a_j.p_i) / s - 2 ln2 c g (w.d_s)) d_s,  A2,
-//   B   = Sum g (a_j + (sigma^-2 / s) (w.d_s) p_j),
-// so dA = sigma^-2 (A13 + A2) and dB = B.
-struct AdjConsts {
-  float c1;  // -1 / s
-  float c3;  // -2 ln 2
-  float kb;  // sigma^-2 / s
-};
-
+// B1 = Sum g a_j, B2 = Sum g (w.d_s) p_j.  The FP32 adjoint pack holds beta
+// scaled by mu = 2 ln2 s (b' = mu b, so w' = mu w).  Because
+// 2 ln2 s^2 = sigma^-2 (s^2 = log2(e) / (2 sigma^2)), the pair kernels then
+// accumulate three sums with no constants,
+//   A13' = Sum (g (a_i.p_j + a_j.p_i) + c g (w'.d_s)) d_s,   A2' = Sum c g w',
+//   B'   = Sum g (a_j + (w'.d_s) p_j),
+// and dA = sigma^-2 (A2' / mu - A13' / s), dB = B'.
 struct AdjEpi {
   double* al;           // N x 3 alpha (updated in place when h != 0)
   double* be;           // N x 3 beta
@@ -297,12 +293,14 @@ struct AdjEpi {
   double* grad;         // N x 3 gradient output
   double inv_s2;        // sigma^-2
   double inv_s;         // 1 / s
+  double mu;            // beta's scale in the adjoint pack
   double h;
   int64_t N;
 };
 
-__host__ __device__ __forceinline__ AdjConsts adj_consts(const AdjEpi& e) {
-  return AdjConsts{(float)(-e.inv_s), -1.3862943611198906f, (float)(e.inv_s2 * e.inv_s)};
+// Beta's scale in the FP32 adjoint pack for coordinate scale s.
+__host__ __device__ __forceinline__ double adj_beta_scale(double s) {
+  return 1.3862943611198906 * s;  // 2 ln 2 s
 }
 
 __device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const double A13[3],
@@ -310,7 +308,7 @@ __device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const do
                                                 const AdjEpi& e) {
   double dA[3], dB[3];
   for (int a = 0; a < 3; a++) {
-    dA[a] = e.inv_s2 * (A13[a] + A2[a]);
+    dA[a] = e.inv_s2 * (A2[a] / e.mu - e.inv_s * A13[a]);
     dB[a] = B[a];
   }
   if (e.dA_out)
@@ -326,8 +324,8 @@ __device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const do
       e.be[3 * i + a] = bn[a];
     }
     if (e.pack_next)
-      pack_write(e.pack_next, ipk, (float)an[0], (float)an[1], (float)an[2], (float)bn[0],
-                 (float)bn[1], (float)bn[2]);
+      pack_write(e.pack_next, ipk, (float)an[0], (float)an[1], (float)an[2],
+                 (float)(e.mu * bn[0]), (float)(e.mu * bn[1]), (float)(e.mu * bn[2]));
     if (e.F0)
       for (int a = 0; a < 3; a++) e.grad[3 * i + a] = bn[a] + e.F0[3 * i + a];
   }

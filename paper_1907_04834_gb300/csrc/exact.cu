@@ -172,16 +172,14 @@ struct VelTarget {
   }
 };
 
-// Adjoint sums of one target over one staged tile (a = alpha^{k+1},
-// b = beta^{k+1}, w = b_i - b_j, d = d_s; the combinations of AdjConsts):
-//   A13 = Sum (c1 g (a_i.p_j + a_j.p_i) + c3 c g (w.d)) d,  A2 = Sum c g w,
-//   B   = Sum g (a_j + kb (w.d) p_j).
+// Adjoint sums of one target over one staged tile (a = alpha^{k+1}, b' the
+// scaled beta^{k+1} of the adjoint pack, w' = b'_i - b'_j, d = d_s):
+//   A13' = Sum (g (a_i.p_j + a_j.p_i) + c g (w'.d)) d,  A2' = Sum c g w',
+//   B'   = Sum g (a_j + (w'.d) p_j).
 struct AdjTarget {
   f2 xi, yi, zi, ui, vi, wi, axi, ayi, azi, bxi, byi, bzi;
-  f2 c1, c3, kb;
   Kahan K[kAdjComps];
-  __device__ __forceinline__ void load(const float4* pk, const float4* ab, int64_t i,
-                                       const AdjConsts& k) {
+  __device__ __forceinline__ void load(const float4* pk, const float4* ab, int64_t i) {
     float qa[3], pa[3], aa[3], ba[3];
     pack_read(pk, i, qa, pa);
     pack_read(ab, i, aa, ba);
@@ -189,7 +187,6 @@ struct AdjTarget {
     ui = f2_dup(pa[0]), vi = f2_dup(pa[1]), wi = f2_dup(pa[2]);
     axi = f2_dup(aa[0]), ayi = f2_dup(aa[1]), azi = f2_dup(aa[2]);
     bxi = f2_dup(ba[0]), byi = f2_dup(ba[1]), bzi = f2_dup(ba[2]);
-    c1 = f2_dup(k.c1), c3 = f2_dup(k.c3), kb = f2_dup(k.kb);
 #pragma unroll
     for (int c = 0; c < kAdjComps; c++) K[c].zero();
   }
@@ -224,14 +221,13 @@ struct AdjTarget {
       a2x = f2_fma(cg, wx, a2x);
       a2y = f2_fma(cg, wy, a2y);
       a2z = f2_fma(cg, wz, a2z);
-      const f2 kap = f2_fma(f2_mul(g, sa), c1, f2_mul(f2_mul(cg, wd), c3));
+      const f2 kap = f2_fma(cg, wd, f2_mul(g, sa));
       ax = f2_fma(kap, dx, ax);
       ay = f2_fma(kap, dy, ay);
       az = f2_fma(kap, dz, az);
-      const f2 t = f2_mul(wd, kb);
-      bx = f2_fma(g, f2_fma(t, q1.y, s0.x), bx);
-      by = f2_fma(g, f2_fma(t, q2.x, s0.y), by);
-      bz = f2_fma(g, f2_fma(t, q2.y, s1v.x), bz);
+      bx = f2_fma(g, f2_fma(wd, q1.y, s0.x), bx);
+      by = f2_fma(g, f2_fma(wd, q2.x, s0.y), by);
+      bz = f2_fma(g, f2_fma(wd, q2.y, s1v.x), bz);
     }
     K[0].add(f2_sum(ax));
     K[1].add(f2_sum(ay));
@@ -317,7 +313,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
   const int64_t i = (int64_t)bi * EX_NT + threadIdx.x;
   const TileRange tr = tile_range(bj, geo.J, geo.n_jtiles);
   AdjTarget tg;
-  tg.load(pk, ab, i, adj_consts(epi));
+  tg.load(pk, ab, i);
   init_barriers(bars);
   const float4* srcs[2] = {pk, ab};
   unsigned done = 0;
@@ -425,7 +421,7 @@ __global__ void __launch_bounds__(EX_NT, 2)
     const float4* sp = pk + (size_t)(pbase / 2) * 3;
     const float4* sa = ab + (size_t)(pbase / 2) * 3;
     AdjTarget tg;
-    tg.load(sp, sa, il, adj_consts(epi));
+    tg.load(sp, sa, il);
     const float4* srcs[2] = {sp, sa};
     if (!stream_tiles<2>(sbuf, bars, srcs, 0, bi.npad[w.x] / EX_TILE, done, status,
                          [&](const float4* st) { tg.tile(st); }))

@@ -106,9 +106,9 @@ cudaError_t launch_pack(const double* q, const double* p, int64_t N, const doubl
 // zero the padding points [N, Npad) of `slots` consecutive packs
 cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, int64_t Npad,
                             cudaStream_t st);
-// adjoint pack of (alpha, beta) as FP32 (no recentring or scaling)
-cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, float4* abpack,
-                           cudaStream_t st);
+// adjoint pack of (alpha, mu beta) as FP32 (mu = adj_beta_scale(s))
+cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, double mu,
+                           float4* abpack, cudaStream_t st);
 // alpha = 2 lambda (q - X), beta = 0, adjoint pack; r2[i] = |q_i - X_i|^2
 cudaError_t launch_adjoint_init(const double* q, const double* X, int64_t N, double lambda,
                                 double* al, double* be, float4* abpack, double* r2,

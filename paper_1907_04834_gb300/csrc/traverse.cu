@@ -201,7 +201,7 @@ struct Acc {
 template <bool ADJ, bool TRUNC>
 __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const unsigned* mask,
                                            int n, int lane, const Own& me, float thr,
-                                           const AdjConsts& ak, int& npair) {
+                                           int& npair) {
   constexpr int NR = ADJ ? 12 : 6;
   auto keep = [&](int e, bool b) {
     if constexpr (TRUNC) {
@@ -245,10 +245,9 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
     A.K[4].add(f2_sum(hy));
     A.K[5].add(f2_sum(hz));
   } else {
-    // the three combined adjoint sums (see AdjConsts): A13, A2, B
+    // the three adjoint sums A13', A2', B' (beta scaled in the records)
     const f2 AX = f2_dup(me.m2.x), AY = f2_dup(me.m2.y), AZ = f2_dup(me.m2.z);
     const f2 BX = f2_dup(me.m3.x), BY = f2_dup(me.m3.y), BZ = f2_dup(me.m3.z);
-    const f2 C1 = f2_dup(ak.c1), C3 = f2_dup(ak.c3), KB = f2_dup(ak.kb);
     f2 ax = 0, ay = 0, az = 0, a2x = 0, a2y = 0, a2z = 0, bx = 0, by = 0, bz = 0;
     for (int e = 0; e < n; e += 2) {
       const bool b0 = keep(e, (mask[e] >> lane) & 1u), b1 = keep(e + 1, (mask[e + 1] >> lane) & 1u);
@@ -278,14 +277,13 @@ __device__ __forceinline__ void eval_batch(Acc<ADJ>& A, const float* soa, const 
       a2x = f2_fma(cg, wx, a2x);
       a2y = f2_fma(cg, wy, a2y);
       a2z = f2_fma(cg, wz, a2z);
-      const f2 kap = f2_fma(f2_mul(g, sa), C1, f2_mul(f2_mul(cg, wd), C3));
+      const f2 kap = f2_fma(cg, wd, f2_mul(g, sa));
       ax = f2_fma(kap, dx, ax);
       ay = f2_fma(kap, dy, ay);
       az = f2_fma(kap, dz, az);
-      const f2 t = f2_mul(wd, KB);
-      bx = f2_fma(g, f2_fma(t, PX, QX), bx);
-      by = f2_fma(g, f2_fma(t, PY, QY), by);
-      bz = f2_fma(g, f2_fma(t, PZ, QZ), bz);
+      bx = f2_fma(g, f2_fma(wd, PX, QX), bx);
+      by = f2_fma(g, f2_fma(wd, PY, QY), by);
+      bz = f2_fma(g, f2_fma(wd, PZ, QZ), bz);
     }
     A.K[0].add(f2_sum(ax));
     A.K[1].add(f2_sum(ay));
@@ -519,8 +517,8 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 // spilled values): measured faster than 3 blocks at 168 registers.
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
-    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, AdjConsts ak,
-              int64_t* counts, const int* __restrict__ order) {
+    k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts,
+              const int* __restrict__ order) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
@@ -568,7 +566,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
     __syncwarp();
-    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, ak, npair);
+    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, npair);
   }
 #pragma unroll
   for (int c = 0; c < NC; c++) L.part[((size_t)e * NC + c) * 32 + lane] = A.K[c].out();
@@ -593,14 +591,13 @@ struct EvalSink {
   const Own* me;
   int cnt, lane;
   float thr;
-  AdjConsts ak;
   int npair;
   __device__ __forceinline__ bool fits(int) const { return true; }
   __device__ __forceinline__ void flush() {
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(*t, node, mask, soa, cnt, lane);
     __syncwarp();
-    eval_batch<ADJ, TRUNC>(*A, soa, mask, ce, lane, *me, thr, ak, npair);
+    eval_batch<ADJ, TRUNC>(*A, soa, mask, ce, lane, *me, thr, npair);
     __syncwarp();
     cnt = 0;
   }
@@ -628,7 +625,7 @@ struct EvalSink {
 template <bool ADJ, bool COUNT, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-                  WalkGroups wg, AdjConsts ak, int64_t* counts) {
+                  WalkGroups wg, int64_t* counts) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ float4 s_box[TR_WARPS][32][2];
@@ -650,7 +647,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     resume = resume_at<true>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   Acc<ADJ> A;
   A.zero();
-  EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, ak, 0};
+  EvalSink<ADJ, TRUNC> sink{&t, s_node[w], s_mask[w], s_soa[w], &A, &me, 0, lane, thr, 0};
   long long np = 0, nn = 0;
   for (int j = 0; j < ws; j++) {
     long long pj = 0, qj = 0;
@@ -807,14 +804,13 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
                         const int* order, cudaStream_t st) {
   const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES);
   const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
-  const AdjConsts ak = adj_consts(ae);
   if (counts)
     k_bh_fallback<ADJ, true, TRUNC>
-        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, ak, counts);
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
   else
     k_bh_fallback<ADJ, false, TRUNC>
-        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, ak, counts);
-  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, ak, counts, order);
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts, order);
   k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae, te);
 }
 

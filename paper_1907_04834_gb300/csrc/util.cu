@@ -91,12 +91,13 @@ __global__ void k_pad_zero(float4* base, size_t slot_f4, int64_t N, int64_t Npad
   pack_write(base + (size_t)blockIdx.y * slot_f4, i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
 }
 
+// Adjoint pack: alpha, and beta scaled by mu (the pair kernels' convention).
 __global__ void k_pack_ab(const double* __restrict__ al, const double* __restrict__ be,
-                          int64_t N, float4* abpack) {
+                          int64_t N, double mu, float4* abpack) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   pack_write(abpack, i, (float)al[3 * i], (float)al[3 * i + 1], (float)al[3 * i + 2],
-             (float)be[3 * i], (float)be[3 * i + 1], (float)be[3 * i + 2]);
+             (float)(mu * be[3 * i]), (float)(mu * be[3 * i + 1]), (float)(mu * be[3 * i + 2]));
 }
 
 __global__ void k_adjoint_init(const double* __restrict__ q, const double* __restrict__ X,
@@ -388,9 +389,9 @@ cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, float4* abpack,
-                           cudaStream_t st) {
-  k_pack_ab<<<blocks_for(N, 256), 256, 0, st>>>(al, be, N, abpack);
+cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, double mu,
+                           float4* abpack, cudaStream_t st) {
+  k_pack_ab<<<blocks_for(N, 256), 256, 0, st>>>(al, be, N, mu, abpack);
   note_launches(1);
   return cudaGetLastError();
 }
