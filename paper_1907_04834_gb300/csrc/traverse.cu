@@ -681,18 +681,20 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
   const GroupInfo gi = target_group(t, N, wg, g);
   if (lane >= gi.count) return;
   const int i = gi.first + lane;
-  double acc[NC];
+  // the slices' Kahan partials summed as FP32 pairs (in slice order), then
+  // handed to the FP64 epilogue
+  Pair S[NC];
 #pragma unroll
-  for (int c = 0; c < NC; c++) acc[c] = 0.0;
+  for (int c = 0; c < NC; c++) S[c] = Pair{0.f, 0.f};
   for (int k = 0; k < BH_SLICES; k++) {
     const int l = g * BH_SLICES + k;
     const float2* src = slice_overflowed(L, l, wg.wsplit) ? L.fb : L.part;
 #pragma unroll
-    for (int c = 0; c < NC; c++) {
-      const float2 v = src[((size_t)l * NC + c) * 32 + lane];
-      acc[c] += (double)v.x + (double)v.y;
-    }
+    for (int c = 0; c < NC; c++) pair_add(S[c], src[((size_t)l * NC + c) * 32 + lane]);
   }
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) acc[c] = (double)S[c].hi + (double)S[c].lo;
   if (wg.xperm) {  // tracer targets: the velocity of Eq. 3 is the F part
     if constexpr (!ADJ) tracer_epilogue(wg.xperm[i], acc, te);
     return;
@@ -707,67 +709,67 @@ __global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdE
   }
 }
 
-// Longest-first orders by length, each a counting sort on kOrderBuckets
-// length classes (len * (kOrderBuckets - 1) / max len) in one block; items of
-// one class land in any order, every item appears once.  First the nw walk
-// lists (worder, and *worder_n = nw), then the nw / ws slices, a slice's
-// length being that of its ws walk lists together (order).
-constexpr int kOrderThreads = 1024, kOrderBuckets = 512;
-template <class Len>
-__device__ void order_by_length(Len len, int n, int* out, int* out2, int* s_cnt, int* s_max) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  int mx = 0;
-  for (int l = tid; l < n; l += kOrderThreads) mx = max(mx, len(l));
-  mx = __reduce_max_sync(FULL, (unsigned)mx);
-  if (lane == 0) s_max[w] = mx;
-  for (int b = tid; b < kOrderBuckets; b += kOrderThreads) s_cnt[b] = 0;
-  __syncthreads();
-  mx = 1;
-  for (int k = 0; k < kOrderThreads / 32; k++) mx = max(mx, s_max[k]);
-  auto cls = [&](int l) {  // class 0 = longest
-    const int v = min(max(len(l), 0), mx);
-    return kOrderBuckets - 1 - (int)((long long)v * (kOrderBuckets - 1) / mx);
-  };
-  for (int l = tid; l < n; l += kOrderThreads) atomicAdd(&s_cnt[cls(l)], 1);
-  __syncthreads();
-  if (w == 0) {  // exclusive scan of the class counts, 16 per lane
-    constexpr int per = kOrderBuckets / 32;
-    int loc = 0;
-    for (int k = 0; k < per; k++) loc += s_cnt[lane * per + k];
-    int inc = loc;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += v;
-    }
-    int run = inc - loc;
-    for (int k = 0; k < per; k++) {
-      const int c = s_cnt[lane * per + k];
-      s_cnt[lane * per + k] = run;
-      run += c;
-    }
+// Longest-first orders of the walk lists (worder, and *worder_n = nw) and of
+// the nw / ws slices (order; a slice's length is that of its ws walk lists
+// together): one block, a counting sort on length classes of about 12% width
+// (the leading bit and the three below it: 8 classes per octave, monotone in
+// the length).  Items of one class land in any order; every item appears
+// once.
+constexpr int kOrderThreads = 1024, kOrderClasses = 256;
+__device__ __forceinline__ int len_class(int v) {
+  if (v < 16) return max(v, 0);
+  const int e = 31 - __clz(v);  // >= 4
+  return min(kOrderClasses - 1, 16 + 8 * (e - 4) + ((v >> (e - 3)) & 7));
+}
+
+__device__ void exclusive_scan_warp(int* cnt, int lane) {  // kOrderClasses counts
+  constexpr int per = kOrderClasses / 32;
+  int loc = 0;
+  for (int k = 0; k < per; k++) loc += cnt[lane * per + k];
+  int inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += v;
   }
-  __syncthreads();
-  for (int l = tid; l < n; l += kOrderThreads) {
-    const int at = atomicAdd(&s_cnt[cls(l)], 1);
-    out[at] = l;
-    if (out2) out2[at] = l;
+  int run = inc - loc;
+  for (int k = 0; k < per; k++) {
+    const int c = cnt[lane * per + k];
+    cnt[lane * per + k] = run;
+    run += c;
   }
-  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kOrderThreads)
     k_list_order(const int* __restrict__ len, int nw, int ws, int* order, int* worder,
                  int* worder_n) {
-  __shared__ int s_cnt[kOrderBuckets];
-  __shared__ int s_max[kOrderThreads / 32];
-  order_by_length([&](int l) { return len[l]; }, nw, worder, nullptr, s_cnt, s_max);
-  auto slice_len = [&](int e) {
+  __shared__ int s_w[kOrderClasses], s_s[kOrderClasses];  // walk lists, slices
+  const int tid = threadIdx.x, ns = nw / ws;
+  for (int b = tid; b < kOrderClasses; b += kOrderThreads) s_w[b] = 0, s_s[b] = 0;
+  __syncthreads();
+  // class index kOrderClasses - 1 - class: longest first
+  for (int e = tid; e < ns; e += kOrderThreads) {
     int v = 0;
-    for (int j = 0; j < ws; j++) v += len[e * ws + j];
-    return v;
-  };
-  order_by_length(slice_len, nw / ws, order, nullptr, s_cnt, s_max);
-  if (threadIdx.x == 0) *worder_n = nw;
+    for (int j = 0; j < ws; j++) {
+      const int lj = len[e * ws + j];
+      atomicAdd(&s_w[kOrderClasses - 1 - len_class(lj)], 1);
+      v += lj;
+    }
+    atomicAdd(&s_s[kOrderClasses - 1 - len_class(v)], 1);
+  }
+  __syncthreads();
+  if (tid < 32) exclusive_scan_warp(s_w, tid);
+  else if (tid < 64) exclusive_scan_warp(s_s, tid - 32);
+  __syncthreads();
+  for (int e = tid; e < ns; e += kOrderThreads) {
+    int v = 0;
+    for (int j = 0; j < ws; j++) {
+      const int lj = len[e * ws + j];
+      worder[atomicAdd(&s_w[kOrderClasses - 1 - len_class(lj)], 1)] = e * ws + j;
+      v += lj;
+    }
+    order[atomicAdd(&s_s[kOrderClasses - 1 - len_class(v)], 1)] = e;
+  }
+  if (tid == 0) *worder_n = nw;
 }
 
 inline unsigned warp_blocks(int64_t warps) { return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS); }

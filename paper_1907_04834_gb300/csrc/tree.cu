@@ -518,33 +518,9 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* _
 }
 
 // ---------------------------------------------------------------- aggregates
-// Member sums are carried as unevaluated FP32 pairs (hi + lo, hi the rounded
-// sum): each addition is Knuth's TwoSum, which returns the rounding error of
-// hi exactly, so a pair holds the sum with about twice FP32's precision at
-// FP32 speed (FP64 arithmetic is the slow path on this GPU).  The pairs are
-// added in the same fixed bottom-up order as the tree's preorder, so results
-// are deterministic.
-struct Pair {
-  float hi, lo;
-};
-__device__ __forceinline__ void pair_add(Pair& s, float x) {
-  const float t = __fadd_rn(s.hi, x);
-  const float bp = __fsub_rn(t, s.hi);
-  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-  s.hi = t;
-  s.lo = __fadd_rn(s.lo, e);
-}
-__device__ __forceinline__ void pair_add(Pair& s, float2 v) {
-  pair_add(s, v.x);
-  s.lo = __fadd_rn(s.lo, v.y);
-}
-// hi + lo renormalised (|lo| <= ulp(hi) / 2), stored as (hi, lo)
-__device__ __forceinline__ float2 pair_store(const Pair& s) {
-  const float t = __fadd_rn(s.hi, s.lo);
-  return make_float2(t, __fsub_rn(s.lo, __fsub_rn(t, s.hi)));
-}
-// the pair's value rounded to FP32
-__device__ __forceinline__ float pair_value(const Pair& s) { return __fadd_rn(s.hi, s.lo); }
+// Member sums are carried as unevaluated FP32 pairs (Pair, pair_add): FP64
+// arithmetic is the slow path on this GPU.  The pairs are added in the same
+// fixed bottom-up order as the tree's preorder, so results are deterministic.
 // (hi + lo) / n rounded to FP32.  n < 2^24 (exact in FP32): q = hi / n, then
 // one correction by the remainder hi - q n (exact by FMA) plus lo.  Larger
 // counts (only the top nodes of trees beyond 2^24 points) divide in FP64.

@@ -136,6 +136,33 @@ __device__ __forceinline__ float box_dist2(float x, float y, float z, const floa
   return __fadd_rn(__fadd_rn(sx, sy), __fmul_rn(dz, dz));
 }
 
+// Unevaluated FP32 pair sums (hi + lo, hi the rounded sum): each addition is
+// Knuth's TwoSum, which returns the rounding error of hi exactly, so a pair
+// holds a sum with about twice FP32's precision at FP32 speed.
+struct Pair {
+  float hi, lo;
+};
+__device__ __forceinline__ void pair_add(Pair& s, float x) {
+  const float t = __fadd_rn(s.hi, x);
+  const float bp = __fsub_rn(t, s.hi);
+  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, e);
+}
+// adds a value given as (x, y) = x + y with |y| small (a pair, or a Kahan
+// sum and its compensation)
+__device__ __forceinline__ void pair_add(Pair& s, float2 v) {
+  pair_add(s, v.x);
+  s.lo = __fadd_rn(s.lo, v.y);
+}
+// hi + lo renormalised (|lo| <= ulp(hi) / 2), stored as (hi, lo)
+__device__ __forceinline__ float2 pair_store(const Pair& s) {
+  const float t = __fadd_rn(s.hi, s.lo);
+  return make_float2(t, __fsub_rn(s.lo, __fsub_rn(t, s.hi)));
+}
+// the pair's value rounded to FP32
+__device__ __forceinline__ float pair_value(const Pair& s) { return __fadd_rn(s.hi, s.lo); }
+
 // Walk groups and, for a forest, the per-subject recentring points used by
 // the forward epilogue.
 struct WalkGroups {
