@@ -96,14 +96,31 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float ext, float
   return k > 1023u ? 1023u : k;
 }
 
-__global__ void k_morton(const float4* __restrict__ raw, int N, const float* __restrict__ part,
-                         int nparts, uint32_t* key, uint32_t* perm, uint32_t* codes, float* bbox) {
+__global__ void __launch_bounds__(256)
+    k_morton(const float4* __restrict__ raw, int N, const float* __restrict__ part, int nparts,
+             uint32_t* key, uint32_t* perm, uint32_t* codes, float* bbox) {
+  // the root box: every block folds the nparts partial boxes, all its
+  // threads at once (min and max are exact: any order gives the same box)
+  __shared__ float sh[6][8];
   __shared__ float box[6];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x)
+    for (int a = 0; a < 3; a++) {
+      lo[a] = fminf(lo[a], part[k * 6 + a]);
+      hi[a] = fmaxf(hi[a], part[k * 6 + 3 + a]);
+    }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int a = 0; a < 3; a++) {
+      lo[a] = fminf(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
+    }
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; a++) sh[a][threadIdx.x >> 5] = lo[a], sh[3 + a][threadIdx.x >> 5] = hi[a];
+  __syncthreads();
   if (threadIdx.x < 6) {
     const int a = threadIdx.x;
-    float v = part[a];
-    for (int k = 1; k < nparts; k++)
-      v = a < 3 ? fminf(v, part[k * 6 + a]) : fmaxf(v, part[k * 6 + a]);
+    float v = sh[a][0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++) v = a < 3 ? fminf(v, sh[a][k]) : fmaxf(v, sh[a][k]);
     box[a] = v;
     if (blockIdx.x == 0) bbox[a] = v;
   }
@@ -482,10 +499,10 @@ __device__ __forceinline__ int node_id(const uint32_t* offs, const uint32_t* mas
 }
 
 // parent of a node spanning sorted [a, b]: the cell of depth
-// max(delta_{a-1}, delta_b) that contains it (-1 when there is none)
+// Dp = max(delta_{a-1}, delta_b) that contains it (-1 when there is none)
 __device__ int parent_of(const uint32_t* sk, const uint32_t* ss, const uint32_t* offs,
-                         const uint32_t* mask, int N, int a, int b) {
-  int Dp = -1;
+                         const uint32_t* mask, int N, int a, int b, int& Dp) {
+  Dp = -1;
   if (a > 0) Dp = delta_at(sk, ss, a - 1);
   if (b < N - 1) Dp = max(Dp, delta_at(sk, ss, b));
   if (Dp < 0) return -1;
@@ -493,18 +510,35 @@ __device__ int parent_of(const uint32_t* sk, const uint32_t* ss, const uint32_t*
   return node_id(offs, mask, pa, Dp);
 }
 
+// A node (first sorted point a) under a parent of depth Dp < 10 lies in the
+// parent's octant (code >> (27 - 3 Dp)) & 7; distinct children have distinct
+// octants, so a child's rank among its siblings (preorder) is the number of
+// occupied octants below its own.  Parents of depth 10 hold runs of equal
+// codes: their children are consecutive leaves.
+__device__ __forceinline__ void note_octant(uint32_t* nocc, int id, int par, int Dp,
+                                            uint32_t code) {
+  if (par < 0 || Dp >= 10) return;
+  const uint32_t oct = (code >> (27 - 3 * Dp)) & 7u;
+  atomicOr(&nocc[par], 1u << oct);
+  atomicOr(&nocc[id], oct << 8);
+}
+
 __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ ss,
                               int N,
                               const uint32_t* __restrict__ mask, const uint32_t* __restrict__ offs,
                               const int32_t* __restrict__ own_a, const int32_t* __restrict__ own_b,
-                              int2* nsc, int2* ninfo, int32_t* nparent, int32_t* acnt) {
+                              int2* nsc, int2* ninfo, int32_t* nparent, uint32_t* nocc,
+                              int32_t* acnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   // the leaf of sorted point i
   const int leaf = i + (int)offs[i + 1];
+  int Dp;
   nsc[leaf] = make_int2(leaf + 1, 1);
   ninfo[leaf] = make_int2(-1, i);
-  nparent[leaf] = parent_of(sk, ss, offs, mask, N, i, i);
+  const int lpar = parent_of(sk, ss, offs, mask, N, i, i, Dp);
+  nparent[leaf] = lpar;
+  note_octant(nocc, leaf, lpar, Dp, sk[i]);
   acnt[leaf] = 0;
   // the internal node owned by boundary i
   if (i < N - 1 && own_a[i] >= 0) {
@@ -512,7 +546,9 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* _
     const int id = node_id(offs, mask, a, D);
     nsc[id] = make_int2(b + 1 + (int)offs[b + 1], b - a + 1);
     ninfo[id] = make_int2(D, a);
-    nparent[id] = parent_of(sk, ss, offs, mask, N, a, b);
+    const int par = parent_of(sk, ss, offs, mask, N, a, b, Dp);
+    nparent[id] = par;
+    note_octant(nocc, id, par, Dp, sk[a]);
     acnt[id] = 0;
   }
 }
@@ -532,9 +568,22 @@ __device__ __forceinline__ float pair_mean(const Pair& s, int count) {
   return __fadd_rn(q, __fdiv_rn(r, n));
 }
 
+// atomicAdd with acquire-release semantics at GPU scope: orders this
+// thread's earlier writes before the add and its later reads after it.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 // One thread per sorted point writes its leaf's record (and box), then walks
-// up: the last child to arrive at a parent (arrival counter) sums the
-// parent's children in preorder and writes its record (and box).
+// up: before arriving at a parent (arrival counter) it enters its node in the
+// parent's child table, and the last child to arrive sums the parent's
+// children in preorder -- their indices all at hand, so the loads of one
+// level go out together -- and writes the parent's record (and box).
 // BOX = false: the boxes (and skips) of this tree are already stored; only
 // the sums and source records are recomputed (backward-stage reuse).
 template <bool ADJ, bool BOX>
@@ -567,19 +616,21 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     const int par = t.nparent[x];
     if (par < 0) break;
     const int2 sc = t.nsc[par];
-    __threadfence();
-    const int old = atomicAdd(&t.acnt[par], nx);
+    const int Dp = t.ninfo[par].x;
+    const uint32_t occ = t.nocc[par] & 0xffu;
+    if (Dp < 10) {
+      const uint32_t oct = (t.nocc[x] >> 8) & 7u;
+      t.child[8 * par + __popc(occ & ((1u << oct) - 1u))] = x;
+    }
+    const int old = atom_add_acq_rel(&t.acnt[par], nx);
     if (old + nx != sc.y) break;
-    __threadfence();
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     Pair S[NS];
 #pragma unroll
     for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
-    int c = par + 1;
-    while (c < sc.x) {
-      const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
-      const int cskip = __float_as_int(bl.w);
+    auto add_child = [&](int c, bool leaf) {
       if (BOX) {
+        const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
         lo[0] = fminf(lo[0], bl.x);
         lo[1] = fminf(lo[1], bl.y);
         lo[2] = fminf(lo[2], bl.z);
@@ -587,7 +638,7 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
         hi[1] = fmaxf(hi[1], bh.y);
         hi[2] = fmaxf(hi[2], bh.z);
       }
-      if (cskip == c + 1) {
+      if (leaf) {
         float4 r[4];
 #pragma unroll
         for (int q = 0; q < NS / 3; q++) r[q] = __ldcg(&t.nrec[4 * c + q]);
@@ -604,7 +655,21 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
 #pragma unroll
         for (int k = 0; k < NS; k++) pair_add(S[k], v[k]);
       }
-      c = cskip;
+    };
+    if (Dp < 10) {  // one child per occupied octant, in octant (= pre-) order
+      const int nch = __popc(occ);
+      int cs[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++)  // (clamped into the subtree: never an outside node)
+        cs[k] = k < nch ? min(max(__ldcg(&t.child[8 * par + k]), par + 1), sc.x - 1) : par + 1;
+      bool lf[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) lf[k] = k < nch && __ldcg(&t.nsc[cs[k]]).y == 1;
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (k < nch) add_child(cs[k], lf[k]);
+    } else {  // a run of equal codes: its points' leaves follow it
+      for (int c = par + 1; c <= par + sc.y; c++) add_child(c, true);
     }
     const int n = sc.y;
 #pragma unroll
@@ -662,7 +727,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_oa = take(4 * N1),
                o_ob = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
-               o_nrec = take(64 * M), o_acnt = take(4 * M),
+               o_nrec = take(64 * M), o_acnt = take(4 * M), o_child = take(32 * M),
                o_isum = take(96 * M), o_cnt = take(16),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
@@ -684,6 +749,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     t->bbox = (float*)(b + o_bb);
     t->nrec = (float4*)(b + o_nrec);
     t->acnt = (int32_t*)(b + o_acnt);
+    t->child = (int32_t*)(b + o_child);
     t->isum = (double*)(b + o_isum);
     t->counts = (int64_t*)(b + o_cnt);
     L->part = (float2*)(b + o_part);
@@ -706,6 +772,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     return at;
   };
   const size_t o_perm = take(4 * N1), o_offs = take(4 * (N1 + 1)), o_npar = take(4 * M),
+               o_nocc = take(4 * M),
                o_nsc = take(8 * M), o_ninfo = take(8 * M), o_nbox = take(32 * M),
                o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
                o_next = take(4 * (size_t)chunks), o_head = take(4 * nw), o_len = take(4 * nw),
@@ -715,6 +782,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     t->perm = (uint32_t*)(b + o_perm);
     t->offs = (uint32_t*)(b + o_offs);
     t->nparent = (int32_t*)(b + o_npar);
+    t->nocc = (uint32_t*)(b + o_nocc);
     t->nsc = (int2*)(b + o_nsc);
     t->ninfo = (int2*)(b + o_ninfo);
     t->nbox = (float4*)(b + o_nbox);
@@ -783,8 +851,9 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     launches++;
   }
   TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
+  TRY(cudaMemsetAsync(t.nocc, 0, sizeof(uint32_t) * 2 * (size_t)N, st));
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.offs, t.own_a, t.own_b,
-                                                 t.nsc, t.ninfo, t.nparent, t.acnt);
+                                                 t.nsc, t.ninfo, t.nparent, t.nocc, t.acnt);
   launch_aggregate(t, N, raw, pack, abpack, true, st);
   note_launches(launches + 3 + 2);
   return cudaGetLastError();

@@ -45,6 +45,9 @@ struct TreeArrays {
   int2* ninfo;      // {depth (-1 = leaf), first sorted position} (kept per step: the
                     // leaf-size variant's walk reads it, also when re-walking a kept tree)
   int32_t* nparent; // preorder id of the parent, -1 for the root
+  uint32_t* nocc;   // per node (kept per step): bits 0-7 the octants its children occupy,
+                    // bits 8-10 its own octant in its parent (parents of depth < 10)
+  int32_t* child;   // 8 per node: children in preorder (bottom-up pass; parents of depth < 10)
   int32_t* acnt;    // arrival counters of the bottom-up pass
   double* isum;     // 12 per node: sums of xs, p, a, b over members (FP32 pairs)
   int64_t* counts;  // {point interactions, node interactions}
