@@ -167,19 +167,17 @@ __device__ __forceinline__ bool slice_overflowed(const BHLists& L, int e, int ws
 template <bool VAR>
 __device__ int resume_at(const TreeArrays& t, int s, float rx, float ry, float rz, float thr,
                          int leaf, int crit, int resume) {
-  int path[12];
-  int n = 0;
-  for (int a = t.nparent[s]; a >= 0 && n < 12; a = t.nparent[a]) path[n++] = a;
-  for (int k = n - 1; k >= 0; k--) {
-    const int a = path[k];
-    if (resume > a) continue;
+  // Tested bottom-up; ancestors' subtrees nest, so the highest qualifying
+  // ancestor -- the first one found from the root down -- has the largest
+  // skip.
+  int r = resume;
+  for (int a = t.nparent[s]; a >= 0; a = t.nparent[a]) {
     const float4 lo = t.nbox[2 * a], hi = t.nbox[2 * a + 1];
     const bool far = VAR ? far_test(rx, ry, rz, lo, hi, thr, crit)
                          : box_dist2(rx, ry, rz, lo, hi) > thr;
-    if (far || (VAR && __float_as_int(hi.w) <= leaf))
-      resume = __float_as_int(lo.w);
+    if (far | (VAR && __float_as_int(hi.w) <= leaf)) r = max(r, __float_as_int(lo.w));
   }
-  return resume;
+  return r;
 }
 
 // ------------------------------------------------------------------ evaluation
