@@ -62,6 +62,8 @@ def _load():
                                        _f64p, _f64p]
     lib.gsref_shoot.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, cint, _f64p,
                                 _f64p, _f64p]
+    lib.gsref_shoot_sympl.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, cint, cint,
+                                      _f64p, _f64p, _f64p]
     lib.gsref_shoot_grad.argtypes = [i64, _f64p, _f64p, _f64p, dbl, cint, dbl, cint, dbl, cint,
                                      cint, _f64p, _f64p, _f64p]
     lib.gsref_morton.argtypes = [i64, _f64p, _u32p, _u32p]
@@ -161,6 +163,17 @@ def shoot(q0, p0, sigma, T, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     H = np.zeros(2)
     _load().gsref_shoot(q0.shape[0], q0, p0, float(sigma), int(T), int(mode), float(thresh),
                         int(leaf), int(crit), q1, p1, H)
+    return q1, p1, H
+
+
+def shoot_sympl(q0, p0, sigma, T, iters, mode=EXACT, thresh=3.0, leaf=1, crit=0):
+    """Semi-implicit symplectic Euler shooting (gsref_shoot_sympl: `iters`
+    fixed-point passes per step; 0 = explicit Euler): q(1), p(1), [H(0), H(1)]."""
+    q0, p0 = _c(q0), _c(p0)
+    q1, p1 = np.empty_like(q0), np.empty_like(q0)
+    H = np.zeros(2)
+    _load().gsref_shoot_sympl(q0.shape[0], q0, p0, float(sigma), int(T), int(mode),
+                              float(thresh), int(leaf), int(crit), int(iters), q1, p1, H)
     return q1, p1, H
 
 

@@ -680,6 +680,47 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
   free(Phi);
 }
 
+/* Semi-implicit symplectic Euler (a variant of the time discretisation, not
+ * the paper's scheme; its Sec. 2.1 only says the flow is discretised in
+ * time).  H is not separable (K depends on q), so the symplectic Euler step
+ *     p^{k+1} = p^k + h Phi(q^k, p^{k+1}),   q^{k+1} = q^k + h F(q^k, p^{k+1})
+ * is implicit in p.  It is solved approximately by `iters` fixed-point passes
+ * with q held at q^k:  r^0 = p^k,  r^{m+1} = p^k + h Phi(q^k, r^m), followed
+ * by the update  q^{k+1} = q^k + h F(q^k, r^iters),  p^{k+1} = p^k + h Phi(q^k,
+ * r^iters).  iters = 0 is the explicit Euler step of gsref_shoot; as iters
+ * grows the step tends to the symplectic Euler step.  H as in gsref_shoot. */
+void gsref_shoot_sympl(int64_t N, const double *q0, const double *p0, double sigma,
+                       int T, int mode, double thresh, int leaf, int crit, int iters,
+                       double *q1, double *p1, double *H) {
+  size_t sz = (size_t)N * 3;
+  double *F = (double *)malloc(sz * sizeof(double));
+  double *Phi = (double *)malloc(sz * sizeof(double));
+  double *r = (double *)malloc(sz * sizeof(double));
+  double h = 1.0 / (double)T;
+  memcpy(q1, q0, sz * sizeof(double));
+  memcpy(p1, p0, sz * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    memcpy(r, p1, sz * sizeof(double));
+    for (int m = 0; m <= iters; m++) {
+      gsref_rhs(N, q1, r, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
+      if (k == 0 && m == 0 && H) H[0] = half_p_dot_F(N, p1, F);
+      if (m < iters)
+        for (size_t i = 0; i < sz; i++) r[i] = p1[i] + h * Phi[i];
+    }
+    for (size_t i = 0; i < sz; i++) {
+      q1[i] += h * F[i];
+      p1[i] += h * Phi[i];
+    }
+  }
+  if (H) {
+    gsref_rhs(N, q1, p1, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
+    H[1] = half_p_dot_F(N, p1, F);
+  }
+  free(F);
+  free(Phi);
+  free(r);
+}
+
 /* Objective (Eq. 2) and its gradient with respect to p0 by the discrete
  * adjoint.  E gets {total, H(q0,p0), lambda * sum |q^T - X|^2}; q1 (optional)
  * gets q^T.  The whole trajectory is stored (plain, no checkpointing). */
