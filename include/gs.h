@@ -95,6 +95,16 @@ typedef struct gs_params {
                             d2, s the largest side of the range, d2 the FP32
                             squared distance to its centre (lo + hi) * 0.5,
                             theta = thresh_sigmas in (0, 1] (dimensionless) */
+  int32_t sympl_iters;   /* gs_shoot time stepping: 0 = explicit Euler (the
+                            scheme of the gradient); M in [1, 64] =
+                            semi-implicit symplectic Euler: per step, M
+                            fixed-point passes r <- p^k + h Phi(q^k, r) from
+                            r = p^k at fixed q^k, then q^{k+1} = q^k + h F(q^k,
+                            r), p^{k+1} = p^k + h Phi(q^k, r) (M + 1 right-hand
+                            sides per step; the step tends to symplectic Euler
+                            as M grows).  Other entry points need 0
+                            (GS_ERR_UNSUPPORTED otherwise) */
+  int32_t reserved;      /* must be 0 */
 } gs_params;
 
 typedef struct gs_ctx gs_ctx;

@@ -34,15 +34,16 @@ class Params(ctypes.Structure):
                 ("thresh_sigmas", ctypes.c_double), ("T", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("leaf_size", ctypes.c_int32),
-                ("criterion", ctypes.c_int32)]
+                ("criterion", ctypes.c_int32), ("sympl_iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def make_params(sigma, T, mode=GS_EXACT, lam=1.0, thresh=3.0, ckpt_every=0, flags=0,
-                leaf_size=1, criterion=0) -> Params:
+                leaf_size=1, criterion=0, sympl_iters=0) -> Params:
     if isinstance(mode, str):
         mode = {"exact": GS_EXACT, "bh": GS_BH, "trunc": GS_TRUNC}[mode.lower()]
     return Params(float(sigma), float(lam), float(thresh), int(T), int(mode), int(ckpt_every),
-                  int(flags), int(leaf_size), int(criterion))
+                  int(flags), int(leaf_size), int(criterion), int(sympl_iters), 0)
 
 
 _lib = None

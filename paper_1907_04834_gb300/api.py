@@ -99,13 +99,15 @@ def _ctx_for(t: torch.Tensor) -> Context:
 
 
 def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, leaf_size=1, criterion=0,
-          stream=None):
-    """Geodesic shooting (Eq. 1, Euler).  Returns (q1, p1, H) with H = None or
-    the tensor [H(q0,p0), H(q1,p1)]."""
+          sympl_iters=0, stream=None):
+    """Geodesic shooting (Eq. 1; explicit Euler, or with sympl_iters = M > 0
+    the semi-implicit symplectic Euler step of M fixed-point passes).  Returns
+    (q1, p1, H) with H = None or the tensor [H(q0,p0), H(q1,p1)]."""
     q0 = _pts(q0, "q0")
     p0 = _pts(p0, "p0", q0.shape[0])
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
+    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion,
+                      sympl_iters=sympl_iters)
     q1, p1 = _like(q0), _like(q0)
     H = _like(q0, (2,)) if with_H else None
     c.check(c.lib.gs_shoot(c.handle, _ptr(q0), _ptr(p0), q0.shape[0], ctypes.byref(prm), _ptr(q1),

@@ -170,7 +170,7 @@ struct Key {
   void params(const gs_params* prm) {
     add(prm->sigma), add(prm->lambda), add(prm->thresh_sigmas);
     add(prm->T), add(prm->mode), add(prm->ckpt_every), add(prm->flags), add(prm->leaf_size);
-    add(prm->criterion);
+    add(prm->criterion), add(prm->sympl_iters);
   }
   void workspace(const gs_ctx* c) {
     for (const DevMem* m : {&c->in_q, &c->in_p, &c->in_X, &c->out_a, &c->out_b, &c->q, &c->p,
@@ -223,7 +223,8 @@ gs_status run_graphed(gs_ctx* c, gs_ctx::GraphCache& gc, const Key& k, cudaStrea
   return GS_OK;
 }
 
-gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
+gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda,
+                       bool sympl_ok = false) {
   if (!prm) return fail(c, GS_ERR_INVALID_ARG, "params is NULL");
   if (!(prm->sigma > 0.0) || !std::isfinite(prm->sigma))
     return fail(c, GS_ERR_INVALID_ARG, "sigma must be finite and > 0 (got %g)", prm->sigma);
@@ -246,6 +247,14 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda) {
   if (prm->criterion == 1 && (prm->mode != GS_BH || !(prm->thresh_sigmas <= 1.0)))
     return fail(c, GS_ERR_INVALID_ARG,
                 "criterion 1 (opening angle) needs GS_BH and theta = thresh_sigmas in (0, 1]");
+  if (prm->reserved != 0) return fail(c, GS_ERR_INVALID_ARG, "reserved must be 0");
+  if (prm->sympl_iters < 0 || prm->sympl_iters > 64)
+    return fail(c, GS_ERR_INVALID_ARG, "sympl_iters must be in [0, 64] (got %d)",
+                prm->sympl_iters);
+  if (prm->sympl_iters != 0 && !sympl_ok)
+    return fail(c, GS_ERR_UNSUPPORTED,
+                "sympl_iters != 0 (semi-implicit symplectic Euler) is supported by gs_shoot "
+                "only");
   return GS_OK;
 }
 
@@ -332,6 +341,7 @@ struct Solver {
   float thr;  // Barnes-Hut threshold (r*r, FP32)
   int leaf;   // Barnes-Hut leaf size (1 = the paper's rule)
   int crit;   // far test: 0 the paper's distance rule, 1 opening angle
+  int iters = 0;  // fixed-point passes per step (semi-implicit symplectic Euler)
   ExactGeom gf, ga;
   size_t pack_f4;  // float4 per pack slot
   int slots;       // pack slots allocated
@@ -523,6 +533,7 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
   S.h = 1.0 / (double)prm->T;
   S.lambda = prm->lambda;
   S.crit = prm->criterion;
+  S.iters = prm->sympl_iters;
   if (S.crit == 1) {  // opening angle: theta^2
     float th = (float)prm->thresh_sigmas;
     S.thr = th * th;
@@ -690,6 +701,29 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     s = bh_eval_fwd(c->tree, b, e, counts != nullptr, S.st);
   }
   if (s != GS_OK) return fail(c, s, "Barnes-Hut forward step failed: %s", bh_last_error());
+  return GS_OK;
+}
+
+// Another forward right-hand side at the positions of the last forward_rhs
+// (a fixed-point pass of a semi-implicit step), momenta from pack slot
+// `slot`.  Barnes-Hut: the tree and interaction lists of tree slot 0 stay
+// valid (the decisions depend on the positions only); only the node sums are
+// recomputed before the lists are evaluated.
+gs_status forward_rhs_same_q(Solver& S, int slot, const FwdEpi& e) {
+  gs_ctx* c = S.c;
+  if (S.mode == GS_EXACT || S.batch) return forward_rhs(S, slot, e, nullptr);
+  BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
+           S.mode == GS_TRUNC, S.crit};
+  gs_status s;
+  {
+    KTimer tm(c, GS_K_TREE_BUILD, S.st);
+    s = bh_aggregate(c->tree, b, nullptr, false, S.st);
+  }
+  if (s == GS_OK) {
+    KTimer tm(c, GS_K_BH_FWD, S.st);
+    s = bh_eval_fwd(c->tree, b, e, false, S.st);
+  }
+  if (s != GS_OK) return fail(c, s, "Barnes-Hut forward pass failed: %s", bh_last_error());
   return GS_OK;
 }
 
@@ -895,16 +929,26 @@ gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
   S.st = st;
   const int64_t N = S.N;
   if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  // Each step: S.iters fixed-point passes (the epilogue writes the next pack
+  // with (q^k, p^k + h Phi) and leaves the state), then the update pass; with
+  // S.iters = 0 the explicit Euler step.  Packs alternate between two slots.
+  int cur = 0;
   for (int k = 0; k < S.T; k++) {
-    FwdEpi e = fwd_epi(S, (k + 1) & 1, S.h);
-    if (k == 0 && H) e.pf_part = c->pf.as<double>();
-    if ((s = forward_rhs(S, k & 1, e, nullptr))) return s;
-    if (k == 0 && H) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+    for (int m = 0; m <= S.iters; m++) {
+      FwdEpi e = fwd_epi(S, cur ^ 1, S.h);
+      e.iterate = m < S.iters;
+      const bool h0 = k == 0 && m == 0 && H;
+      if (h0) e.pf_part = c->pf.as<double>();
+      if ((s = m == 0 ? forward_rhs(S, cur, e, nullptr) : forward_rhs_same_q(S, cur, e)))
+        return s;
+      if (h0) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
+      cur ^= 1;
+    }
   }
   if (H) {
     FwdEpi e = fwd_epi(S, -1, 0.0);
     e.pf_part = c->pf.as<double>();
-    if ((s = forward_rhs(S, S.T & 1, e, nullptr))) return s;
+    if ((s = forward_rhs(S, cur, e, nullptr))) return s;
     CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H1), st), "sum");
   }
   return GS_OK;
@@ -1163,7 +1207,7 @@ gs_status gs_shoot(gs_ctx* c, const double* q0, const double* p0, int64_t N,
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
-  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false, true))) return s;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   bool hq = false, hp = false, hh = false;

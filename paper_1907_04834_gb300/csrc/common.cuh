@@ -199,6 +199,8 @@ struct FwdEpi {
   double s;             // coordinate scale
   double phi_scale;     // sigma^-2 / s
   double h;             // Euler step (0 = no update)
+  bool iterate;         // fixed-point pass of a semi-implicit step: the next pack
+                        // gets (q, p + h Phi), the state is not changed
   int64_t N;
 };
 
@@ -224,11 +226,11 @@ __device__ __forceinline__ void fwd_epilogue_at(int64_t i, int64_t ipk, const do
   if (e.h != 0.0) {
     double qn[3], pn[3];
     for (int a = 0; a < 3; a++) {
-      qn[a] = q[a] + e.h * F[a];
+      qn[a] = e.iterate ? q[a] : q[a] + e.h * F[a];
       pn[a] = p[a] + e.h * Phi[a];
-      q[a] = qn[a];
-      p[a] = pn[a];
     }
+    if (!e.iterate)
+      for (int a = 0; a < 3; a++) q[a] = qn[a], p[a] = pn[a];
     PackScale ps{center[0], center[1], center[2], e.s};
     if (e.pack_next) pack_state(e.pack_next, ipk, qn, pn, ps);
     if (e.raw_next)

@@ -51,7 +51,7 @@ def test_params_layout_matches_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     names = ["sigma", "lambda", "thresh_sigmas", "T", "mode", "ckpt_every", "flags", "leaf_size",
-             "criterion"]
+             "criterion", "sympl_iters", "reserved"]
     src = tmp_path / "layout.c"
     src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"gs.h\"\n"
                    "int main(void) { printf(\"%zu\", sizeof(gs_params));"
@@ -62,7 +62,7 @@ def test_params_layout_matches_header(tmp_path):
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                            check=True).stdout.split()]
     fields = ["sigma", "lambda_", "thresh_sigmas", "T", "mode", "ckpt_every", "flags", "leaf_size",
-              "criterion"]
+              "criterion", "sympl_iters", "reserved"]
     assert vals[0] == ctypes.sizeof(_lib.Params)
     assert vals[1:] == [getattr(_lib.Params, f).offset for f in fields]
     p = _lib.make_params(2.0, 7, "bh", 0.5, 3.0, 2)
