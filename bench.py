@@ -399,6 +399,23 @@ def run_ours(args):
         line["trunc_variant"] = {"ms_per_gradient": statistics.median(tms),
                                  "grad_rel_l2_vs_exact":
                                  float(torch.linalg.norm(g_tr - g_ex)) / nrm}
+        # semi-implicit symplectic Euler shooting (forward only): the cost of
+        # its fixed-point passes, which reuse each step's tree and lists
+        def shoot_ms(M):
+            gs.shoot(q0, p0, w.sigma, w.T, mode="bh", thresh=THRESH, sympl_iters=M)
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                a_ev = torch.cuda.Event(enable_timing=True)
+                b_ev = torch.cuda.Event(enable_timing=True)
+                a_ev.record()
+                gs.shoot(q0, p0, w.sigma, w.T, mode="bh", thresh=THRESH, sympl_iters=M)
+                b_ev.record()
+                torch.cuda.synchronize()
+                ts.append(a_ev.elapsed_time(b_ev))
+            return statistics.median(ts)
+        line["sympl_variant"] = {"passes": 2, "bh_ms_per_shoot": shoot_ms(2),
+                                 "explicit_bh_ms_per_shoot": shoot_ms(0)}
     if rank == 0 and args.e2e_steps > 0:
         # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
         h = lambda a: torch.as_tensor(a, dtype=torch.float64).pin_memory()
