@@ -509,6 +509,65 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   }
 }
 
+// ------------------------------------------------------------------ combine
+// Group g once all its slices are summed: per point (one lane each) the
+// slices' partial sums in slice order as FP32 pairs, then the FP64 epilogue.
+template <bool ADJ>
+__device__ __forceinline__ void combine_group(const TreeArrays& t, int N, const BHLists& L,
+                                              const WalkGroups& wg, int g, int lane,
+                                              const FwdEpi& fe, const AdjEpi& ae,
+                                              const TracerEpi& te) {
+  constexpr int NC = Acc<ADJ>::NC;
+  const GroupInfo gi = target_group(t, N, wg, g);
+  if (lane >= gi.count) return;
+  const int i = gi.first + lane;
+  Pair S[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) S[c] = Pair{0.f, 0.f};
+  for (int k = 0; k < BH_SLICES; k++) {
+    const int l = g * BH_SLICES + k;
+    const float2* src = slice_overflowed(L, l, wg.wsplit) ? L.fb : L.part;
+#pragma unroll
+    for (int c = 0; c < NC; c++) pair_add(S[c], __ldcg(&src[((size_t)l * NC + c) * 32 + lane]));
+  }
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) acc[c] = (double)S[c].hi + (double)S[c].lo;
+  if (wg.xperm) {  // tracer targets: the velocity of Eq. 3 is the F part
+    if constexpr (!ADJ) tracer_epilogue(wg.xperm[i], acc, te);
+    return;
+  }
+  const int o = (int)t.perm[i];
+  if constexpr (!ADJ) {
+    // a forest's subjects have their own recentring points
+    const double* c = wg.centers ? wg.centers + 3 * subject_of(wg.off, wg.S, o) : fe.center;
+    fwd_epilogue_at(o, o, c, acc, acc + 3, fe);
+  } else {
+    adj_epilogue(o, acc, acc + 3, acc + 6, ae);
+  }
+}
+
+// Called by a warp that has written the partial sums of one slice of group
+// g (list evaluation or fallback): the group's ticket counts its finished
+// slices, and the warp that finishes the last one combines the group (each
+// writer fences its sums before counting, the combiner after).
+template <bool ADJ>
+__device__ __forceinline__ void finish_slice(const TreeArrays& t, int N, const BHLists& L,
+                                             const WalkGroups& wg, int g, int lane,
+                                             const FwdEpi& fe, const AdjEpi& ae,
+                                             const TracerEpi& te) {
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) {
+    last = atomicAdd(&L.gticket[g], 1) == BH_SLICES - 1;
+    if (last) L.gticket[g] = 0;
+  }
+  if (!__shfl_sync(FULL, last, 0)) return;
+  __threadfence();
+  combine_group<ADJ>(t, N, L, wg, g, lane, fe, ae, te);
+}
+
 // ------------------------------------------------------------------ evaluate
 // One warp per slice: partial sums of its entries, part[(e*NC + c)*32 + lane].
 // The entries of the slice's walk lists are read as one sequence, BH_CHUNK
@@ -518,7 +577,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts,
-              const int* __restrict__ order) {
+              const int* __restrict__ order, FwdEpi fe, AdjEpi ae, TracerEpi te) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
@@ -575,6 +634,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     if (lane == 0)
       atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)tot);
   }
+  finish_slice<ADJ>(t, N, L, wg, e / BH_SLICES, lane, fe, ae, te);
 }
 
 // ------------------------------------------------------------------ fallback
@@ -625,7 +685,7 @@ struct EvalSink {
 template <bool ADJ, bool COUNT, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_fallback(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-                  WalkGroups wg, int64_t* counts) {
+                  WalkGroups wg, int64_t* counts, FwdEpi fe, AdjEpi ae, TracerEpi te) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
   __shared__ float4 s_box[TR_WARPS][32][2];
@@ -666,47 +726,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
   }
-}
-
-// ------------------------------------------------------------------ combine
-// Per point: the slices' partial sums (and resumed parts) in a fixed order,
-// then the epilogue.
-template <bool ADJ>
-__global__ void k_bh_combine(TreeArrays t, int N, BHLists L, WalkGroups wg, FwdEpi fe,
-                             AdjEpi ae, TracerEpi te) {
-  constexpr int NC = Acc<ADJ>::NC;
-  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = gl >> 5, lane = gl & 31;
-  if (g >= wg.G) return;
-  const GroupInfo gi = target_group(t, N, wg, g);
-  if (lane >= gi.count) return;
-  const int i = gi.first + lane;
-  // the slices' Kahan partials summed as FP32 pairs (in slice order), then
-  // handed to the FP64 epilogue
-  Pair S[NC];
-#pragma unroll
-  for (int c = 0; c < NC; c++) S[c] = Pair{0.f, 0.f};
-  for (int k = 0; k < BH_SLICES; k++) {
-    const int l = g * BH_SLICES + k;
-    const float2* src = slice_overflowed(L, l, wg.wsplit) ? L.fb : L.part;
-#pragma unroll
-    for (int c = 0; c < NC; c++) pair_add(S[c], src[((size_t)l * NC + c) * 32 + lane]);
-  }
-  double acc[NC];
-#pragma unroll
-  for (int c = 0; c < NC; c++) acc[c] = (double)S[c].hi + (double)S[c].lo;
-  if (wg.xperm) {  // tracer targets: the velocity of Eq. 3 is the F part
-    if constexpr (!ADJ) tracer_epilogue(wg.xperm[i], acc, te);
-    return;
-  }
-  const int o = (int)t.perm[i];
-  if constexpr (!ADJ) {
-    // a forest's subjects have their own recentring points
-    const double* c = wg.centers ? wg.centers + 3 * subject_of(wg.off, wg.S, o) : fe.center;
-    fwd_epilogue_at(o, o, c, acc, acc + 3, fe);
-  } else {
-    adj_epilogue(o, acc, acc + 3, acc + 6, ae);
-  }
+  finish_slice<ADJ>(t, N, L, wg, g, lane, fe, ae, te);
 }
 
 // Longest-first orders of the walk lists (worder, and *worder_n = nw) and of
@@ -805,15 +825,16 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
                         const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
                         const int* order, cudaStream_t st) {
   const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES);
-  const unsigned nc = (unsigned)(((int64_t)wg.G * 32 + 255) / 256);
+  // list evaluation, then the fallback for overflowed slices; the warp that
+  // finishes a group's last slice (in either kernel) combines the group
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts, order, fe, ae,
+                                                      te);
   if (counts)
     k_bh_fallback<ADJ, true, TRUNC>
-        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, fe, ae, te);
   else
     k_bh_fallback<ADJ, false, TRUNC>
-        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts);
-  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts, order);
-  k_bh_combine<ADJ><<<nc, 256, 0, st>>>(t, N, L, wg, fe, ae, te);
+        <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, fe, ae, te);
 }
 
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,
@@ -828,7 +849,7 @@ cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float 
     if (!adj) eval_launch<false, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
     else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
   }
-  note_launches(3);
+  note_launches(2);
   return cudaGetLastError();
 }
 

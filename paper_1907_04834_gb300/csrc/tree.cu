@@ -618,9 +618,9 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     const int2 sc = t.nsc[par];
     const int Dp = t.ninfo[par].x;
     const uint32_t occ = t.nocc[par] & 0xffu;
-    if (Dp < 10) {
+    if (Dp < 10) {  // a leaf is entered as ~x (x >= 0), so the parent knows it without a load
       const uint32_t oct = (t.nocc[x] >> 8) & 7u;
-      t.child[8 * par + __popc(occ & ((1u << oct) - 1u))] = x;
+      t.child[8 * par + __popc(occ & ((1u << oct) - 1u))] = nx == 1 ? ~x : x;
     }
     const int old = atom_add_acq_rel(&t.acnt[par], nx);
     if (old + nx != sc.y) break;
@@ -659,12 +659,13 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     if (Dp < 10) {  // one child per occupied octant, in octant (= pre-) order
       const int nch = __popc(occ);
       int cs[8];
-#pragma unroll
-      for (int k = 0; k < 8; k++)  // (clamped into the subtree: never an outside node)
-        cs[k] = k < nch ? min(max(__ldcg(&t.child[8 * par + k]), par + 1), sc.x - 1) : par + 1;
       bool lf[8];
 #pragma unroll
-      for (int k = 0; k < 8; k++) lf[k] = k < nch && __ldcg(&t.nsc[cs[k]]).y == 1;
+      for (int k = 0; k < 8; k++) {  // (clamped into the subtree: never an outside node)
+        const int v = k < nch ? __ldcg(&t.child[8 * par + k]) : par + 1;
+        lf[k] = v < 0;
+        cs[k] = min(max(v < 0 ? ~v : v, par + 1), sc.x - 1);
+      }
 #pragma unroll
       for (int k = 0; k < 8; k++)
         if (k < nch) add_child(cs[k], lf[k]);
@@ -731,7 +732,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_isum = take(96 * M), o_cnt = take(16),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
-               o_wordn = take(4);
+               o_wordn = take(4), o_gtick = take(4 * (size_t)groups);
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->key = (uint32_t*)(b + o_key);
@@ -756,6 +757,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     L->fb = (float2*)(b + o_fb);
     L->worder = (int*)(b + o_word);
     L->worder_n = (int*)(b + o_wordn);
+    L->gticket = (int*)(b + o_gtick);
   }
   return o;
 }
@@ -964,8 +966,10 @@ gs_status tree_reserve(TreeWork& w, int64_t N, int slots, cudaStream_t st, int64
   w.lcap_from_req = w.lcap_req;
   views(w, 0, &t, &L);
   w.d_counts = t.counts;
-  // no walk order yet: the first walk takes its lists in index order
-  if (cudaMemset(L.worder_n, 0xff, sizeof(int)) != cudaSuccess) {
+  // no walk order yet: the first walk takes its lists in index order; group
+  // tickets start at zero (each combining warp puts its group's back)
+  if (cudaMemset(L.worder_n, 0xff, sizeof(int)) != cudaSuccess ||
+      cudaMemset(L.gticket, 0, sizeof(int) * (size_t)groups) != cudaSuccess) {
     cudaGetLastError();
     tree_release(w);
     return GS_ERR_CUDA;

@@ -81,6 +81,7 @@ struct BHLists {
   int* order;     // per slice (this step)
   int* worder;    // per walk list (shared by the steps)
   int* worder_n;  // list count of worder; -1 when it holds none
+  int* gticket;   // per group: slices summed so far (the last one combines; back to 0)
 };
 
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
