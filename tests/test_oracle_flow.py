@@ -183,3 +183,22 @@ def test_energy_terms(oracle):
     assert E[0] == pytest.approx(E[1] + E[2], rel=1e-15)
     q1s, _, _ = oracle.shoot(w.q0, w.p0, w.sigma, w.T)
     assert np.array_equal(q1, q1s)
+
+
+def test_angular_momentum(oracle):
+    """H is rotation invariant, so the flow conserves L = sum_i q_i x p_i:
+    the right-hand side satisfies sum_i (F_i x p_i + q_i x Phi_i) = 0 (Phi_ij
+    along d_ij), and an Euler step changes L only by h^2 sum_i F_i x Phi_i, a
+    drift that halves when T doubles."""
+    q, p = _rand_cloud(50, 12, scale=1.5, pscale=0.5)
+    F, Phi, _ = oracle.rhs(q, p, 1.2)
+    r = (np.cross(F, p) + np.cross(q, Phi)).sum(axis=0)
+    scale = np.abs(np.cross(F, p)).sum() + np.abs(np.cross(q, Phi)).sum()
+    assert np.abs(r).max() <= 1e-13 * scale
+    L0 = np.cross(q, p).sum(axis=0)
+    drift = []
+    for T in (20, 40, 80):
+        q1, p1, _ = oracle.shoot(q, p, 1.2, T)
+        drift.append(np.abs(np.cross(q1, p1).sum(axis=0) - L0).max())
+    ratios = [drift[k] / drift[k + 1] for k in range(2)]
+    assert all(1.8 < x < 2.2 for x in ratios), (drift, ratios)
