@@ -52,9 +52,12 @@ ALU_PEAK_OPS = 152 * 128 * 2.07e9
 OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 40, "bh_fwd": 16, "bh_adj": 40, "bh_walk": 16}
 ISSUED_OPS_PER_PAIR = {"exact_fwd": 16, "exact_adj": 36, "bh_fwd": 16, "bh_adj": 36,
                        "bh_walk": 16}
-# algorithmic bytes per point of one tree build (read FP32 positions + pack,
-# sort passes, node records written): see the design notes
-TREE_BYTES_PER_POINT = 250.0
+# algorithmic bytes per point of one tree pass, averaged over the forward
+# builds (about 250 B: FP32 positions and pack read, four sort passes, node
+# boxes and records written) and the backward aggregations (about 200 B:
+# both packs read, leaf and node records and pair sums written), which
+# alternate in the class
+TREE_BYTES_PER_POINT = 225.0
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -356,6 +359,27 @@ def run_ours(args):
     roof["share"] = ms / max(sum(v[1] for v in kern.values()), 1e-9)
     tr = measured_traffic(dom)
     roof["traffic"] = tr
+    # every timed class against its own roof (the pair classes against the
+    # FP32 pipe, the tree class -- forward builds and backward aggregations
+    # alternate, TREE_BYTES_PER_POINT on average -- against HBM); the walk
+    # issues compares and branches, no pair arithmetic, and has none
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    class_roofs = {}
+    for cls, (ncl, mcl) in kern.items():
+        per = mcl / max(ncl, 1) * 1e-3
+        if cls == "tree_build":
+            gbs = TREE_BYTES_PER_POINT * w.N / per / 1e9
+            class_roofs[cls] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                "unit": "GB/s", "frac": gbs / hbm_peak,
+                                "bytes_per_point": TREE_BYTES_PER_POINT}
+        elif cls in ("exact_fwd", "exact_adj", "bh_fwd", "bh_adj"):
+            units = w.N * w.N if cls.startswith("exact") else bh_inter_step
+            ach = OPS_PER_PAIR[cls] * units / per / 1e12
+            class_roofs[cls] = {"bound": "alu", "achieved": ach, "peak": ALU_PEAK_OPS / 1e12,
+                                "unit": "Tops/s", "frac": ach * 1e12 / ALU_PEAK_OPS,
+                                "issued_frac": ISSUED_OPS_PER_PAIR[cls] * units / per
+                                / ALU_PEAK_OPS}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
@@ -369,6 +393,7 @@ def run_ours(args):
             "bh_interactions_per_point_step": bh_inter_step / w.N,
             "roofline": roof,
             "kernels": {k: {"launch_groups": v[0], "ms": v[1]} for k, v in kern.items()},
+            "class_rooflines": class_roofs,
             "gpu_launches": launches, "wall_s": wall, "clocks": ck}
 
     if rank == 0 and not args.no_variants:
