@@ -114,13 +114,15 @@ __global__ void __launch_bounds__(256)
       lo[a] = fminf(lo[a], __shfl_down_sync(0xffffffffu, lo[a], o));
       hi[a] = fmaxf(hi[a], __shfl_down_sync(0xffffffffu, hi[a], o));
     }
+  const int wid = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
-    for (int a = 0; a < 3; a++) sh[a][threadIdx.x >> 5] = lo[a], sh[3 + a][threadIdx.x >> 5] = hi[a];
+    for (int a = 0; a < 3; a++) sh[a][wid] = lo[a], sh[3 + a][wid] = hi[a];
   __syncthreads();
   if (threadIdx.x < 6) {
     const int a = threadIdx.x;
     float v = sh[a][0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); k++) v = a < 3 ? fminf(v, sh[a][k]) : fmaxf(v, sh[a][k]);
+    for (int k = 1; k < (int)(blockDim.x >> 5); k++)
+      v = a < 3 ? fminf(v, sh[a][k]) : fmaxf(v, sh[a][k]);
     box[a] = v;
     if (blockIdx.x == 0) bbox[a] = v;
   }

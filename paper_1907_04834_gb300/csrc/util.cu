@@ -361,7 +361,8 @@ cudaError_t launch_batch_energy(double* E, int S, cudaStream_t st) {
 }
 
 int bbox_blocks(int64_t N) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(kBoxBlocks, (N + kBoxThreads - 1) / kBoxThreads));
+  const int64_t need = (N + kBoxThreads - 1) / kBoxThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kBoxBlocks, need));
 }
 
 cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, double* part,
