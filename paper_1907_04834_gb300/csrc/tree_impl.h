@@ -58,7 +58,7 @@ struct TreeArrays {
 // order; the walk may split each slice into `wsplit` walk lists (walk slices
 // per group wk = BH_SLICES * wsplit) to spread a small tree's walk over more
 // warps.  The evaluation reads a slice's walk lists as one entry sequence in
-// batches of BH_CHUNK, so the sums do not depend on the split.  Entries live
+// fixed batches, so the sums do not depend on the split.  Entries live
 // in a pool of chunks of BH_CHUNK entries; a walk list is the chain of chunks
 // starting at head[l] (next[c] links them in order).
 constexpr int BH_SLICES = 4;
