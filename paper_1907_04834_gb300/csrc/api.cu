@@ -1799,7 +1799,7 @@ gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_
   cudaStream_t st = (cudaStream_t)stream;
   const double* dq;
   if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
-  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0, 0};
+  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0, 0, 0, 0};
   Solver S;
   if ((s = solver_init(c, S, N, &prm, 1, false, st))) return s;
   if ((s = solver_load(S, dq, dq, 0))) return s;

@@ -56,7 +56,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TR_WARPS = 4;
-constexpr int TR_BUF = 32;
 constexpr int TR_CAP = 2 * BH_CHUNK;  // evaluation batch (entries staged at a time)
 
 // Per-lane own data (record of the lane's point).
