@@ -613,19 +613,30 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
       t.nrec[4 * x + 3] = make_float4(b[0], b[1], b[2], 0.f);
     }
   }
+  // The parent chain and the nodes' words (nsc, ninfo, nocc) are read-only
+  // here, so each level's are fetched one level ahead: the parent's index
+  // before this thread's arrival is decided, its words while the last
+  // arriver sums the children below.
   int nx = 1;
-  while (true) {
-    const int par = t.nparent[x];
-    if (par < 0) break;
-    const int2 sc = t.nsc[par];
-    const int Dp = t.ninfo[par].x;
-    const uint32_t occ = t.nocc[par] & 0xffu;
+  uint32_t own = t.nocc[x];  // x's octant word
+  int par = t.nparent[x];
+  int2 sc = make_int2(0, 0);
+  int Dp = 0;
+  uint32_t pw = 0u;
+  if (par >= 0) sc = t.nsc[par], Dp = t.ninfo[par].x, pw = t.nocc[par];
+  while (par >= 0) {
+    const uint32_t occ = pw & 0xffu;
     if (Dp < 10) {  // a leaf is entered as ~x (x >= 0), so the parent knows it without a load
-      const uint32_t oct = (t.nocc[x] >> 8) & 7u;
+      const uint32_t oct = (own >> 8) & 7u;
       t.child[8 * par + __popc(occ & ((1u << oct) - 1u))] = nx == 1 ? ~x : x;
     }
+    const int gpar = t.nparent[par];
     const int old = atom_add_acq_rel(&t.acnt[par], nx);
     if (old + nx != sc.y) break;
+    int2 sc_n = make_int2(0, 0);
+    int Dp_n = 0;
+    uint32_t pw_n = 0u;
+    if (gpar >= 0) sc_n = t.nsc[gpar], Dp_n = t.ninfo[gpar].x, pw_n = t.nocc[gpar];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     Pair S[NS];
 #pragma unroll
@@ -691,6 +702,11 @@ __global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
     }
     x = par;
     nx = sc.y;
+    own = pw;
+    par = gpar;
+    sc = sc_n;
+    Dp = Dp_n;
+    pw = pw_n;
   }
 }
 
