@@ -71,3 +71,27 @@ def test_walk_split_option_checked():
     with pytest.raises(Exception):
         gs.set_option("bh_walk_split", 3)
     gs.set_option("bh_walk_split", 0)
+
+
+@pytest.mark.parametrize("cap", [0, 9])
+def test_walk_split_forest_bit_exact(cap):
+    """A forest of several subjects (batched Barnes-Hut) gives the same
+    energies and gradients with one or two walk lists per slice."""
+    specs = [("slab", 1200, 51), ("blobs", 700, 52), ("slab", 3, 53), ("ellipsoid", 513, 54)]
+    ws = []
+    for k, (g, n, seed) in enumerate(specs):
+        w = inputs.make(g, n, seed, T=3, sigma=2.0)
+        w.q0, w.X = w.q0 + 100.0 * k, w.X + 100.0 * k
+        ws.append(w)
+    q0 = np.concatenate([w.q0 for w in ws])
+    p0 = np.concatenate([w.p0 for w in ws])
+    X = np.concatenate([w.X for w in ws])
+    off = np.cumsum([0] + [len(w.q0) for w in ws])
+
+    def run():
+        return gs.shoot_batched(dt(q0), dt(p0), dt(X), off, 2.0, 3, 1.0, mode="bh")
+
+    one = _run_split(1, cap, run)
+    two = _run_split(2, cap, run)
+    for a, b in zip(one, two):
+        assert torch.equal(a, b)
