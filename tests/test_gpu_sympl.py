@@ -26,16 +26,19 @@ def test_zero_passes_is_explicit_euler(mode):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("mode,geom,n,seed,M", [("exact", "blobs", 1500, 3, 2),
-                                                ("exact", "slab", 2000, 4, 3),
-                                                ("bh", "blobs", 3000, 7, 2),
-                                                ("bh", "sphere", 3000, 6, 1)])
-def test_sympl_matches_oracle(oracle, mode, geom, n, seed, M):
+@pytest.mark.parametrize("mode,geom,n,seed,M,leaf", [("exact", "blobs", 1500, 3, 2, 1),
+                                                     ("exact", "slab", 2000, 4, 3, 1),
+                                                     ("bh", "blobs", 3000, 7, 2, 1),
+                                                     ("bh", "sphere", 3000, 6, 1, 1),
+                                                     ("bh", "blobs", 2500, 8, 2, 8),
+                                                     ("trunc", "blobs", 2000, 9, 2, 1)])
+def test_sympl_matches_oracle(oracle, mode, geom, n, seed, M, leaf):
     w = inputs.make(geom, n, seed)
     T = 8
-    q1, p1, H = gs.shoot(dt(w.q0), dt(w.p0), w.sigma, T, mode=mode, with_H=True, sympl_iters=M)
-    q1o, p1o, Ho = oracle.shoot_sympl(w.q0, w.p0, w.sigma, T, M,
-                                      mode=oracle.BH if mode == "bh" else oracle.EXACT)
+    q1, p1, H = gs.shoot(dt(w.q0), dt(w.p0), w.sigma, T, mode=mode, with_H=True, sympl_iters=M,
+                         leaf_size=leaf)
+    omode = {"exact": oracle.EXACT, "bh": oracle.BH, "trunc": oracle.TRUNC}[mode]
+    q1o, p1o, Ho = oracle.shoot_sympl(w.q0, w.p0, w.sigma, T, M, mode=omode, leaf=leaf)
     dq = np.abs(npy(q1) - q1o).max() / w.sigma
     dp = np.abs(npy(p1) - p1o).max() / np.abs(p1o).max()
     eH = np.abs(npy(H) - Ho).max() / abs(Ho[0])
