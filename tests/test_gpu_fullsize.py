@@ -104,3 +104,26 @@ def test_exact_gradient_slab20k(oracle):
     print(f"\nexact gradient at N=20k, T={T}: max|dq1|/sigma {dq:.2e} (tol 1e-5), grad rel L2 "
           f"{eg:.2e} (tol 1e-4), E rel {eE:.2e}")
     assert dq <= 1e-5 and eg <= 1e-4 and eE <= 1e-6
+
+
+def test_exact_rhs_sampled_rows_1m(oracle):
+    """The exact forward and adjoint right-hand sides at the largest workload
+    (sphere1m, N = 1,000,000: 10^12 pairs per launch), 200 sampled rows
+    against the oracle's FP64 sums over all sources."""
+    v = inputs.config("sphere1m")
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(v.N, 200, replace=False))
+    rows[-1] = v.N - 1
+    F, Phi, _ = gs.rhs(dt(v.q0), dt(v.p0), v.sigma)
+    Fo, Phio = oracle.rhs_rows(v.q0, v.p0, v.sigma, rows)
+    eF = np.abs(npy(F)[rows] - Fo).max() / np.abs(Fo).max()
+    eP = np.abs(npy(Phi)[rows] - Phio).max() / np.abs(Phio).max()
+    al = rng.normal(size=v.q0.shape)
+    be = rng.normal(scale=0.1, size=v.q0.shape)
+    dA, dB, _ = gs.adj_rhs(dt(v.q0), dt(v.p0), dt(al), dt(be), v.sigma)
+    dAo, dBo = oracle.adj_rhs_rows(v.q0, v.p0, al, be, v.sigma, rows)
+    eA = np.abs(npy(dA)[rows] - dAo).max() / np.abs(dAo).max()
+    eB = np.abs(npy(dB)[rows] - dBo).max() / np.abs(dBo).max()
+    print(f"\nexact RHS at N=1M, 200 rows: F {eF:.2e}, Phi {eP:.2e}, dA {eA:.2e}, dB {eB:.2e} "
+          f"(tol 1e-5)")
+    assert max(eF, eP, eA, eB) <= 1e-5
