@@ -397,7 +397,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       const int cn = (bottom || bucket) ? ncount : 0;
       // stop before x (state unchanged) when the sink is full
       if (!sink.fits((ms ? 1 : 0) + cn)) return false;
-      if (ms) sink.add(x, 1, ms, false);
+      if (ms) sink.add1(x, ms);
       if (bottom) sink.add(x + 1, cn, mo, false);
       if (bucket) sink.add(t.ninfo[x].y, cn, mo, true);
       if (COUNT && !(VAR && trunc)) nn += __popc(mt), np += (long long)__popc(mo) * cn;
@@ -458,6 +458,16 @@ struct ListSink {
     const int rest = c2 - BH_CHUNK;
     if (lane < rest) buf[lane] = make_int2(enc((n - rest) + lane), (int)mask);
     cnt = rest;
+  }
+  // one entry (a far node: the most frequent case), written by lane 0
+  __device__ __forceinline__ void add1(int node, unsigned mask) {
+    if (ovf) return;
+    if (lane == 0) buf[cnt] = make_int2(node, (int)mask);
+    if (++cnt < BH_CHUNK) return;
+    __syncwarp();
+    put_chunk(BH_CHUNK);
+    __syncwarp();
+    cnt = 0;
   }
   __device__ __forceinline__ void finish() {
     __syncwarp();
@@ -660,6 +670,7 @@ struct EvalSink {
     __syncwarp();
     cnt = 0;
   }
+  __device__ __forceinline__ void add1(int node, unsigned mk) { add(node, 1, mk, false); }
   __device__ __forceinline__ void add(int node0, int n, unsigned mk, bool points) {
     while (n > 0) {
       const int take = min(n, TR_CAP - cnt);
