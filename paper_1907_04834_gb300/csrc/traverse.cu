@@ -372,7 +372,8 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       const unsigned mk = __ballot_sync(FULL, resume <= x);
       if (mk) {
         if (!sink.fits(r)) return false;
-        sink.add(x, r, mk, false);
+        if (r == 1) sink.add1(x, mk);
+        else sink.add(x, r, mk, false);
         if (COUNT && !(VAR && trunc)) np += (long long)__popc(mk) * r;
       }
       x += r;
