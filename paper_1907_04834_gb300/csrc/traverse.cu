@@ -742,10 +742,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 
 // Longest-first orders of the walk lists (worder, and *worder_n = nw) and of
 // the nw / ws slices (order; a slice's length is that of its ws walk lists
-// together): one block, a counting sort on length classes of about 12% width
-// (the leading bit and the three below it: 8 classes per octave, monotone in
-// the length).  Items of one class land in any order; every item appears
-// once.
+// together): one block each, a counting sort on length classes of about 12%
+// width (the leading bit and the three below it: 8 classes per octave,
+// monotone in the length).  Items of one class land in any order; every item
+// appears once.
 constexpr int kOrderThreads = 1024, kOrderClasses = 256;
 __device__ __forceinline__ int len_class(int v) {
   if (v < 16) return max(v, 0);
@@ -773,34 +773,24 @@ __device__ void exclusive_scan_warp(int* cnt, int lane) {  // kOrderClasses coun
 __global__ void __launch_bounds__(kOrderThreads)
     k_list_order(const int* __restrict__ len, int nw, int ws, int* order, int* worder,
                  int* worder_n) {
-  __shared__ int s_w[kOrderClasses], s_s[kOrderClasses];  // walk lists, slices
-  const int tid = threadIdx.x, ns = nw / ws;
-  for (int b = tid; b < kOrderClasses; b += kOrderThreads) s_w[b] = 0, s_s[b] = 0;
+  __shared__ int s_c[kOrderClasses];
+  const int tid = threadIdx.x;
+  const bool slices = blockIdx.x == 1;  // block 0: the walk lists, block 1: the slices
+  const int n = slices ? nw / ws : nw, per = slices ? ws : 1;
+  int* out = slices ? order : worder;
+  for (int b = tid; b < kOrderClasses; b += kOrderThreads) s_c[b] = 0;
   __syncthreads();
-  // class index kOrderClasses - 1 - class: longest first
-  for (int e = tid; e < ns; e += kOrderThreads) {
+  auto cls = [&](int e) {  // class index kOrderClasses - 1 - class: longest first
     int v = 0;
-    for (int j = 0; j < ws; j++) {
-      const int lj = len[e * ws + j];
-      atomicAdd(&s_w[kOrderClasses - 1 - len_class(lj)], 1);
-      v += lj;
-    }
-    atomicAdd(&s_s[kOrderClasses - 1 - len_class(v)], 1);
-  }
+    for (int j = 0; j < per; j++) v += len[e * per + j];
+    return kOrderClasses - 1 - len_class(v);
+  };
+  for (int e = tid; e < n; e += kOrderThreads) atomicAdd(&s_c[cls(e)], 1);
   __syncthreads();
-  if (tid < 32) exclusive_scan_warp(s_w, tid);
-  else if (tid < 64) exclusive_scan_warp(s_s, tid - 32);
+  if (tid < 32) exclusive_scan_warp(s_c, tid);
   __syncthreads();
-  for (int e = tid; e < ns; e += kOrderThreads) {
-    int v = 0;
-    for (int j = 0; j < ws; j++) {
-      const int lj = len[e * ws + j];
-      worder[atomicAdd(&s_w[kOrderClasses - 1 - len_class(lj)], 1)] = e * ws + j;
-      v += lj;
-    }
-    order[atomicAdd(&s_s[kOrderClasses - 1 - len_class(v)], 1)] = e;
-  }
-  if (tid == 0) *worder_n = nw;
+  for (int e = tid; e < n; e += kOrderThreads) out[atomicAdd(&s_c[cls(e)], 1)] = e;
+  if (!slices && tid == 0) *worder_n = nw;
 }
 
 inline unsigned warp_blocks(int64_t warps) { return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS); }
@@ -824,7 +814,7 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
   else
     k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   if (scheduled)
-    k_list_order<<<1, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
+    k_list_order<<<2, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
                                               L.worder_n);
   note_launches(scheduled ? 2 : 1);
   return cudaGetLastError();
