@@ -62,6 +62,7 @@ def _load():
                                        _f64p, _f64p]
     lib.gsref_shoot.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, cint, _f64p,
                                 _f64p, _f64p]
+    lib.gsref_shoot_rk4.argtypes = [i64, _f64p, _f64p, dbl, cint, _f64p, _f64p]
     lib.gsref_shoot_sympl.argtypes = [i64, _f64p, _f64p, dbl, cint, cint, dbl, cint, cint, cint,
                                       _f64p, _f64p, _f64p]
     lib.gsref_shoot_grad.argtypes = [i64, _f64p, _f64p, _f64p, dbl, cint, dbl, cint, dbl, cint,
@@ -164,6 +165,15 @@ def shoot(q0, p0, sigma, T, mode=EXACT, thresh=3.0, leaf=1, crit=0):
     _load().gsref_shoot(q0.shape[0], q0, p0, float(sigma), int(T), int(mode), float(thresh),
                         int(leaf), int(crit), q1, p1, H)
     return q1, p1, H
+
+
+def shoot_rk4(q0, p0, sigma, T):
+    """Exact-kernel shooting by classical RK4 (a check of the right-hand side,
+    not a scheme of the method): q(1), p(1)."""
+    q0, p0 = _c(q0), _c(p0)
+    q1, p1 = np.empty_like(q0), np.empty_like(q0)
+    _load().gsref_shoot_rk4(q0.shape[0], q0, p0, float(sigma), int(T), q1, p1)
+    return q1, p1
 
 
 def shoot_sympl(q0, p0, sigma, T, iters, mode=EXACT, thresh=3.0, leaf=1, crit=0):

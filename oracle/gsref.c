@@ -680,6 +680,41 @@ void gsref_shoot(int64_t N, const double *q0, const double *p0, double sigma,
   free(Phi);
 }
 
+/* Classical fourth-order Runge-Kutta shooting (test infrastructure for the
+ * right-hand side: its trajectories converge at fourth order to the exact
+ * flow, so an error in F or Phi shows as a lost order; not a scheme of the
+ * method).  h = 1/T; k1 = f(y), k2 = f(y + h/2 k1), k3 = f(y + h/2 k2),
+ * k4 = f(y + h k3), y += h/6 (k1 + 2 k2 + 2 k3 + k4), f = (F, Phi). */
+void gsref_shoot_rk4(int64_t N, const double *q0, const double *p0, double sigma, int T,
+                     double *q1, double *p1) {
+  size_t sz = (size_t)N * 3;
+  double *kq = (double *)malloc(4 * sz * sizeof(double));
+  double *kp = (double *)malloc(4 * sz * sizeof(double));
+  double *yq = (double *)malloc(sz * sizeof(double));
+  double *yp = (double *)malloc(sz * sizeof(double));
+  double h = 1.0 / (double)T;
+  const double c[4] = {0.0, 0.5, 0.5, 1.0};
+  memcpy(q1, q0, sz * sizeof(double));
+  memcpy(p1, p0, sz * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    for (int s = 0; s < 4; s++) {
+      for (size_t i = 0; i < sz; i++) {
+        yq[i] = s ? q1[i] + c[s] * h * kq[(size_t)(s - 1) * sz + i] : q1[i];
+        yp[i] = s ? p1[i] + c[s] * h * kp[(size_t)(s - 1) * sz + i] : p1[i];
+      }
+      gsref_rhs(N, yq, yp, sigma, 0, 0.0, 1, 0, kq + (size_t)s * sz, kp + (size_t)s * sz, NULL);
+    }
+    for (size_t i = 0; i < sz; i++) {
+      q1[i] += h / 6.0 * (kq[i] + 2.0 * kq[sz + i] + 2.0 * kq[2 * sz + i] + kq[3 * sz + i]);
+      p1[i] += h / 6.0 * (kp[i] + 2.0 * kp[sz + i] + 2.0 * kp[2 * sz + i] + kp[3 * sz + i]);
+    }
+  }
+  free(kq);
+  free(kp);
+  free(yq);
+  free(yp);
+}
+
 /* Semi-implicit symplectic Euler (a variant of the time discretisation, not
  * the paper's scheme; its Sec. 2.1 only says the flow is discretised in
  * time).  H is not separable (K depends on q), so the symplectic Euler step

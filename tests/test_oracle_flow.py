@@ -202,3 +202,30 @@ def test_angular_momentum(oracle):
         drift.append(np.abs(np.cross(q1, p1).sum(axis=0) - L0).max())
     ratios = [drift[k] / drift[k + 1] for k in range(2)]
     assert all(1.8 < x < 2.2 for x in ratios), (drift, ratios)
+
+
+def test_rk4_converges_at_fourth_order(oracle):
+    """The right-hand side integrated by classical RK4 converges to an
+    adaptive 8th-order solution of the symbolic field at fourth order (error
+    ratio about 16 per halving of h): F and Phi are Hamilton's vector field to
+    well below the Euler tests' resolution."""
+    integ = pytest.importorskip("scipy.integrate")
+    n, sigma = 3, 1.0
+    field, _ = _sympy_field(n, sigma)
+    rng = np.random.default_rng(17)
+    q0 = rng.normal(scale=0.8, size=(n, 3))
+    p0 = rng.normal(scale=0.6, size=(n, 3))
+
+    def f(_t, y):
+        a, b = field(y[: 3 * n].reshape(n, 3), y[3 * n:].reshape(n, 3))
+        return np.concatenate([a.ravel(), b.ravel()])
+
+    sol = integ.solve_ivp(f, (0.0, 1.0), np.concatenate([q0.ravel(), p0.ravel()]),
+                          method="DOP853", rtol=1e-13, atol=1e-13)
+    y_true = sol.y[:, -1]
+    errs = []
+    for T in (8, 16, 32):
+        q1, p1 = oracle.shoot_rk4(q0, p0, sigma, T)
+        errs.append(np.abs(np.concatenate([q1.ravel(), p1.ravel()]) - y_true).max())
+    ratios = [errs[k] / errs[k + 1] for k in range(2)]
+    assert all(13.0 < r < 19.0 for r in ratios), (errs, ratios)
