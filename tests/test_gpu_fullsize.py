@@ -127,3 +127,18 @@ def test_exact_rhs_sampled_rows_1m(oracle):
     print(f"\nexact RHS at N=1M, 200 rows: F {eF:.2e}, Phi {eP:.2e}, dA {eA:.2e}, dB {eB:.2e} "
           f"(tol 1e-5)")
     assert max(eF, eP, eA, eB) <= 1e-5
+
+
+def test_bh_rhs_1m(oracle):
+    """The Barnes-Hut forward right-hand side at the largest workload
+    (sphere1m, N = 1,000,000) against the oracle's pointer-tree traversal:
+    the same decisions (interaction counts equal) and values to FP32
+    rounding."""
+    v = inputs.config("sphere1m")
+    F, Phi, cnt = gs.rhs(dt(v.q0), dt(v.p0), v.sigma, mode="bh")
+    Fo, Phio, cnto = oracle.rhs(v.q0, v.p0, v.sigma, mode=oracle.BH)
+    assert tuple(cnt) == tuple(int(c) for c in cnto)
+    eF = np.abs(npy(F) - Fo).max() / np.abs(Fo).max()
+    eP = np.abs(npy(Phi) - Phio).max() / np.abs(Phio).max()
+    print(f"\nBH RHS at N=1M: counts {tuple(cnt)}; F {eF:.2e}, Phi {eP:.2e} (tol 1e-5)")
+    assert max(eF, eP) <= 1e-5
