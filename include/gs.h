@@ -122,6 +122,14 @@ const char *gs_last_error(const gs_ctx *ctx);
 /* Waits for `stream`, then returns and clears the device status word. */
 gs_status gs_sync(gs_ctx *ctx, void *stream);
 
+/* Failure-detection self-test.  Runs one kernel whose bounded device-side
+ * wait (the one the bulk-copy pipelines use) cannot complete: it waits on a
+ * barrier nothing arrives at, gives up after about 2e6 SM clocks (about 1 ms)
+ * and records a timeout in the context's status word; the call then
+ * synchronises `stream` and returns GS_ERR_TIMEOUT.  The context stays
+ * usable: no trap, no fault, the status word is cleared. */
+gs_status gs_selftest_timeout(gs_ctx *ctx, void *stream);
+
 /*
  * Geodesic shooting (Sec. 2.1 Eq. 1, Euler with T steps; GS_BH: Sec. 2.2 at
  * every step).  q0, p0: N x 3 inputs.  q1, p1: N x 3 outputs q(1), p(1)

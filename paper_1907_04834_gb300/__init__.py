@@ -11,7 +11,7 @@ _API = ("shoot", "shoot_grad", "shoot_batched", "descend_batched", "lbfgs", "aut
         "rhs",
         "adj_rhs", "tree",
         "energy", "GeodesicShoot", "Context", "context", "GSError", "timing", "timing_read",
-        "alu_peaks", "set_option")
+        "alu_peaks", "set_option", "selftest_timeout")
 
 
 def __getattr__(name):

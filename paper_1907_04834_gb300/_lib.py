@@ -53,6 +53,7 @@ _SIGS = {
     "gs_destroy": (None, [_vp]),
     "gs_last_error": (ctypes.c_char_p, [_vp]),
     "gs_sync": (ctypes.c_int, [_vp, _vp]),
+    "gs_selftest_timeout": (ctypes.c_int, [_vp, _vp]),
     "gs_shoot": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp, _vp]),
     "gs_shoot_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp,
                                      _vp, _vp]),

@@ -298,6 +298,14 @@ def set_option(name: str, value: int, device: int | None = None):
     c.check(c.lib.gs_set_option(c.handle, name.encode(), int(value)))
 
 
+def selftest_timeout(device: int | None = None, stream=None):
+    """Failure-detection self-test (gs_selftest_timeout): a device-side
+    bounded wait that cannot complete must give up and report GS_ERR_TIMEOUT;
+    raises GSError with that status when it does."""
+    c = context(device)
+    c.check(c.lib.gs_selftest_timeout(c.handle, _stream_ptr(c.device, stream)))
+
+
 def timing(enable: bool = True, device: int | None = None):
     """Turns per-kernel-class event timing on or off (see gs_timing)."""
     c = context(device)

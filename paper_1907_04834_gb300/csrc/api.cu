@@ -1202,6 +1202,15 @@ gs_status gs_sync(gs_ctx* c, void* stream) {
   return read_status(c, (cudaStream_t)stream);
 }
 
+gs_status gs_selftest_timeout(gs_ctx* c, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_wait_selftest(c->d_status, 2000000LL, st), "self-test kernel");
+  return read_status(c, st);
+}
+
 gs_status gs_shoot(gs_ctx* c, const double* q0, const double* p0, int64_t N,
                    const gs_params* prm, double* q1, double* p1, double* H, void* stream) {
   if (!c) return GS_ERR_INVALID_ARG;

@@ -106,6 +106,8 @@ cudaError_t launch_pack(const double* q, const double* p, int64_t N, const doubl
 // zero the padding points [N, Npad) of `slots` consecutive packs
 cudaError_t launch_pad_zero(float4* base, size_t slot_f4, int slots, int64_t N, int64_t Npad,
                             cudaStream_t st);
+// failure-detection self-test: a bounded wait that cannot complete (ST_TIMEOUT)
+cudaError_t launch_wait_selftest(int* status, long long limit, cudaStream_t st);
 // adjoint pack of (alpha, mu beta) as FP32 (mu = adj_beta_scale(s))
 cudaError_t launch_pack_ab(const double* al, const double* be, int64_t N, double mu,
                            float4* abpack, cudaStream_t st);

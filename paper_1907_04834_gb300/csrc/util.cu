@@ -75,6 +75,20 @@ __global__ void k_bbox_fin(const double* __restrict__ part, int G, double* cente
     for (int a = 0; a < 3; a++) center[a] = 0.5 * (lo[a] + hi[a]);
 }
 
+// Failure-detection self-test: one thread waits, with the bounded wait the
+// bulk-copy pipelines use, on an mbarrier that nothing arrives at.  The wait
+// gives up after `limit` SM clocks and records ST_TIMEOUT in the status word,
+// exactly as a wait on a copy that never lands would; the kernel then ends.
+__global__ void k_wait_selftest(int* status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) (void)mbar_wait_bounded(&bar, 0u, status, limit);
+}
+
 __global__ void k_pack(const double* __restrict__ q, const double* __restrict__ p, int64_t N,
                        const double* __restrict__ center, double s, float4* pack, float4* raw) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,6 +385,12 @@ cudaError_t launch_bbox_center(const double* q, int64_t N, double* center, doubl
   k_bbox_part<<<G, kBoxThreads, 0, st>>>(q, N, part);
   k_bbox_fin<<<1, 32, 0, st>>>(part, G, center);
   note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int* status, long long limit, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(status, limit);
+  note_launches(1);
   return cudaGetLastError();
 }
 
