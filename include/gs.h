@@ -22,6 +22,8 @@
  *     the layout of a contiguous (N, 3) tensor.  Each pointer may be host or
  *     device memory (detected per pointer with cudaPointerGetAttributes);
  *     device pointers must be on the context's device.  Inputs are only read.
+ *   - Point counts N are in [1, 2^30]; an empty set (N = 0) or a larger one
+ *     returns GS_ERR_INVALID_ARG before any work is enqueued.
  *     The caller owns all inputs and outputs; the context owns its workspace
  *     (grown on demand, reused across calls, freed by gs_destroy).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default

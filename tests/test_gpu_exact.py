@@ -10,6 +10,7 @@ import torch
 
 import paper_1907_04834_gb300 as gs
 from paper_1907_04834_gb300 import inputs
+from paper_1907_04834_gb300._lib import GS_ERR_INVALID_ARG
 from gpu_util import dt, npy, max_rel, rel_l2, phi_floor
 
 pytestmark = pytest.mark.gpu
@@ -137,5 +138,13 @@ def test_invalid_arguments_raise():
         gs.shoot(dt(w.q0), dt(w.p0), -1.0, 4)
     with pytest.raises(gs.GSError):
         gs.shoot(dt(w.q0), dt(w.p0), 1.0, 0)
+    empty = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    for mode in ("exact", "bh"):
+        with pytest.raises(gs.GSError) as ei:
+            gs.shoot(empty, empty, 1.0, 4, mode=mode)
+        assert ei.value.status == GS_ERR_INVALID_ARG
+        with pytest.raises(gs.GSError) as ei:
+            gs.shoot_grad(empty, empty, empty, 1.0, 4, mode=mode)
+        assert ei.value.status == GS_ERR_INVALID_ARG
     with pytest.raises(gs.GSError):
         gs.shoot_grad(dt(w.q0), dt(w.p0), dt(w.X), 1.0, 4, lam=-1.0)
