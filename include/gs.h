@@ -82,7 +82,8 @@ typedef struct gs_params {
   int32_t mode;          /* gs_mode */
   int32_t ckpt_every;    /* gs_shoot_grad: 0 = keep every step's state for the
                             backward pass; k > 0 = keep every k-th state and
-                            recompute the others (memory (T/k + k) x N) */
+                            recompute the others (memory (T/k + k) x N);
+                            -1 = k = round(sqrt(T)), which minimises T/k + k */
   uint32_t flags;        /* reserved, must be 0 */
   int32_t leaf_size;     /* GS_BH: 0 or 1 = the paper's rule (a leaf is one
                             point, every near node is opened); L in [2, 32] =
@@ -231,6 +232,28 @@ gs_status gs_autotune(gs_ctx *ctx, const double *q, const double *p, int64_t N,
                       const gs_params *prm, const int32_t *cand, int32_t n_cand,
                       int32_t *best, double *ms, void *stream);
 
+/*
+ * Autotuner of the exact kernels' tile shape for a state (q, p) of N points
+ * (prm: GS_EXACT and its sigma).  A block of the all-pairs kernels owns 256
+ * targets and sweeps 1/J of the sources (512-source tiles); J, the number of
+ * source splits, is the one tile dimension chosen at run time.  For each
+ * candidate J it times one forward and one adjoint right-hand side (CUDA
+ * events on the stream, best of three after a warm-up) and writes the
+ * fastest J of each to best[0] (forward) and best[1] (adjoint), as applied:
+ * a candidate above the number of source tiles, ceil(N / 512), acts as that
+ * number.  cand: n_cand values in [1, 4096] (n_cand <= 64), or NULL for
+ * {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}; ms: NULL or 2 x n_cand times in
+ * milliseconds (forward, adjoint per candidate).  J changes the order in which
+ * the FP32 tile partials are combined, so results move by rounding only; the
+ * choice is the caller's (gs_set_option "exact_splits_fwd" and
+ * "exact_splits_adj"), never applied by the library.  Synchronises the
+ * stream.
+ */
+gs_status gs_autotune_exact(gs_ctx *ctx, const double *q, const double *p,
+                            int64_t N, const gs_params *prm,
+                            const int32_t *cand, int32_t n_cand, int32_t *best,
+                            double *ms, void *stream);
+
 /* ---- single-step entry points (one right-hand side, for checks) ---------- */
 
 /* Velocity field of Eq. 3 at M >= 1 points x (M x 3): v = sum_i G(|x - q_i|)
@@ -286,6 +309,11 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
  *   of 32 points has four slices): 1 or 2, or 0 (default) = 2 for trees of
  *   fewer than 48 x (SM count) groups, else 1.  Splitting spreads a small
  *   tree's walk over more warps; results are bit-identical either way.
+ *   "exact_splits_fwd", "exact_splits_adj": source splits J of the exact
+ *   single-point-set forward and adjoint kernels (gs_autotune_exact), in
+ *   [1, 4096], capped at ceil(N / 512); 0 (default) = the built-in choice
+ *   (the J that fills whole waves of blocks over the SMs).  Partial sums
+ *   take J x 9 x N x 8 bytes of workspace.
  *   "graphs": 1 (default) = gs_shoot, gs_shoot_grad, gs_shoot_batched and
  *   gs_descend_batched capture their step loop (every launch between the
  *   input staging and the result copies) into a CUDA graph the first time

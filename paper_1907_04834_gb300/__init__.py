@@ -6,7 +6,8 @@ re-exported here are thin tensor wrappers around its entry points.  Importing
 the package does not load CUDA; the first call does, and it fails loudly if
 the library has not been built.
 """
-_API = ("shoot", "shoot_grad", "shoot_batched", "descend_batched", "lbfgs", "autotune", "flow",
+_API = ("shoot", "shoot_grad", "shoot_batched", "descend_batched", "lbfgs", "autotune",
+        "autotune_exact", "flow",
         "velocity",
         "rhs",
         "adj_rhs", "tree",

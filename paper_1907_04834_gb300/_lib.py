@@ -65,6 +65,8 @@ _SIGS = {
                                 ctypes.c_double, _vp, _vp, _vp]),
     "gs_autotune": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _i32, _vp,
                                    _vp, _vp]),
+    "gs_autotune_exact": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _i32,
+                                         _vp, _vp, _vp]),
     "gs_flow": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp, _vp,
                                _vp, _vp]),
     "gs_velocity": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(Params), _vp,

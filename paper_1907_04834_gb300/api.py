@@ -211,6 +211,25 @@ def autotune(q, p, sigma, thresh=3.0, candidates=(1, 2, 4, 8, 16, 32), stream=No
     return best.value, {int(v): ms[k] for k, v in enumerate(candidates)}
 
 
+def autotune_exact(q, p, sigma, candidates=(1, 2, 3, 4, 6, 8, 12, 16, 24, 32), stream=None):
+    """Source splits J of the exact forward and adjoint kernels that run one
+    right-hand side each fastest on state (q, p) (gs_autotune_exact).
+    Returns ((J_fwd, J_adj), {J: (fwd ms, adj ms)}); apply with
+    set_option("exact_splits_fwd", J_fwd) and set_option("exact_splits_adj", J_adj)."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    p = _pts(p, "p", n)
+    c = _ctx_for(q)
+    prm = make_params(sigma, 1, "exact", 0.0)
+    cand = (ctypes.c_int32 * len(candidates))(*[int(v) for v in candidates])
+    ms = (ctypes.c_double * (2 * len(candidates)))()
+    best = (ctypes.c_int32 * 2)()
+    c.check(c.lib.gs_autotune_exact(c.handle, _ptr(q), _ptr(p), n, ctypes.byref(prm), cand,
+                                    len(candidates), best, ms, _stream_ptr(c.device, stream)))
+    return (best[0], best[1]), {int(v): (ms[2 * k], ms[2 * k + 1])
+                                for k, v in enumerate(candidates)}
+
+
 def flow(q0, p0, x0, sigma, T, mode="exact", thresh=3.0, leaf_size=1, criterion=0,
          stream=None):
     """Shooting that carries tracer points x0 (M, 3) through the velocity

@@ -56,6 +56,9 @@ struct gs_ctx {
   long long launch_mark = 0;
   int device = 0;
   int num_sms = 0;
+  // source splits of the exact single-set kernels (gs_set_option
+  // "exact_splits_fwd" / "exact_splits_adj"; 0 = choose_J)
+  int xs_fwd = 0, xs_adj = 0;
   std::string err;
   int* d_status = nullptr;  // device status word (ST_* bits)
   // staging of host inputs / outputs
@@ -181,7 +184,7 @@ struct Key {
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
-    add(c->tree.wsplit_req);
+    add(c->tree.wsplit_req), add(c->xs_fwd), add(c->xs_adj);
   }
 };
 
@@ -237,8 +240,8 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda,
     return fail(c, GS_ERR_INVALID_ARG, "thresh_sigmas must be > 0 (got %g)", prm->thresh_sigmas);
   if (need_lambda && (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda)))
     return fail(c, GS_ERR_INVALID_ARG, "lambda must be finite and >= 0 (got %g)", prm->lambda);
-  if (prm->ckpt_every < 0)
-    return fail(c, GS_ERR_INVALID_ARG, "ckpt_every must be >= 0 (got %d)", prm->ckpt_every);
+  if (prm->ckpt_every < -1)
+    return fail(c, GS_ERR_INVALID_ARG, "ckpt_every must be >= -1 (got %d)", prm->ckpt_every);
   if (prm->flags != 0) return fail(c, GS_ERR_INVALID_ARG, "flags must be 0");
   if (prm->leaf_size < 0 || prm->leaf_size > 32)
     return fail(c, GS_ERR_INVALID_ARG, "leaf_size must be in [0, 32] (got %d)", prm->leaf_size);
@@ -484,6 +487,8 @@ gs_status batch_take_queue(gs_ctx* c, Batch& b, BatchInfo* bi) {
   return GS_OK;
 }
 
+constexpr int kMaxSplits = 4096;  // source splits an option or the autotuner may ask for
+
 int choose_J(int n_itiles, int n_jtiles, int slots) {
   // smallest J giving >= 2 full waves, then the J (up to 4 waves) whose last
   // wave is fullest
@@ -549,9 +554,11 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
   g.Npad = S.Npad;
   g.n_itiles = (int)(S.Npad / EX_NT);
   g.n_jtiles = (int)(S.Npad / EX_TILE);
-  g.J = choose_J(g.n_itiles, g.n_jtiles, 3 * c->num_sms);
+  g.J = c->xs_fwd > 0 ? std::min(c->xs_fwd, g.n_jtiles)
+                      : choose_J(g.n_itiles, g.n_jtiles, 3 * c->num_sms);
   S.gf = g;
-  g.J = choose_J(g.n_itiles, g.n_jtiles, 2 * c->num_sms);
+  g.J = c->xs_adj > 0 ? std::min(c->xs_adj, g.n_jtiles)
+                      : choose_J(g.n_itiles, g.n_jtiles, 2 * c->num_sms);
   S.ga = g;
   const size_t n3 = (size_t)N * 3;
   CK(c->q.ensure(n3 * 8), "workspace");
@@ -810,7 +817,11 @@ gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, c
   gs_status s;
   R.batch = batch;
   R.T = prm->T;
-  R.ck = prm->ckpt_every > 0 && prm->ckpt_every < R.T ? prm->ckpt_every : 0;
+  // -1: every round(sqrt(T))-th state, the spacing that minimises the kept
+  // states plus a segment's recomputed ones, T/k + k
+  const int ce = prm->ckpt_every < 0 ? std::max(1, (int)std::lround(std::sqrt((double)R.T)))
+                                     : prm->ckpt_every;
+  R.ck = ce > 0 && ce < R.T ? ce : 0;
   // pack slots: every step (store-all) or one segment (checkpointing)
   const int slots = R.ck ? R.ck + 1 : R.T + 1;
   // Barnes-Hut: one tree slot per step kept for the backward stage (a
@@ -1157,6 +1168,13 @@ gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
   if (strcmp(name, "graphs") == 0) {
     if (value != 0 && value != 1) return fail(c, GS_ERR_INVALID_ARG, "graphs must be 0 or 1");
     c->graphs = value != 0;
+    return GS_OK;
+  }
+  const bool xf = strcmp(name, "exact_splits_fwd") == 0, xa = strcmp(name, "exact_splits_adj") == 0;
+  if (xf || xa) {
+    if (value < 0 || value > kMaxSplits)
+      return fail(c, GS_ERR_INVALID_ARG, "%s must be in [0, %d]", name, kMaxSplits);
+    (xf ? c->xs_fwd : c->xs_adj) = (int)value;
     return GS_OK;
   }
   return fail(c, GS_ERR_INVALID_ARG, "unknown option '%s'", name);
@@ -1706,6 +1724,93 @@ gs_status gs_autotune(gs_ctx* c, const double* q, const double* p, int64_t N,
   cudaEventDestroy(e1);
   if (rc != GS_OK) return rc;
   *best = best_l;
+  return read_status(c, st);
+}
+
+gs_status gs_autotune_exact(gs_ctx* c, const double* q, const double* p, int64_t N,
+                            const gs_params* prm, const int32_t* cand, int32_t n_cand,
+                            int32_t* best, double* ms, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if (prm->mode != GS_EXACT)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_autotune_exact tunes the exact mode (GS_EXACT)");
+  static const int32_t kDefault[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  if (!cand) {
+    cand = kDefault;
+    n_cand = 10;
+  }
+  if (n_cand < 1 || n_cand > 64) return fail(c, GS_ERR_INVALID_ARG, "n_cand must be in [1, 64]");
+  for (int k = 0; k < n_cand; k++)
+    if (cand[k] < 1 || cand[k] > kMaxSplits)
+      return fail(c, GS_ERR_INVALID_ARG, "candidate splits must be in [1, %d]", kMaxSplits);
+  if (!best) return fail(c, GS_ERR_INVALID_ARG, "best is NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double *dq, *dp;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)))
+    return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0), "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, GS_ERR_CUDA, "event create failed");
+  }
+  // best of three launches after a warm-up
+  auto time_best = [&](auto&& enqueue, float* out) -> gs_status {
+    float bt = 0.f;
+    for (int rep = 0; rep < 4; rep++) {
+      cudaEventRecord(e0, st);
+      if (gs_status r = enqueue()) return r;
+      cudaEventRecord(e1, st);
+      float t = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "autotune timing");
+      if (rep == 1 || (rep > 1 && t < bt)) bt = t;
+    }
+    *out = bt;
+    return GS_OK;
+  };
+  const int keep_f = c->xs_fwd, keep_a = c->xs_adj;
+  const bool was_timing = c->timing;
+  c->timing = false;
+  float bf = 0.f, ba = 0.f;
+  int32_t jf = 1, ja = 1;
+  gs_status rc = GS_OK;
+  for (int k = 0; k < n_cand && rc == GS_OK; k++) {
+    c->xs_fwd = c->xs_adj = cand[k];
+    Solver S;
+    if ((rc = solver_init(c, S, N, prm, 1, true, st))) break;
+    if ((rc = solver_load(S, dq, dp, 0))) break;
+    // adjoint variables zero (their values do not change the work)
+    if (cudaMemsetAsync(c->al.p, 0, (size_t)N * 24, st) != cudaSuccess ||
+        cudaMemsetAsync(c->be.p, 0, (size_t)N * 24, st) != cudaSuccess ||
+        launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, adj_beta_scale(S.s),
+                       S.abpack(0), st) != cudaSuccess) {
+      rc = cuda_fail(c, cudaGetLastError(), "autotune setup");
+      break;
+    }
+    float tf = 0.f, ta = 0.f;
+    if ((rc = time_best([&] { return forward_rhs(S, 0, fwd_epi(S, -1, 0.0), nullptr, 0); }, &tf)))
+      break;
+    if ((rc = time_best(
+             [&] {
+               return adjoint_rhs(S, 0, 0, adj_epi(S, -1, 0.0, false, nullptr), nullptr, 0, true);
+             },
+             &ta)))
+      break;
+    if (ms) ms[2 * k] = tf, ms[2 * k + 1] = ta;
+    if (k == 0 || tf < bf) bf = tf, jf = S.gf.J;
+    if (k == 0 || ta < ba) ba = ta, ja = S.ga.J;
+  }
+  c->xs_fwd = keep_f, c->xs_adj = keep_a;
+  c->timing = was_timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GS_OK) return rc;
+  best[0] = jf, best[1] = ja;
   return read_status(c, st);
 }
 
