@@ -454,6 +454,36 @@ def run_ours(args):
             return statistics.median(ts)
         line["sympl_variant"] = {"passes": 2, "bh_ms_per_shoot": shoot_ms(2),
                                  "explicit_bh_ms_per_shoot": shoot_ms(0)}
+        # tile shape of the exact kernels (source splits J) picked by the
+        # autotuner on the initial state, against the built-in choice: one
+        # plain exact gradient each (J changes rounding only)
+        (jf, ja), jms = gs.autotune_exact(q0, p0, w.sigma)
+
+        def plain_ms():
+            plain_grad()
+            ts = []
+            for _ in range(2):
+                flush.zero_()
+                a_ev = torch.cuda.Event(enable_timing=True)
+                b_ev = torch.cuda.Event(enable_timing=True)
+                a_ev.record()
+                plain_grad()
+                b_ev.record()
+                torch.cuda.synchronize()
+                ts.append(a_ev.elapsed_time(b_ev))
+            return min(ts)
+        builtin_ms = plain_ms()
+        gs.set_option("exact_splits_fwd", jf)
+        gs.set_option("exact_splits_adj", ja)
+        try:
+            tuned_ms = plain_ms()
+        finally:
+            gs.set_option("exact_splits_fwd", 0)
+            gs.set_option("exact_splits_adj", 0)
+        line["exact_tile_variant"] = {
+            "splits_fwd": jf, "splits_adj": ja, "ms_per_gradient": tuned_ms,
+            "builtin_ms_per_gradient": builtin_ms,
+            "autotune_ms_per_fwd_adj_rhs": {str(k): v for k, v in jms.items()}}
     if rank == 0 and args.e2e_steps > 0:
         # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
         h = lambda a: torch.as_tensor(a, dtype=torch.float64).pin_memory()
