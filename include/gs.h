@@ -309,6 +309,13 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
  *   of 32 points has four slices): 1 or 2, or 0 (default) = 2 for trees of
  *   fewer than 48 x (SM count) groups, else 1.  Splitting spreads a small
  *   tree's walk over more warps; results are bit-identical either way.
+ *   "trunc_grid": 1 = GS_TRUNC on one point set searches its pairs with a
+ *   uniform cell grid instead of the octree: cells of side 0.51 r (r =
+ *   thresh_sigmas * sigma; doubled while there would be more than 8 N + 4096
+ *   cells), points sorted stably by cell, and each warp of 32 consecutive
+ *   points sweeps the cells within two of its own.  The kept pairs, and so
+ *   the counts, are the same as the octree's; sums differ by rounding order
+ *   only.  Batched calls keep the octree.  0 (default) = the octree.
  *   "exact_splits_fwd", "exact_splits_adj": source splits J of the exact
  *   single-point-set forward and adjoint kernels (gs_autotune_exact), in
  *   [1, 4096], capped at ceil(N / 512); 0 (default) = the built-in choice

@@ -81,9 +81,11 @@ struct gs_ctx {
   // tracer points of the velocity field (gs_flow, gs_velocity)
   DevMem in_x, xs, xpks, xpart, xtickets, xraws, xsort;
   DevMem lb;  // L-BFGS vectors
+  DevMem grid;  // cell grid of the truncation variant (option "trunc_grid")
   size_t xtickets_n = 0;
   cudaStream_t cap = nullptr;  // capture stream
   bool graphs = true;
+  bool trunc_grid = false;  // GS_TRUNC on one point set: uniform grid, not the octree
   TreeWork tree;  // Barnes-Hut workspace (tree.h)
 };
 
@@ -180,11 +182,11 @@ struct Key {
                             &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
                             &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                             &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                            &c->lb, &c->xraws, &c->xsort})
+                            &c->lb, &c->xraws, &c->xsort, &c->grid})
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
-    add(c->tree.wsplit_req), add(c->xs_fwd), add(c->xs_adj);
+    add(c->tree.wsplit_req), add(c->xs_fwd), add(c->xs_adj), add(c->trunc_grid);
   }
 };
 
@@ -342,6 +344,8 @@ struct Solver {
   int T, mode;
   double sigma, s, h, lambda;
   float thr;  // Barnes-Hut threshold (r*r, FP32)
+  float rcut = 0.f;  // truncation radius r (FP32), grid cell size
+  bool grid = false;  // truncation over the uniform cell grid
   int leaf;   // Barnes-Hut leaf size (1 = the paper's rule)
   int crit;   // far test: 0 the paper's distance rule, 1 opening angle
   int iters = 0;  // fixed-point passes per step (semi-implicit symplectic Euler)
@@ -597,9 +601,13 @@ gs_status solver_init(gs_ctx* c, Solver& S, int64_t N, const gs_params* prm, int
     }
     CK(cudaMemsetAsync(c->tickets.p, 0, tn * sizeof(unsigned), st), "memset");
   } else {
-    gs_status s =
-        tree_reserve(c->tree, N, tree_slots, st, batch ? (int64_t)batch->groups.size() : 0);
+    // the grid variant keeps no trees (one slot holds the pair counters)
+    S.grid = S.mode == GS_TRUNC && c->trunc_grid && !batch;
+    S.rcut = (float)(prm->thresh_sigmas * prm->sigma);
+    gs_status s = tree_reserve(c->tree, N, S.grid ? 1 : tree_slots, st,
+                               batch ? (int64_t)batch->groups.size() : 0);
     if (s != GS_OK) return fail(c, s, "Barnes-Hut workspace allocation failed");
+    if (S.grid) CK(c->grid.ensure(grid_scratch_bytes(N)), "grid workspace");
   }
   return GS_OK;
 }
@@ -692,6 +700,13 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
     }
     return GS_OK;
   }
+  if (S.grid) {
+    KTimer tm(c, GS_K_BH_FWD, S.st);
+    gs_status s = grid_rhs(c->grid.p, S.N, S.raw(slot), S.pack(slot), nullptr, S.rcut, S.thr,
+                           false, e, AdjEpi{}, counts ? c->tree.d_counts : nullptr, S.st);
+    if (s != GS_OK) return fail(c, s, "truncation grid step failed: %s", bh_last_error());
+    return GS_OK;
+  }
   BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
            S.mode == GS_TRUNC, S.crit};
   gs_status s;
@@ -718,7 +733,7 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
 // recomputed before the lists are evaluated.
 gs_status forward_rhs_same_q(Solver& S, int slot, const FwdEpi& e) {
   gs_ctx* c = S.c;
-  if (S.mode == GS_EXACT || S.batch) return forward_rhs(S, slot, e, nullptr);
+  if (S.mode == GS_EXACT || S.batch || S.grid) return forward_rhs(S, slot, e, nullptr);
   BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
            S.mode == GS_TRUNC, S.crit};
   gs_status s;
@@ -774,6 +789,13 @@ gs_status adjoint_rhs(Solver& S, int slot, int ab, const AdjEpi& e, int64_t* cou
       counts[0] = S.N * S.N;
       counts[1] = 0;
     }
+    return GS_OK;
+  }
+  if (S.grid) {  // the grid is rebuilt for the state: it is cheap beside the sums
+    KTimer tm(c, GS_K_BH_ADJ, S.st);
+    gs_status s = grid_rhs(c->grid.p, S.N, S.raw(slot), S.pack(slot), S.abpack(ab), S.rcut,
+                           S.thr, true, FwdEpi{}, e, counts ? c->tree.d_counts : nullptr, S.st);
+    if (s != GS_OK) return fail(c, s, "truncation grid step failed: %s", bh_last_error());
     return GS_OK;
   }
   BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
@@ -1133,7 +1155,7 @@ void gs_destroy(gs_ctx* c) {
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                       &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                      &c->lb, &c->xraws, &c->xsort})
+                      &c->lb, &c->xraws, &c->xsort, &c->grid})
       m->release();
     for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch, &c->g_flow})
       if (gc->exec) cudaGraphExecDestroy(gc->exec);
@@ -1168,6 +1190,11 @@ gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
   if (strcmp(name, "graphs") == 0) {
     if (value != 0 && value != 1) return fail(c, GS_ERR_INVALID_ARG, "graphs must be 0 or 1");
     c->graphs = value != 0;
+    return GS_OK;
+  }
+  if (strcmp(name, "trunc_grid") == 0) {
+    if (value != 0 && value != 1) return fail(c, GS_ERR_INVALID_ARG, "trunc_grid must be 0 or 1");
+    c->trunc_grid = value != 0;
     return GS_OK;
   }
   const bool xf = strcmp(name, "exact_splits_fwd") == 0, xa = strcmp(name, "exact_splits_adj") == 0;

@@ -795,6 +795,115 @@ __global__ void __launch_bounds__(kOrderThreads)
 
 inline unsigned warp_blocks(int64_t warps) { return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS); }
 
+// ------------------------------------------------------------------ grid
+// Truncation over the uniform cell grid.  Warp g takes the sorted points
+// [32 g, 32 g + 32) as targets (consecutive in cell order: nearly always one
+// or two cells) and sweeps the cells within GRID_REACH of the warp's cell
+// range one (z, y) row at a time -- a row of cells is one contiguous range of
+// sorted positions -- staging TR_CAP sources at a time from the packs.  Every
+// staged source carries a full lane mask: the list evaluation's truncation
+// test decides each pair, and counts the kept ones.  Sums in row order, then
+// the epilogue.
+template <bool ADJ>
+__global__ void __launch_bounds__(TR_WARPS * 32)
+    k_grid_eval(GridView gv, int N, const float4* __restrict__ pack,
+                const float4* __restrict__ abpack, const float4* __restrict__ raw, float thr,
+                int64_t* counts, FwdEpi fe, AdjEpi ae) {
+  constexpr int NR = ADJ ? 12 : 6;
+  constexpr int NC = Acc<ADJ>::NC;
+  __shared__ __align__(16) float s_soa[TR_WARPS][(NR + 3) * TR_CAP];
+  __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int first = (blockIdx.x * TR_WARPS + w) * 32;
+  if (first >= N) return;  // the whole warp
+  const int cnt = min(32, N - first);
+  const bool valid = lane < cnt;
+  const int sp = first + (valid ? lane : cnt - 1);
+  const int o = (int)gv.perm[sp];
+  Own me;
+  me.i = sp;
+  me.o = o;
+  me.valid = valid;
+  {
+    float a[3], b[3];
+    pack_read(pack, o, a, b);
+    me.m0 = make_float4(a[0], a[1], a[2], 0.f);
+    me.m1 = make_float4(b[0], b[1], b[2], 0.f);
+    me.m2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    me.m3 = me.m2;
+    if (ADJ) {
+      pack_read(abpack, o, a, b);
+      me.m2 = make_float4(a[0], a[1], a[2], 0.f);
+      me.m3 = make_float4(b[0], b[1], b[2], 0.f);
+    }
+    const float4 r = raw[o];
+    me.rx = r.x, me.ry = r.y, me.rz = r.z;
+  }
+  const int nx = gv.dims[0], ny = gv.dims[1], nz = gv.dims[2];
+  const uint32_t key = gv.key[sp];
+  const unsigned cx = key % (uint32_t)nx, cy = (key / (uint32_t)nx) % (uint32_t)ny,
+                 cz = key / ((uint32_t)nx * (uint32_t)ny);
+  const int x0 = max((int)__reduce_min_sync(FULL, cx) - GRID_REACH, 0);
+  const int x1 = min((int)__reduce_max_sync(FULL, cx) + GRID_REACH, nx - 1);
+  const int y0 = max((int)__reduce_min_sync(FULL, cy) - GRID_REACH, 0);
+  const int y1 = min((int)__reduce_max_sync(FULL, cy) + GRID_REACH, ny - 1);
+  const int z0 = max((int)__reduce_min_sync(FULL, cz) - GRID_REACH, 0);
+  const int z1 = min((int)__reduce_max_sync(FULL, cz) + GRID_REACH, nz - 1);
+  Acc<ADJ> A;
+  A.zero();
+  int npair = 0;
+  float* soa = s_soa[w];
+  unsigned* mask = s_mask[w];
+  for (int z = z0; z <= z1; z++)
+    for (int y = y0; y <= y1; y++) {
+      const int row = (z * ny + y) * nx;  // < C <= 2^30
+      const int s0 = gv.cstart[row + x0], s1 = gv.cstart[row + x1 + 1];
+      for (int b0 = s0; b0 < s1; b0 += TR_CAP) {
+        const int n = min(TR_CAP, s1 - b0);
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) {
+          const int so = (int)gv.perm[b0 + e];
+          float a[3], b[3];
+          pack_read(pack, so, a, b);
+          soa[0 * TR_CAP + e] = a[0], soa[1 * TR_CAP + e] = a[1], soa[2 * TR_CAP + e] = a[2];
+          soa[3 * TR_CAP + e] = b[0], soa[4 * TR_CAP + e] = b[1], soa[5 * TR_CAP + e] = b[2];
+          if (ADJ) {
+            pack_read(abpack, so, a, b);
+            soa[6 * TR_CAP + e] = a[0], soa[7 * TR_CAP + e] = a[1], soa[8 * TR_CAP + e] = a[2];
+            soa[9 * TR_CAP + e] = b[0], soa[10 * TR_CAP + e] = b[1], soa[11 * TR_CAP + e] = b[2];
+          }
+          const float4 r = raw[so];
+          soa[NR * TR_CAP + e] = r.x, soa[(NR + 1) * TR_CAP + e] = r.y;
+          soa[(NR + 2) * TR_CAP + e] = r.z;
+          mask[e] = FULL;
+        }
+        int ne = n;
+        if (n & 1) {  // pad to an even count with an entry no lane takes
+          if (lane == 0) mask[n] = 0u;
+          if (lane < NR + 3) soa[lane * TR_CAP + n] = 0.f;
+          ne++;
+        }
+        __syncwarp();
+        eval_batch<ADJ, true>(A, soa, mask, ne, lane, me, thr, npair);
+      }
+    }
+  if (counts) {
+    long long tot = valid ? npair : 0;
+    for (int d = 16; d > 0; d >>= 1) tot += __shfl_down_sync(FULL, tot, d);
+    if (lane == 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)tot);
+  }
+  if (!valid) return;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    const float2 v = A.K[c].out();
+    acc[c] = (double)v.x + (double)v.y;
+  }
+  if constexpr (!ADJ) fwd_epilogue_at(o, o, fe.center, acc, acc + 3, fe);
+  else adj_epilogue(o, acc, acc + 3, acc + 6, ae);
+}
+
 }  // namespace
 
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
@@ -851,6 +960,19 @@ cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float 
     else eval_launch<true, false>(t, N, raw, thr, L, wg, fe, ae, te, counts, ord, st);
   }
   note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_eval(const GridView& g, int N, const float4* pack, const float4* abpack,
+                             const float4* raw, float thr, bool adj, const FwdEpi& fe,
+                             const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+  const int groups = (N + 31) / 32;
+  const unsigned nb = (unsigned)((groups + TR_WARPS - 1) / TR_WARPS);
+  if (!adj)
+    k_grid_eval<false><<<nb, TR_WARPS * 32, 0, st>>>(g, N, pack, abpack, raw, thr, counts, fe, ae);
+  else
+    k_grid_eval<true><<<nb, TR_WARPS * 32, 0, st>>>(g, N, pack, abpack, raw, thr, counts, fe, ae);
+  note_launches(1);
   return cudaGetLastError();
 }
 

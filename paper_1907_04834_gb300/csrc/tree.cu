@@ -1252,4 +1252,160 @@ gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cons
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
+// ---------------------------------------------------------------- cell grid
+// Uniform grid of the truncation variant.  The FP32 bounding box of the
+// positions; cells of side h = 0.51 r, doubled while the grid would have more
+// than grid_cells(N) cells; cell coordinates k = min(trunc((x - lo) * (1/h)),
+// n - 1) in FP32; a stable radix sort of (cell id, index).  A pair that passes
+// the FP32 truncation test is less than r (1 + 1e-6) apart on every axis,
+// i.e. less than 1.97 cells, so its cells differ by at most GRID_REACH = 2.
+namespace {
+int64_t grid_cells(int64_t N) { return std::min<int64_t>(8 * N + 4096, int64_t(1) << 30); }
+
+struct GridScratch {
+  uint32_t *key, *key2, *perm, *perm2, *hist, *hscan, *bsum;
+  float *part, *geo;
+  int *dims, *cstart;
+};
+
+size_t carve_grid(void* mem, int64_t N, GridScratch* g) {
+  const size_t N1 = (size_t)N + 1, nb = nblocks(N, RS_TILE), hist_n = 256 * nb + 1;
+  const size_t bsum_n = nblocks((int64_t)hist_n, SCAN_TILE) + 1;
+  const size_t C1 = (size_t)grid_cells(N) + 1;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t o_key = take(4 * N1), o_key2 = take(4 * N1), o_perm = take(4 * N1),
+               o_perm2 = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
+               o_bsum = take(4 * bsum_n), o_part = take(4 * 6 * (size_t)kMaxBBoxBlocks),
+               o_geo = take(4 * 4), o_dims = take(4 * 4), o_cstart = take(4 * C1);
+  if (mem) {
+    char* b = static_cast<char*>(mem);
+    g->key = (uint32_t*)(b + o_key);
+    g->key2 = (uint32_t*)(b + o_key2);
+    g->perm = (uint32_t*)(b + o_perm);
+    g->perm2 = (uint32_t*)(b + o_perm2);
+    g->hist = (uint32_t*)(b + o_hist);
+    g->hscan = (uint32_t*)(b + o_hscan);
+    g->bsum = (uint32_t*)(b + o_bsum);
+    g->part = (float*)(b + o_part);
+    g->geo = (float*)(b + o_geo);
+    g->dims = (int*)(b + o_dims);
+    g->cstart = (int*)(b + o_cstart);
+  }
+  return o;
+}
+
+// One thread folds the partial boxes and picks the cell side: geo = {lo,
+// 1/h}, dims = {nx, ny, nz, C}.  Extents are capped at 1e6 cells before the
+// product is taken; a side that cannot be made large enough (a vanishing r)
+// puts every point in one cell, which is still correct.
+__global__ void k_grid_geometry(const float* __restrict__ part, int nparts, float r, int64_t cap,
+                                float* geo, int* dims) {
+  if (threadIdx.x != 0) return;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int k = 0; k < nparts; k++)
+    for (int a = 0; a < 3; a++) {
+      lo[a] = fminf(lo[a], part[6 * k + a]);
+      hi[a] = fmaxf(hi[a], part[6 * k + 3 + a]);
+    }
+  float inv = 1.0f / (0.51f * r);
+  long long n[3] = {1, 1, 1}, C = 1;
+  bool fits = false;
+  for (int it = 0; it < 80 && !fits; it++) {
+    C = 1;
+    for (int a = 0; a < 3; a++) {
+      double u = (double)__fmul_rn(__fsub_rn(hi[a], lo[a]), inv);
+      if (!(u >= 0.0)) u = 0.0;  // NaN, or an empty box
+      if (u > 1e6) u = 1e6;
+      n[a] = (long long)u + 1;
+      C *= n[a];
+    }
+    fits = C <= cap;
+    if (!fits) inv *= 0.5f;
+  }
+  if (!fits) n[0] = n[1] = n[2] = 1, C = 1, inv = 0.f;
+  for (int a = 0; a < 3; a++) geo[a] = lo[a];
+  geo[3] = inv;
+  for (int a = 0; a < 3; a++) dims[a] = (int)n[a];
+  dims[3] = (int)C;
+}
+
+// Cell id of every point (input order) and the identity permutation.
+__global__ void k_grid_keys(const float4* __restrict__ raw, int N, const float* __restrict__ geo,
+                            const int* __restrict__ dims, uint32_t* key, uint32_t* perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 r = raw[i];
+  const float x[3] = {r.x, r.y, r.z};
+  int c[3];
+  for (int a = 0; a < 3; a++) {
+    const float u = __fmul_rn(__fsub_rn(x[a], geo[a]), geo[3]);
+    const int k = u >= 0.f ? (int)fminf(u, 2.0e9f) : 0;  // NaN -> 0
+    c[a] = min(k, dims[a] - 1);
+  }
+  key[i] = (uint32_t)(((int64_t)c[2] * dims[1] + c[1]) * dims[0] + c[0]);
+  perm[i] = (uint32_t)i;
+}
+
+// cstart[c] = the first sorted position whose cell id is >= c, c in [0, C]:
+// each sorted position fills the ids after its predecessor's up to its own,
+// the last one also those up to C.
+__global__ void k_grid_starts(const uint32_t* __restrict__ key, int N, const int* __restrict__ dims,
+                              int* cstart) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const int64_t cur = key[s], prev = s > 0 ? (int64_t)key[s - 1] : -1;
+  for (int64_t c = prev + 1; c <= cur; c++) cstart[c] = s;
+  if (s == N - 1)
+    for (int64_t c = cur + 1; c <= (int64_t)dims[3]; c++) cstart[c] = N;
+}
+}  // namespace
+
+size_t grid_scratch_bytes(int64_t N) {
+  GridScratch g;
+  return carve_grid(nullptr, std::max<int64_t>(N, 1), &g);
+}
+
+gs_status grid_rhs(void* scratch, int64_t N, const float4* raw, const float4* pack,
+                   const float4* abpack, float r, float thr, bool adj, const FwdEpi& fe,
+                   const AdjEpi& ae, int64_t* counts, cudaStream_t st) {
+  GridScratch g;
+  carve_grid(scratch, N, &g);
+  const int Ni = (int)N;
+  cudaError_t err = cudaSuccess;
+  if (counts && (err = cudaMemsetAsync(counts, 0, 16, st)) != cudaSuccess) return cuda_err(err);
+  const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
+  k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, Ni, g.part);
+  k_grid_geometry<<<1, 32, 0, st>>>(g.part, (int)nbb, r, grid_cells(N), g.geo, g.dims);
+  k_grid_keys<<<nblocks(N, 256), 256, 0, st>>>(raw, Ni, g.geo, g.dims, g.key, g.perm);
+  err = cudaGetLastError();
+  // stable radix sort of the 32-bit cell ids, 4 passes of 8 bits
+  const int nb = (int)nblocks(N, RS_TILE);
+  uint32_t *k0 = g.key, *v0 = g.perm, *k1 = g.key2, *v1 = g.perm2;
+  for (int pass = 0; pass < 4 && err == cudaSuccess; pass++) {
+    k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, Ni, 8 * pass, g.hist);
+    err = scan(g.hist, 256 * nb, g.bsum, g.hscan, Ident(), st);
+    k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, Ni, 8 * pass, g.hscan, k1, v1);
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  if (err == cudaSuccess) {
+    k_grid_starts<<<nblocks(N, 256), 256, 0, st>>>(k0, Ni, g.dims, g.cstart);
+    err = cudaGetLastError();
+  }
+  note_launches(4 + 4 * 5);
+  if (err != cudaSuccess) return cuda_err(err);
+  GridView v;
+  v.perm = v0;
+  v.key = k0;
+  v.cstart = g.cstart;
+  v.dims = g.dims;
+  err = launch_grid_eval(v, Ni, pack, abpack, raw, thr, adj, fe, ae, counts, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
 }  // namespace gs

@@ -104,6 +104,16 @@ gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cons
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
                       uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,
                       int64_t* n_nodes, cudaStream_t st);
+// Uniform-grid neighbour search of the truncation variant (GS_TRUNC with
+// the "trunc_grid" option, one point set): cells of side 0.51 r (doubled
+// until at most grid_cells(N) cells cover the FP32 bounding box), points
+// sorted stably by cell in `scratch` (grid_scratch_bytes(N) bytes), then one
+// right-hand side whose pairs are exactly those passing the truncation
+// test.  counts: NULL or 2 device int64, set to {kept pairs, 0}.
+size_t grid_scratch_bytes(int64_t N);
+gs_status grid_rhs(void* scratch, int64_t N, const float4* raw, const float4* pack,
+                   const float4* abpack, float r, float thr, bool adj, const FwdEpi& fe,
+                   const AdjEpi& ae, int64_t* counts, cudaStream_t st);
 const char* bh_last_error();
 
 }  // namespace gs

@@ -217,4 +217,24 @@ cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float 
                            const AdjEpi& ae, const TracerEpi& te, int64_t* counts,
                            bool scheduled, cudaStream_t st);
 
+// Uniform cell grid of the truncation variant (device views; see grid_build
+// in tree.h).  Points sorted stably by cell id (z * ny + y) * nx + x; cell c
+// holds sorted positions [cstart[c], cstart[c + 1]).  Cells have side
+// h >= 0.51 r, so two points within r of each other lie at most
+// GRID_REACH cells apart per axis.
+constexpr int GRID_REACH = 2;
+struct GridView {
+  const uint32_t* perm = nullptr;  // N: sorted position -> input index
+  const uint32_t* key = nullptr;   // N: cell id per sorted position
+  const int* cstart = nullptr;     // C + 1 (C = dims[3])
+  const int* dims = nullptr;       // {nx, ny, nz, C}
+};
+// One warp per 32 consecutive sorted points: sources are the points of the
+// cells within GRID_REACH cells of any of them (row by row), cut by the
+// truncation test; fixed-order sums, then the epilogue.  counts: NULL or 2
+// int64 accumulating {kept pairs, 0}.
+cudaError_t launch_grid_eval(const GridView& g, int N, const float4* pack, const float4* abpack,
+                             const float4* raw, float thr, bool adj, const FwdEpi& fe,
+                             const AdjEpi& ae, int64_t* counts, cudaStream_t st);
+
 }  // namespace gs
