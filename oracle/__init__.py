@@ -78,6 +78,7 @@ def _load():
     lib.gsref_bh_list.argtypes = [i64, _f64p, _f64p, dbl, dbl, cint, cint, i64, i64, _i64p,
                                   _i64p]
     lib.gsref_bh_list.restype = i64
+    lib.gsref_bh_tally.argtypes = [i64, _f64p, dbl, dbl, cint, cint, _i64p]
     lib.gsref_num_threads.restype = cint
     _lib = lib
     return lib
@@ -242,3 +243,15 @@ def bh_list(q, p, sigma, m, thresh=3.0, leaf=1, crit=0):
     L = _load().gsref_bh_list(q.shape[0], q, p, float(sigma), float(thresh), int(leaf),
                               int(crit), int(m), cap, kind, ids)
     return kind[:L], ids[:L]
+
+
+def bh_tally(q, sigma, thresh=3.0, leaf=1, crit=0):
+    """Per-target record of the Barnes-Hut decisions on the tree of q: an
+    (N, 4) array {point interactions, node interactions, fingerprint of the
+    points taken, fingerprint of the nodes summarised}; the fingerprints are
+    sums modulo 2**64 of splitmix64(key) over the sources, key = (DFS first
+    position << 32) | member count (columns 2-3 as uint64 bit patterns)."""
+    q = _c(q)
+    out = np.zeros((q.shape[0], 4), np.int64)
+    _load().gsref_bh_tally(q.shape[0], q, float(sigma), float(thresh), int(leaf), int(crit), out)
+    return out

@@ -444,9 +444,36 @@ typedef struct {
   double acc0[3], acc1[3];
   int64_t n_point, n_node;
   ilist *list;
+  /* decision fingerprint (gsref_bh_tally): DFS position of each point, DFS
+   * first position of each node's members; NULL when not wanted */
+  const int64_t *tpos, *tfirst;
+  uint64_t h_point, h_node;
 } visit_ctx;
 
+/* splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the output of the generator whose state is
+ * `key`, used as a 64-bit mix of an interaction's identity. */
+static uint64_t mix64(uint64_t key) {
+  uint64_t z = key + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+/* Identity of a source as the set of points it stands for: the DFS position
+ * of its first member (the DFS order is the stable Morton order) and its
+ * member count; a point is the set of itself. */
+static uint64_t source_key(int64_t first, int64_t n) {
+  return ((uint64_t)first << 32) | (uint64_t)n;
+}
+
 static void record(visit_ctx *v, int64_t kind, int64_t id) {
+  if (v->tpos) {
+    if (kind == 0)
+      v->h_point += mix64(source_key(v->tpos[id], 1));
+    else
+      v->h_node += mix64(source_key(v->tfirst[id], v->t->nodes[id].n));
+  }
   if (!v->list) return;
   if (v->list->len < v->list->cap) {
     v->list->kind[v->list->len] = kind;
@@ -1056,6 +1083,67 @@ int64_t gsref_bh_list(int64_t N, const double *q, const double *p,
   free(c.remap);
   tree_free(&t);
   return L.len;
+}
+
+/* DFS positions (children in octant order, a leaf's points in insertion
+ * order): pos[i] of every point i, first[k] of every node k (the position
+ * of its first member). */
+static void dfs_positions(const otree *t, int64_t N, int64_t *pos, int64_t *first) {
+  int64_t *stack = (int64_t *)malloc((size_t)(t->count + 1) * sizeof(int64_t));
+  int64_t sp = 0, at = 0;
+  stack[sp++] = 0;
+  while (sp) {
+    int64_t k = stack[--sp];
+    first[k] = at;
+    if (t->nodes[k].leaf) {
+      for (int64_t s = t->nodes[k].head; s >= 0; s = t->next[s]) pos[s] = at++;
+    } else {
+      for (int o = 7; o >= 0; o--)
+        if (t->nodes[k].child[o] >= 0) stack[sp++] = t->nodes[k].child[o];
+    }
+  }
+  (void)N;
+  free(stack);
+}
+
+/* Per-target record of the Barnes-Hut decisions (Sec. 2.2, three cases) on
+ * the tree of positions q: tally[4 m .. 4 m + 3] = {point interactions,
+ * node interactions, sum over the point interactions of mix64(key), the same
+ * sum over the node interactions} for every target m, sums modulo 2^64.  A
+ * source's key is (DFS first position << 32) | member count, so two targets'
+ * records agree exactly when they took the same sources, whatever the order. */
+void gsref_bh_tally(int64_t N, const double *q, double sigma, double thresh, int leaf,
+                    int crit, int64_t *tally) {
+  otree t;
+  tree_build(&t, N, q, q, NULL, NULL); /* decisions depend on positions only */
+  int64_t *pos = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+  int64_t *first = (int64_t *)malloc((size_t)t.count * sizeof(int64_t));
+  dfs_positions(&t, N, pos, first);
+  float thr = rule_threshold(crit, thresh, sigma);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t m = 0; m < N; m++) {
+    visit_ctx v;
+    memset(&v, 0, sizeof(v));
+    v.t = &t;
+    v.sigma = sigma;
+    v.thr = thr;
+    v.leaf = leaf;
+    v.crit = crit;
+    v.tq = t.q + 3 * m;
+    v.tp = t.p + 3 * m;
+    v.tq32 = t.q32 + 3 * m;
+    v.m = m;
+    v.tpos = pos;
+    v.tfirst = first;
+    visit(&v, 0);
+    tally[4 * m + 0] = v.n_point;
+    tally[4 * m + 1] = v.n_node;
+    tally[4 * m + 2] = (int64_t)v.h_point;
+    tally[4 * m + 3] = (int64_t)v.h_node;
+  }
+  free(pos);
+  free(first);
+  tree_free(&t);
 }
 
 int gsref_num_threads(void) {

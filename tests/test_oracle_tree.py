@@ -332,3 +332,46 @@ def test_opening_angle_limits_and_error(oracle):
         F, _, _ = oracle.rhs(w.q0, w.p0, w.sigma, mode=1, thresh=theta, crit=1)
         errs.append(np.abs(F - Fe).max())
     assert errs[0] > errs[1] > errs[2]
+
+
+def _splitmix64(key):
+    """splitmix64 (Steele, Lea and Flood, OOPSLA 2014): the generator's output
+    for state `key`, in Python integers modulo 2**64."""
+    m = (1 << 64) - 1
+    z = (key + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+@pytest.mark.parametrize("geom,n,leaf,crit,thresh", [("blobs", 250, 1, 0, 3.0),
+                                                     ("slab", 300, 1, 0, 2.0),
+                                                     ("blobs", 220, 4, 0, 3.0),
+                                                     ("ellipsoid", 200, 1, 1, 0.6)])
+def test_decision_tally_matches_interaction_lists(oracle, geom, n, leaf, crit, thresh):
+    """The per-target decision record (counts and fingerprints) equals the one
+    recomputed here from each target's interaction list and the exported
+    tree: a point's key is its DFS position, a node's its first DFS position
+    and member count.  Duplicated points put a depth-10 list in the tree."""
+    w = inputs.make(geom, n, 17)
+    q = w.q0.copy()
+    q[5] = q[2]
+    q[6] = q[2]
+    tally = oracle.bh_tally(q, w.sigma, thresh, leaf=leaf, crit=crit)
+    t = oracle.tree(q, np.zeros_like(q))
+    pos = np.empty(n, np.int64)
+    pos[t["order"]] = np.arange(n)
+    mask = (1 << 64) - 1
+    for m in range(n):
+        kind, ids = oracle.bh_list(q, w.p0, w.sigma, m, thresh, leaf=leaf, crit=crit)
+        hp = hn = 0
+        for k, i in zip(kind, ids):
+            if k == 0:
+                hp = (hp + _splitmix64((int(pos[i]) << 32) | 1)) & mask
+            else:
+                hn = (hn + _splitmix64((int(t["first"][i]) << 32) | int(t["n"][i]))) & mask
+        want = [int((kind == 0).sum()), int((kind == 1).sum()), hp, hn]
+        got = [int(tally[m, 0]), int(tally[m, 1]), int(tally[m, 2]) & mask,
+               int(tally[m, 3]) & mask]
+        assert got == want, m
+
