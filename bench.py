@@ -218,13 +218,19 @@ def run_reference(args):
     for _ in range(args.warmup):
         step()
     ts = [step() for _ in range(args.steps)]
-    ms = 1e3 * sum(ts) / len(ts) * w.T
+    step_ms = 1e3 * sum(ts) / len(ts)
+    ms = step_ms * w.T
     sample = (f"each step: one Barnes-Hut forward + one adjoint right-hand side of the FP64 oracle "
-              f"at full N={w.N}, extrapolated x T={w.T} to one gradient")
+              f"at full N={w.N} (ms_per_step, measured); value extrapolates x T={w.T} to one "
+              f"gradient")
+    cfg = config_dict(w, {"parallelism": "host cores",
+                          "step": "one Barnes-Hut forward + one adjoint right-hand side of the "
+                                  "FP64 oracle at full N (a T-th of one gradient); value = "
+                                  "ms_per_step x T"})
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(w, {"parallelism": "host cores"}),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": ms, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,6 +284,9 @@ def run_ours(args):
     def plain_grad():
         return gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="exact")
 
+    # this GPU's measured issue rates (gs_alu_peaks): FP32 FMA lane-ops/s,
+    # FP32 lane-ops/s through packed f32x2 FMA, MUFU ex2/s
+    alu = gs.alu_peaks(dev.index or 0)
     # interactions per step at t = 0 (the per-gradient count is estimated as 2T x this)
     _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
     bh_inter_step = cnt[0] + cnt[1]
@@ -354,6 +363,12 @@ def run_ours(args):
                 "issued_ops_per_pair": ISSUED_OPS_PER_PAIR[dom],
                 "issued_frac": ISSUED_OPS_PER_PAIR[dom] * units / per_launch_s / ALU_PEAK_OPS}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof["bound"] == "alu":
+        # one MUFU ex2 per pair, against this run's measured ex2 rate
+        roof["mufu"] = {"achieved": units / per_launch_s / 1e12, "peak": alu[2] / 1e12,
+                        "unit": "T ex2/s", "frac": units / per_launch_s / alu[2],
+                        "peak_kind": "measured (gs_alu_peaks)"}
+        roof["frac_of_measured_f32x2"] = alg / per_launch_s / alu[1]
     roof["kernel"] = dom
     roof["launch_ms"] = per_launch_s * 1e3
     roof["share"] = ms / max(sum(v[1] for v in kern.values()), 1e-9)
@@ -379,7 +394,8 @@ def run_ours(args):
             class_roofs[cls] = {"bound": "alu", "achieved": ach, "peak": ALU_PEAK_OPS / 1e12,
                                 "unit": "Tops/s", "frac": ach * 1e12 / ALU_PEAK_OPS,
                                 "issued_frac": ISSUED_OPS_PER_PAIR[cls] * units / per
-                                / ALU_PEAK_OPS}
+                                / ALU_PEAK_OPS,
+                                "mufu_frac": units / per / alu[2]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
@@ -394,7 +410,10 @@ def run_ours(args):
             "roofline": roof,
             "kernels": {k: {"launch_groups": v[0], "ms": v[1]} for k, v in kern.items()},
             "class_rooflines": class_roofs,
-            "gpu_launches": launches, "wall_s": wall, "clocks": ck}
+            "gpu_launches": launches, "wall_s": wall, "clocks": ck,
+            "alu_peaks_measured": {"fp32_fma_lane_ops_per_s": alu[0],
+                                   "fp32_f32x2_lane_ops_per_s": alu[1], "mufu_ex2_per_s": alu[2],
+                                   "derived_fp32_peak_lane_ops_per_s": ALU_PEAK_OPS}}
 
     if rank == 0 and not args.no_variants:
         # leaf-size variant picked by the autotuner on the initial state (a
@@ -484,6 +503,29 @@ def run_ours(args):
             "splits_fwd": jf, "splits_adj": ja, "ms_per_gradient": tuned_ms,
             "builtin_ms_per_gradient": builtin_ms,
             "autotune_ms_per_fwd_adj_rhs": {str(k): v for k, v in jms.items()}}
+    if rank == 0 and not args.no_variants:
+        # the same workload with momenta 10x larger: points move by about
+        # half a kernel width (median) over t in [0, 1], so the decisions
+        # change from step to step
+        p10 = 10.0 * p0
+        dgrad = lambda: gs.shoot_grad(q0, p10, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH)
+        dgrad()
+        tms = []
+        for _ in range(3):
+            flush.zero_()
+            a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_ev.record()
+            dgrad()
+            b_ev.record()
+            torch.cuda.synchronize()
+            tms.append(a_ev.elapsed_time(b_ev))
+        q1d, _, _ = gs.shoot(q0, p10, w.sigma, w.T, mode="bh", thresh=THRESH)
+        mv = torch.linalg.norm(q1d - q0, dim=1) / w.sigma
+        line["deforming_variant"] = {
+            "momenta": "10x the workload's", "ms_per_gradient": statistics.median(tms),
+            "displacement_sigmas": {"median": float(mv.median()), "max": float(mv.max())}}
+        line["batched"] = batched_summary(gs, torch, steps=1, warmup=1)
+        line["sphere1m"] = sphere_summary(gs, torch, steps=2, warmup=1)
     if rank == 0 and args.e2e_steps > 0:
         # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
         h = lambda a: torch.as_tensor(a, dtype=torch.float64).pin_memory()
@@ -538,6 +580,69 @@ def run_probe(args):
     torch.cuda.synchronize()
     print(json.dumps({"probe": args.probe, "N": w.N, "ok": True}))
     return 0
+
+
+def _timed(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def batched_summary(gs, torch, steps=1, warmup=1):
+    """64 bent-slab subjects (N log-uniform in [5000, 40000], sigma = 2,
+    T = 20): ms per gradient of all subjects, batched Barnes-Hut (one forest
+    per step) against plain per-subject exact calls, and the Barnes-Hut
+    gradient's relative L2 distance from the batched exact gradient."""
+    import numpy as np
+    from paper_1907_04834_gb300 import inputs
+    ws, off = inputs.batch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cat = lambda k: torch.as_tensor(np.concatenate([getattr(w, k) for w in ws]), device=dev)
+    q0, p0, X = cat("q0"), cat("p0"), cat("X")
+    sig, T, lam = ws[0].sigma, ws[0].T, ws[0].lam
+
+    def plain():
+        for k in range(len(ws)):
+            sl = slice(int(off[k]), int(off[k + 1]))
+            gs.shoot_grad(q0[sl], p0[sl], X[sl], sig, T, lam, mode="exact")
+
+    bh = lambda: gs.shoot_batched(q0, p0, X, off, sig, T, lam, mode="bh", thresh=THRESH)
+    ms_bh = _timed(torch, bh, steps, warmup)
+    ms_pl = _timed(torch, plain, steps, warmup)
+    _, gb = bh()
+    _, ge = gs.shoot_batched(q0, p0, X, off, sig, T, lam, mode="exact")
+    return {"ms_batched_bh": ms_bh, "ms_plain_per_subject_exact": ms_pl,
+            "speedup_batched_bh_vs_plain": ms_pl / ms_bh,
+            "bh_vs_exact_grad_rel_l2": float(torch.linalg.norm(gb - ge) / torch.linalg.norm(ge)),
+            "workload": f"{len(ws)} bent-slab subjects, N log-uniform in [5000, 40000] (total "
+                        f"{int(off[-1])}), sigma={sig} mm, T={T}, lambda={lam}",
+            "steps": steps, "warmup": warmup}
+
+
+def sphere_summary(gs, torch, steps=2, warmup=1):
+    """sphere1m (N = 1,000,000, sigma = 1, T = 40): ms per Barnes-Hut
+    gradient with the trajectory checkpointed every 6 steps."""
+    from paper_1907_04834_gb300 import inputs
+    w = inputs.config("sphere1m")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    q0, p0, X = t(w.q0), t(w.p0), t(w.X)
+    _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
+    fn = lambda: gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH,
+                               ckpt_every=6)
+    return {"ms_per_gradient": _timed(torch, fn, steps, warmup),
+            "bh_interactions_per_point_step": (cnt[0] + cnt[1]) / w.N,
+            "workload": f"sphere1m: N={w.N}, sigma={w.sigma} mm, T={w.T}, checkpoint every 6",
+            "steps": steps, "warmup": warmup}
 
 
 def run_batched(args):

@@ -145,6 +145,19 @@ gs_status gs_shoot(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
                    void *stream);
 
 /*
+ * Geodesic shooting as gs_shoot (Sec. 2.1 Eq. 1 with T Euler steps, or the
+ * semi-implicit variant of sympl_iters; GS_BH: Sec. 2.2 at every step) that
+ * also returns the whole discrete path: qtraj, ptraj are NULL or
+ * (T + 1) x N x 3 outputs (state k at rows [k N, (k + 1) N), state 0 = q0,
+ * p0), at least one of them non-NULL.  The path is what the paper's
+ * registrations deform meshes along (Sec. 3.2).  Launches kernel by kernel
+ * (no graph replay).
+ */
+gs_status gs_shoot_traj(gs_ctx *ctx, const double *q0, const double *p0, int64_t N,
+                        const gs_params *prm, double *qtraj, double *ptraj,
+                        void *stream);
+
+/*
  * Objective of Eq. 2 and its gradient with respect to p0 (discrete adjoint,
  * backward stage of Sec. 2.2).  X: N x 3 targets.  E: 3 doubles {E, H(q0,p0),
  * lambda sum |q(1) - X|^2}.  grad: N x 3 dE/dp0.  q1: NULL or N x 3 q(1).
@@ -296,6 +309,40 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
                   int32_t *order, int32_t *nodes, float *range, int64_t cap,
                   int64_t *n_nodes, void *stream);
 
+/*
+ * Per-target record of the Barnes-Hut decisions (Sec. 2.2, the three cases
+ * and the summaries of Eq. 4) on the tree of positions q (N x 3): the walk
+ * of every GS_BH step, with its decisions recorded instead of listed.  prm:
+ * mode GS_BH with its sigma, thresh_sigmas, leaf_size and criterion (other
+ * modes: GS_ERR_UNSUPPORTED).  tally: N x 4 int64, row i (input order) =
+ * {point interactions of target i, node interactions, sum over the points
+ * it takes exactly of mix(key), the same sum over the nodes it summarises},
+ * sums modulo 2^64 (bit patterns in int64), mix = the splitmix64 output
+ * function (Steele, Lea and Flood, OOPSLA 2014) of the 64-bit state key,
+ * key = (sorted position of the source's first member << 32) | member
+ * count, sorted = the stable Morton order of gs_tree.  Two records agree
+ * exactly when the targets took the same sources, in any order; the totals
+ * of gs_rhs's counts are the column sums of the first two columns.
+ */
+gs_status gs_bh_tally(gs_ctx *ctx, const double *q, int64_t N, const gs_params *prm,
+                      int64_t *tally, void *stream);
+
+/*
+ * Sums over each node of the octree of gs_tree (same nodes, same preorder)
+ * for state (q, p) and, if given, the adjoint variables (al, be): sums is
+ * NULL or cap x 12 doubles per node {sum q (3), sum p (3), sum alpha (3),
+ * sum beta (3)} over its members (a leaf: its point), in input units --
+ * the statistics of Sec. 2.2 from which the summaries of Eq. 4 (centroid
+ * sum q / n, P = sum p) and of the backward stage (A = sum alpha, B / n)
+ * are formed.  al, be: both N x 3 or both NULL (sums of alpha and beta are
+ * then 0).  The sums are the library's compensated FP32-pair sums of the
+ * FP32-rounded values, converted to FP64.  *n_nodes (may be NULL)
+ * receives the node count.  Synchronises the stream.
+ */
+gs_status gs_tree_sums(gs_ctx *ctx, const double *q, const double *p, const double *al,
+                       const double *be, int64_t N, double *sums, int64_t cap,
+                       int64_t *n_nodes, void *stream);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 
 /* Tuning options of a context:
@@ -375,17 +422,26 @@ gs_status gs_alu_peaks(int device, double *out);
  * (host buffers are rejected with GS_ERR_INVALID_ARG); sigma > 0;
  * 1 <= N <= GS_RHS_NOALLOC_MAX_N, larger N returns GS_ERR_INVALID_ARG.  No
  * context is needed.  Work is enqueued on `stream` and the call returns
- * without waiting; device-side conditions (a bounded wait that gave up) are
- * not reported by this call.
+ * without waiting; device-side conditions are not reported by this call: if
+ * a bounded wait of the kernel's copy pipeline gives up (it cannot complete
+ * only when the GPU is failing; the context-based entry points report it as
+ * GS_ERR_TIMEOUT, and gs_selftest_timeout exercises that wait), F and Phi
+ * are undefined and nothing tells the caller.
  *
  * Scratch: one fixed array of about 6.4 MiB of device memory that every GPU
- * loading the library holds until the process exits.  Every call on that
+ * on which the library's device code has been loaded (see the first call,
+ * below) holds until the process exits.  Every call on that
  * GPU shares it and it keeps the previous call's contents (the call clears
  * what must start at zero); calls whose GPU work overlaps -- on different
  * streams or from concurrent host threads -- race on it, so serialise them.
  * The first call on a device looks up the array's device address and sets
- * up the kernel, with that device current; make that first call before any
- * stream capture.
+ * up the kernel, with that device current.  Under CUDA's default lazy
+ * module loading (CUDA_MODULE_LOADING=LAZY) that first call is also when
+ * the driver loads this library's device code and commits the array: it
+ * takes device memory and may synchronise, and it fails if the caller's
+ * pool has already reserved all of the GPU's memory.  So make one warm-up
+ * call at initialisation, before the pool reserves its memory and before
+ * any stream capture; later calls take no memory.
  */
 gs_status gs_rhs_exact_noalloc(const double *q, const double *p, int64_t N,
                                double sigma, double *F, double *Phi,

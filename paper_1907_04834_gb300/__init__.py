@@ -10,7 +10,7 @@ _API = ("shoot", "shoot_grad", "shoot_batched", "descend_batched", "lbfgs", "aut
         "autotune_exact", "flow",
         "velocity",
         "rhs",
-        "adj_rhs", "tree",
+        "adj_rhs", "tree", "shoot_traj", "bh_tally", "tree_sums",
         "energy", "GeodesicShoot", "Context", "context", "GSError", "timing", "timing_read",
         "alu_peaks", "set_option", "selftest_timeout")
 

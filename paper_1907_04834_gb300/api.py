@@ -311,6 +311,55 @@ def tree(q, stream=None):
     return dict(codes=codes, order=order, nodes=nodes[:M], range=rng[:M], n_nodes=M)
 
 
+def shoot_traj(q0, p0, sigma, T, mode="exact", thresh=3.0, leaf_size=1, criterion=0,
+               sympl_iters=0, stream=None):
+    """Shooting that returns the discrete path (gs_shoot_traj): (qtraj, ptraj),
+    each (T + 1, N, 3), state k = after k steps."""
+    q0 = _pts(q0, "q0")
+    n = q0.shape[0]
+    p0 = _pts(p0, "p0", n)
+    c = _ctx_for(q0)
+    prm = make_params(sigma, T, mode, 0.0, thresh, leaf_size=leaf_size, criterion=criterion,
+                      sympl_iters=sympl_iters)
+    qt, pt = _like(q0, (int(T) + 1, n, 3)), _like(q0, (int(T) + 1, n, 3))
+    c.check(c.lib.gs_shoot_traj(c.handle, _ptr(q0), _ptr(p0), n, ctypes.byref(prm), _ptr(qt),
+                                _ptr(pt), _stream_ptr(c.device, stream)))
+    return qt, pt
+
+
+def bh_tally(q, sigma, thresh=3.0, leaf_size=1, criterion=0, stream=None):
+    """Per-target record of the Barnes-Hut decisions on the tree of q
+    (gs_bh_tally): int64 (N, 4) {point interactions, node interactions,
+    fingerprint of the points, fingerprint of the nodes}."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    c = _ctx_for(q)
+    prm = make_params(sigma, 1, "bh", 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
+    out = torch.empty((n, 4), dtype=torch.int64, device=q.device)
+    c.check(c.lib.gs_bh_tally(c.handle, _ptr(q), n, ctypes.byref(prm), _ptr(out),
+                              _stream_ptr(c.device, stream)))
+    return out
+
+
+def tree_sums(q, p, al=None, be=None, stream=None):
+    """Per-node sums {q, p, alpha, beta} (M, 12) of the octree of q in
+    gs_tree's preorder (gs_tree_sums)."""
+    q = _pts(q, "q")
+    n = q.shape[0]
+    p = _pts(p, "p", n)
+    if (al is None) != (be is None):
+        raise ValueError("al and be must both be given or both be None")
+    if al is not None:
+        al, be = _pts(al, "al", n), _pts(be, "be", n)
+    c = _ctx_for(q)
+    cap = 2 * n + 8
+    sums = torch.empty((cap, 12), dtype=torch.float64, device=q.device)
+    m = ctypes.c_int64()
+    c.check(c.lib.gs_tree_sums(c.handle, _ptr(q), _ptr(p), _ptr(al), _ptr(be), n, _ptr(sums),
+                               cap, ctypes.byref(m), _stream_ptr(c.device, stream)))
+    return sums[: m.value]
+
+
 def set_option(name: str, value: int, device: int | None = None):
     """Sets a tuning option of the device's context (see gs_set_option)."""
     c = context(device)

@@ -955,13 +955,26 @@ gs_status batched_grad(gs_ctx* c, Batch& b, const double* dq0, const double* dp0
 
 // Forward shooting of one point set: state left in c->q, c->p; with H,
 // H(q0, p0) and H(q1, p1) in scal[SC_H0], scal[SC_H1] (capturable).
+// qtraj, ptraj: NULL or (T + 1) x N x 3 outputs receiving every step's state
+// (not captured: gs_shoot_traj launches eagerly).
 gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* qtraj = nullptr, double* ptraj = nullptr) {
   gs_status s;
   gs_ctx* c = S.c;
   S.st = st;
   const int64_t N = S.N;
   if ((s = solver_load(S, dq0, dp0, 0))) return s;
+  const size_t b3 = (size_t)N * 3 * sizeof(double);
+  auto keep = [&](int k) -> gs_status {
+    if (qtraj)
+      CK(cudaMemcpyAsync(qtraj + (size_t)k * N * 3, c->q.p, b3, cudaMemcpyDefault, st),
+         "trajectory copy");
+    if (ptraj)
+      CK(cudaMemcpyAsync(ptraj + (size_t)k * N * 3, c->p.p, b3, cudaMemcpyDefault, st),
+         "trajectory copy");
+    return GS_OK;
+  };
+  if ((s = keep(0))) return s;
   // Each step: S.iters fixed-point passes (the epilogue writes the next pack
   // with (q^k, p^k + h Phi) and leaves the state), then the update pass; with
   // S.iters = 0 the explicit Euler step.  Packs alternate between two slots.
@@ -977,6 +990,7 @@ gs_status shoot_enqueue(Solver& S, const double* dq0, const double* dp0, bool H,
       if (h0) CK(launch_sum(c->pf.as<double>(), N, 0.5, S.scal(SC_H0), st), "sum");
       cur ^= 1;
     }
+    if ((s = keep(k + 1))) return s;
   }
   if (H) {
     FwdEpi e = fwd_epi(S, -1, 0.0);
@@ -1949,5 +1963,97 @@ gs_status gs_tree(gs_ctx* c, const double* q, int64_t N, uint32_t* codes, int32_
   return read_status(c, st);
 }
 
+gs_status gs_shoot_traj(gs_ctx* c, const double* q0, const double* p0, int64_t N,
+                        const gs_params* prm, double* qtraj, double* ptraj, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false, true))) return s;
+  if (!qtraj && !ptraj) return fail(c, GS_ERR_INVALID_ARG, "qtraj and ptraj are both NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool hq = false, hp = false;
+  if (qtraj && (s = output(c, qtraj, "qtraj", &hq))) return s;
+  if (ptraj && (s = output(c, ptraj, "ptraj", &hp))) return s;
+  const double *dq0, *dp0;
+  if ((s = input(c, q0, (size_t)N * 3, "q0", c->in_q, st, &dq0)) ||
+      (s = input(c, p0, (size_t)N * 3, "p0", c->in_p, st, &dp0)))
+    return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 2, false, st))) return s;
+  if ((s = shoot_enqueue(S, dq0, dp0, false, st, qtraj, ptraj))) return s;
+  CK(launch_check_finite(c->q.as<double>(), N * 3, c->d_status, st), "check");
+  CK(launch_check_finite(c->p.as<double>(), N * 3, c->d_status, st), "check");
+  if (hq || hp) return read_status(c, st);
+  CK(cudaGetLastError(), "launch");
+  return GS_OK;
+}
+
+gs_status gs_bh_tally(gs_ctx* c, const double* q, int64_t N, const gs_params* prm,
+                      int64_t* tally, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, false))) return s;
+  if (prm->mode != GS_BH) return fail(c, GS_ERR_UNSUPPORTED, "gs_bh_tally needs mode GS_BH");
+  if (!tally) return fail(c, GS_ERR_INVALID_ARG, "tally is NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool ht = false;
+  if ((s = output(c, tally, "tally", &ht))) return s;
+  const double* dq;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
+  Solver S;
+  if ((s = solver_init(c, S, N, prm, 1, false, st))) return s;
+  if ((s = solver_load(S, dq, dq, 0))) return s;  // decisions depend on positions only
+  const size_t bytes = (size_t)N * 4 * sizeof(int64_t);
+  CK(c->out_a.ensure(bytes), "workspace");
+  BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(0), S.raw(0), BHForest{}, S.leaf, false, S.crit};
+  s = bh_build(c->tree, b, nullptr, false, st);
+  if (s == GS_OK) s = bh_tally(c->tree, b, c->out_a.as<int64_t>(), st);
+  if (s != GS_OK) return fail(c, s, "decision tally failed: %s", bh_last_error());
+  if ((s = copy_out(c, tally, c->out_a.p, bytes, st))) return s;
+  if (ht) return read_status(c, st);
+  return GS_OK;
+}
+
+gs_status gs_tree_sums(gs_ctx* c, const double* q, const double* p, const double* al,
+                       const double* be, int64_t N, double* sums, int64_t cap,
+                       int64_t* n_nodes, void* stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->err.clear();
+  gs_status s;
+  if ((s = check_n(c, N))) return s;
+  if (cap < 0) return fail(c, GS_ERR_INVALID_ARG, "cap must be >= 0");
+  if ((al == nullptr) != (be == nullptr))
+    return fail(c, GS_ERR_INVALID_ARG, "al and be must both be given or both be NULL");
+  bool h;
+  if (sums && (s = output(c, sums, "sums", &h))) return s;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool adj = al != nullptr;
+  const double *dq, *dp, *da = nullptr, *db = nullptr;
+  if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq)) ||
+      (s = input(c, p, (size_t)N * 3, "p", c->in_p, st, &dp)))
+    return s;
+  if (adj && ((s = input(c, al, (size_t)N * 3, "al", c->in_a, st, &da)) ||
+              (s = input(c, be, (size_t)N * 3, "be", c->in_b, st, &db))))
+    return s;
+  gs_params prm{1.0, 0.0, 3.0, 1, GS_BH, 0, 0, 0, 0, 0, 0};
+  Solver S;
+  if ((s = solver_init(c, S, N, &prm, 1, adj, st))) return s;
+  if ((s = solver_load(S, dq, dp, 0))) return s;
+  const double mu = adj_beta_scale(S.s);
+  if (adj) {
+    const size_t b3 = (size_t)N * 3 * sizeof(double);
+    CK(cudaMemcpyAsync(c->al.p, da, b3, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->be.p, db, b3, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(launch_pack_ab(c->al.as<double>(), c->be.as<double>(), N, mu, S.abpack(0), st), "pack");
+  }
+  s = tree_sums(c->tree, S.raw(0), S.pack(0), adj ? S.abpack(0) : nullptr, N, S.scal(SC_CENTER),
+                S.s, mu, sums, cap, n_nodes, st);
+  if (s != GS_OK) return fail(c, s, "tree sums export failed: %s", bh_last_error());
+  return read_status(c, st);
+}
 
 }  // extern "C"

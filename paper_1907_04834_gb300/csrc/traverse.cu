@@ -519,6 +519,82 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   }
 }
 
+// ------------------------------------------------------------------ tally
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the generator's output for state `key`.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long key) {
+  unsigned long long z = key + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Sink of the decision record: per lane, the number of points and nodes the
+// lane takes and the sums (mod 2^64) of mix64(key) over them, key = (first
+// sorted position << 32) | member count -- the same sources give the same
+// record whatever the order.  Entries are those the list walk emits: one
+// entry (a far node or a single leaf), or n point entries (a leaf run, an
+// all-leaf node's children, or a leaf-size bucket's points).
+struct TallySink {
+  const TreeArrays* t;
+  int lane;
+  long long np, nn;
+  unsigned long long hp, hn;
+  __device__ __forceinline__ bool fits(int) const { return true; }
+  __device__ __forceinline__ void add1(int node, unsigned mask) {
+    if (!((mask >> lane) & 1u)) return;
+    const int skip = __float_as_int(t->nbox[2 * node].w);
+    const int cnt = __float_as_int(t->nbox[2 * node + 1].w);
+    const unsigned long long key =
+        ((unsigned long long)(unsigned)t->ninfo[node].y << 32) | (unsigned)cnt;
+    if (skip == node + 1) np++, hp += mix64(key);  // a leaf: one point
+    else nn++, hn += mix64(key);
+  }
+  __device__ __forceinline__ void add(int node0, int n, unsigned mask, bool points) {
+    if (!((mask >> lane) & 1u)) return;
+    for (int k = 0; k < n; k++) {
+      const int pos = points ? node0 + k : t->ninfo[node0 + k].y;
+      np++;
+      hp += mix64(((unsigned long long)(unsigned)pos << 32) | 1u);
+    }
+  }
+};
+
+// Decision record of every target (tests): one warp per walk list, exactly
+// the walk of k_bh_walk (slice cuts, ancestor test at the slice start, the
+// same walk_nodes), with the tally sink in place of the list; per target
+// tally[4 o + {0, 1, 2, 3}] += {points, nodes, point sum, node sum}.
+template <bool VAR>
+__global__ void __launch_bounds__(TR_WARPS * 32)
+    k_bh_tally(TreeArrays t, int N, const float4* __restrict__ raw, float thr, WalkGroups wg,
+               unsigned long long* tally) {
+  __shared__ float4 s_box[TR_WARPS][32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int wk = BH_SLICES * wg.wsplit;
+  const int l = blockIdx.x * TR_WARPS + w;
+  if (l >= wg.G * wk) return;
+  const int g = l / wk, k = l % wk;
+  const GroupInfo gi = target_group(t, N, wg, g);
+  const bool valid = lane < gi.count;
+  const int ti = gi.first + (valid ? lane : 0);
+  const int o = (int)t.perm[ti];
+  const float4 rr = raw[o];
+  int x = walk_cut(gi, k, wk);
+  const int end = walk_cut(gi, k + 1, wk);
+  int resume = valid ? 0 : INT_MAX;
+  if (k > 0 && valid && x < end)
+    resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
+  TallySink sink{&t, lane, 0, 0, 0ull, 0ull};
+  long long np = 0, nn = 0;
+  walk_nodes<false, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, false, wg.crit, resume, sink,
+                         lane, np, nn);
+  if (!valid) return;
+  atomicAdd(&tally[4 * (size_t)o + 0], (unsigned long long)sink.np);
+  atomicAdd(&tally[4 * (size_t)o + 1], (unsigned long long)sink.nn);
+  atomicAdd(&tally[4 * (size_t)o + 2], sink.hp);
+  atomicAdd(&tally[4 * (size_t)o + 3], sink.hn);
+}
+
 // ------------------------------------------------------------------ combine
 // Group g once all its slices are summed: per point (one lane each) the
 // slices' partial sums in slice order as FP32 pairs, then the FP64 epilogue.
@@ -926,6 +1002,18 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
     k_list_order<<<2, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
                                               L.worder_n);
   note_launches(scheduled ? 2 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bh_tally(const TreeArrays& t, int N, const float4* raw, float thr,
+                            const WalkGroups& wg, int64_t* tally, cudaStream_t st) {
+  const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES * wg.wsplit);
+  auto* out = reinterpret_cast<unsigned long long*>(tally);
+  if (wg.leaf > 1 || wg.crit != 0)
+    k_bh_tally<true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out);
+  else
+    k_bh_tally<false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out);
+  note_launches(1);
   return cudaGetLastError();
 }
 

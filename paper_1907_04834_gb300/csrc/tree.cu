@@ -1075,6 +1075,16 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
+gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, b.slot, &t, &L);
+  cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(int64_t) * 4 * (size_t)b.N, st);
+  if (err == cudaSuccess)
+    err = launch_bh_tally(t, (int)b.N, b.raw, b.thr, walk_groups(w, b), tally, st);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
+}
+
 void bh_counts(TreeWork& w, int64_t* cnt) {
   cnt[0] = cnt[1] = 0;
   if (w.d_counts) cudaMemcpy(cnt, w.d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost);
@@ -1096,6 +1106,37 @@ __global__ void k_export_nodes(TreeArrays t, int m, int32_t* nodes, float* range
   range[6 * x + 3] = hi.x;
   range[6 * x + 4] = hi.y;
   range[6 * x + 5] = hi.z;
+}
+
+// Node sums in input units (tests): per preorder node x, {sum q, sum p,
+// sum alpha, sum beta} in FP64 from the FP32-pair sums of the bottom-up pass
+// (a leaf: its own FP32 record).  The pack holds (q - c) s and mu beta, so
+// sum q = (sum xs) / s + n c and sum beta = (sum mu beta) / mu.
+__global__ void k_export_sums(TreeArrays t, int m, const double* __restrict__ center,
+                              double inv_s, double inv_mu, bool adj, double* out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= m) return;
+  const int skip = __float_as_int(t.nbox[2 * x].w), count = __float_as_int(t.nbox[2 * x + 1].w);
+  double v[12];
+  if (skip == x + 1) {
+    for (int r = 0; r < 4; r++) {
+      const float4 f = (r < 2 || adj) ? t.nrec[4 * x + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[3 * r] = f.x, v[3 * r + 1] = f.y, v[3 * r + 2] = f.z;
+    }
+  } else {
+    const float2* isum = reinterpret_cast<const float2*>(t.isum);
+    for (int k = 0; k < 12; k++) {
+      const float2 pr = (k < 6 || adj) ? isum[12 * (size_t)x + k] : make_float2(0.f, 0.f);
+      v[k] = (double)pr.x + (double)pr.y;
+    }
+  }
+  double* o = out + 12 * (size_t)x;
+  for (int a = 0; a < 3; a++) {
+    o[a] = v[a] * inv_s + (double)count * center[a];
+    o[3 + a] = v[3 + a];
+    o[6 + a] = v[6 + a];
+    o[9 + a] = v[9 + a] * inv_mu;
+  }
 }
 }  // namespace
 
@@ -1139,6 +1180,36 @@ gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_
     if (err != cudaSuccess) return cuda_err(err);
   }
   return GS_OK;
+}
+
+gs_status tree_sums(TreeWork& w, const float4* raw, const float4* pack, const float4* abpack,
+                    int64_t N, const double* center, double s, double mu, double* sums,
+                    int64_t cap, int64_t* n_nodes, cudaStream_t st) {
+  TreeArrays t;
+  BHLists L;
+  views(w, 0, &t, &L);
+  cudaError_t err;
+  if ((err = build(t, (int)N, raw, pack, abpack, BHForest{}, st)) != cudaSuccess)
+    return cuda_err(err);
+  uint32_t nint = 0;
+  if ((err = cudaMemcpyAsync(&nint, t.offs + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_err(err);
+  const int64_t M = N + (int64_t)nint;
+  if (n_nodes) *n_nodes = M;
+  const int64_t m = std::min(M, cap);
+  if (!sums || m <= 0) return GS_OK;
+  double* d = nullptr;
+  if ((err = cudaMalloc(&d, 96 * m)) != cudaSuccess) return cuda_err(err);
+  k_export_sums<<<nblocks(m, 256), 256, 0, st>>>(t, (int)m, center, 1.0 / s, 1.0 / mu,
+                                                   abpack != nullptr, d);
+  note_launches(1);
+  err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaMemcpyAsync(sums, d, 96 * m, cudaMemcpyDefault, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  cudaFree(d);
+  return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
 // ---------------------------------------------------------------- tracers

@@ -79,6 +79,9 @@ gs_status bh_eval_fwd(TreeWork& w, const BHStep& b, const FwdEpi& e, bool counts
 gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts,
                       cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
+// Per-target decision record of the tree in b.slot (one point set, not the
+// truncation variant): tally = 4 N device int64 (see gs_bh_tally in gs.h).
+gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, cudaStream_t st);
 
 // Outside points (tracers, forward only) walking the tree of b.slot as
 // targets: positions xraw (FP32, by index), records xrec (scaled, by index);
@@ -104,6 +107,13 @@ gs_status bh_eval_targets(TreeWork& w, const BHStep& b, const BHTargets& x, cons
 gs_status tree_export(TreeWork& w, const float4* raw, const float4* pack, int64_t N,
                       uint32_t* codes, int32_t* order, int32_t* nodes, float* range, int64_t cap,
                       int64_t* n_nodes, cudaStream_t st);
+// Builds the tree on one state with its forward (abpack NULL) or adjoint
+// sums and exports each node's sums in input units (see gs_tree_sums in
+// gs.h); center, s, mu: the pack's recentring point (device), scale and
+// beta scale.
+gs_status tree_sums(TreeWork& w, const float4* raw, const float4* pack, const float4* abpack,
+                    int64_t N, const double* center, double s, double mu, double* sums,
+                    int64_t cap, int64_t* n_nodes, cudaStream_t st);
 // Uniform-grid neighbour search of the truncation variant (GS_TRUNC with
 // the "trunc_grid" option, one point set): cells of side 0.51 r (doubled
 // until at most grid_cells(N) cells cover the FP32 bounding box), points

@@ -210,6 +210,12 @@ __device__ __forceinline__ GroupInfo target_group(const TreeArrays& t, int N, co
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            bool scheduled, cudaStream_t st);
+// Decision record of every target of one point set (no truncation): tally
+// (4 N int64, zeroed by the caller) accumulates per original index {point
+// interactions, node interactions, fingerprint sums of each} -- the walk's
+// own decisions, recorded instead of listed.
+cudaError_t launch_bh_tally(const TreeArrays& t, int N, const float4* raw, float thr,
+                            const WalkGroups& wg, int64_t* tally, cudaStream_t st);
 // fallback for overflowed lists, evaluation, fixed-order combine + epilogue;
 // scheduled: evaluate in L.order (written by a scheduled walk of these lists)
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,

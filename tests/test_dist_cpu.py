@@ -84,6 +84,9 @@ def test_reference_arm_prints_the_contract_line():
               "vs_baseline", "dtype", "data", "config"):
         assert k in d, k
     assert d["steps"] == 1 and d["warmup"] == 0 and "workload" in d["config"]
+    # ms_per_step is the measured step (one forward + one adjoint right-hand
+    # side); value extrapolates it to one gradient of T steps
+    assert abs(d["value"] - d["ms_per_step"] * d["config"]["T"]) <= 1e-9 * d["value"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]

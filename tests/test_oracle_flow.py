@@ -229,3 +229,18 @@ def test_rk4_converges_at_fourth_order(oracle):
         errs.append(np.abs(np.concatenate([q1.ravel(), p1.ravel()]) - y_true).max())
     ratios = [errs[k] / errs[k + 1] for k in range(2)]
     assert all(13.0 < r < 19.0 for r in ratios), (errs, ratios)
+
+
+def test_python_euler_loop_equals_shoot(oracle):
+    """The step loop the GPU trajectory tests write in numpy (q += h F,
+    p += h Phi with the oracle's right-hand side) is the oracle's own
+    shooting, bit for bit, exact and Barnes-Hut."""
+    w = inputs.make("blobs", 300, 31, T=5)
+    for mode in (oracle.EXACT, oracle.BH):
+        q, p = w.q0.copy(), w.p0.copy()
+        h = 1.0 / w.T
+        for _ in range(w.T):
+            F, Phi, _ = oracle.rhs(q, p, w.sigma, mode=mode)
+            q, p = q + h * F, p + h * Phi
+        q1, p1, _ = oracle.shoot(w.q0, w.p0, w.sigma, w.T, mode=mode)
+        assert np.array_equal(q, q1) and np.array_equal(p, p1)
