@@ -1156,6 +1156,7 @@ gs_status gs_create(int device, gs_ctx** out) {
     delete c;
     return GS_ERR_CUDA;
   }
+  c->tree.d_status = c->d_status;
   *out = c;
   return GS_OK;
 }

@@ -40,6 +40,12 @@ constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// single-pass sort of one point set: three passes of 10-bit digits over the
+// 30-bit codes, OS_TILE keys per tile
+constexpr int OS_BITS = 10, OS_BINS = 1 << OS_BITS, OS_PASSES = 3;
+constexpr int OS_THREADS = 256, OS_WARPS = OS_THREADS / 32, OS_R = 8;
+constexpr int OS_TILE = OS_THREADS * OS_R;
+constexpr int MORTON_PTS = 4;  // points per thread of the Morton kernel
 
 thread_local char g_err[256] = "";
 
@@ -96,13 +102,20 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float ext, float
   return k > 1023u ? 1023u : k;
 }
 
+// Morton codes of one point set, MORTON_PTS points per thread: the root
+// box, each point's code (into key and codes), the digit histograms of the
+// three sort passes (hist, 3 x 1024, zeroed by the caller), and the node
+// bit masks and octant words of the node list zeroed for its build.
 __global__ void __launch_bounds__(256)
     k_morton(const float4* __restrict__ raw, int N, const float* __restrict__ part, int nparts,
-             uint32_t* key, uint32_t* perm, uint32_t* codes, float* bbox) {
+             uint32_t* key, uint32_t* codes, float* bbox, uint32_t* hist, uint32_t* mask,
+             uint32_t* nocc) {
   // the root box: every block folds the nparts partial boxes, all its
   // threads at once (min and max are exact: any order gives the same box)
   __shared__ float sh[6][8];
   __shared__ float box[6];
+  __shared__ uint32_t s_h[OS_PASSES * OS_BINS];
+  for (int k = threadIdx.x; k < OS_PASSES * OS_BINS; k += blockDim.x) s_h[k] = 0u;
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int k = threadIdx.x; k < nparts; k += blockDim.x)
     for (int a = 0; a < 3; a++) {
@@ -127,21 +140,30 @@ __global__ void __launch_bounds__(256)
     if (blockIdx.x == 0) bbox[a] = v;
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const float4 r = raw[i];
   float ext[3], inv[3];
   for (int a = 0; a < 3; a++) {
     ext[a] = __fsub_rn(box[3 + a], box[a]);
     inv[a] = ext[a] > 0.f ? __fdiv_rn(1024.0f, ext[a]) : 0.f;
   }
-  const uint32_t kx = quantise(r.x, box[0], ext[0], inv[0]);
-  const uint32_t ky = quantise(r.y, box[1], ext[1], inv[1]);
-  const uint32_t kz = quantise(r.z, box[2], ext[2], inv[2]);
-  const uint32_t c = (spread10(kx) << 2) | (spread10(ky) << 1) | spread10(kz);
-  key[i] = c;
-  perm[i] = (uint32_t)i;
-  codes[i] = c;
+  for (int r = 0; r < MORTON_PTS; r++) {
+    const int i = (blockIdx.x * MORTON_PTS + r) * blockDim.x + threadIdx.x;
+    if (i >= N) break;
+    const float4 q = raw[i];
+    const uint32_t kx = quantise(q.x, box[0], ext[0], inv[0]);
+    const uint32_t ky = quantise(q.y, box[1], ext[1], inv[1]);
+    const uint32_t kz = quantise(q.z, box[2], ext[2], inv[2]);
+    const uint32_t c = (spread10(kx) << 2) | (spread10(ky) << 1) | spread10(kz);
+    key[i] = c;
+    codes[i] = c;
+    mask[i] = 0u;
+    nocc[2 * i] = 0u;
+    nocc[2 * i + 1] = 0u;
+    for (int p = 0; p < OS_PASSES; p++)
+      atomicAdd(&s_h[p * OS_BINS + ((c >> (OS_BITS * p)) & (OS_BINS - 1))], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < OS_PASSES * OS_BINS; k += blockDim.x)
+    if (s_h[k]) atomicAdd(&hist[k], s_h[k]);
 }
 
 // Forest: one block per subject, its FP32 bounding box into sbox[6 s ..].
@@ -404,6 +426,198 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ key, const uint32_t* _
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------- single-pass sort
+// Stable LSD radix sort of the 30-bit codes of one point set in three passes
+// of 10 bits with one kernel per pass.  A tile of OS_TILE keys ranks its
+// keys stably by digit, publishes its count of each digit and adds up the
+// counts of the tiles before it by decoupled look-back (the single-pass
+// prefix scan of Merrill and Garland, 2016, applied per digit as in the
+// one-kernel-per-digit radix sort of Adinets and Merrill, 2022); the digit
+// histograms of all three passes come from the Morton kernel.  Tiles are
+// numbered in the order blocks start, so every tile a look-back waits for
+// belongs to a block that is running or done.
+//
+// Look-back word of a (tile, digit): bits 62-63 the kind (0 nothing yet,
+// LB_AGG the tile's own count, LB_PRE the count of this and every earlier
+// tile), bits 0-61 the count.
+constexpr unsigned long long LB_AGG = 1ull << 62, LB_PRE = 2ull << 62;
+constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
+constexpr long long LB_SPIN_CYCLES = 2000000000LL;  // about 1 s of SM clock
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Publishes the tile's own count (tile > 0; tile 0 publishes its prefix).
+__device__ __forceinline__ void lb_publish(unsigned long long* word, int tile,
+                                           unsigned long long cnt) {
+  lb_store(word, (tile == 0 ? LB_PRE : LB_AGG) | cnt);
+}
+
+// Exclusive prefix of tile `tile` (words of tile j at stat[j * stride]),
+// whose own count `cnt` is published: adds the counts of the tiles before it
+// back to the first one with a published prefix, then publishes its own
+// prefix.  A word that stays empty for about a second records ST_TIMEOUT in
+// *status and ends the look-back (the result is then wrong, and the call
+// reports the timeout; every position computed from it is bounds-checked).
+__device__ unsigned long long lb_prefix(unsigned long long* stat, size_t stride, int tile,
+                                        unsigned long long cnt, int* status) {
+  if (tile == 0) return 0ull;
+  unsigned long long excl = 0ull;
+  int j = tile - 1;
+  long long t0 = clock64();
+  while (true) {
+    const unsigned long long v = lb_load(stat + (size_t)j * stride);
+    const unsigned long long kind = v & ~LB_VAL;
+    if (kind == 0ull) {
+      if (clock64() - t0 > LB_SPIN_CYCLES) {
+        atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += v & LB_VAL;
+    if (kind == LB_PRE || j == 0) break;
+    j--;
+    t0 = clock64();
+  }
+  lb_store(stat + (size_t)tile * stride, LB_PRE | (excl + cnt));
+  return excl;
+}
+
+// One pass over digit (key >> shift) & 1023.  val_in NULL: the values are
+// the input positions (the first pass).  ghist: the pass's 1024 digit counts
+// over all keys.
+__global__ void __launch_bounds__(OS_THREADS)
+    k_os_pass(const uint32_t* __restrict__ key_in, const uint32_t* __restrict__ val_in, int N,
+              int shift, const uint32_t* __restrict__ ghist, unsigned long long* stat, int* ctr,
+              int* status, uint32_t* key_out, uint32_t* val_out) {
+  __shared__ uint32_t s_wc[OS_WARPS][OS_BINS];  // per warp and digit: count, then offset
+  __shared__ uint32_t s_base[OS_BINS];          // global start of the digit, then + tile's
+  __shared__ uint32_t s_wsum[OS_WARPS];
+  __shared__ int s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(ctr, 1);
+  for (int k = tid; k < OS_WARPS * OS_BINS; k += OS_THREADS) (&s_wc[0][0])[k] = 0u;
+  // global start of each digit: exclusive scan of ghist, 4 digits per thread
+  constexpr int PER = OS_BINS / OS_THREADS;
+  uint32_t h[PER], hs = 0u;
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    h[k] = ghist[PER * tid + k];
+    hs += h[k];
+  }
+  uint32_t inc = hs;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_wsum[w] = inc;
+  __syncthreads();
+  uint32_t before = 0u;
+  for (int k = 0; k < w; k++) before += s_wsum[k];
+  uint32_t run = before + inc - hs;
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    s_base[PER * tid + k] = run;
+    run += h[k];
+  }
+  __syncthreads();
+  const int tile = s_tile;
+  // stable ranks within the warp's keys (input order: warp, round, lane)
+  const int base = tile * OS_TILE + w * (32 * OS_R);
+  uint32_t kk[OS_R], vv[OS_R], rk[OS_R];
+#pragma unroll
+  for (int r = 0; r < OS_R; r++) {
+    const int i = base + r * 32 + lane;
+    const bool valid = i < N;
+    kk[r] = valid ? key_in[i] : 0u;
+    vv[r] = valid ? (val_in ? val_in[i] : (uint32_t)i) : 0u;
+    const uint32_t d = valid ? (kk[r] >> shift) & (OS_BINS - 1) : (uint32_t)OS_BINS;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0u;
+    if (valid && lane == leader) {
+      old = s_wc[w][d];
+      s_wc[w][d] = old + (uint32_t)__popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rk[r] = old + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: offsets of the warps within the tile, the tile's count,
+  // published first for all of this thread's digits, then the look-back
+  uint32_t cnt[PER];
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    const int d = tid + k * OS_THREADS;
+    uint32_t acc = 0u;
+    for (int ww = 0; ww < OS_WARPS; ww++) {
+      const uint32_t c = s_wc[ww][d];
+      s_wc[ww][d] = acc;
+      acc += c;
+    }
+    cnt[k] = acc;
+    lb_publish(stat + (size_t)tile * OS_BINS + d, tile, acc);
+  }
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    const int d = tid + k * OS_THREADS;
+    s_base[d] += (uint32_t)lb_prefix(stat + d, OS_BINS, tile, cnt[k], status);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < OS_R; r++) {
+    const int i = base + r * 32 + lane;
+    if (i >= N) continue;
+    const uint32_t d = (kk[r] >> shift) & (OS_BINS - 1);
+    const uint32_t pos = s_base[d] + s_wc[w][d] + rk[r];
+    if (pos < (uint32_t)N) {
+      key_out[pos] = kk[r];
+      val_out[pos] = vv[r];
+    }
+  }
+}
+
+// Single-pass exclusive scan of popc(in[0..n)) into out[0..n], out[n] =
+// total (the node offsets), with the same look-back over tiles.
+__global__ void __launch_bounds__(SCAN_THREADS)
+    k_scan_popc_1p(const uint32_t* __restrict__ in, int n, uint32_t* out,
+                   unsigned long long* stat, int* ctr, int* status) {
+  __shared__ int s_tile;
+  __shared__ uint32_t s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS], sum = 0u;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = base + k < n ? (uint32_t)__popc(in[base + k]) : 0u;
+    sum += v[k];
+  }
+  uint32_t tot;
+  uint32_t ex = block_excl_scan(sum, &tot);
+  if (threadIdx.x == 0) {
+    lb_publish(stat + tile, tile, tot);
+    s_excl = (uint32_t)lb_prefix(stat, 1, tile, tot, status);
+  }
+  __syncthreads();
+  ex += s_excl;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = s_excl + tot;
 }
 
 // ---------------------------------------------------------------- node list
@@ -751,6 +965,12 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
                o_wordn = take(4), o_gtick = take(4 * (size_t)groups);
+  // the single-pass sort's histograms, tile counters and look-back words and
+  // the node-offset scan's look-back words, contiguous (one memset per build)
+  const size_t os_tiles = nblocks(n, OS_TILE), sc_tiles = nblocks(std::max<int64_t>(n, 1), SCAN_TILE);
+  const size_t os_hist_b = 4 * OS_PASSES * OS_BINS, os_ctr_b = 64;
+  const size_t os_stat_b = 8 * OS_PASSES * os_tiles * OS_BINS, sc_stat_b = 8 * sc_tiles;
+  const size_t o_osreg = take(os_hist_b + os_ctr_b + os_stat_b + sc_stat_b);
   if (mem) {
     char* b = static_cast<char*>(mem);
     t->key = (uint32_t*)(b + o_key);
@@ -776,6 +996,11 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     L->worder = (int*)(b + o_word);
     L->worder_n = (int*)(b + o_wordn);
     L->gticket = (int*)(b + o_gtick);
+    t->os_hist = (uint32_t*)(b + o_osreg);
+    t->os_ctr = (int*)(b + o_osreg + os_hist_b);
+    t->os_stat = (unsigned long long*)(b + o_osreg + os_hist_b + os_ctr_b);
+    t->sc_stat = (unsigned long long*)(b + o_osreg + os_hist_b + os_ctr_b + os_stat_b);
+    t->os_bytes = os_hist_b + os_ctr_b + os_stat_b + sc_stat_b;
   }
   return o;
 }
@@ -834,10 +1059,35 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     k_morton_subjects<<<nblocks(N, 256), 256, 0, st>>>(raw, N, f.off, f.S, f.sbox, t.key, t.perm,
                                                        t.codes);
   } else {
+    // one point set: codes, the three digit histograms, then the
+    // single-pass sort (three kernels) and the single-pass node-offset scan
     const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
+    TRY(cudaMemsetAsync(t.os_hist, 0, t.os_bytes, st));
     k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
-    k_morton<<<nblocks(N, 256), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb, t.key, t.perm,
-                                              t.codes, t.bbox);
+    k_morton<<<nblocks(N, 256 * MORTON_PTS), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb,
+                                                             t.key_alt, t.codes, t.bbox,
+                                                             t.os_hist, t.mask, t.nocc);
+    const unsigned ntiles = nblocks(N, OS_TILE);
+    const size_t stat_pass = (size_t)ntiles * OS_BINS;
+    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key_alt, nullptr, N, 0, t.os_hist, t.os_stat,
+                                             t.os_ctr, t.status, t.key, t.perm);
+    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key, t.perm, N, OS_BITS, t.os_hist + OS_BINS,
+                                             t.os_stat + stat_pass, t.os_ctr + 1, t.status,
+                                             t.key_alt, t.perm_alt);
+    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key_alt, t.perm_alt, N, 2 * OS_BITS,
+                                             t.os_hist + 2 * OS_BINS, t.os_stat + 2 * stat_pass,
+                                             t.os_ctr + 2, t.status, t.key, t.perm);
+    TRY(cudaGetLastError());
+    if (N > 1)
+      k_owners<<<nblocks(N - 1, 256), 256, 0, st>>>(t.key, nullptr, N, t.mask, t.own_a, t.own_b);
+    k_scan_popc_1p<<<nblocks(N, SCAN_TILE), SCAN_THREADS, 0, st>>>(t.mask, N, t.offs, t.sc_stat,
+                                                                   t.os_ctr + 3, t.status);
+    k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, nullptr, N, t.mask, t.offs, t.own_a,
+                                                   t.own_b, t.nsc, t.ninfo, t.nparent, t.nocc,
+                                                   t.acnt);
+    launch_aggregate(t, N, raw, pack, abpack, true, st);
+    note_launches(9 + (N > 1 ? 1 : 0));
+    return cudaGetLastError();
   }
   launches += 2;
   TRY(cudaGetLastError());
@@ -894,6 +1144,7 @@ void views(const TreeWork& w, int slot, TreeArrays* t, BHLists* L) {
   carve_shared(w.mem, w.cap_n, w.cap_groups, t, L);
   carve_slot(static_cast<char*>(w.smem) + (size_t)slot * w.slot_bytes, w.cap_n, w.cap_groups,
              w.lcap, t, L);
+  t->status = w.d_status;
 }
 
 // Walk lists per slice for G groups: the request, else two when one list

@@ -25,6 +25,7 @@ struct TreeWork {
   int lcap_req = 0;      // requested entries per list (0 = budget-based pool)
   int lcap_from_req = 0; // the request the current allocation was made for
   int wsplit_req = 0;    // walk lists per slice: 0 = by tree size, else 1 or 2
+  int* d_status = nullptr;  // device status word of the owning context
 };
 
 // Many independent point sets ("subjects") in one forest.  Subject s owns

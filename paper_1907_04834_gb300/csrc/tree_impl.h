@@ -51,6 +51,13 @@ struct TreeArrays {
   int32_t* acnt;    // arrival counters of the bottom-up pass
   double* isum;     // 12 per node: sums of xs, p, a, b over members (FP32 pairs)
   int64_t* counts;  // {point interactions, node interactions}
+  // single-pass sort and scan of one point set (zeroed together, os_bytes):
+  uint32_t* os_hist;            // 3 x 1024 digit counts of the 30-bit codes
+  int* os_ctr;                  // tile counters: 3 sort passes, the node-offset scan
+  unsigned long long* os_stat;  // 3 passes x sort tiles x 1024 look-back words
+  unsigned long long* sc_stat;  // scan tiles look-back words
+  size_t os_bytes;
+  int* status;      // the context's device status word (bounded waits record here)
 };
 
 // Interaction lists of one traversal.  A group of 32 points has BH_SLICES

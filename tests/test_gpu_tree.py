@@ -76,3 +76,21 @@ def test_tree_flat_axis(oracle):
     t = oracle.tree(q, np.zeros_like(q))
     ref, _ = oracle_node_list(t)
     assert np.array_equal(npy(g["nodes"]).astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("n,distinct,seed", [(9000, 7, 21), (70000, 3000, 22), (5000, 1, 23)])
+def test_tree_heavy_duplicates(oracle, n, distinct, seed):
+    """Many equal codes spread over many sort tiles: the sort must keep
+    equal codes in input order (the oracle's insertion order), whole
+    depth-10 lists included."""
+    w = inputs.make("blobs", distinct + 1, seed)
+    rng = np.random.default_rng(seed)
+    q = w.q0[rng.integers(0, distinct, size=n)].copy() if distinct > 1 else \
+        np.repeat(w.q0[:1], n, axis=0)
+    g = gs.tree(dt(q))
+    _, code = oracle.morton(q)
+    assert np.array_equal(npy(g["codes"]).view(np.uint32), code)
+    t = oracle.tree(q, np.zeros_like(q))
+    assert np.array_equal(npy(g["order"]).astype(np.int64), t["order"])
+    ref, _ = oracle_node_list(t)
+    assert np.array_equal(npy(g["nodes"]).astype(np.int64), ref)

@@ -72,3 +72,20 @@ def test_adjoint_rows_match_full(oracle):
     F, Phi, _ = oracle.rhs(w.q0, w.p0, w.sigma)
     rF, rP = oracle.rhs_rows(w.q0, w.p0, w.sigma, rows)
     assert np.array_equal(rF, F[rows]) and np.array_equal(rP, Phi[rows])
+
+
+def test_adjoint_along_a_given_path_is_the_oracles(oracle):
+    """The numpy step and adjoint loops of the path helpers reproduce the
+    oracle's own shooting and gradient on its own path: states bit for bit,
+    the gradient bit for bit, E to summation order (exact and Barnes-Hut)."""
+    from oracle_paths import euler_path, grad_on_path, step_residual
+    w = inputs.make("blobs", 400, 33, T=5)
+    for mode in (oracle.EXACT, oracle.BH):
+        qs, ps = euler_path(oracle, w.q0, w.p0, w.sigma, w.T, mode)
+        q1, p1, _ = oracle.shoot(w.q0, w.p0, w.sigma, w.T, mode=mode)
+        assert np.array_equal(qs[-1], q1) and np.array_equal(ps[-1], p1)
+        assert step_residual(oracle, qs, ps, w.sigma, mode) == (0.0, 0.0)
+        E, g = grad_on_path(oracle, qs, ps, w.X, w.sigma, w.lam, mode)
+        Eo, go, _ = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, w.T, w.lam, mode=mode)
+        assert np.array_equal(g, go)
+        np.testing.assert_allclose(E, Eo, rtol=1e-13)
