@@ -78,6 +78,8 @@ def _load():
     lib.gsref_bh_list.argtypes = [i64, _f64p, _f64p, dbl, dbl, cint, cint, i64, i64, _i64p,
                                   _i64p]
     lib.gsref_bh_list.restype = i64
+    lib.gsref_shoot_grad_sympl.argtypes = [i64, _f64p, _f64p, _f64p, dbl, cint, dbl, cint, dbl,
+                                           cint, cint, cint, _f64p, _f64p, _f64p]
     lib.gsref_bh_tally.argtypes = [i64, _f64p, dbl, dbl, cint, cint, _i64p]
     lib.gsref_num_threads.restype = cint
     _lib = lib
@@ -196,6 +198,19 @@ def shoot_grad(q0, p0, X, sigma, T, lam, mode=EXACT, thresh=3.0, leaf=1, crit=0)
     grad, q1 = np.empty_like(q0), np.empty_like(q0)
     _load().gsref_shoot_grad(q0.shape[0], q0, p0, X, float(sigma), int(T), float(lam),
                              int(mode), float(thresh), int(leaf), int(crit), E, grad, q1)
+    return E, grad, q1
+
+
+def shoot_grad_sympl(q0, p0, X, sigma, T, lam, iters, mode=EXACT, thresh=3.0, leaf=1, crit=0):
+    """Objective (Eq. 2) and dE/dp0 for the semi-implicit scheme of
+    shoot_sympl (`iters` fixed-point passes per step; 0 = shoot_grad), by
+    the discrete adjoint of its step: (E, grad, q1)."""
+    q0, p0, X = _c(q0), _c(p0), _c(X)
+    E = np.zeros(3)
+    grad, q1 = np.empty_like(q0), np.empty_like(q0)
+    _load().gsref_shoot_grad_sympl(q0.shape[0], q0, p0, X, float(sigma), int(T), float(lam),
+                                   int(mode), float(thresh), int(leaf), int(crit), int(iters),
+                                   E, grad, q1)
     return E, grad, q1
 
 

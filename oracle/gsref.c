@@ -847,6 +847,114 @@ void gsref_shoot_grad(int64_t N, const double *q0, const double *p0,
   free(dB);
 }
 
+/* Objective (Eq. 2) and its gradient with respect to p0 for the
+ * semi-implicit scheme of gsref_shoot_sympl (M = iters fixed-point passes
+ * per step): the discrete adjoint of that step, in the same spirit as the
+ * backward stage of gsref_shoot_grad.  With r_0 = p^k and r_m = p^k + h
+ * Phi(q^k, r_{m-1}), a = dE/dq^{k+1}, b = dE/dp^{k+1}, and [x, y](r) the
+ * adjoint right-hand side of gsref_adj_rhs at (q^k, r) with alpha = x,
+ * beta = y (its two parts dA, dB):
+ *   rho_M     = h dB[a, b](r_M)
+ *   rho_{m-1} = h dB[0, rho_m](r_{m-1}),                m = M .. 1
+ *   dE/dq^k   = a + h dA[a, b](r_M) + sum_{m=1..M} h dA[0, rho_m](r_{m-1})
+ *   dE/dp^k   = b + sum_{m=0..M} rho_m
+ * (r_M enters the update q^{k+1} = q^k + h F(q^k, r_M), p^{k+1} = p^k + h
+ * Phi(q^k, r_M); each r_m depends on p^k directly and through r_{m-1}, and
+ * on q^k).  dE/dp0 = beta^0 + F(q0, p0).  The passes are recomputed from
+ * (q^k, p^k) in the backward sweep.  M = 0 is gsref_shoot_grad. */
+void gsref_shoot_grad_sympl(int64_t N, const double *q0, const double *p0,
+                            const double *X, double sigma, int T, double lambda,
+                            int mode, double thresh, int leaf, int crit, int iters,
+                            double *E, double *grad, double *q1) {
+  size_t sz = (size_t)N * 3;
+  int M = iters;
+  double *qs = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
+  double *ps = (double *)malloc((size_t)(T + 1) * sz * sizeof(double));
+  double *rs = (double *)malloc((size_t)(M + 1) * sz * sizeof(double));
+  double *F = (double *)malloc(sz * sizeof(double));
+  double *F0 = (double *)malloc(sz * sizeof(double));
+  double *Phi = (double *)malloc(sz * sizeof(double));
+  double *al = (double *)malloc(sz * sizeof(double));
+  double *be = (double *)malloc(sz * sizeof(double));
+  double *dA = (double *)malloc(sz * sizeof(double));
+  double *dB = (double *)malloc(sz * sizeof(double));
+  double *rho = (double *)malloc(sz * sizeof(double));
+  double *zero = (double *)calloc(sz, sizeof(double));
+  double h = 1.0 / (double)T;
+  memcpy(qs, q0, sz * sizeof(double));
+  memcpy(ps, p0, sz * sizeof(double));
+  for (int k = 0; k < T; k++) {
+    double *qk = qs + (size_t)k * sz, *pk = ps + (size_t)k * sz;
+    memcpy(rs, pk, sz * sizeof(double));
+    for (int m = 0; m <= M; m++) {
+      gsref_rhs(N, qk, rs, sigma, mode, thresh, leaf, crit, F, Phi, NULL);
+      if (k == 0 && m == 0) memcpy(F0, F, sz * sizeof(double));
+      if (m < M)
+        for (size_t i = 0; i < sz; i++) rs[i] = pk[i] + h * Phi[i];
+    }
+    for (size_t i = 0; i < sz; i++) {
+      qk[sz + i] = qk[i] + h * F[i];
+      pk[sz + i] = pk[i] + h * Phi[i];
+    }
+  }
+  const double *qT = qs + (size_t)T * sz;
+  double data = 0.0;
+  for (size_t i = 0; i < sz; i++) {
+    double r = qT[i] - X[i];
+    data += r * r;
+  }
+  double H0 = half_p_dot_F(N, p0, F0);
+  E[0] = H0 + lambda * data;
+  E[1] = H0;
+  E[2] = lambda * data;
+  for (size_t i = 0; i < sz; i++) {
+    al[i] = 2.0 * lambda * (qT[i] - X[i]);
+    be[i] = 0.0;
+  }
+  for (int k = T - 1; k >= 0; k--) {
+    const double *qk = qs + (size_t)k * sz, *pk = ps + (size_t)k * sz;
+    /* the passes of step k: rs[m] = r_m */
+    memcpy(rs, pk, sz * sizeof(double));
+    for (int m = 1; m <= M; m++) {
+      gsref_rhs(N, qk, rs + (size_t)(m - 1) * sz, sigma, mode, thresh, leaf, crit, F, Phi,
+                NULL);
+      for (size_t i = 0; i < sz; i++) rs[(size_t)m * sz + i] = pk[i] + h * Phi[i];
+    }
+    /* the update's terms at r_M, then the passes' terms back to r_0; al and
+     * be accumulate dE/dq^k and dE/dp^k */
+    gsref_adj_rhs(N, qk, rs + (size_t)M * sz, al, be, sigma, mode, thresh, leaf, crit, dA,
+                  dB, NULL);
+    for (size_t i = 0; i < sz; i++) {
+      al[i] += h * dA[i];
+      rho[i] = h * dB[i];
+      be[i] += rho[i];
+    }
+    for (int m = M; m >= 1; m--) {
+      gsref_adj_rhs(N, qk, rs + (size_t)(m - 1) * sz, zero, rho, sigma, mode, thresh, leaf,
+                    crit, dA, dB, NULL);
+      for (size_t i = 0; i < sz; i++) {
+        al[i] += h * dA[i];
+        rho[i] = h * dB[i];
+        be[i] += rho[i];
+      }
+    }
+  }
+  for (size_t i = 0; i < sz; i++) grad[i] = be[i] + F0[i];
+  if (q1) memcpy(q1, qT, sz * sizeof(double));
+  free(qs);
+  free(ps);
+  free(rs);
+  free(F);
+  free(F0);
+  free(Phi);
+  free(al);
+  free(be);
+  free(dA);
+  free(dB);
+  free(rho);
+  free(zero);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense velocity field (Eq. 3) and points carried by it.                     */
 /* ------------------------------------------------------------------------ */

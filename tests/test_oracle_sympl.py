@@ -100,3 +100,47 @@ def test_sympl_converges_to_dop853(oracle):
             for T in (50, 100, 200)]
     ratios = [errs[k] / errs[k + 1] for k in range(2)]
     assert all(1.8 < r < 2.2 for r in ratios), (errs, ratios)
+
+
+def test_gradient_zero_passes_is_explicit_gradient(oracle):
+    """The semi-implicit scheme's gradient with no passes is the explicit
+    scheme's, bit for bit (exact and Barnes-Hut)."""
+    from paper_1907_04834_gb300 import inputs
+    w = inputs.make("blobs", 300, 6, T=5)
+    for mode in (oracle.EXACT, oracle.BH):
+        a = oracle.shoot_grad(w.q0, w.p0, w.X, w.sigma, w.T, w.lam, mode=mode)
+        b = oracle.shoot_grad_sympl(w.q0, w.p0, w.X, w.sigma, w.T, w.lam, 0, mode=mode)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("M", [1, 2, 4])
+def test_gradient_matches_finite_differences(oracle, M):
+    """Central differences of the objective E(p0) = H(q0, p0) + lambda |q(1) -
+    X|^2 of the semi-implicit shooting (forward map of shoot_sympl, FP64)
+    along random directions against the adjoint gradient; strongly moving
+    points (momenta of several sigma per unit time) so the passes matter."""
+    q, p = _rand_cloud(40, 21 + M)
+    p = 3.0 * p
+    sigma, T, lam = 1.3, 6, 0.7
+    X = q + np.random.default_rng(M).normal(scale=0.5, size=q.shape)
+    E, g, q1 = oracle.shoot_grad_sympl(q, p, X, sigma, T, lam, M)
+    q1s, _, H = oracle.shoot_sympl(q, p, sigma, T, M)
+    assert np.array_equal(q1, q1s)
+    assert abs(E[0] - (H[0] + lam * np.sum((q1s - X) ** 2))) <= 1e-12 * abs(E[0])
+
+    def Eof(pp):
+        qq, _, HH = oracle.shoot_sympl(q, pp, sigma, T, M)
+        return HH[0] + lam * np.sum((qq - X) ** 2)
+
+    rng = np.random.default_rng(100 + M)
+    eps = 1e-5
+    for _ in range(6):
+        v = rng.normal(size=p.shape)
+        v /= np.linalg.norm(v)
+        fd = (Eof(p + eps * v) - Eof(p - eps * v)) / (2 * eps)
+        d = float(np.sum(g * v))
+        assert abs(fd - d) <= 1e-6 * np.linalg.norm(g), (fd, d)
+    # the passes change the gradient: it is not the explicit scheme's
+    _, g0, _ = oracle.shoot_grad(q, p, X, sigma, T, lam)
+    assert np.linalg.norm(g - g0) > 1e-4 * np.linalg.norm(g0)
