@@ -3,14 +3,17 @@
 //   2. 10-bit quantised coordinates per axis and 30-bit Morton codes:
 //      ext = hi - lo, inv = 1024 / ext, u = (x - lo) * inv, k = min(trunc(u), 1023),
 //      k = 0 on a zero-extent axis (all FP32, round to nearest, no contraction);
-//   3. stable LSD radix sort of (code, index), 4 passes of 8 bits;
+//   3. stable LSD radix sort of (code, index): one point set in three
+//      passes of 10 bits, one kernel each (decoupled look-back); a forest
+//      in 8-bit passes with the subject index as the leading digits;
 //   4. the compressed octree in depth-first preorder (see tree_impl.h): one
 //      owner boundary per internal node, node offsets by a prefix sum of the
 //      per-position depth masks, skip pointers and parents by galloping search
 //      over the sorted codes;
-//   5. bottom-up aggregates (count, FP32 actual range, FP64 sums of scaled
-//      positions, momenta and, in the backward stage, alpha and beta): the
-//      last child to arrive at a node (atomic counter) finishes it.
+//   5. node aggregates (count, FP32 actual range, sums of scaled positions,
+//      momenta and, in the backward stage, alpha and beta as compensated
+//      FP32 pairs) over each node's range of sorted points, from the points
+//      and the precomputed sums of aligned chunks of 32 and 1024 points.
 // The paper inserts points one at a time into a pointer tree; the node set,
 // the members of every node and the depth-first order are the same here (the
 // tests compare them bit for bit with the oracle's insertion tree).
@@ -105,11 +108,10 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float ext, float
 // Morton codes of one point set, MORTON_PTS points per thread: the root
 // box, each point's code (into key and codes), the digit histograms of the
 // three sort passes (hist, 3 x 1024, zeroed by the caller), and the node
-// bit masks and octant words of the node list zeroed for its build.
+// bit masks of the node list zeroed for its build.
 __global__ void __launch_bounds__(256)
     k_morton(const float4* __restrict__ raw, int N, const float* __restrict__ part, int nparts,
-             uint32_t* key, uint32_t* codes, float* bbox, uint32_t* hist, uint32_t* mask,
-             uint32_t* nocc) {
+             uint32_t* key, uint32_t* codes, float* bbox, uint32_t* hist, uint32_t* mask) {
   // the root box: every block folds the nparts partial boxes, all its
   // threads at once (min and max are exact: any order gives the same box)
   __shared__ float sh[6][8];
@@ -156,8 +158,6 @@ __global__ void __launch_bounds__(256)
     key[i] = c;
     codes[i] = c;
     mask[i] = 0u;
-    nocc[2 * i] = 0u;
-    nocc[2 * i + 1] = 0u;
     for (int p = 0; p < OS_PASSES; p++)
       atomicAdd(&s_h[p * OS_BINS + ((c >> (OS_BITS * p)) & (OS_BINS - 1))], 1u);
   }
@@ -726,25 +726,15 @@ __device__ int parent_of(const uint32_t* sk, const uint32_t* ss, const uint32_t*
   return node_id(offs, mask, pa, Dp);
 }
 
-// A node (first sorted point a) under a parent of depth Dp < 10 lies in the
-// parent's octant (code >> (27 - 3 Dp)) & 7; distinct children have distinct
-// octants, so a child's rank among its siblings (preorder) is the number of
-// occupied octants below its own.  Parents of depth 10 hold runs of equal
-// codes: their children are consecutive leaves.
-__device__ __forceinline__ void note_octant(uint32_t* nocc, int id, int par, int Dp,
-                                            uint32_t code) {
-  if (par < 0 || Dp >= 10) return;
-  const uint32_t oct = (code >> (27 - 3 * Dp)) & 7u;
-  atomicOr(&nocc[par], 1u << oct);
-  atomicOr(&nocc[id], oct << 8);
-}
-
+// Leaf of every sorted point and the internal node owned by each boundary:
+// {skip, count}, {depth, first}, parent, and the internal node's entry in
+// the list of internal nodes (its rank among them: its preorder id minus the
+// number of leaves before it, which is its first member's position).
 __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ ss,
                               int N,
                               const uint32_t* __restrict__ mask, const uint32_t* __restrict__ offs,
                               const int32_t* __restrict__ own_a, const int32_t* __restrict__ own_b,
-                              int2* nsc, int2* ninfo, int32_t* nparent, uint32_t* nocc,
-                              int32_t* acnt) {
+                              int2* nsc, int2* ninfo, int32_t* nparent, int32_t* inode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   // the leaf of sorted point i
@@ -752,28 +742,23 @@ __global__ void k_write_nodes(const uint32_t* __restrict__ sk, const uint32_t* _
   int Dp;
   nsc[leaf] = make_int2(leaf + 1, 1);
   ninfo[leaf] = make_int2(-1, i);
-  const int lpar = parent_of(sk, ss, offs, mask, N, i, i, Dp);
-  nparent[leaf] = lpar;
-  note_octant(nocc, leaf, lpar, Dp, sk[i]);
-  acnt[leaf] = 0;
+  nparent[leaf] = parent_of(sk, ss, offs, mask, N, i, i, Dp);
   // the internal node owned by boundary i
   if (i < N - 1 && own_a[i] >= 0) {
     const int a = own_a[i], b = own_b[i], D = delta_at(sk, ss, i);
     const int id = node_id(offs, mask, a, D);
     nsc[id] = make_int2(b + 1 + (int)offs[b + 1], b - a + 1);
     ninfo[id] = make_int2(D, a);
-    const int par = parent_of(sk, ss, offs, mask, N, a, b, Dp);
-    nparent[id] = par;
-    note_octant(nocc, id, par, Dp, sk[a]);
-    acnt[id] = 0;
+    nparent[id] = parent_of(sk, ss, offs, mask, N, a, b, Dp);
+    inode[id - a] = id;
   }
 }
 
 // ---------------------------------------------------------------- aggregates
 // Member sums are carried as unevaluated FP32 pairs (Pair, pair_add): FP64
-// arithmetic is the slow path on this GPU.  The pairs are added in the same
-// fixed bottom-up order as the tree's preorder, so results are deterministic.
-// (hi + lo) / n rounded to FP32.  n < 2^24 (exact in FP32): q = hi / n, then
+// arithmetic is the slow path on this GPU.  Each node's pairs are added in
+// a fixed order (below), so results are deterministic.
+// pair_mean: (hi + lo) / n rounded to FP32.  n < 2^24 (exact in FP32): q = hi / n, then
 // one correction by the remainder hi - q n (exact by FMA) plus lo.  Larger
 // counts (only the top nodes of trees beyond 2^24 points) divide in FP64.
 __device__ __forceinline__ float pair_mean(const Pair& s, int count) {
@@ -784,155 +769,191 @@ __device__ __forceinline__ float pair_mean(const Pair& s, int count) {
   return __fadd_rn(q, __fdiv_rn(r, n));
 }
 
-// atomicAdd with acquire-release semantics at GPU scope: orders this
-// thread's earlier writes before the add and its later reads after it.
-__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
-  int old;
-  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
-               : "=r"(old)
-               : "l"(p), "r"(v)
-               : "memory");
-  return old;
-}
+// Node sums over member ranges.  A node's members are the sorted points
+// [first, first + count), so its sums are taken over that range, cut at
+// multiples of 32 and 1024 into at most 31 points, at most 31 chunks of 32,
+// whole chunks of 1024, at most 31 chunks of 32 and at most 31 points, in
+// that order; the chunks' sums are formed once per aggregation.  Every sum
+// is a compensated FP32 pair (TwoSum per addition) in a fixed order, so the
+// results are deterministic, and no node waits for another.
+//
+// ADJ: the sums of alpha and beta too (12 components, else 6: xs and p).
+// BOX: also the FP32 actual ranges and the nodes' boxes (forward build);
+// without, the boxes stored with this tree stay (backward-stage reuse).
 
-// One thread per sorted point writes its leaf's record (and box), then walks
-// up: before arriving at a parent (arrival counter) it enters its node in the
-// parent's child table, and the last child to arrive sums the parent's
-// children in preorder -- their indices all at hand, so the loads of one
-// level go out together -- and writes the parent's record (and box).
-// BOX = false: the boxes (and skips) of this tree are already stored; only
-// the sums and source records are recomputed (backward-stage reuse).
+// Pass 1, one thread per sorted point, a block per chunk of 1024: the
+// leaf's record (and box), the sorted copy of the point's values, and the
+// sums (and ranges) of its chunk of 32 and of 1024 (butterfly over lanes;
+// lane 0's additions are in a fixed order).
 template <bool ADJ, bool BOX>
-__global__ void k_aggregate(TreeArrays t, int N, const float4* __restrict__ raw,
-                            const float4* __restrict__ pack, const float4* __restrict__ abpack) {
+__global__ void __launch_bounds__(1024)
+    k_range_points(TreeArrays t, int N, const float4* __restrict__ raw,
+                   const float4* __restrict__ pack, const float4* __restrict__ abpack) {
   constexpr int NS = ADJ ? 12 : 6;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int o = (int)t.perm[i];
-  int x = i + (int)t.offs[i + 1];
-  float2* isum = reinterpret_cast<float2*>(t.isum);
-  {
-    if (BOX) {
-      const float4 r = raw[o];
-      t.nbox[2 * x] = make_float4(r.x, r.y, r.z, __int_as_float(x + 1));
-      t.nbox[2 * x + 1] = make_float4(r.x, r.y, r.z, __int_as_float(1));
-    }
+  __shared__ float2 s_sum[32][NS];
+  __shared__ float s_box[32][6];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  const bool valid = i < N;
+  float v[NS];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+  for (int k = 0; k < NS; k++) v[k] = 0.f;
+  if (valid) {
+    const int o = (int)t.perm[i];
+    const int x = i + (int)t.offs[i + 1];
     float a[3], b[3];
     pack_read(pack, o, a, b);
-    t.nrec[4 * x] = make_float4(a[0], a[1], a[2], 0.f);
-    t.nrec[4 * x + 1] = make_float4(b[0], b[1], b[2], 0.f);
+    v[0] = a[0], v[1] = a[1], v[2] = a[2], v[3] = b[0], v[4] = b[1], v[5] = b[2];
     if (ADJ) {
       pack_read(abpack, o, a, b);
-      t.nrec[4 * x + 2] = make_float4(a[0], a[1], a[2], 0.f);
-      t.nrec[4 * x + 3] = make_float4(b[0], b[1], b[2], 0.f);
+      v[NS - 6] = a[0], v[NS - 5] = a[1], v[NS - 4] = a[2];
+      v[NS - 3] = b[0], v[NS - 2] = b[1], v[NS - 1] = b[2];
     }
-  }
-  // The parent chain and the nodes' words (nsc, ninfo, nocc) are read-only
-  // here, so each level's are fetched one level ahead: the parent's index
-  // before this thread's arrival is decided, its words while the last
-  // arriver sums the children below.
-  int nx = 1;
-  uint32_t own = t.nocc[x];  // x's octant word
-  int par = t.nparent[x];
-  int2 sc = make_int2(0, 0);
-  int Dp = 0;
-  uint32_t pw = 0u;
-  if (par >= 0) sc = t.nsc[par], Dp = t.ninfo[par].x, pw = t.nocc[par];
-  while (par >= 0) {
-    const uint32_t occ = pw & 0xffu;
-    if (Dp < 10) {  // a leaf is entered as ~x (x >= 0), so the parent knows it without a load
-      const uint32_t oct = (own >> 8) & 7u;
-      t.child[8 * par + __popc(occ & ((1u << oct) - 1u))] = nx == 1 ? ~x : x;
-    }
-    const int gpar = t.nparent[par];
-    const int old = atom_add_acq_rel(&t.acnt[par], nx);
-    if (old + nx != sc.y) break;
-    int2 sc_n = make_int2(0, 0);
-    int Dp_n = 0;
-    uint32_t pw_n = 0u;
-    if (gpar >= 0) sc_n = t.nsc[gpar], Dp_n = t.ninfo[gpar].x, pw_n = t.nocc[gpar];
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    Pair S[NS];
 #pragma unroll
-    for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
-    auto add_child = [&](int c, bool leaf) {
-      if (BOX) {
-        const float4 bl = __ldcg(&t.nbox[2 * c]), bh = __ldcg(&t.nbox[2 * c + 1]);
-        lo[0] = fminf(lo[0], bl.x);
-        lo[1] = fminf(lo[1], bl.y);
-        lo[2] = fminf(lo[2], bl.z);
-        hi[0] = fmaxf(hi[0], bh.x);
-        hi[1] = fmaxf(hi[1], bh.y);
-        hi[2] = fmaxf(hi[2], bh.z);
-      }
-      if (leaf) {
-        float4 r[4];
-#pragma unroll
-        for (int q = 0; q < NS / 3; q++) r[q] = __ldcg(&t.nrec[4 * c + q]);
-#pragma unroll
-        for (int q = 0; q < NS / 3; q++) {
-          pair_add(S[3 * q], r[q].x);
-          pair_add(S[3 * q + 1], r[q].y);
-          pair_add(S[3 * q + 2], r[q].z);
-        }
-      } else {
-        float2 v[NS];
-#pragma unroll
-        for (int k = 0; k < NS; k++) v[k] = __ldcg(&isum[12 * (size_t)c + k]);
-#pragma unroll
-        for (int k = 0; k < NS; k++) pair_add(S[k], v[k]);
-      }
-    };
-    if (Dp < 10) {  // one child per occupied octant, in octant (= pre-) order
-      const int nch = __popc(occ);
-      int cs[8];
-      bool lf[8];
-#pragma unroll
-      for (int k = 0; k < 8; k++) {  // (clamped into the subtree: never an outside node)
-        const int v = k < nch ? __ldcg(&t.child[8 * par + k]) : par + 1;
-        lf[k] = v < 0;
-        cs[k] = min(max(v < 0 ? ~v : v, par + 1), sc.x - 1);
-      }
-#pragma unroll
-      for (int k = 0; k < 8; k++)
-        if (k < nch) add_child(cs[k], lf[k]);
-    } else {  // a run of equal codes: its points' leaves follow it
-      for (int c = par + 1; c <= par + sc.y; c++) add_child(c, true);
-    }
-    const int n = sc.y;
-#pragma unroll
-    for (int k = 0; k < NS; k++) isum[12 * (size_t)par + k] = pair_store(S[k]);
-    t.nrec[4 * par] = make_float4(pair_mean(S[0], n), pair_mean(S[1], n), pair_mean(S[2], n), 0.f);
-    t.nrec[4 * par + 1] = make_float4(pair_value(S[3]), pair_value(S[4]), pair_value(S[5]), 0.f);
-    if (ADJ) {
-      t.nrec[4 * par + 2] =
-          make_float4(pair_value(S[6]), pair_value(S[7]), pair_value(S[8]), 0.f);
-      t.nrec[4 * par + 3] =
-          make_float4(pair_mean(S[9], n), pair_mean(S[10], n), pair_mean(S[11], n), 0.f);
+    for (int r = 0; r < NS / 3; r++) {
+      const float4 f = make_float4(v[3 * r], v[3 * r + 1], v[3 * r + 2], 0.f);
+      t.nrec[4 * x + r] = f;
+      t.spt[4 * (size_t)i + r] = f;
     }
     if (BOX) {
-      t.nbox[2 * par] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
-      t.nbox[2 * par + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(sc.y));
+      const float4 q = raw[o];
+      t.nbox[2 * x] = make_float4(q.x, q.y, q.z, __int_as_float(x + 1));
+      t.nbox[2 * x + 1] = make_float4(q.x, q.y, q.z, __int_as_float(1));
+      t.sraw[i] = q;
+      lo[0] = hi[0] = q.x, lo[1] = hi[1] = q.y, lo[2] = hi[2] = q.z;
     }
-    x = par;
-    nx = sc.y;
-    own = pw;
-    par = gpar;
-    sc = sc_n;
-    Dp = Dp_n;
-    pw = pw_n;
+  }
+  Pair S[NS];
+#pragma unroll
+  for (int k = 0; k < NS; k++) S[k] = Pair{v[k], 0.f};
+  auto butterfly = [&]() {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+        const float oh = __shfl_xor_sync(0xffffffffu, S[k].hi, d);
+        const float ol = __shfl_xor_sync(0xffffffffu, S[k].lo, d);
+        pair_add(S[k], make_float2(oh, ol));
+      }
+      if (BOX)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], d));
+          hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], d));
+        }
+    }
+  };
+  butterfly();
+  const int c1 = i >> 5;  // this warp's chunk of 32
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; k++) s_sum[w][k] = make_float2(S[k].hi, S[k].lo);
+#pragma unroll
+    for (int a = 0; a < 3; a++) s_box[w][a] = lo[a], s_box[w][3 + a] = hi[a];
+    if (valid) {  // a chunk with at least one point
+#pragma unroll
+      for (int k = 0; k < NS; k++) t.c1sum[12 * (size_t)c1 + k] = make_float2(S[k].hi, S[k].lo);
+      if (BOX) {
+        t.c1box[2 * (size_t)c1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        t.c1box[2 * (size_t)c1 + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  if (w != 0) return;
+#pragma unroll
+  for (int k = 0; k < NS; k++) S[k] = Pair{s_sum[lane][k].x, s_sum[lane][k].y};
+#pragma unroll
+  for (int a = 0; a < 3; a++) lo[a] = s_box[lane][a], hi[a] = s_box[lane][3 + a];
+  butterfly();
+  if (lane == 0) {
+    const size_t c2 = blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < NS; k++) t.c2sum[12 * c2 + k] = make_float2(S[k].hi, S[k].lo);
+    if (BOX) {
+      t.c2box[2 * c2] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      t.c2box[2 * c2 + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+  }
+}
+
+// Pass 2, one thread per internal node (in preorder): sums (and range) over
+// its member range from points and chunks, then its record, its pair sums
+// and (BOX) its box with skip and count.
+template <bool ADJ, bool BOX>
+__global__ void __launch_bounds__(256) k_range_nodes(TreeArrays t, int N) {
+  constexpr int NS = ADJ ? 12 : 6;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int)t.offs[N]) return;
+  const int id = t.inode[r];
+  const int2 inf = t.ninfo[id], sc = t.nsc[id];
+  const int end = inf.y + sc.y;
+  Pair S[NS];
+#pragma unroll
+  for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  auto point = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < NS / 3; q++) {
+      const float4 f = __ldcg(&t.spt[4 * (size_t)i + q]);
+      pair_add(S[3 * q], f.x);
+      pair_add(S[3 * q + 1], f.y);
+      pair_add(S[3 * q + 2], f.z);
+    }
+    if (BOX) {
+      const float4 p = __ldcg(&t.sraw[i]);
+      lo[0] = fminf(lo[0], p.x), lo[1] = fminf(lo[1], p.y), lo[2] = fminf(lo[2], p.z);
+      hi[0] = fmaxf(hi[0], p.x), hi[1] = fmaxf(hi[1], p.y), hi[2] = fmaxf(hi[2], p.z);
+    }
+  };
+  auto chunk = [&](const float2* cs, const float4* cb, size_t c) {
+#pragma unroll
+    for (int k = 0; k < NS; k++) pair_add(S[k], __ldcg(&cs[12 * c + k]));
+    if (BOX) {
+      const float4 a = __ldcg(&cb[2 * c]), b = __ldcg(&cb[2 * c + 1]);
+      lo[0] = fminf(lo[0], a.x), lo[1] = fminf(lo[1], a.y), lo[2] = fminf(lo[2], a.z);
+      hi[0] = fmaxf(hi[0], b.x), hi[1] = fmaxf(hi[1], b.y), hi[2] = fmaxf(hi[2], b.z);
+    }
+  };
+  int i = inf.y;
+  while (i < end && (i & 31)) point(i++);
+  while (i + 32 <= end && (i & 1023)) chunk(t.c1sum, t.c1box, (size_t)(i >> 5)), i += 32;
+  while (i + 1024 <= end) chunk(t.c2sum, t.c2box, (size_t)(i >> 10)), i += 1024;
+  while (i + 32 <= end) chunk(t.c1sum, t.c1box, (size_t)(i >> 5)), i += 32;
+  while (i < end) point(i++);
+  float2* isum = reinterpret_cast<float2*>(t.isum);
+#pragma unroll
+  for (int k = 0; k < NS; k++) isum[12 * (size_t)id + k] = pair_store(S[k]);
+  const int n = sc.y;
+  t.nrec[4 * id] = make_float4(pair_mean(S[0], n), pair_mean(S[1], n), pair_mean(S[2], n), 0.f);
+  t.nrec[4 * id + 1] = make_float4(pair_value(S[3]), pair_value(S[4]), pair_value(S[5]), 0.f);
+  if (ADJ) {
+    t.nrec[4 * id + 2] = make_float4(pair_value(S[6]), pair_value(S[7]), pair_value(S[8]), 0.f);
+    t.nrec[4 * id + 3] =
+        make_float4(pair_mean(S[9], n), pair_mean(S[10], n), pair_mean(S[11], n), 0.f);
+  }
+  if (BOX) {
+    t.nbox[2 * id] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
+    t.nbox[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(n));
   }
 }
 
 void launch_aggregate(const TreeArrays& t, int N, const float4* raw, const float4* pack,
                       const float4* abpack, bool box, cudaStream_t st) {
-  const unsigned nb = nblocks(N, 256);
-  if (abpack) {
-    if (box) k_aggregate<true, true><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
-    else k_aggregate<true, false><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
+  const unsigned nb1 = nblocks(N, 1024), nb2 = nblocks(N, 256);
+  if (abpack && box) {
+    k_range_points<true, true><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
+    k_range_nodes<true, true><<<nb2, 256, 0, st>>>(t, N);
+  } else if (abpack) {
+    k_range_points<true, false><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
+    k_range_nodes<true, false><<<nb2, 256, 0, st>>>(t, N);
+  } else if (box) {
+    k_range_points<false, true><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
+    k_range_nodes<false, true><<<nb2, 256, 0, st>>>(t, N);
   } else {
-    if (box) k_aggregate<false, true><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
-    else k_aggregate<false, false><<<nb, 256, 0, st>>>(t, N, raw, pack, abpack);
+    k_range_points<false, false><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
+    k_range_nodes<false, false><<<nb2, 256, 0, st>>>(t, N);
   }
 }
 
@@ -960,8 +981,10 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_oa = take(4 * N1),
                o_ob = take(4 * N1), o_hist = take(4 * hist_n), o_hscan = take(4 * (hist_n + 1)),
                o_bsum = take(4 * bsum_n), o_bbp = take(4 * 6 * nb_bb), o_bb = take(4 * 6),
-               o_nrec = take(64 * M), o_acnt = take(4 * M), o_child = take(32 * M),
-               o_isum = take(96 * M), o_cnt = take(16),
+               o_nrec = take(64 * M), o_isum = take(96 * M), o_cnt = take(16),
+               o_spt = take(64 * N1), o_sraw = take(16 * N1),
+               o_c1s = take(96 * (N1 / 32 + 1)), o_c1b = take(32 * (N1 / 32 + 1)),
+               o_c2s = take(96 * (N1 / 1024 + 1)), o_c2b = take(32 * (N1 / 1024 + 1)),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
                o_wordn = take(4), o_gtick = take(4 * (size_t)groups);
@@ -987,9 +1010,13 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     t->bbox_part = (float*)(b + o_bbp);
     t->bbox = (float*)(b + o_bb);
     t->nrec = (float4*)(b + o_nrec);
-    t->acnt = (int32_t*)(b + o_acnt);
-    t->child = (int32_t*)(b + o_child);
     t->isum = (double*)(b + o_isum);
+    t->spt = (float4*)(b + o_spt);
+    t->sraw = (float4*)(b + o_sraw);
+    t->c1sum = (float2*)(b + o_c1s);
+    t->c1box = (float4*)(b + o_c1b);
+    t->c2sum = (float2*)(b + o_c2s);
+    t->c2box = (float4*)(b + o_c2b);
     t->counts = (int64_t*)(b + o_cnt);
     L->part = (float2*)(b + o_part);
     L->fb = (float2*)(b + o_fb);
@@ -1017,7 +1044,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     return at;
   };
   const size_t o_perm = take(4 * N1), o_offs = take(4 * (N1 + 1)), o_npar = take(4 * M),
-               o_nocc = take(4 * M),
+               o_inode = take(4 * N1),
                o_nsc = take(8 * M), o_ninfo = take(8 * M), o_nbox = take(32 * M),
                o_ent = take((size_t)chunks * BH_CHUNK * sizeof(int2)),
                o_next = take(4 * (size_t)chunks), o_head = take(4 * nw), o_len = take(4 * nw),
@@ -1027,7 +1054,7 @@ size_t carve_slot(void* mem, int64_t n, int64_t groups, int64_t chunks, TreeArra
     t->perm = (uint32_t*)(b + o_perm);
     t->offs = (uint32_t*)(b + o_offs);
     t->nparent = (int32_t*)(b + o_npar);
-    t->nocc = (uint32_t*)(b + o_nocc);
+    t->inode = (int32_t*)(b + o_inode);
     t->nsc = (int2*)(b + o_nsc);
     t->ninfo = (int2*)(b + o_ninfo);
     t->nbox = (float4*)(b + o_nbox);
@@ -1066,7 +1093,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
     k_morton<<<nblocks(N, 256 * MORTON_PTS), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb,
                                                              t.key_alt, t.codes, t.bbox,
-                                                             t.os_hist, t.mask, t.nocc);
+                                                             t.os_hist, t.mask);
     const unsigned ntiles = nblocks(N, OS_TILE);
     const size_t stat_pass = (size_t)ntiles * OS_BINS;
     k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key_alt, nullptr, N, 0, t.os_hist, t.os_stat,
@@ -1083,8 +1110,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     k_scan_popc_1p<<<nblocks(N, SCAN_TILE), SCAN_THREADS, 0, st>>>(t.mask, N, t.offs, t.sc_stat,
                                                                    t.os_ctr + 3, t.status);
     k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, nullptr, N, t.mask, t.offs, t.own_a,
-                                                   t.own_b, t.nsc, t.ninfo, t.nparent, t.nocc,
-                                                   t.acnt);
+                                                   t.own_b, t.nsc, t.ninfo, t.nparent, t.inode);
     launch_aggregate(t, N, raw, pack, abpack, true, st);
     note_launches(9 + (N > 1 ? 1 : 0));
     return cudaGetLastError();
@@ -1121,11 +1147,10 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     launches++;
   }
   TRY(scan(t.mask, N, t.bsum, t.offs, Popc(), st));
-  TRY(cudaMemsetAsync(t.nocc, 0, sizeof(uint32_t) * 2 * (size_t)N, st));
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.offs, t.own_a, t.own_b,
-                                                 t.nsc, t.ninfo, t.nparent, t.nocc, t.acnt);
+                                                 t.nsc, t.ninfo, t.nparent, t.inode);
   launch_aggregate(t, N, raw, pack, abpack, true, st);
-  note_launches(launches + 3 + 2);
+  note_launches(launches + 3 + 3);
   return cudaGetLastError();
 }
 
@@ -1286,11 +1311,8 @@ gs_status bh_aggregate(TreeWork& w, const BHStep& b, const float4* abpack, bool 
   cudaError_t err;
   if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
     return cuda_err(err);
-  if ((err = cudaMemsetAsync(t.acnt, 0, sizeof(int32_t) * (2 * (size_t)b.N + 2), st)) !=
-      cudaSuccess)
-    return cuda_err(err);
   launch_aggregate(t, (int)b.N, b.raw, b.pack, abpack, false, st);
-  note_launches(1);
+  note_launches(2);
   err = cudaGetLastError();
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
@@ -1360,7 +1382,7 @@ __global__ void k_export_nodes(TreeArrays t, int m, int32_t* nodes, float* range
 }
 
 // Node sums in input units (tests): per preorder node x, {sum q, sum p,
-// sum alpha, sum beta} in FP64 from the FP32-pair sums of the bottom-up pass
+// sum alpha, sum beta} in FP64 from the FP32-pair sums of the aggregation
 // (a leaf: its own FP32 record).  The pack holds (q - c) s and mu beta, so
 // sum q = (sum xs) / s + n c and sum beta = (sum mu beta) / mu.
 __global__ void k_export_sums(TreeArrays t, int m, const double* __restrict__ center,

@@ -45,11 +45,17 @@ struct TreeArrays {
   int2* ninfo;      // {depth (-1 = leaf), first sorted position} (kept per step: the
                     // leaf-size variant's walk reads it, also when re-walking a kept tree)
   int32_t* nparent; // preorder id of the parent, -1 for the root
-  uint32_t* nocc;   // per node (kept per step): bits 0-7 the octants its children occupy,
-                    // bits 8-10 its own octant in its parent (parents of depth < 10)
-  int32_t* child;   // 8 per node: children in preorder (bottom-up pass; parents of depth < 10)
-  int32_t* acnt;    // arrival counters of the bottom-up pass
+  int32_t* inode;   // internal nodes in preorder (kept per step): k-th -> its preorder id
   double* isum;     // 12 per node: sums of xs, p, a, b over members (FP32 pairs)
+  // node sums over member ranges (scratch of each aggregation): per sorted
+  // point its values (4 float4: xs, p, a, b) and FP32 position; per chunk of
+  // 32 and of 1024 sorted points, the sums (12 FP32 pairs) and the range
+  float4* spt;
+  float4* sraw;
+  float2* c1sum;
+  float4* c1box;
+  float2* c2sum;
+  float4* c2box;
   int64_t* counts;  // {point interactions, node interactions}
   // single-pass sort and scan of one point set (zeroed together, os_bytes):
   uint32_t* os_hist;            // 3 x 1024 digit counts of the 30-bit codes
