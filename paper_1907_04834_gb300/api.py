@@ -116,14 +116,16 @@ def shoot(q0, p0, sigma, T, mode="exact", thresh=3.0, with_H=False, leaf_size=1,
 
 
 def shoot_grad(q0, p0, X, sigma, T, lam=1.0, mode="exact", thresh=3.0, ckpt_every=0,
-               leaf_size=1, criterion=0, stream=None):
-    """Objective of Eq. 2 and dE/dp0.  Returns (E, grad, q1) with
-    E = [E, H(q0,p0), lambda |q1 - X|^2]."""
+               leaf_size=1, criterion=0, sympl_iters=0, stream=None):
+    """Objective of Eq. 2 and dE/dp0 (sympl_iters = M > 0: of the
+    semi-implicit scheme with M fixed-point passes per step).  Returns
+    (E, grad, q1) with E = [E, H(q0,p0), lambda |q1 - X|^2]."""
     q0 = _pts(q0, "q0")
     n = q0.shape[0]
     p0, X = _pts(p0, "p0", n), _pts(X, "X", n)
     c = _ctx_for(q0)
-    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size, criterion=criterion)
+    prm = make_params(sigma, T, mode, lam, thresh, ckpt_every, leaf_size=leaf_size,
+                      criterion=criterion, sympl_iters=sympl_iters)
     E = _like(q0, (3,))
     grad, q1 = _like(q0), _like(q0)
     c.check(c.lib.gs_shoot_grad(c.handle, _ptr(q0), _ptr(p0), _ptr(X), n, ctypes.byref(prm),

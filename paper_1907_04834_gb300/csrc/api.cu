@@ -65,7 +65,7 @@ struct gs_ctx {
   DevMem in_q, in_p, in_a, in_b, in_X, out_a, out_b;
   // solver state
   DevMem q, p, al, be, F0, pf, r2, scal;
-  DevMem packs, raws, abpacks, ckpt;
+  DevMem packs, raws, abpacks, ckpt, st64, rho;
   DevMem part, tickets;
   size_t tickets_n = 0;
   // many-subject calls: per-subject layout, queues, energies and gradients
@@ -182,7 +182,7 @@ struct Key {
                             &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs, &c->raws,
                             &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                             &c->gd_p, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                            &c->lb, &c->xraws, &c->xsort, &c->grid})
+                            &c->lb, &c->xraws, &c->xsort, &c->grid, &c->st64, &c->rho})
       add(m->p), add(m->bytes);
     add(c->tree.mem), add(c->tree.smem), add(c->tree.lcap), add(c->tree.cap_n);
     add(c->tree.cap_groups), add(c->tree.nslots), add(c->tree.slot_bytes), add(c->d_status);
@@ -258,8 +258,8 @@ gs_status check_params(gs_ctx* c, const gs_params* prm, bool need_lambda,
                 prm->sympl_iters);
   if (prm->sympl_iters != 0 && !sympl_ok)
     return fail(c, GS_ERR_UNSUPPORTED,
-                "sympl_iters != 0 (semi-implicit symplectic Euler) is supported by gs_shoot "
-                "only");
+                "sympl_iters != 0 (semi-implicit symplectic Euler) is supported by gs_shoot, "
+                "gs_shoot_traj and gs_shoot_grad only");
   return GS_OK;
 }
 
@@ -731,10 +731,10 @@ gs_status forward_rhs(Solver& S, int slot, const FwdEpi& e, int64_t* counts, int
 // `slot`.  Barnes-Hut: the tree and interaction lists of tree slot 0 stay
 // valid (the decisions depend on the positions only); only the node sums are
 // recomputed before the lists are evaluated.
-gs_status forward_rhs_same_q(Solver& S, int slot, const FwdEpi& e) {
+gs_status forward_rhs_same_q(Solver& S, int slot, const FwdEpi& e, int tslot = 0) {
   gs_ctx* c = S.c;
-  if (S.mode == GS_EXACT || S.batch || S.grid) return forward_rhs(S, slot, e, nullptr);
-  BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
+  if (S.mode == GS_EXACT || S.batch || S.grid) return forward_rhs(S, slot, e, nullptr, tslot);
+  BHStep b{tslot, S.N, S.Npad, S.s, S.thr, S.pack(slot), S.raw(slot), bh_forest(S), S.leaf,
            S.mode == GS_TRUNC, S.crit};
   gs_status s;
   {
@@ -832,6 +832,10 @@ struct GradRun {
   Batch* batch = nullptr;
   int T = 0, ck = 0, nck = 0;
   double* ckq = nullptr;
+  // semi-implicit scheme (M = S.iters passes per step): the FP64 state of
+  // every step of a segment, and M pack slots for the passes' momenta
+  double* st64 = nullptr;
+  int pass0 = 0;  // first pack slot of the passes
 };
 
 gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, cudaStream_t st,
@@ -845,7 +849,10 @@ gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, c
                                      : prm->ckpt_every;
   R.ck = ce > 0 && ce < R.T ? ce : 0;
   // pack slots: every step (store-all) or one segment (checkpointing)
-  const int slots = R.ck ? R.ck + 1 : R.T + 1;
+  const int steps = R.ck ? R.ck + 1 : R.T + 1;
+  const int M = prm->sympl_iters;
+  const int slots = steps + M;
+  R.pass0 = steps;
   // Barnes-Hut: one tree slot per step kept for the backward stage (a
   // segment's steps with checkpointing)
   const int tslots = prm->mode != GS_EXACT ? (R.ck ? R.ck : R.T) : 1;
@@ -854,6 +861,12 @@ gs_status grad_setup(gs_ctx* c, int64_t N, const gs_params* prm, Batch* batch, c
   R.nck = R.ck ? (R.T + R.ck - 1) / R.ck : 0;
   if (R.ck) CK(c->ckpt.ensure((size_t)R.nck * 2 * b3), "checkpoint allocation");
   R.ckq = R.ck ? c->ckpt.as<double>() : nullptr;
+  if (M > 0) {
+    CK(c->st64.ensure((size_t)(steps - 1) * 2 * b3 + (size_t)N * 3 * sizeof(double)),
+       "state allocation");
+    R.st64 = c->st64.as<double>();
+    CK(c->rho.ensure(b3), "workspace");
+  }
   return GS_OK;
 }
 
@@ -871,6 +884,36 @@ gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const d
   if (batch && (s = batch_zero_queues(c, *batch, st))) return s;
   if ((s = solver_load(S, dq0, dp0, 0))) return s;
 
+  const int M = S.iters;
+  // FP64 state j of the semi-implicit scheme's backward sweep (the passes'
+  // epilogues form p^k + h Phi from it)
+  auto save_state = [&](int j) -> gs_status {
+    if (M == 0) return GS_OK;
+    double* dst = R.st64 + (size_t)j * 2 * n3;
+    CK(cudaMemcpyAsync(dst, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "state copy");
+    CK(cudaMemcpyAsync(dst + n3, c->p.p, b3, cudaMemcpyDeviceToDevice, st), "state copy");
+    return GS_OK;
+  };
+  // One step from pack slot `in` (tree slot ts), the next state's pack into
+  // `outs`; first: also F(q0, p0) and p0.F.  Semi-implicit: M passes at
+  // fixed q (pack slots pass0 ..), then the update with the last pass.
+  auto fwd_step = [&](int in, int outs, int ts, bool first) -> gs_status {
+    for (int m = 0; m <= M; m++) {
+      const bool last = m == M;
+      FwdEpi e = fwd_epi(S, last ? outs : R.pass0 + m, S.h);
+      e.iterate = !last;
+      if (first && m == 0) {
+        e.F_out = c->F0.as<double>();
+        e.pf_part = c->pf.as<double>();
+      }
+      const int from = m == 0 ? in : R.pass0 + m - 1;
+      gs_status r = m == 0 ? forward_rhs(S, from, e, nullptr, ts)
+                           : forward_rhs_same_q(S, from, e, ts);
+      if (r) return r;
+    }
+    return GS_OK;
+  };
+
   // ---- forward pass
   for (int k = 0; k < T; k++) {
     int in = ck ? (k & 1) : k, outs = ck ? ((k + 1) & 1) : k + 1;
@@ -879,12 +922,8 @@ gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const d
       CK(cudaMemcpyAsync(dst, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
       CK(cudaMemcpyAsync(dst + n3, c->p.p, b3, cudaMemcpyDeviceToDevice, st), "checkpoint");
     }
-    FwdEpi e = fwd_epi(S, outs, S.h);
-    if (k == 0) {
-      e.F_out = c->F0.as<double>();
-      e.pf_part = c->pf.as<double>();
-    }
-    if ((s = forward_rhs(S, in, e, nullptr, ck ? 0 : k))) return s;
+    if (!ck && (s = save_state(k))) return s;
+    if ((s = fwd_step(in, outs, ck ? 0 : k, k == 0))) return s;
   }
   if (q1) CK(cudaMemcpyAsync(q1, c->q.p, b3, cudaMemcpyDeviceToDevice, st), "q1 copy");
   // ---- adjoint initialisation and objective
@@ -907,15 +946,40 @@ gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const d
   }
   // ---- backward pass
   int ab = 0;
-  auto back_step = [&](int k, int slot) -> gs_status {
-    AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, grad);
-    gs_status r = adjoint_rhs(S, slot, ab, e, nullptr, slot, true);
-    ab ^= 1;
-    return r;
+  // Backward step k on pack and tree slot `slot` (state j of st64).
+  // Semi-implicit: the passes r_1 .. r_M are recomputed from state k, then
+  // the adjoint terms at r_M with (alpha, beta) and at r_{m-1} with (0,
+  // rho_m), m = M .. 1; alpha and beta accumulate dE/dq^k and dE/dp^k (the
+  // discrete adjoint of the step, as the oracle's gsref_shoot_grad_sympl).
+  auto back_step = [&](int k, int slot, int j) -> gs_status {
+    if (M == 0) {
+      AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0, grad);
+      gs_status r = adjoint_rhs(S, slot, ab, e, nullptr, slot, true);
+      ab ^= 1;
+      return r;
+    }
+    const double* src = R.st64 + (size_t)j * 2 * n3;
+    CK(cudaMemcpyAsync(c->q.p, src, b3, cudaMemcpyDeviceToDevice, st), "state copy");
+    CK(cudaMemcpyAsync(c->p.p, src + n3, b3, cudaMemcpyDeviceToDevice, st), "state copy");
+    for (int m = 1; m <= M; m++) {
+      FwdEpi e = fwd_epi(S, R.pass0 + m - 1, S.h);
+      e.iterate = true;
+      gs_status r = forward_rhs_same_q(S, m == 1 ? slot : R.pass0 + m - 2, e, slot);
+      if (r) return r;
+    }
+    for (int m = M; m >= 0; m--) {
+      AdjEpi e = adj_epi(S, ab ^ 1, S.h, k == 0 && m == 0, grad);
+      e.rho = c->rho.as<double>();
+      e.pack_rho = m > 0;
+      gs_status r = adjoint_rhs(S, m == 0 ? slot : R.pass0 + m - 1, ab, e, nullptr, slot, true);
+      ab ^= 1;
+      if (r) return r;
+    }
+    return GS_OK;
   };
   if (!ck) {
     for (int k = T - 1; k >= 0; k--)
-      if ((s = back_step(k, k))) return s;
+      if ((s = back_step(k, k, k))) return s;
   } else {
     for (int seg = nck - 1; seg >= 0; seg--) {
       const int k0 = seg * ck, k1 = std::min(T, k0 + ck);
@@ -924,15 +988,18 @@ gs_status grad_enqueue(GradRun& R, const double* dq0, const double* dp0, const d
       CK(cudaMemcpyAsync(c->p.p, src + n3, b3, cudaMemcpyDeviceToDevice, st), "restore");
       if ((s = solver_pack(S, 0))) return s;
       for (int k = k0; k < k1; k++) {
+        if ((s = save_state(k - k0))) return s;
         // the last step of the segment only builds its tree and lists
         // (its state update is not needed): the adjoint reuses them
-        if (S.mode != GS_EXACT || k < k1 - 1) {
-          FwdEpi e = fwd_epi(S, k < k1 - 1 ? k - k0 + 1 : -1, k < k1 - 1 ? S.h : 0.0);
+        if (k < k1 - 1) {
+          if ((s = fwd_step(k - k0, k - k0 + 1, k - k0, false))) return s;
+        } else if (S.mode != GS_EXACT) {
+          FwdEpi e = fwd_epi(S, -1, 0.0);
           if ((s = forward_rhs(S, k - k0, e, nullptr, k - k0))) return s;
         }
       }
       for (int k = k1 - 1; k >= k0; k--)
-        if ((s = back_step(k, k - k0))) return s;
+        if ((s = back_step(k, k - k0, k - k0))) return s;
     }
   }
   return GS_OK;
@@ -1170,7 +1237,7 @@ void gs_destroy(gs_ctx* c) {
                       &c->q, &c->p, &c->al, &c->be, &c->F0, &c->pf, &c->r2, &c->scal, &c->packs,
                       &c->raws, &c->abpacks, &c->ckpt, &c->part, &c->tickets, &c->bmeta, &c->bout,
                       &c->gd_p, &c->gd_E, &c->in_x, &c->xs, &c->xpks, &c->xpart, &c->xtickets,
-                      &c->lb, &c->xraws, &c->xsort, &c->grid})
+                      &c->lb, &c->xraws, &c->xsort, &c->grid, &c->st64, &c->rho})
       m->release();
     for (auto* gc : {&c->g_shoot, &c->g_grad, &c->g_batch, &c->g_flow})
       if (gc->exec) cudaGraphExecDestroy(gc->exec);
@@ -1320,7 +1387,7 @@ gs_status gs_shoot_grad(gs_ctx* c, const double* q0, const double* p0, const dou
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
-  if ((s = check_n(c, N)) || (s = check_params(c, prm, true))) return s;
+  if ((s = check_n(c, N)) || (s = check_params(c, prm, true, true))) return s;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   bool hE = false, hg = false, hq = false;

@@ -293,6 +293,8 @@ struct AdjEpi {
   double* dB_out;       // N x 3 (NULL = none)
   const double* F0;     // when non-NULL (last backward step): grad = beta + F0
   double* grad;         // N x 3 gradient output
+  double* rho;          // N x 3 (NULL = none): receives h dB (semi-implicit adjoint)
+  bool pack_rho;        // the next adjoint pack gets (0, rho) instead of (alpha, beta)
   double inv_s2;        // sigma^-2
   double inv_s;         // 1 / s
   double mu;            // beta's scale in the adjoint pack
@@ -318,14 +320,20 @@ __device__ __forceinline__ void adj_epilogue_at(int64_t i, int64_t ipk, const do
   if (e.dB_out)
     for (int a = 0; a < 3; a++) e.dB_out[3 * i + a] = dB[a];
   if (e.h != 0.0) {
-    double an[3], bn[3];
+    double an[3], bn[3], hb[3];
     for (int a = 0; a < 3; a++) {
+      hb[a] = e.h * dB[a];
       an[a] = e.al[3 * i + a] + e.h * dA[a];
-      bn[a] = e.be[3 * i + a] + e.h * dB[a];
+      bn[a] = e.be[3 * i + a] + hb[a];
       e.al[3 * i + a] = an[a];
       e.be[3 * i + a] = bn[a];
     }
-    if (e.pack_next)
+    if (e.rho)
+      for (int a = 0; a < 3; a++) e.rho[3 * i + a] = hb[a];
+    if (e.pack_next && e.pack_rho)
+      pack_write(e.pack_next, ipk, 0.f, 0.f, 0.f, (float)(e.mu * hb[0]), (float)(e.mu * hb[1]),
+                 (float)(e.mu * hb[2]));
+    else if (e.pack_next)
       pack_write(e.pack_next, ipk, (float)an[0], (float)an[1], (float)an[2],
                  (float)(e.mu * bn[0]), (float)(e.mu * bn[1]), (float)(e.mu * bn[2]));
     if (e.F0)
