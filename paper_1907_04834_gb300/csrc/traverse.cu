@@ -330,8 +330,8 @@ __device__ __forceinline__ int stage_records(const TreeArrays& t, const int* nod
 // (no summarised ancestor) take their decision; `sink` receives runs of
 // entries (first node, count, lane mask): a summarised node, a run of
 // consecutive leaves, or -- when an opened node's children are all leaves --
-// those children at once.  sink.fits(n) false stops the walk before node x
-// (x and resume are then the state to resume from).  Returns false if stopped.
+// those children at once.  sink.full() true (checked once per node) stops
+// the walk; returns false if stopped.
 // VAR = false compiles the paper's rule only (leaf and trunc ignored).
 template <bool COUNT, bool VAR, class Sink>
 __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2], int& x,
@@ -342,6 +342,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
   // window bit masks (bit j = node base + j): leaf, "all children leaves"
   unsigned leafmask = 0u, botmask = 0u;
   while (x < end) {
+    if (sink.full()) return false;
     int off = x - base;
     if ((unsigned)off >= 32u) {  // stage the next 32 node boxes
       __syncwarp();
@@ -371,7 +372,6 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
       r = min(r, rmin - x);
       const unsigned mk = __ballot_sync(FULL, resume <= x);
       if (mk) {
-        if (!sink.fits(r)) return false;
         if (r == 1) sink.add1(x, mk);
         else sink.add(x, r, mk, false);
         if (COUNT && !(VAR && trunc)) np += (long long)__popc(mk) * r;
@@ -396,8 +396,6 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const unsigned ms = (VAR && trunc) ? 0u : mt;
     if (ms | ((bottom || bucket) ? 1u : 0u)) {
       const int cn = (bottom || bucket) ? ncount : 0;
-      // stop before x (state unchanged) when the sink is full
-      if (!sink.fits((ms ? 1 : 0) + cn)) return false;
       if (ms) sink.add1(x, ms);
       if (bottom) sink.add(x + 1, cn, mo, false);
       if (bucket) sink.add(t.ninfo[x].y, cn, mo, true);
@@ -419,8 +417,9 @@ struct ListSink {
   int head, tail, written, cnt, lane;
   bool ovf;
   int res_next, res_end;  // chunks reserved by this warp, not yet used
-  __device__ __forceinline__ bool fits(int) const { return !ovf; }
+  __device__ __forceinline__ bool full() const { return ovf; }
   __device__ __forceinline__ void put_chunk(int n) {
+    if (ovf) return;
     if (res_next == res_end) {
       int c = 0;
       if (lane == 0) c = atomicAdd(L->used, kReserve);
@@ -445,7 +444,6 @@ struct ListSink {
   // n <= 32 entries (a leaf run, a node's children or points, or one node),
   // so at most one chunk fills per call; points: entries ~(node0 + k)
   __device__ __forceinline__ void add(int node0, int n, unsigned mask, bool points) {
-    if (ovf) return;
     const int c2 = cnt + n;
     auto enc = [&](int k) { return points ? ~(node0 + k) : node0 + k; };
     if (lane < n && cnt + lane < BH_CHUNK) buf[cnt + lane] = make_int2(enc(lane), (int)mask);
@@ -462,7 +460,6 @@ struct ListSink {
   }
   // one entry (a far node: the most frequent case), written by lane 0
   __device__ __forceinline__ void add1(int node, unsigned mask) {
-    if (ovf) return;
     if (lane == 0) buf[cnt] = make_int2(node, (int)mask);
     if (++cnt < BH_CHUNK) return;
     __syncwarp();
@@ -540,7 +537,7 @@ struct TallySink {
   int lane;
   long long np, nn;
   unsigned long long hp, hn;
-  __device__ __forceinline__ bool fits(int) const { return true; }
+  __device__ __forceinline__ bool full() const { return false; }
   __device__ __forceinline__ void add1(int node, unsigned mask) {
     if (!((mask >> lane) & 1u)) return;
     const int skip = __float_as_int(t->nbox[2 * node].w);
@@ -738,7 +735,7 @@ struct EvalSink {
   int cnt, lane;
   float thr;
   int npair;
-  __device__ __forceinline__ bool fits(int) const { return true; }
+  __device__ __forceinline__ bool full() const { return false; }
   __device__ __forceinline__ void flush() {
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(*t, node, mask, soa, cnt, lane);

@@ -568,10 +568,52 @@ __global__ void __launch_bounds__(OS_THREADS)
     cnt[k] = acc;
     lb_publish(stat + (size_t)tile * OS_BINS + d, tile, acc);
   }
+  // the look-backs of this thread's digits advance together (their loads
+  // in flight at once); the wait gives up only when none of them advances
+  unsigned long long excl[PER];
+  int jj[PER];
+  bool busy[PER];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < PER; k++) {
+    excl[k] = 0ull;
+    jj[k] = tile - 1;
+    busy[k] = tile > 0;
+    any = any || busy[k];
+  }
+  long long t0 = clock64();
+  while (any) {
+    unsigned long long v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++)
+      v[k] = busy[k] ? lb_load(stat + (size_t)jj[k] * OS_BINS + tid + k * OS_THREADS) : 0ull;
+    any = false;
+    bool moved = false;
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+      if (!busy[k]) continue;
+      const unsigned long long kind = v[k] & ~LB_VAL;
+      if (kind == 0ull) {
+        any = true;
+        continue;
+      }
+      excl[k] += v[k] & LB_VAL;
+      moved = true;
+      if (kind == LB_PRE || jj[k] == 0) busy[k] = false;
+      else jj[k]--, any = true;
+    }
+    if (moved) {
+      t0 = clock64();
+    } else if (any && clock64() - t0 > LB_SPIN_CYCLES) {
+      atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < PER; k++) {
     const int d = tid + k * OS_THREADS;
-    s_base[d] += (uint32_t)lb_prefix(stat + d, OS_BINS, tile, cnt[k], status);
+    if (tile > 0) lb_store(stat + (size_t)tile * OS_BINS + d, LB_PRE | (excl[k] + cnt[k]));
+    s_base[d] += (uint32_t)excl[k];
   }
   __syncthreads();
 #pragma unroll
@@ -878,64 +920,153 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Pass 2, one thread per internal node (in preorder): sums (and range) over
-// its member range from points and chunks, then its record, its pair sums
-// and (BOX) its box with skip and count.
+// The pieces of a member range [a, e): points [a, h1) up to a multiple of
+// 32, chunks of 32 [h1, h2) up to a multiple of 1024, chunks of 1024
+// [h2, h3), chunks of 32 [h3, h4), points [h4, e); item k of the range is
+// the k-th piece in that order.
+struct RangeCut {
+  int a, h1, h2, h3, h4, e;
+  __device__ __forceinline__ RangeCut(int a_, int e_) : a(a_), e(e_) {
+    h1 = (a & 31) ? min(e, (a + 31) & ~31) : a;
+    const int to1024 = (((h1 + 1023) & ~1023) - h1) >> 5;
+    h2 = h1 + 32 * min(to1024, (e - h1) >> 5);
+    h3 = (h2 & 1023) ? h2 : h2 + 1024 * ((e - h2) >> 10);
+    h4 = h3 + 32 * ((e - h3) >> 5);
+  }
+  __device__ __forceinline__ int items() const {
+    return (h1 - a) + ((h2 - h1) >> 5) + ((h3 - h2) >> 10) + ((h4 - h3) >> 5) + (e - h4);
+  }
+  // kind 0: sorted point, 1: chunk of 32, 2: chunk of 1024; its index
+  __device__ __forceinline__ int2 item(int k) const {
+    int n = h1 - a;
+    if (k < n) return make_int2(0, a + k);
+    k -= n, n = (h2 - h1) >> 5;
+    if (k < n) return make_int2(1, (h1 >> 5) + k);
+    k -= n, n = (h3 - h2) >> 10;
+    if (k < n) return make_int2(2, (h2 >> 10) + k);
+    k -= n, n = (h4 - h3) >> 5;
+    if (k < n) return make_int2(1, (h3 >> 5) + k);
+    return make_int2(0, h4 + k - n);
+  }
+};
+
+template <int NS, bool BOX>
+struct RangeAcc {
+  Pair S[NS];
+  float lo[3], hi[3];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; a++) lo[a] = INFINITY, hi[a] = -INFINITY;
+  }
+  __device__ __forceinline__ void add(const TreeArrays& t, int2 it) {
+    if (it.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NS / 3; q++) {
+        const float4 f = __ldcg(&t.spt[4 * (size_t)it.y + q]);
+        pair_add(S[3 * q], f.x);
+        pair_add(S[3 * q + 1], f.y);
+        pair_add(S[3 * q + 2], f.z);
+      }
+      if (BOX) {
+        const float4 p = __ldcg(&t.sraw[it.y]);
+        lo[0] = fminf(lo[0], p.x), lo[1] = fminf(lo[1], p.y), lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x), hi[1] = fmaxf(hi[1], p.y), hi[2] = fmaxf(hi[2], p.z);
+      }
+    } else {
+      const float2* cs = it.x == 1 ? t.c1sum : t.c2sum;
+      const float4* cb = it.x == 1 ? t.c1box : t.c2box;
+#pragma unroll
+      for (int k = 0; k < NS; k++) pair_add(S[k], __ldcg(&cs[12 * (size_t)it.y + k]));
+      if (BOX) {
+        const float4 u = __ldcg(&cb[2 * (size_t)it.y]), v = __ldcg(&cb[2 * (size_t)it.y + 1]);
+        lo[0] = fminf(lo[0], u.x), lo[1] = fminf(lo[1], u.y), lo[2] = fminf(lo[2], u.z);
+        hi[0] = fmaxf(hi[0], v.x), hi[1] = fmaxf(hi[1], v.y), hi[2] = fmaxf(hi[2], v.z);
+      }
+    }
+  }
+  // every lane's accumulator folded into lane 0's (fixed order)
+  __device__ __forceinline__ void warp_fold() {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+        const float oh = __shfl_down_sync(0xffffffffu, S[k].hi, d);
+        const float ol = __shfl_down_sync(0xffffffffu, S[k].lo, d);
+        pair_add(S[k], make_float2(oh, ol));
+      }
+      if (BOX)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          lo[a] = fminf(lo[a], __shfl_down_sync(0xffffffffu, lo[a], d));
+          hi[a] = fmaxf(hi[a], __shfl_down_sync(0xffffffffu, hi[a], d));
+        }
+    }
+  }
+  // the node's pair sums, record and (BOX) box with skip and count
+  __device__ __forceinline__ void write(const TreeArrays& t, int id, int2 sc, bool adj) const {
+    float2* isum = reinterpret_cast<float2*>(t.isum);
+#pragma unroll
+    for (int k = 0; k < NS; k++) isum[12 * (size_t)id + k] = pair_store(S[k]);
+    const int n = sc.y;
+    t.nrec[4 * id] = make_float4(pair_mean(S[0], n), pair_mean(S[1], n), pair_mean(S[2], n), 0.f);
+    t.nrec[4 * id + 1] = make_float4(pair_value(S[3]), pair_value(S[4]), pair_value(S[5]), 0.f);
+    if (adj) {
+      t.nrec[4 * id + 2] =
+          make_float4(pair_value(S[NS - 6]), pair_value(S[NS - 5]), pair_value(S[NS - 4]), 0.f);
+      t.nrec[4 * id + 3] = make_float4(pair_mean(S[NS - 3], n), pair_mean(S[NS - 2], n),
+                                       pair_mean(S[NS - 1], n), 0.f);
+    }
+    if (BOX) {
+      t.nbox[2 * id] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
+      t.nbox[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(n));
+    }
+  }
+};
+
+// Pass 2, a warp per 32 consecutive internal nodes (preorder): a node of at
+// most kRangeSmall pieces is summed by its own lane, piece after piece; a
+// larger one by the whole warp (lane j takes pieces j, j + 32, ..., then
+// the lanes' sums are folded), one such node after another.
+constexpr int kRangeSmall = 8;
 template <bool ADJ, bool BOX>
 __global__ void __launch_bounds__(256) k_range_nodes(TreeArrays t, int N) {
   constexpr int NS = ADJ ? 12 : 6;
+  const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int)t.offs[N]) return;
-  const int id = t.inode[r];
-  const int2 inf = t.ninfo[id], sc = t.nsc[id];
-  const int end = inf.y + sc.y;
-  Pair S[NS];
-#pragma unroll
-  for (int k = 0; k < NS; k++) S[k] = Pair{0.f, 0.f};
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  auto point = [&](int i) {
-#pragma unroll
-    for (int q = 0; q < NS / 3; q++) {
-      const float4 f = __ldcg(&t.spt[4 * (size_t)i + q]);
-      pair_add(S[3 * q], f.x);
-      pair_add(S[3 * q + 1], f.y);
-      pair_add(S[3 * q + 2], f.z);
-    }
-    if (BOX) {
-      const float4 p = __ldcg(&t.sraw[i]);
-      lo[0] = fminf(lo[0], p.x), lo[1] = fminf(lo[1], p.y), lo[2] = fminf(lo[2], p.z);
-      hi[0] = fmaxf(hi[0], p.x), hi[1] = fmaxf(hi[1], p.y), hi[2] = fmaxf(hi[2], p.z);
-    }
-  };
-  auto chunk = [&](const float2* cs, const float4* cb, size_t c) {
-#pragma unroll
-    for (int k = 0; k < NS; k++) pair_add(S[k], __ldcg(&cs[12 * c + k]));
-    if (BOX) {
-      const float4 a = __ldcg(&cb[2 * c]), b = __ldcg(&cb[2 * c + 1]);
-      lo[0] = fminf(lo[0], a.x), lo[1] = fminf(lo[1], a.y), lo[2] = fminf(lo[2], a.z);
-      hi[0] = fmaxf(hi[0], b.x), hi[1] = fmaxf(hi[1], b.y), hi[2] = fmaxf(hi[2], b.z);
-    }
-  };
-  int i = inf.y;
-  while (i < end && (i & 31)) point(i++);
-  while (i + 32 <= end && (i & 1023)) chunk(t.c1sum, t.c1box, (size_t)(i >> 5)), i += 32;
-  while (i + 1024 <= end) chunk(t.c2sum, t.c2box, (size_t)(i >> 10)), i += 1024;
-  while (i + 32 <= end) chunk(t.c1sum, t.c1box, (size_t)(i >> 5)), i += 32;
-  while (i < end) point(i++);
-  float2* isum = reinterpret_cast<float2*>(t.isum);
-#pragma unroll
-  for (int k = 0; k < NS; k++) isum[12 * (size_t)id + k] = pair_store(S[k]);
-  const int n = sc.y;
-  t.nrec[4 * id] = make_float4(pair_mean(S[0], n), pair_mean(S[1], n), pair_mean(S[2], n), 0.f);
-  t.nrec[4 * id + 1] = make_float4(pair_value(S[3]), pair_value(S[4]), pair_value(S[5]), 0.f);
-  if (ADJ) {
-    t.nrec[4 * id + 2] = make_float4(pair_value(S[6]), pair_value(S[7]), pair_value(S[8]), 0.f);
-    t.nrec[4 * id + 3] =
-        make_float4(pair_mean(S[9], n), pair_mean(S[10], n), pair_mean(S[11], n), 0.f);
+  const int nint = (int)t.offs[N];
+  if (r - lane >= nint) return;  // the whole warp
+  int id = 0, K = 0;
+  int2 sc = make_int2(0, 0);
+  RangeCut cut(0, 0);
+  if (r < nint) {
+    id = t.inode[r];
+    const int2 inf = t.ninfo[id];
+    sc = t.nsc[id];
+    cut = RangeCut(inf.y, inf.y + sc.y);
+    K = cut.items();
   }
-  if (BOX) {
-    t.nbox[2 * id] = make_float4(lo[0], lo[1], lo[2], __int_as_float(sc.x));
-    t.nbox[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], __int_as_float(n));
+  RangeAcc<NS, BOX> A;
+  if (K > 0 && K <= kRangeSmall) {
+    A.zero();
+    for (int k = 0; k < K; k++) A.add(t, cut.item(k));
+    A.write(t, id, sc, ADJ);
+  }
+  unsigned big = __ballot_sync(0xffffffffu, K > kRangeSmall);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const int Kb = __shfl_sync(0xffffffffu, K, src);
+    const int idb = __shfl_sync(0xffffffffu, id, src);
+    const int2 scb = make_int2(__shfl_sync(0xffffffffu, sc.x, src),
+                               __shfl_sync(0xffffffffu, sc.y, src));
+    const int ab = t.ninfo[idb].y;
+    const RangeCut cb(ab, ab + scb.y);
+    A.zero();
+    for (int k = lane; k < Kb; k += 32) A.add(t, cb.item(k));
+    A.warp_fold();
+    if (lane == 0) A.write(t, idb, scb, ADJ);
   }
 }
 
