@@ -413,7 +413,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
 constexpr int kReserve = 8;  // chunks reserved from the pool at a time
 struct ListSink {
   const BHLists* L;
-  int2* buf;     // BH_CHUNK entries in shared memory
+  int2* buf;     // 2 * BH_CHUNK entries in shared memory
   int head, tail, written, cnt, lane;
   bool ovf;
   int res_next, res_end;  // chunks reserved by this warp, not yet used
@@ -467,12 +467,95 @@ struct ListSink {
     __syncwarp();
     cnt = 0;
   }
+  // hands the first BH_CHUNK buffered entries over and moves the others
+  // (at most BH_CHUNK) to the front
+  __device__ __forceinline__ void flush_front() {
+    __syncwarp();
+    put_chunk(BH_CHUNK);
+    const int rest = cnt - BH_CHUNK;
+    int2 v0 = make_int2(0, 0), v1 = make_int2(0, 0);
+    if (lane < rest) v0 = buf[BH_CHUNK + lane];
+    if (lane + 32 < rest) v1 = buf[BH_CHUNK + 32 + lane];
+    __syncwarp();
+    if (lane < rest) buf[lane] = v0;
+    if (lane + 32 < rest) buf[32 + lane] = v1;
+    __syncwarp();
+    cnt = rest;
+  }
   __device__ __forceinline__ void finish() {
     __syncwarp();
+    while (cnt >= BH_CHUNK && !ovf) flush_front();
     if (cnt && !ovf) put_chunk(cnt);
     cnt = 0;
   }
 };
+
+// The list walk of the paper's rule (leaf size 1, distance criterion, no
+// truncation): the decisions and entries of walk_nodes<false, false>, in
+// the same order, appended by predicated stores to the sink's two-chunk
+// buffer (a node adds at most 33 entries) and handed over a chunk at a
+// time.  Returns false if the list pool ran out.
+__device__ __forceinline__ bool walk_paper(const TreeArrays& t, float4 (*sbox)[2], int& x,
+                                           int end, const float4& rr, float thr, int& resume,
+                                           ListSink& sink, int lane) {
+  int base = INT_MIN / 2;
+  unsigned leafmask = 0u, botmask = 0u;
+  int2* buf = sink.buf;
+  while (x < end) {
+    if (sink.cnt >= BH_CHUNK) {
+      sink.flush_front();
+      if (sink.ovf) return false;
+    }
+    int off = x - base;
+    if ((unsigned)off >= 32u) {  // stage the next 32 node boxes
+      __syncwarp();
+      base = x;
+      off = 0;
+      const int j = base + lane;
+      bool lf = false, bt = false;
+      if (j < end) {
+        const float4 lo = t.nbox[2 * j], hi = t.nbox[2 * j + 1];
+        sbox[lane][0] = lo;
+        sbox[lane][1] = hi;
+        const int sk = __float_as_int(lo.w), cn = __float_as_int(hi.w);
+        lf = sk == j + 1;
+        bt = !lf && sk - j == cn + 1 && cn <= 32 && sk <= end;
+      }
+      leafmask = __ballot_sync(FULL, lf);
+      botmask = __ballot_sync(FULL, bt);
+      __syncwarp();
+    }
+    const int cnt = sink.cnt;
+    if ((leafmask >> off) & 1u) {
+      // a run of consecutive leaves, cut at the first resume point in it
+      const unsigned rest = ~(leafmask >> off);
+      int r = rest ? __ffs(rest) - 1 : 32 - off;
+      const int rmin = __reduce_min_sync(FULL, resume > x ? resume : INT_MAX);
+      r = min(r, rmin - x);
+      const unsigned mk = __ballot_sync(FULL, resume <= x);
+      if (mk && lane < r) buf[cnt + lane] = make_int2(x + lane, (int)mk);
+      sink.cnt = cnt + (mk ? r : 0);
+      x += r;
+      continue;
+    }
+    const float4 bl = sbox[off][0], bh = sbox[off][1];
+    const int skip = __float_as_int(bl.w);
+    const bool active = x >= resume;
+    const bool far = active & (box_dist2(rr.x, rr.y, rr.z, bl, bh) > thr);
+    const unsigned mt = __ballot_sync(FULL, far), mo = __ballot_sync(FULL, active && !far);
+    const bool bottom = mo && ((botmask >> off) & 1u);
+    // the summary entry, then (an opened node whose children are all
+    // leaves) those children at once
+    if (mt && lane == 0) buf[cnt] = make_int2(x, (int)mt);
+    const int c1 = cnt + (mt ? 1 : 0);
+    const int cn = bottom ? __float_as_int(bh.w) : 0;
+    if (lane < cn) buf[c1 + lane] = make_int2(x + 1 + lane, (int)mo);
+    sink.cnt = c1 + cn;
+    if (far) resume = skip;
+    x = (mo && !bottom) ? x + 1 : skip;
+  }
+  return true;
+}
 
 // One warp per (group, slice): emits the ordered interaction list.
 template <bool COUNT, bool VAR>
@@ -482,7 +565,7 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   // word: NULL, or an order of the lists that is used when *L.worder_n says
   // it holds as many lists as this walk has
   __shared__ float4 s_box[TR_WARPS][32][2];
-  __shared__ int2 s_ent[TR_WARPS][BH_CHUNK];
+  __shared__ int2 s_ent[TR_WARPS][2 * BH_CHUNK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wk = BH_SLICES * wg.wsplit;
   const int nl = wg.G * wk, wl = blockIdx.x * TR_WARPS + w;
@@ -501,8 +584,12 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
   ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
-  bool done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, wg.crit,
-                                     resume, sink, lane, np, nn);
+  bool done;
+  if (!COUNT && !VAR)
+    done = walk_paper(t, s_box[w], x, end, rr, thr, resume, sink, lane);
+  else
+    done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, wg.crit,
+                                  resume, sink, lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -858,11 +945,27 @@ __global__ void __launch_bounds__(kOrderThreads)
     for (int j = 0; j < per; j++) v += len[e * per + j];
     return kOrderClasses - 1 - len_class(v);
   };
-  for (int e = tid; e < n; e += kOrderThreads) atomicAdd(&s_c[cls(e)], 1);
+  // lists of similar length share a class: one shared atomic per class and
+  // warp (the warp's items of a class take consecutive places)
+  const int lane = tid & 31;
+  const int nr = (n + kOrderThreads - 1) / kOrderThreads * kOrderThreads;
+  for (int e = tid; e < nr; e += kOrderThreads) {
+    const int c = e < n ? cls(e) : -1;
+    const unsigned peers = __match_any_sync(FULL, c);
+    if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_c[c], __popc(peers));
+  }
   __syncthreads();
   if (tid < 32) exclusive_scan_warp(s_c, tid);
   __syncthreads();
-  for (int e = tid; e < n; e += kOrderThreads) out[atomicAdd(&s_c[cls(e)], 1)] = e;
+  for (int e = tid; e < nr; e += kOrderThreads) {
+    const int c = e < n ? cls(e) : -1;
+    const unsigned peers = __match_any_sync(FULL, c);
+    const int leader = __ffs(peers) - 1;
+    int at = 0;
+    if (c >= 0 && lane == leader) at = atomicAdd(&s_c[c], __popc(peers));
+    at = __shfl_sync(FULL, at, leader) + __popc(peers & ((1u << lane) - 1u));
+    if (c >= 0) out[at] = e;
+  }
   if (!slices && tid == 0) *worder_n = nw;
 }
 

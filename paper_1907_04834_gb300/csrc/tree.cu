@@ -568,8 +568,10 @@ __global__ void __launch_bounds__(OS_THREADS)
     cnt[k] = acc;
     lb_publish(stat + (size_t)tile * OS_BINS + d, tile, acc);
   }
-  // the look-backs of this thread's digits advance together (their loads
-  // in flight at once); the wait gives up only when none of them advances
+  // the look-backs of this thread's digits advance together, each over a
+  // window of LB_WIN earlier tiles at a time (all those loads in flight at
+  // once); the wait gives up only when none of them advances
+  constexpr int LB_WIN = 4;
   unsigned long long excl[PER];
   int jj[PER];
   bool busy[PER];
@@ -583,24 +585,34 @@ __global__ void __launch_bounds__(OS_THREADS)
   }
   long long t0 = clock64();
   while (any) {
-    unsigned long long v[PER];
+    unsigned long long v[PER][LB_WIN];
 #pragma unroll
     for (int k = 0; k < PER; k++)
-      v[k] = busy[k] ? lb_load(stat + (size_t)jj[k] * OS_BINS + tid + k * OS_THREADS) : 0ull;
+#pragma unroll
+      for (int u = 0; u < LB_WIN; u++)
+        v[k][u] = (busy[k] && jj[k] - u >= 0)
+                      ? lb_load(stat + (size_t)(jj[k] - u) * OS_BINS + tid + k * OS_THREADS)
+                      : 0ull;
     any = false;
     bool moved = false;
 #pragma unroll
     for (int k = 0; k < PER; k++) {
       if (!busy[k]) continue;
-      const unsigned long long kind = v[k] & ~LB_VAL;
-      if (kind == 0ull) {
-        any = true;
-        continue;
+      int j = jj[k];
+#pragma unroll
+      for (int u = 0; u < LB_WIN; u++) {
+        const unsigned long long kind = v[k][u] & ~LB_VAL;
+        if (kind == 0ull) break;  // not published yet: wait there
+        excl[k] += v[k][u] & LB_VAL;
+        moved = true;
+        if (kind == LB_PRE || j == 0) {
+          busy[k] = false;
+          break;
+        }
+        j--;
       }
-      excl[k] += v[k] & LB_VAL;
-      moved = true;
-      if (kind == LB_PRE || jj[k] == 0) busy[k] = false;
-      else jj[k]--, any = true;
+      jj[k] = j;
+      any = any || busy[k];
     }
     if (moved) {
       t0 = clock64();
