@@ -1037,10 +1037,9 @@ struct RangeAcc {
   }
 };
 
-// Pass 2, a warp per 32 consecutive internal nodes (preorder): a node of at
-// most kRangeSmall pieces is summed by its own lane, piece after piece; a
-// larger one by the whole warp (lane j takes pieces j, j + 32, ..., then
-// the lanes' sums are folded), one such node after another.
+// Pass 2, one thread per internal node (preorder): a node of at most
+// kRangeSmall pieces is summed by its own lane, piece after piece; a larger
+// one is queued for pass 3 (its place in the queue does not change its sums).
 constexpr int kRangeSmall = 8;
 template <bool ADJ, bool BOX>
 __global__ void __launch_bounds__(256) k_range_nodes(TreeArrays t, int N) {
@@ -1059,44 +1058,64 @@ __global__ void __launch_bounds__(256) k_range_nodes(TreeArrays t, int N) {
     cut = RangeCut(inf.y, inf.y + sc.y);
     K = cut.items();
   }
-  RangeAcc<NS, BOX> A;
   if (K > 0 && K <= kRangeSmall) {
+    RangeAcc<NS, BOX> A;
     A.zero();
     for (int k = 0; k < K; k++) A.add(t, cut.item(k));
     A.write(t, id, sc, ADJ);
   }
-  unsigned big = __ballot_sync(0xffffffffu, K > kRangeSmall);
-  while (big) {
-    const int src = __ffs(big) - 1;
-    big &= big - 1;
-    const int Kb = __shfl_sync(0xffffffffu, K, src);
-    const int idb = __shfl_sync(0xffffffffu, id, src);
-    const int2 scb = make_int2(__shfl_sync(0xffffffffu, sc.x, src),
-                               __shfl_sync(0xffffffffu, sc.y, src));
-    const int ab = t.ninfo[idb].y;
-    const RangeCut cb(ab, ab + scb.y);
+  const unsigned big = __ballot_sync(0xffffffffu, K > kRangeSmall);
+  if (big) {
+    const int leader = __ffs(big) - 1;
+    int at = 0;
+    if (lane == leader) at = atomicAdd(t.bigc, __popc(big));
+    at = __shfl_sync(0xffffffffu, at, leader) + __popc(big & ((1u << lane) - 1u));
+    if (K > kRangeSmall) t.bigq[at] = id;
+  }
+}
+
+// Pass 3, a warp per queued node (grid-stride over the queue): lane j takes
+// pieces j, j + 32, ..., then the lanes' sums are folded in a fixed order.
+template <bool ADJ, bool BOX>
+__global__ void __launch_bounds__(256) k_range_big(TreeArrays t) {
+  constexpr int NS = ADJ ? 12 : 6;
+  const int lane = threadIdx.x & 31;
+  const int nq = *t.bigc;
+  const int nw = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int q = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
+    const int id = t.bigq[q];
+    const int2 inf = t.ninfo[id], sc = t.nsc[id];
+    const RangeCut cut(inf.y, inf.y + sc.y);
+    const int K = cut.items();
+    RangeAcc<NS, BOX> A;
     A.zero();
-    for (int k = lane; k < Kb; k += 32) A.add(t, cb.item(k));
+    for (int k = lane; k < K; k += 32) A.add(t, cut.item(k));
     A.warp_fold();
-    if (lane == 0) A.write(t, idb, scb, ADJ);
+    if (lane == 0) A.write(t, id, sc, ADJ);
   }
 }
 
 void launch_aggregate(const TreeArrays& t, int N, const float4* raw, const float4* pack,
                       const float4* abpack, bool box, cudaStream_t st) {
   const unsigned nb1 = nblocks(N, 1024), nb2 = nblocks(N, 256);
+  const unsigned nb3 = std::min<unsigned>(nb2, 2048);
+  cudaMemsetAsync(t.bigc, 0, sizeof(int32_t), st);
   if (abpack && box) {
     k_range_points<true, true><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
     k_range_nodes<true, true><<<nb2, 256, 0, st>>>(t, N);
+    k_range_big<true, true><<<nb3, 256, 0, st>>>(t);
   } else if (abpack) {
     k_range_points<true, false><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
     k_range_nodes<true, false><<<nb2, 256, 0, st>>>(t, N);
+    k_range_big<true, false><<<nb3, 256, 0, st>>>(t);
   } else if (box) {
     k_range_points<false, true><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
     k_range_nodes<false, true><<<nb2, 256, 0, st>>>(t, N);
+    k_range_big<false, true><<<nb3, 256, 0, st>>>(t);
   } else {
     k_range_points<false, false><<<nb1, 1024, 0, st>>>(t, N, raw, pack, abpack);
     k_range_nodes<false, false><<<nb2, 256, 0, st>>>(t, N);
+    k_range_big<false, false><<<nb3, 256, 0, st>>>(t);
   }
 }
 
@@ -1128,6 +1147,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_spt = take(64 * N1), o_sraw = take(16 * N1),
                o_c1s = take(96 * (N1 / 32 + 1)), o_c1b = take(32 * (N1 / 32 + 1)),
                o_c2s = take(96 * (N1 / 1024 + 1)), o_c2b = take(32 * (N1 / 1024 + 1)),
+               o_bigq = take(4 * N1), o_bigc = take(4),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
                o_wordn = take(4), o_gtick = take(4 * (size_t)groups);
@@ -1160,6 +1180,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     t->c1box = (float4*)(b + o_c1b);
     t->c2sum = (float2*)(b + o_c2s);
     t->c2box = (float4*)(b + o_c2b);
+    t->bigq = (int32_t*)(b + o_bigq);
+    t->bigc = (int32_t*)(b + o_bigc);
     t->counts = (int64_t*)(b + o_cnt);
     L->part = (float2*)(b + o_part);
     L->fb = (float2*)(b + o_fb);
@@ -1234,28 +1256,30 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
     const unsigned nbb = std::min<unsigned>(nblocks(N, kBBoxThreads), kMaxBBoxBlocks);
     TRY(cudaMemsetAsync(t.os_hist, 0, t.os_bytes, st));
     k_bbox_partial<<<nbb, kBBoxThreads, 0, st>>>(raw, N, t.bbox_part);
-    k_morton<<<nblocks(N, 256 * MORTON_PTS), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb,
-                                                             t.key_alt, t.codes, t.bbox,
-                                                             t.os_hist, t.mask);
+    // the passes alternate between the two key/value buffers and end in
+    // key/perm: the codes start in the buffer that makes that so
+    uint32_t *k0 = t.key, *v0 = t.perm, *k1 = t.key_alt, *v1 = t.perm_alt;
+    if (OS_PASSES & 1) std::swap(k0, k1), std::swap(v0, v1);
+    k_morton<<<nblocks(N, 256 * MORTON_PTS), 256, 0, st>>>(raw, N, t.bbox_part, (int)nbb, k0,
+                                                             t.codes, t.bbox, t.os_hist, t.mask);
     const unsigned ntiles = nblocks(N, OS_TILE);
     const size_t stat_pass = (size_t)ntiles * OS_BINS;
-    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key_alt, nullptr, N, 0, t.os_hist, t.os_stat,
-                                             t.os_ctr, t.status, t.key, t.perm);
-    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key, t.perm, N, OS_BITS, t.os_hist + OS_BINS,
-                                             t.os_stat + stat_pass, t.os_ctr + 1, t.status,
-                                             t.key_alt, t.perm_alt);
-    k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(t.key_alt, t.perm_alt, N, 2 * OS_BITS,
-                                             t.os_hist + 2 * OS_BINS, t.os_stat + 2 * stat_pass,
-                                             t.os_ctr + 2, t.status, t.key, t.perm);
+    for (int p = 0; p < OS_PASSES; p++) {
+      k_os_pass<<<ntiles, OS_THREADS, 0, st>>>(k0, p == 0 ? nullptr : v0, N, OS_BITS * p,
+                                               t.os_hist + p * OS_BINS, t.os_stat + p * stat_pass,
+                                               t.os_ctr + p, t.status, k1, v1);
+      std::swap(k0, k1);
+      std::swap(v0, v1);
+    }
     TRY(cudaGetLastError());
     if (N > 1)
       k_owners<<<nblocks(N - 1, 256), 256, 0, st>>>(t.key, nullptr, N, t.mask, t.own_a, t.own_b);
     k_scan_popc_1p<<<nblocks(N, SCAN_TILE), SCAN_THREADS, 0, st>>>(t.mask, N, t.offs, t.sc_stat,
-                                                                   t.os_ctr + 3, t.status);
+                                                                   t.os_ctr + OS_PASSES, t.status);
     k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, nullptr, N, t.mask, t.offs, t.own_a,
                                                    t.own_b, t.nsc, t.ninfo, t.nparent, t.inode);
     launch_aggregate(t, N, raw, pack, abpack, true, st);
-    note_launches(9 + (N > 1 ? 1 : 0));
+    note_launches(7 + OS_PASSES + (N > 1 ? 1 : 0));
     return cudaGetLastError();
   }
   launches += 2;
@@ -1293,7 +1317,7 @@ cudaError_t build(const TreeArrays& t, int N, const float4* raw, const float4* p
   k_write_nodes<<<nblocks(N, 256), 256, 0, st>>>(t.key, ss, N, t.mask, t.offs, t.own_a, t.own_b,
                                                  t.nsc, t.ninfo, t.nparent, t.inode);
   launch_aggregate(t, N, raw, pack, abpack, true, st);
-  note_launches(launches + 3 + 3);
+  note_launches(launches + 3 + 4);
   return cudaGetLastError();
 }
 
@@ -1350,7 +1374,7 @@ WalkGroups walk_groups(const TreeWork& w, const BHStep& b) {
 }
 }  // namespace
 
-cudaError_t tree_setup() { return cudaSuccess; }
+cudaError_t tree_setup() { return traverse_setup(); }
 
 // Chunks in each slot's pool: the requested number of entries per list times
 // the list count, else the slot's share of the storage budget (at most a
@@ -1455,7 +1479,7 @@ gs_status bh_aggregate(TreeWork& w, const BHStep& b, const float4* abpack, bool 
   if (zero_counts && (err = cudaMemsetAsync(t.counts, 0, 16, st)) != cudaSuccess)
     return cuda_err(err);
   launch_aggregate(t, (int)b.N, b.raw, b.pack, abpack, false, st);
-  note_launches(2);
+  note_launches(3);
   err = cudaGetLastError();
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }

@@ -56,6 +56,8 @@ struct TreeArrays {
   float4* c1box;
   float2* c2sum;
   float4* c2box;
+  int32_t* bigq;    // internal nodes of many range pieces, summed a warp each
+  int32_t* bigc;    // their count
   int64_t* counts;  // {point interactions, node interactions}
   // single-pass sort and scan of one point set (zeroed together, os_bytes):
   uint32_t* os_hist;            // 3 x 1024 digit counts of the 30-bit codes
@@ -214,6 +216,10 @@ __device__ __forceinline__ GroupInfo target_group(const TreeArrays& t, int N, co
   gi.mid = wg.xmid[g];
   return gi;
 }
+
+// Kernel attributes of the traversal (dynamic shared memory of the list
+// evaluation); once per device.
+cudaError_t traverse_setup();
 
 // counts: NULL or 2 int64 accumulating {point, node} interactions.
 // scheduled: take the lists in the previous walk's longest-first order (when
