@@ -262,11 +262,12 @@ def bh_list(q, p, sigma, m, thresh=3.0, leaf=1, crit=0):
 
 def bh_tally(q, sigma, thresh=3.0, leaf=1, crit=0):
     """Per-target record of the Barnes-Hut decisions on the tree of q: an
-    (N, 4) array {point interactions, node interactions, fingerprint of the
-    points taken, fingerprint of the nodes summarised}; the fingerprints are
-    sums modulo 2**64 of splitmix64(key) over the sources, key = (DFS first
-    position << 32) | member count (columns 2-3 as uint64 bit patterns)."""
+    (N, 5) array {point interactions, node interactions, fingerprint of the
+    points taken, fingerprint of the nodes summarised, nodes of >= 2 points
+    reached}; the fingerprints are sums modulo 2**64 of splitmix64(key) over
+    the sources, key = (DFS first position << 32) | member count (columns
+    2-3 as uint64 bit patterns); reached nodes exclude single-child cells."""
     q = _c(q)
-    out = np.zeros((q.shape[0], 4), np.int64)
+    out = np.zeros((q.shape[0], 5), np.int64)
     _load().gsref_bh_tally(q.shape[0], q, float(sigma), float(thresh), int(leaf), int(crit), out)
     return out

@@ -448,6 +448,7 @@ typedef struct {
    * first position of each node's members; NULL when not wanted */
   const int64_t *tpos, *tfirst;
   uint64_t h_point, h_node;
+  int64_t n_reached; /* nodes of >= 2 points reached (chain cells of one child excluded) */
 } visit_ctx;
 
 /* splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
@@ -527,6 +528,12 @@ static void visit(visit_ctx *v, int64_t k) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
   if (nd->n == 0) return;
+  if (nd->n >= 2) { /* reached: counted unless a cell with a single child */
+    int nc = 0;
+    if (!nd->leaf)
+      for (int c = 0; c < 8; c++) nc += nd->child[c] >= 0;
+    if (nd->leaf || nc >= 2) v->n_reached++;
+  }
   const float *x = v->tq32;
   if (nd->n >= 2 && (v->crit ? is_far_angle(x, nd, v->thr) : is_far(x, nd, v->thr))) {
     node_source(v, k); /* case 2: summarised far node */
@@ -1215,11 +1222,15 @@ static void dfs_positions(const otree *t, int64_t N, int64_t *pos, int64_t *firs
 }
 
 /* Per-target record of the Barnes-Hut decisions (Sec. 2.2, three cases) on
- * the tree of positions q: tally[4 m .. 4 m + 3] = {point interactions,
+ * the tree of positions q: tally[5 m .. 5 m + 4] = {point interactions,
  * node interactions, sum over the point interactions of mix64(key), the same
- * sum over the node interactions} for every target m, sums modulo 2^64.  A
- * source's key is (DFS first position << 32) | member count, so two targets'
- * records agree exactly when they took the same sources, whatever the order. */
+ * sum over the node interactions, nodes of >= 2 points reached} for every
+ * target m, sums modulo 2^64.  A source's key is (DFS first position << 32) |
+ * member count, so two targets' records agree exactly when they took the
+ * same sources, whatever the order.  Reached nodes are those the recursion
+ * tests (summarised, opened, or taken whole), without the cells that have a
+ * single non-empty child (they repeat their child's members and range);
+ * with the points taken they are the traversal's node visits. */
 void gsref_bh_tally(int64_t N, const double *q, double sigma, double thresh, int leaf,
                     int crit, int64_t *tally) {
   otree t;
@@ -1244,10 +1255,11 @@ void gsref_bh_tally(int64_t N, const double *q, double sigma, double thresh, int
     v.tpos = pos;
     v.tfirst = first;
     visit(&v, 0);
-    tally[4 * m + 0] = v.n_point;
-    tally[4 * m + 1] = v.n_node;
-    tally[4 * m + 2] = (int64_t)v.h_point;
-    tally[4 * m + 3] = (int64_t)v.h_node;
+    tally[5 * m + 0] = v.n_point;
+    tally[5 * m + 1] = v.n_node;
+    tally[5 * m + 2] = (int64_t)v.h_point;
+    tally[5 * m + 3] = (int64_t)v.h_node;
+    tally[5 * m + 4] = v.n_reached;
   }
   free(pos);
   free(first);

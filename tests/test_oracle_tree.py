@@ -372,6 +372,53 @@ def test_decision_tally_matches_interaction_lists(oracle, geom, n, leaf, crit, t
                 hn = (hn + _splitmix64((int(t["first"][i]) << 32) | int(t["n"][i]))) & mask
         want = [int((kind == 0).sum()), int((kind == 1).sum()), hp, hn]
         got = [int(tally[m, 0]), int(tally[m, 1]), int(tally[m, 2]) & mask,
-               int(tally[m, 3]) & mask]
+               int(tally[m, 3]) & mask]  # (column 4: nodes reached, pinned below)
         assert got == want, m
 
+
+
+@pytest.mark.parametrize("geom,n,leaf,thresh", [("blobs", 160, 1, 3.0), ("slab", 200, 1, 2.0),
+                                                ("blobs", 150, 4, 3.0)])
+def test_decision_tally_counts_by_independent_recursion(oracle, geom, n, leaf, thresh):
+    """Points taken, nodes summarised and nodes reached per target, recounted
+    by a recursion over the exported tree written here (FP32 far test in
+    numpy float32, one rounding per operation): the traversal's node visits
+    that the GPU walk's work is compared with."""
+    w = inputs.make(geom, n, 23)
+    q = w.q0.copy()
+    q[5] = q[2]
+    t = oracle.tree(q, np.zeros_like(q))
+    M = len(t["n"])
+    kids = [[] for _ in range(M)]
+    for k in range(1, M):
+        kids[int(t["parent"][k])].append(k)
+    r = np.float32(thresh * w.sigma)
+    thr = np.float32(r * r)
+    q32 = q.astype(np.float32)
+
+    def far(x, k):
+        d = [max(np.float32(t["lo"][k][a] - x[a]), np.float32(0), np.float32(x[a] - t["hi"][k][a]))
+             for a in range(3)]
+        d2 = np.float32(np.float32(d[0] * d[0]) + np.float32(d[1] * d[1]))
+        return np.float32(d2 + np.float32(d[2] * d[2])) > thr
+
+    tally = oracle.bh_tally(q, w.sigma, thresh, leaf=leaf)
+    for m in range(n):
+        cnt = [0, 0, 0]  # points, nodes, reached
+
+        def visit(k):
+            nk = int(t["n"][k])
+            if nk == 0:
+                return
+            if nk >= 2 and (t["leaf"][k] or t["nchild"][k] >= 2):
+                cnt[2] += 1
+            if nk >= 2 and far(q32[m], k):
+                cnt[1] += 1
+                return
+            if t["leaf"][k] or nk <= leaf:
+                cnt[0] += nk
+                return
+            for c in kids[k]:
+                visit(c)
+        visit(0)
+        assert [int(tally[m, 0]), int(tally[m, 1]), int(tally[m, 4])] == cnt, m
