@@ -290,6 +290,10 @@ def run_ours(args):
     # interactions per step at t = 0 (the per-gradient count is estimated as 2T x this)
     _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
     bh_inter_step = cnt[0] + cnt[1]
+    # the traversal's node visits at t = 0 (points taken + nodes reached), the
+    # walk's warp iterations and the list entries it emits (gs_bh_tally)
+    tal, (walk_iters, list_entries) = gs.bh_tally(q0, w.sigma, THRESH, with_stats=True)
+    visits_step = int(tal[:, 0].sum() + tal[:, 4].sum())
     for _ in range(args.warmup):
         bh_grad()
         plain_grad()
@@ -396,6 +400,22 @@ def run_ours(args):
                                 "issued_frac": ISSUED_OPS_PER_PAIR[cls] * units / per
                                 / ALU_PEAK_OPS,
                                 "mufu_frac": units / per / alu[2]}
+            if cls.startswith("bh"):
+                # lanes evaluate every list entry of their warp; the share of
+                # those lane-slots holding an interaction, and the issued
+                # fraction per evaluated lane-slot
+                slots = 32.0 * list_entries
+                class_roofs[cls]["lane_slots_taken"] = bh_inter_step / slots
+                class_roofs[cls]["issued_frac_per_lane_slot"] = (
+                    ISSUED_OPS_PER_PAIR[cls] * slots / per / ALU_PEAK_OPS)
+        elif cls == "bh_walk":
+            # no arithmetic roof: the algorithmic work is the per-point
+            # traversal's node visits, against the walk's lane-slots
+            class_roofs[cls] = {"bound": "issue", "node_visits": visits_step,
+                                "warp_iterations": walk_iters,
+                                "visits_per_lane_slot": visits_step / (32.0 * walk_iters),
+                                "visits_per_s": visits_step / per,
+                                "ms_per_walk": per * 1e3}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
@@ -639,8 +659,25 @@ def sphere_summary(gs, torch, steps=2, warmup=1):
     _, _, cnt = gs.rhs(q0, p0, w.sigma, mode="bh", thresh=THRESH)
     fn = lambda: gs.shoot_grad(q0, p0, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH,
                                ckpt_every=6)
-    return {"ms_per_gradient": _timed(torch, fn, steps, warmup),
+    ms = _timed(torch, fn, steps, warmup)
+    # the tree build at 10^6 points against HBM (kernel classes, one gradient)
+    gs.timing(True)
+    gs.timing_read()
+    fn()
+    torch.cuda.synchronize()
+    kern, _ = gs.timing_read()
+    gs.timing(False)
+    nb, tb = kern["tree_build"]
+    per = tb / max(nb, 1) * 1e-3
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    gbs = TREE_BYTES_PER_POINT * w.N / per / 1e9
+    return {"ms_per_gradient": ms,
             "bh_interactions_per_point_step": (cnt[0] + cnt[1]) / w.N,
+            "class_ms_per_gradient": {k: v[1] for k, v in kern.items() if v[0]},
+            "tree_build": {"bound": "hbm", "us_per_pass": per * 1e6, "achieved": gbs,
+                           "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                           "bytes_per_point": TREE_BYTES_PER_POINT},
             "workload": f"sphere1m: N={w.N}, sigma={w.sigma} mm, T={w.T}, checkpoint every 6",
             "steps": steps, "warmup": warmup}
 

@@ -105,8 +105,11 @@ typedef struct gs_params {
                             r = p^k at fixed q^k, then q^{k+1} = q^k + h F(q^k,
                             r), p^{k+1} = p^k + h Phi(q^k, r) (M + 1 right-hand
                             sides per step; the step tends to symplectic Euler
-                            as M grows).  Other entry points need 0
-                            (GS_ERR_UNSUPPORTED otherwise) */
+                            as M grows).  gs_shoot, gs_shoot_traj and
+                            gs_shoot_grad (the gradient of this scheme: the
+                            discrete adjoint of its passes) take it; other
+                            entry points need 0 (GS_ERR_UNSUPPORTED
+                            otherwise) */
   int32_t reserved;      /* must be 0 */
 } gs_params;
 
@@ -163,7 +166,13 @@ gs_status gs_shoot_traj(gs_ctx *ctx, const double *q0, const double *p0, int64_t
  * lambda sum |q(1) - X|^2}.  grad: N x 3 dE/dp0.  q1: NULL or N x 3 q(1).
  * In GS_BH mode the backward steps use the tree approximation as the paper
  * prescribes (summaries of alpha and beta), which is not the derivative of
- * the discontinuous Barnes-Hut forward map.
+ * the discontinuous Barnes-Hut forward map.  With prm->sympl_iters = M > 0
+ * the objective is that of the semi-implicit scheme and the gradient its
+ * discrete adjoint: per step, with r_0 = p^k and r_m = p^k + h Phi(q^k,
+ * r_{m-1}), rho_M = h dB[a, b](r_M), rho_{m-1} = h dB[0, rho_m](r_{m-1}),
+ * dE/dq^k = a + h dA[a, b](r_M) + sum_{m=1..M} h dA[0, rho_m](r_{m-1}),
+ * dE/dp^k = b + sum_{m=0..M} rho_m ([x, y](r): the adjoint right-hand side
+ * of gs_adj_rhs at (q^k, r) with alpha = x, beta = y).
  */
 gs_status gs_shoot_grad(gs_ctx *ctx, const double *q0, const double *p0,
                         const double *X, int64_t N, const gs_params *prm,
@@ -314,18 +323,23 @@ gs_status gs_tree(gs_ctx *ctx, const double *q, int64_t N, uint32_t *codes,
  * and the summaries of Eq. 4) on the tree of positions q (N x 3): the walk
  * of every GS_BH step, with its decisions recorded instead of listed.  prm:
  * mode GS_BH with its sigma, thresh_sigmas, leaf_size and criterion (other
- * modes: GS_ERR_UNSUPPORTED).  tally: N x 4 int64, row i (input order) =
+ * modes: GS_ERR_UNSUPPORTED).  tally: N x 5 int64, row i (input order) =
  * {point interactions of target i, node interactions, sum over the points
- * it takes exactly of mix(key), the same sum over the nodes it summarises},
- * sums modulo 2^64 (bit patterns in int64), mix = the splitmix64 output
- * function (Steele, Lea and Flood, OOPSLA 2014) of the 64-bit state key,
- * key = (sorted position of the source's first member << 32) | member
- * count, sorted = the stable Morton order of gs_tree.  Two records agree
- * exactly when the targets took the same sources, in any order; the totals
- * of gs_rhs's counts are the column sums of the first two columns.
+ * it takes exactly of mix(key), the same sum over the nodes it summarises,
+ * nodes of >= 2 points the traversal reaches for target i (tests: summarised,
+ * opened or taken whole; gs_tree's nodes, so a cell whose points all lie in
+ * one child cell is counted once)}, sums modulo 2^64 (bit patterns in
+ * int64), mix = the splitmix64 output function (Steele, Lea and Flood,
+ * OOPSLA 2014) of the 64-bit state key, key = (sorted position of the
+ * source's first member << 32) | member count, sorted = the stable Morton
+ * order of gs_tree.  Two records agree exactly when the targets took the
+ * same sources, in any order; the totals of gs_rhs's counts are the column
+ * sums of the first two columns, and points + nodes reached are the
+ * traversal's node visits.  stats: NULL or 2 int64 {iterations of the
+ * warp-cooperative walk (all warps), interaction-list entries it emits}.
  */
 gs_status gs_bh_tally(gs_ctx *ctx, const double *q, int64_t N, const gs_params *prm,
-                      int64_t *tally, void *stream);
+                      int64_t *tally, int64_t *stats, void *stream);
 
 /*
  * Sums over each node of the octree of gs_tree (same nodes, same preorder)

@@ -81,7 +81,7 @@ _SIGS = {
     "gs_rhs_exact_noalloc": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp]),
     "gs_timing_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "gs_shoot_traj": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp]),
-    "gs_bh_tally": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp]),
+    "gs_bh_tally": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp]),
     "gs_tree_sums": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
 }
 

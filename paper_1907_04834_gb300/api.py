@@ -329,18 +329,20 @@ def shoot_traj(q0, p0, sigma, T, mode="exact", thresh=3.0, leaf_size=1, criterio
     return qt, pt
 
 
-def bh_tally(q, sigma, thresh=3.0, leaf_size=1, criterion=0, stream=None):
+def bh_tally(q, sigma, thresh=3.0, leaf_size=1, criterion=0, with_stats=False, stream=None):
     """Per-target record of the Barnes-Hut decisions on the tree of q
-    (gs_bh_tally): int64 (N, 4) {point interactions, node interactions,
-    fingerprint of the points, fingerprint of the nodes}."""
+    (gs_bh_tally): int64 (N, 5) {point interactions, node interactions,
+    fingerprint of the points, fingerprint of the nodes, nodes reached}; with
+    with_stats also (walk iterations, list entries)."""
     q = _pts(q, "q")
     n = q.shape[0]
     c = _ctx_for(q)
     prm = make_params(sigma, 1, "bh", 0.0, thresh, leaf_size=leaf_size, criterion=criterion)
-    out = torch.empty((n, 4), dtype=torch.int64, device=q.device)
+    out = torch.empty((n, 5), dtype=torch.int64, device=q.device)
+    st = (ctypes.c_int64 * 2)()
     c.check(c.lib.gs_bh_tally(c.handle, _ptr(q), n, ctypes.byref(prm), _ptr(out),
-                              _stream_ptr(c.device, stream)))
-    return out
+                              st if with_stats else None, _stream_ptr(c.device, stream)))
+    return (out, (st[0], st[1])) if with_stats else out
 
 
 def tree_sums(q, p, al=None, be=None, stream=None):

@@ -2058,7 +2058,7 @@ gs_status gs_shoot_traj(gs_ctx* c, const double* q0, const double* p0, int64_t N
 }
 
 gs_status gs_bh_tally(gs_ctx* c, const double* q, int64_t N, const gs_params* prm,
-                      int64_t* tally, void* stream) {
+                      int64_t* tally, int64_t* stats, void* stream) {
   if (!c) return GS_ERR_INVALID_ARG;
   c->err.clear();
   gs_status s;
@@ -2067,21 +2067,24 @@ gs_status gs_bh_tally(gs_ctx* c, const double* q, int64_t N, const gs_params* pr
   if (!tally) return fail(c, GS_ERR_INVALID_ARG, "tally is NULL");
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
-  bool ht = false;
+  bool ht = false, hs = false;
   if ((s = output(c, tally, "tally", &ht))) return s;
+  if (stats && (s = output(c, stats, "stats", &hs))) return s;
   const double* dq;
   if ((s = input(c, q, (size_t)N * 3, "q", c->in_q, st, &dq))) return s;
   Solver S;
   if ((s = solver_init(c, S, N, prm, 1, false, st))) return s;
   if ((s = solver_load(S, dq, dq, 0))) return s;  // decisions depend on positions only
-  const size_t bytes = (size_t)N * 4 * sizeof(int64_t);
-  CK(c->out_a.ensure(bytes), "workspace");
+  const size_t bytes = (size_t)N * 5 * sizeof(int64_t);
+  CK(c->out_a.ensure(bytes + 2 * sizeof(int64_t)), "workspace");
+  int64_t* dstats = c->out_a.as<int64_t>() + (size_t)N * 5;
   BHStep b{0, S.N, S.Npad, S.s, S.thr, S.pack(0), S.raw(0), BHForest{}, S.leaf, false, S.crit};
   s = bh_build(c->tree, b, nullptr, false, st);
-  if (s == GS_OK) s = bh_tally(c->tree, b, c->out_a.as<int64_t>(), st);
+  if (s == GS_OK) s = bh_tally(c->tree, b, c->out_a.as<int64_t>(), stats ? dstats : nullptr, st);
   if (s != GS_OK) return fail(c, s, "decision tally failed: %s", bh_last_error());
   if ((s = copy_out(c, tally, c->out_a.p, bytes, st))) return s;
-  if (ht) return read_status(c, st);
+  if (stats && (s = copy_out(c, stats, dstats, 2 * sizeof(int64_t), st))) return s;
+  if (ht || hs) return read_status(c, st);
   return GS_OK;
 }
 

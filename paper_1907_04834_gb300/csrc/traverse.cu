@@ -343,6 +343,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
   unsigned leafmask = 0u, botmask = 0u;
   while (x < end) {
     if (sink.full()) return false;
+    sink.step();
     int off = x - base;
     if ((unsigned)off >= 32u) {  // stage the next 32 node boxes
       __syncwarp();
@@ -382,6 +383,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
     const float4 bl = sbox[off][0], bh = sbox[off][1];
     const int skip = __float_as_int(bl.w);
     const bool active = x >= resume;
+    sink.reach(active);
     // (bitwise &: the test is computed on every lane, no branch; measured
     // 5% faster than the short-circuit form)
     const bool far = active & (VAR ? far_test(rr.x, rr.y, rr.z, bl, bh, thr, crit)
@@ -418,6 +420,8 @@ struct ListSink {
   bool ovf;
   int res_next, res_end;  // chunks reserved by this warp, not yet used
   __device__ __forceinline__ bool full() const { return ovf; }
+  __device__ __forceinline__ void step() {}
+  __device__ __forceinline__ void reach(bool) {}
   __device__ __forceinline__ void put_chunk(int n) {
     if (ovf) return;
     if (res_next == res_end) {
@@ -622,10 +626,14 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long key) {
 struct TallySink {
   const TreeArrays* t;
   int lane;
-  long long np, nn;
+  long long np, nn, nr;       // this lane's points, nodes, nodes reached
   unsigned long long hp, hn;
+  long long iters, entries;   // the warp's walk iterations and list entries
   __device__ __forceinline__ bool full() const { return false; }
+  __device__ __forceinline__ void step() { iters++; }
+  __device__ __forceinline__ void reach(bool active) { nr += active ? 1 : 0; }
   __device__ __forceinline__ void add1(int node, unsigned mask) {
+    entries++;
     if (!((mask >> lane) & 1u)) return;
     const int skip = __float_as_int(t->nbox[2 * node].w);
     const int cnt = __float_as_int(t->nbox[2 * node + 1].w);
@@ -635,6 +643,7 @@ struct TallySink {
     else nn++, hn += mix64(key);
   }
   __device__ __forceinline__ void add(int node0, int n, unsigned mask, bool points) {
+    entries += n;
     if (!((mask >> lane) & 1u)) return;
     for (int k = 0; k < n; k++) {
       const int pos = points ? node0 + k : t->ninfo[node0 + k].y;
@@ -651,7 +660,7 @@ struct TallySink {
 template <bool VAR>
 __global__ void __launch_bounds__(TR_WARPS * 32)
     k_bh_tally(TreeArrays t, int N, const float4* __restrict__ raw, float thr, WalkGroups wg,
-               unsigned long long* tally) {
+               unsigned long long* tally, unsigned long long* stats) {
   __shared__ float4 s_box[TR_WARPS][32][2];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wk = BH_SLICES * wg.wsplit;
@@ -668,15 +677,20 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   int resume = valid ? 0 : INT_MAX;
   if (k > 0 && valid && x < end)
     resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
-  TallySink sink{&t, lane, 0, 0, 0ull, 0ull};
+  TallySink sink{&t, lane, 0, 0, 0, 0ull, 0ull, 0, 0};
   long long np = 0, nn = 0;
   walk_nodes<false, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, false, wg.crit, resume, sink,
                          lane, np, nn);
+  if (stats && lane == 0) {
+    atomicAdd(&stats[0], (unsigned long long)sink.iters);
+    atomicAdd(&stats[1], (unsigned long long)sink.entries);
+  }
   if (!valid) return;
-  atomicAdd(&tally[4 * (size_t)o + 0], (unsigned long long)sink.np);
-  atomicAdd(&tally[4 * (size_t)o + 1], (unsigned long long)sink.nn);
-  atomicAdd(&tally[4 * (size_t)o + 2], sink.hp);
-  atomicAdd(&tally[4 * (size_t)o + 3], sink.hn);
+  atomicAdd(&tally[5 * (size_t)o + 0], (unsigned long long)sink.np);
+  atomicAdd(&tally[5 * (size_t)o + 1], (unsigned long long)sink.nn);
+  atomicAdd(&tally[5 * (size_t)o + 2], sink.hp);
+  atomicAdd(&tally[5 * (size_t)o + 3], sink.hn);
+  atomicAdd(&tally[5 * (size_t)o + 4], (unsigned long long)sink.nr);
 }
 
 // ------------------------------------------------------------------ combine
@@ -739,183 +753,63 @@ __device__ __forceinline__ void finish_slice(const TreeArrays& t, int N, const B
 }
 
 // ------------------------------------------------------------------ evaluate
-// Asynchronous 4-byte copies global -> shared (cp.async), and waits for this
-// thread's groups of them.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Reader of a slice's entries: its walk lists one after another, each a
-// chain of BH_CHUNK-entry chunks.  A batch of up to TR_CAP entries spans
-// at most kMaxSegs runs of consecutive entries in one chunk (chunk ends
-// inside the batch: at most two per walk list touched, two lists; one list
-// end), found by the warp together; lane l then copies the batch's entries
-// l, l + 32, ... to shared memory asynchronously.
-constexpr int kMaxSegs = 6;
-constexpr int kPerLane = TR_CAP / 32;
-struct SliceReader {
-  int j, chunk, off, left;
-  __device__ __forceinline__ void copy(const BHLists& L, int l0, int cn, int lane, int2* dst) {
-    const int2* sp[kMaxSegs];
-    int sb[kMaxSegs];
-    int got = 0;
-#pragma unroll
-    for (int q = 0; q < kMaxSegs; q++) {
-      sp[q] = L.ent;
-      sb[q] = cn;
-      if (got < cn) {
-        while (left == 0) {  // next walk list of the slice (entries remain)
-          j++;
-          chunk = L.head[l0 + j];
-          off = 0;
-          left = L.len[l0 + j];
-        }
-        const int take = min(min(BH_CHUNK - off, left), cn - got);
-        sp[q] = L.ent + (size_t)chunk * BH_CHUNK + off;
-        sb[q] = got;
-        got += take;
-        off += take;
-        left -= take;
-        if (off == BH_CHUNK && left > 0) {
-          chunk = L.next[chunk];
-          off = 0;
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kPerLane; k++) {
-      const int e = lane + 32 * k;
-      if (e >= cn) continue;
-      const int2* src = sp[0] + (e - sb[0]);
-#pragma unroll
-      for (int q = 1; q < kMaxSegs; q++)
-        if (e >= sb[q]) src = sp[q] + (e - sb[q]);
-      const unsigned a = (unsigned)__cvta_generic_to_shared(dst + e);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(src) : "memory");
-    }
-  }
-};
-
-// Issues the copies of a batch's source records (its entries in ent, cn of
-// them, already in shared memory) into soa (component-major, stride
-// TR_CAP) and writes its lane masks; an odd count is padded with an entry
-// no lane takes.  Returns the padded count.
-template <bool ADJ, bool TRUNC>
-__device__ __forceinline__ int issue_records(const TreeArrays& t, const int2* ent, int cn,
-                                             float* soa, unsigned* mask, int lane) {
-  constexpr int NR = ADJ ? 12 : 6;
-  const float* rec = reinterpret_cast<const float*>(t.nrec);
-  const float* box = reinterpret_cast<const float*>(t.nbox);
-#pragma unroll
-  for (int k = 0; k < kPerLane; k++) {
-    const int e = lane + 32 * k;
-    if (e >= cn) continue;
-    const int2 v = ent[e];
-    int nd = v.x;
-    if (nd < 0) nd = ~nd + (int)t.offs[~nd + 1];  // point entry -> its leaf
-    mask[e] = (unsigned)v.y;
-#pragma unroll
-    for (int c = 0; c < NR; c++)
-      cp_async4(soa + c * TR_CAP + e, rec + 16 * (size_t)nd + 4 * (c / 3) + (c % 3));
-    if (TRUNC)
-#pragma unroll
-      for (int c = 0; c < 3; c++)
-        cp_async4(soa + (NR + c) * TR_CAP + e, box + 8 * (size_t)nd + c);
-  }
-  if (cn & 1) {
-    if (lane == 0) mask[cn] = 0u;
-    if (lane < NR + (TRUNC ? 3 : 0)) soa[lane * TR_CAP + cn] = 0.f;
-    return cn + 1;
-  }
-  return cn;
-}
-
-// Dynamic shared memory of the evaluation, per warp: two batch buffers of
-// the record components and one mask word per entry, and three buffers of
-// list entries.
-template <bool ADJ, bool TRUNC>
-__host__ __device__ constexpr int eval_buf_floats() {
-  return ((ADJ ? 12 : 6) + (TRUNC ? 3 : 0) + 1) * TR_CAP;
-}
-template <bool ADJ, bool TRUNC>
-__host__ __device__ constexpr int eval_warp_floats() {
-  return 2 * eval_buf_floats<ADJ, TRUNC>() + 3 * 2 * TR_CAP;
-}
-template <bool ADJ, bool TRUNC>
-__host__ __device__ constexpr size_t eval_smem_bytes() {
-  return sizeof(float) * eval_warp_floats<ADJ, TRUNC>() * TR_WARPS;
-}
-
 // One warp per slice: partial sums of its entries, part[(e*NC + c)*32 + lane].
-// The entries of the slice's walk lists are read as one sequence, TR_CAP at
-// a time (two list chunks), so the batches (and the sums) are those of an
-// unsplit walk.  Software pipeline of asynchronous copies: while batch b is
-// evaluated, the records of batch b + 1 and the list entries of batch b + 2
-// are on their way to shared memory.  The adjoint variant is held to 128
-// registers (4 blocks per SM).
+// The entries of the slice's walk lists are read as one sequence, TR_CAP
+// at a time (two list chunks; measured 4% faster than one), so the batches
+// (and the sums) are those of an unsplit walk.  The adjoint variant is held
+// to 128 registers (4 blocks per SM): measured faster than 3 blocks at 168.
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
     k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts,
               const int* __restrict__ order, FwdEpi fe, AdjEpi ae, TracerEpi te) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
   constexpr int NC = Acc<ADJ>::NC;
-  constexpr int BUF = eval_buf_floats<ADJ, TRUNC>();
-  extern __shared__ __align__(16) float s_dyn[];
+  __shared__ __align__(16) float s_soa[TR_WARPS][NR * TR_CAP];
+  __shared__ int s_node[TR_WARPS][TR_CAP];
+  __shared__ unsigned s_mask[TR_WARPS][TR_CAP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wl = blockIdx.x * TR_WARPS + w;
   if (wl >= wg.G * BH_SLICES) return;
   const int e = order ? order[wl] : list_of_warp(wl, wg.G);
   const int ws = wg.wsplit, l0 = e * ws;
   if (slice_overflowed(L, e, ws)) return;  // evaluated whole by the fallback
-  float* wbase = s_dyn + (size_t)w * eval_warp_floats<ADJ, TRUNC>();
-  int2* ents = reinterpret_cast<int2*>(wbase + 2 * BUF);  // 3 x TR_CAP entries
   const Own me = load_own(t, wg, target_group(t, N, wg, e / BH_SLICES), lane, ADJ);
   Acc<ADJ> A;
   A.zero();
   int npair = 0;
   int n = 0;
   for (int j = 0; j < ws; j++) n += L.len[l0 + j];
-  const int nb = (n + TR_CAP - 1) / TR_CAP;
-  SliceReader rd{0, L.head[l0], 0, L.len[l0]};
-  auto cnt = [&](int b) { return min(TR_CAP, n - b * TR_CAP); };
-  auto recs = [&](int b) { return wbase + (b & 1) * BUF; };
-  auto ent = [&](int b) { return ents + (b % 3) * TR_CAP; };
-  int ce_cur = 0, ce_next = 0;
-  if (nb > 0) {  // prologue: entries of batches 0 and 1, records of batch 0
-    rd.copy(L, l0, cnt(0), lane, ent(0));
-    cp_async_commit();
-    if (nb > 1) rd.copy(L, l0, cnt(1), lane, ent(1));
-    cp_async_commit();
-    cp_async_wait<1>();
+  // reader state: walk list j, its current chunk, offset there, entries left
+  int j = 0, chunk = L.head[l0], off = 0, left = L.len[l0];
+  for (int c0 = 0; c0 < n; c0 += TR_CAP) {
+    const int cn = min(TR_CAP, n - c0);
     __syncwarp();
-    ce_next = issue_records<ADJ, TRUNC>(t, ent(0), cnt(0), recs(0),
-                                        reinterpret_cast<unsigned*>(recs(0) + NR * TR_CAP), lane);
-    cp_async_commit();
-  }
-  for (int b = 0; b < nb; b++) {
-    ce_cur = ce_next;
-    // everything issued so far has landed: records of b, entries of b + 1
-    cp_async_wait<0>();
-    __syncwarp();
-    if (b + 1 < nb) {
-      float* nx = recs(b + 1);
-      ce_next = issue_records<ADJ, TRUNC>(t, ent(b + 1), cnt(b + 1), nx,
-                                          reinterpret_cast<unsigned*>(nx + NR * TR_CAP), lane);
-      if (b + 2 < nb) rd.copy(L, l0, cnt(b + 2), lane, ent(b + 2));
-      cp_async_commit();
+    for (int got = 0; got < cn;) {
+      while (left == 0) {  // next walk list of the slice (entries remain)
+        j++;
+        chunk = L.head[l0 + j];
+        off = 0;
+        left = L.len[l0 + j];
+      }
+      const int take = min(min(BH_CHUNK - off, left), cn - got);
+      const int2* src = L.ent + (size_t)chunk * BH_CHUNK + off;
+      for (int q = lane; q < take; q += 32) {
+        const int2 v = src[q];
+        s_node[w][got + q] = v.x;
+        s_mask[w][got + q] = (unsigned)v.y;
+      }
+      got += take;
+      off += take;
+      left -= take;
+      if (off == BH_CHUNK && left > 0) {
+        chunk = L.next[chunk];
+        off = 0;
+      }
     }
-    float* cur = recs(b);
-    eval_batch<ADJ, TRUNC>(A, cur, reinterpret_cast<const unsigned*>(cur + NR * TR_CAP), ce_cur,
-                           lane, me, thr, npair);
     __syncwarp();
+    const int ce = stage_records<ADJ, TRUNC>(t, s_node[w], s_mask[w], s_soa[w], cn, lane);
+    __syncwarp();
+    eval_batch<ADJ, TRUNC>(A, s_soa[w], s_mask[w], ce, lane, me, thr, npair);
   }
 #pragma unroll
   for (int c = 0; c < NC; c++) L.part[((size_t)e * NC + c) * 32 + lane] = A.K[c].out();
@@ -943,6 +837,8 @@ struct EvalSink {
   float thr;
   int npair;
   __device__ __forceinline__ bool full() const { return false; }
+  __device__ __forceinline__ void step() {}
+  __device__ __forceinline__ void reach(bool) {}
   __device__ __forceinline__ void flush() {
     __syncwarp();
     const int ce = stage_records<ADJ, TRUNC>(*t, node, mask, soa, cnt, lane);
@@ -1186,19 +1082,6 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 
 }  // namespace
 
-cudaError_t traverse_setup() {
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f, size_t bytes) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  };
-  set((const void*)k_bh_eval<false, false>, eval_smem_bytes<false, false>());
-  set((const void*)k_bh_eval<true, false>, eval_smem_bytes<true, false>());
-  set((const void*)k_bh_eval<false, true>, eval_smem_bytes<false, true>());
-  set((const void*)k_bh_eval<true, true>, eval_smem_bytes<true, true>());
-  return e;
-}
-
 cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float thr,
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            bool scheduled, cudaStream_t st) {
@@ -1223,13 +1106,15 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
 }
 
 cudaError_t launch_bh_tally(const TreeArrays& t, int N, const float4* raw, float thr,
-                            const WalkGroups& wg, int64_t* tally, cudaStream_t st) {
+                            const WalkGroups& wg, int64_t* tally, int64_t* stats,
+                            cudaStream_t st) {
   const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES * wg.wsplit);
   auto* out = reinterpret_cast<unsigned long long*>(tally);
+  auto* sts = reinterpret_cast<unsigned long long*>(stats);
   if (wg.leaf > 1 || wg.crit != 0)
-    k_bh_tally<true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out);
+    k_bh_tally<true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out, sts);
   else
-    k_bh_tally<false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out);
+    k_bh_tally<false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, wg, out, sts);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1242,8 +1127,8 @@ static void eval_launch(const TreeArrays& t, int N, const float4* raw, float thr
   const unsigned nb = warp_blocks((int64_t)wg.G * BH_SLICES);
   // list evaluation, then the fallback for overflowed slices; the warp that
   // finishes a group's last slice (in either kernel) combines the group
-  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, eval_smem_bytes<ADJ, TRUNC>(), st>>>(
-      t, N, L, wg, thr, counts, order, fe, ae, te);
+  k_bh_eval<ADJ, TRUNC><<<nb, TR_WARPS * 32, 0, st>>>(t, N, L, wg, thr, counts, order, fe, ae,
+                                                      te);
   if (counts)
     k_bh_fallback<ADJ, true, TRUNC>
         <<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, fe, ae, te);

@@ -1374,7 +1374,7 @@ WalkGroups walk_groups(const TreeWork& w, const BHStep& b) {
 }
 }  // namespace
 
-cudaError_t tree_setup() { return traverse_setup(); }
+cudaError_t tree_setup() { return cudaSuccess; }
 
 // Chunks in each slot's pool: the requested number of entries per list times
 // the list count, else the slot's share of the storage budget (at most a
@@ -1515,13 +1515,15 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 
-gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, cudaStream_t st) {
+gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, int64_t* stats,
+                   cudaStream_t st) {
   TreeArrays t;
   BHLists L;
   views(w, b.slot, &t, &L);
-  cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(int64_t) * 4 * (size_t)b.N, st);
+  cudaError_t err = cudaMemsetAsync(tally, 0, sizeof(int64_t) * 5 * (size_t)b.N, st);
+  if (err == cudaSuccess && stats) err = cudaMemsetAsync(stats, 0, 2 * sizeof(int64_t), st);
   if (err == cudaSuccess)
-    err = launch_bh_tally(t, (int)b.N, b.raw, b.thr, walk_groups(w, b), tally, st);
+    err = launch_bh_tally(t, (int)b.N, b.raw, b.thr, walk_groups(w, b), tally, stats, st);
   return err == cudaSuccess ? GS_OK : cuda_err(err);
 }
 

@@ -81,8 +81,10 @@ gs_status bh_eval_adj(TreeWork& w, const BHStep& b, const AdjEpi& e, bool counts
                       cudaStream_t st);
 void bh_counts(TreeWork& w, int64_t* cnt);
 // Per-target decision record of the tree in b.slot (one point set, not the
-// truncation variant): tally = 4 N device int64 (see gs_bh_tally in gs.h).
-gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, cudaStream_t st);
+// truncation variant): tally = 5 N device int64, stats = NULL or 2 device
+// int64 (see gs_bh_tally in gs.h).
+gs_status bh_tally(TreeWork& w, const BHStep& b, int64_t* tally, int64_t* stats,
+                   cudaStream_t st);
 
 // Outside points (tracers, forward only) walking the tree of b.slot as
 // targets: positions xraw (FP32, by index), records xrec (scaled, by index);

@@ -217,10 +217,6 @@ __device__ __forceinline__ GroupInfo target_group(const TreeArrays& t, int N, co
   return gi;
 }
 
-// Kernel attributes of the traversal (dynamic shared memory of the list
-// evaluation); once per device.
-cudaError_t traverse_setup();
-
 // counts: NULL or 2 int64 accumulating {point, node} interactions.
 // scheduled: take the lists in the previous walk's longest-first order (when
 // it has as many lists), then sort this walk's lists by length into L.order
@@ -230,11 +226,14 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            bool scheduled, cudaStream_t st);
 // Decision record of every target of one point set (no truncation): tally
-// (4 N int64, zeroed by the caller) accumulates per original index {point
-// interactions, node interactions, fingerprint sums of each} -- the walk's
-// own decisions, recorded instead of listed.
+// (5 N int64, zeroed by the caller) accumulates per original index {point
+// interactions, node interactions, fingerprint sums of each, nodes reached}
+// -- the walk's own decisions, recorded instead of listed; stats (NULL or 2
+// int64, zeroed by the caller) accumulates the walk's warp iterations and
+// list entries.
 cudaError_t launch_bh_tally(const TreeArrays& t, int N, const float4* raw, float thr,
-                            const WalkGroups& wg, int64_t* tally, cudaStream_t st);
+                            const WalkGroups& wg, int64_t* tally, int64_t* stats,
+                            cudaStream_t st);
 // fallback for overflowed lists, evaluation, fixed-order combine + epilogue;
 // scheduled: evaluate in L.order (written by a scheduled walk of these lists)
 cudaError_t launch_bh_eval(const TreeArrays& t, int N, const float4* raw, float thr,

@@ -4,12 +4,13 @@ traversal, the node statistics n, sum q, sum p and the backward stage's
 sum alpha, sum beta behind the summaries of Eq. 4).
 
 Decisions: for every target, the number of points it takes exactly, the
-number of nodes it summarises and a fingerprint of each set (a sum modulo
-2^64 of a 64-bit mix of each source's identity) must equal the oracle's bit
-for bit; a decision moved from one target to another, or swapped between
-two sources of one target, changes a record even where the totals stay
-equal.  Node statistics: member counts exactly, sums within the rounding of
-their FP32 inputs (bound computed per node from the members)."""
+number of nodes it summarises, a fingerprint of each set (a sum modulo
+2^64 of a 64-bit mix of each source's identity) and the number of nodes the
+traversal reaches must equal the oracle's bit for bit; a decision moved
+from one target to another, or swapped between two sources of one target,
+changes a record even where the totals stay equal.  Node statistics:
+member counts exactly, sums within the rounding of their FP32 inputs (bound
+computed per node from the members)."""
 import numpy as np
 import pytest
 
@@ -64,11 +65,17 @@ def test_decisions_per_target_full_size(oracle, name):
     """Every target's decisions at the benchmark's N = 100,000 and the largest
     workload's N = 1,000,000."""
     w = inputs.config(name)
-    t = npy(gs.bh_tally(dt(w.q0), w.sigma))
+    t, (iters, entries) = gs.bh_tally(dt(w.q0), w.sigma, with_stats=True)
+    t = npy(t)
     to = oracle.bh_tally(w.q0, w.sigma)
     bad = np.flatnonzero(np.any(t != to, axis=1))
+    visits = int(t[:, 0].sum() + t[:, 4].sum())
+    taken = int(t[:, 0].sum() + t[:, 1].sum())
     print(f"\n{name}: {w.N} targets, {int(t[:, 0].sum())} point and {int(t[:, 1].sum())} node "
-          f"interactions; targets whose decisions differ from the oracle's: {bad.size}")
+          f"interactions; targets whose decisions differ from the oracle's: {bad.size}; "
+          f"traversal node visits {visits}, walk iterations {iters} ({visits / (32 * iters):.3f} "
+          f"of their lane-slots), list entries {entries} ({taken / (32 * entries):.3f} of their "
+          f"lane-slots taken)")
     assert bad.size == 0
 
 
