@@ -76,10 +76,11 @@ def parse_args():
     ap.add_argument("--sphere", action="store_true",
                     help="measure the 1M-point sphere workload: Barnes-Hut gradient, T = 40, "
                          "checkpoint every 6 steps (separate JSON line)")
-    ap.add_argument("--probe", choices=["bh", "exact", "batched"],
+    ap.add_argument("--probe", choices=["bh", "exact", "batched", "bhgrad"],
                     help="for profiler captures: two rounds of one forward and one adjoint "
                          "right-hand side at the workload's initial state (batched: one "
-                         "exact gradient of the 64-subject workload), then exit")
+                         "exact gradient of the 64-subject workload; bhgrad: two Barnes-Hut "
+                         "gradients, the benchmark's kernels), then exit")
     return ap.parse_args()
 
 
@@ -592,6 +593,13 @@ def run_probe(args):
         gs.shoot_batched(cat("q0"), cat("p0"), cat("X"), off, ws[0].sigma, ws[0].T, ws[0].lam)
         torch.cuda.synchronize()
         print(json.dumps({"probe": "batched", "N": int(off[-1]), "ok": True}))
+        return 0
+    if args.probe == "bhgrad":
+        X = t(w.X)
+        for _ in range(2):
+            gs.shoot_grad(q, p, X, w.sigma, w.T, w.lam, mode="bh", thresh=THRESH)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": "bhgrad", "N": w.N, "ok": True}))
         return 0
     mode = "bh" if args.probe == "bh" else "exact"
     for _ in range(2):

@@ -266,7 +266,7 @@ def bh_tally(q, sigma, thresh=3.0, leaf=1, crit=0):
     points taken, fingerprint of the nodes summarised, nodes of >= 2 points
     reached}; the fingerprints are sums modulo 2**64 of splitmix64(key) over
     the sources, key = (DFS first position << 32) | member count (columns
-    2-3 as uint64 bit patterns); reached nodes exclude single-child cells."""
+    2-3 as uint64 bit patterns); a chain of single-child cells counts once."""
     q = _c(q)
     out = np.zeros((q.shape[0], 5), np.int64)
     _load().gsref_bh_tally(q.shape[0], q, float(sigma), float(thresh), int(leaf), int(crit), out)

@@ -448,7 +448,7 @@ typedef struct {
    * first position of each node's members; NULL when not wanted */
   const int64_t *tpos, *tfirst;
   uint64_t h_point, h_node;
-  int64_t n_reached; /* nodes of >= 2 points reached (chain cells of one child excluded) */
+  int64_t n_reached; /* nodes of >= 2 points reached, a chain of single-child cells once */
 } visit_ctx;
 
 /* splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
@@ -524,16 +524,17 @@ static void all_points(visit_ctx *v, int64_t k) {
     if (nd->child[c] >= 0) all_points(v, nd->child[c]);
 }
 
-static void visit(visit_ctx *v, int64_t k) {
+/* top: k is the root or its parent has >= 2 non-empty children, i.e. k is
+ * the first of a chain of cells with the same members (and the same range,
+ * so the same decision); only that one is counted as reached. */
+static void visit(visit_ctx *v, int64_t k, int top) {
   const otree *t = v->t;
   const onode *nd = &t->nodes[k];
   if (nd->n == 0) return;
-  if (nd->n >= 2) { /* reached: counted unless a cell with a single child */
-    int nc = 0;
-    if (!nd->leaf)
-      for (int c = 0; c < 8; c++) nc += nd->child[c] >= 0;
-    if (nd->leaf || nc >= 2) v->n_reached++;
-  }
+  int nc = 0;
+  if (!nd->leaf)
+    for (int c = 0; c < 8; c++) nc += nd->child[c] >= 0;
+  if (nd->n >= 2 && top) v->n_reached++;
   const float *x = v->tq32;
   if (nd->n >= 2 && (v->crit ? is_far_angle(x, nd, v->thr) : is_far(x, nd, v->thr))) {
     node_source(v, k); /* case 2: summarised far node */
@@ -548,7 +549,7 @@ static void visit(visit_ctx *v, int64_t k) {
     return;
   }
   for (int c = 0; c < 8; c++) /* case 3: open the node */
-    if (nd->child[c] >= 0) visit(v, nd->child[c]);
+    if (nd->child[c] >= 0) visit(v, nd->child[c], nc >= 2);
 }
 
 static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
@@ -569,7 +570,7 @@ static void bh_target(const otree *t, double sigma, float thr, int64_t leaf,
   v.adjoint = adjoint;
   v.m = m;
   v.list = list;
-  visit(&v, 0);
+  visit(&v, 0, 1);
   for (int a = 0; a < 3; a++) {
     o0[a] = v.acc0[a];
     o1[a] = v.acc1[a];
@@ -1009,7 +1010,7 @@ void gsref_velocity_bh(int64_t N, const double *q, const double *p, int64_t M,
     vc.tq = x + 3 * m;
     vc.tp = zero;
     vc.tq32 = x32 + 3 * m;
-    visit(&vc, 0);
+    visit(&vc, 0, 1);
     for (int a = 0; a < 3; a++) v[3 * m + a] = vc.acc0[a];
   }
   free(x32);
@@ -1228,9 +1229,10 @@ static void dfs_positions(const otree *t, int64_t N, int64_t *pos, int64_t *firs
  * target m, sums modulo 2^64.  A source's key is (DFS first position << 32) |
  * member count, so two targets' records agree exactly when they took the
  * same sources, whatever the order.  Reached nodes are those the recursion
- * tests (summarised, opened, or taken whole), without the cells that have a
- * single non-empty child (they repeat their child's members and range);
- * with the points taken they are the traversal's node visits. */
+ * tests (summarised, opened, or taken whole), a chain of cells with a single
+ * non-empty child counted once (its cells have the same members and range,
+ * so the first one decides); with the points taken they are the
+ * traversal's node visits. */
 void gsref_bh_tally(int64_t N, const double *q, double sigma, double thresh, int leaf,
                     int crit, int64_t *tally) {
   otree t;
@@ -1254,7 +1256,7 @@ void gsref_bh_tally(int64_t N, const double *q, double sigma, double thresh, int
     v.m = m;
     v.tpos = pos;
     v.tfirst = first;
-    visit(&v, 0);
+    visit(&v, 0, 1);
     tally[5 * m + 0] = v.n_point;
     tally[5 * m + 1] = v.n_node;
     tally[5 * m + 2] = (int64_t)v.h_point;

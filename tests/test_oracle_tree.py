@@ -410,7 +410,8 @@ def test_decision_tally_counts_by_independent_recursion(oracle, geom, n, leaf, t
             nk = int(t["n"][k])
             if nk == 0:
                 return
-            if nk >= 2 and (t["leaf"][k] or t["nchild"][k] >= 2):
+            # a chain of single-child cells (same members) counts once, at its top
+            if nk >= 2 and (k == 0 or t["nchild"][int(t["parent"][k])] >= 2):
                 cnt[2] += 1
             if nk >= 2 and far(q32[m], k):
                 cnt[1] += 1
