@@ -367,8 +367,8 @@ gs_status gs_tree_sums(gs_ctx *ctx, const double *q, const double *p, const doub
  *   lists do not fit are evaluated by a slower fused walk-and-evaluate pass
  *   that gives bit-identical results.
  *   "bh_walk_split": walk lists per slice of the Barnes-Hut walk (each group
- *   of 32 points has four slices): 1 or 2, or 0 (default) = 2 for trees of
- *   fewer than 48 x (SM count) groups, else 1.  Splitting spreads a small
+ *   of 32 points has four slices): 1, 2 or 4, or 0 (default) = 2 for trees
+ *   of fewer than 48 x (SM count) groups, else 1.  Splitting spreads a small
  *   tree's walk over more warps; results are bit-identical either way.
  *   "trunc_grid": 1 = GS_TRUNC on one point set searches its pairs with a
  *   uniform cell grid instead of the octree: cells of side 0.51 r (r =

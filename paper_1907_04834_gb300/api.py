@@ -265,8 +265,10 @@ def velocity(q, p, x, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0,
     return v
 
 
-def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=None):
-    """One forward right-hand side: (F, Phi, (point pairs, node pairs))."""
+def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, with_counts=True,
+        stream=None):
+    """One forward right-hand side: (F, Phi, (point pairs, node pairs)), or
+    (F, Phi) with with_counts=False (no counts requested: the lean walk)."""
     q = _pts(q, "q")
     p = _pts(p, "p", q.shape[0])
     c = _ctx_for(q)
@@ -274,12 +276,14 @@ def rhs(q, p, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=
     F, Phi = torch.empty_like(q), torch.empty_like(q)
     cnt = (ctypes.c_int64 * 2)()
     c.check(c.lib.gs_rhs(c.handle, _ptr(q), _ptr(p), q.shape[0], ctypes.byref(prm), _ptr(F),
-                         _ptr(Phi), cnt, _stream_ptr(c.device, stream)))
-    return F, Phi, (cnt[0], cnt[1])
+                         _ptr(Phi), cnt if with_counts else None, _stream_ptr(c.device, stream)))
+    return (F, Phi, (cnt[0], cnt[1])) if with_counts else (F, Phi)
 
 
-def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0, stream=None):
-    """One adjoint right-hand side: (dA, dB, counts)."""
+def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, leaf_size=1, criterion=0,
+            with_counts=True, stream=None):
+    """One adjoint right-hand side: (dA, dB, counts), or (dA, dB) with
+    with_counts=False."""
     q = _pts(q, "q")
     n = q.shape[0]
     p, al, be = _pts(p, "p", n), _pts(al, "al", n), _pts(be, "be", n)
@@ -288,9 +292,9 @@ def adj_rhs(q, p, al, be, sigma, mode="exact", thresh=3.0, leaf_size=1, criterio
     dA, dB = torch.empty_like(q), torch.empty_like(q)
     cnt = (ctypes.c_int64 * 2)()
     c.check(c.lib.gs_adj_rhs(c.handle, _ptr(q), _ptr(p), _ptr(al), _ptr(be), n,
-                             ctypes.byref(prm), _ptr(dA), _ptr(dB), cnt,
+                             ctypes.byref(prm), _ptr(dA), _ptr(dB), cnt if with_counts else None,
                              _stream_ptr(c.device, stream)))
-    return dA, dB, (cnt[0], cnt[1])
+    return (dA, dB, (cnt[0], cnt[1])) if with_counts else (dA, dB)
 
 
 def tree(q, stream=None):

@@ -1264,8 +1264,8 @@ gs_status gs_set_option(gs_ctx* c, const char* name, int64_t value) {
     return GS_OK;
   }
   if (strcmp(name, "bh_walk_split") == 0) {
-    if (value != 0 && value != 1 && value != 2)
-      return fail(c, GS_ERR_INVALID_ARG, "bh_walk_split must be 0, 1 or 2");
+    if (value != 0 && value != 1 && value != 2 && value != 4)
+      return fail(c, GS_ERR_INVALID_ARG, "bh_walk_split must be 0, 1, 2 or 4");
     c->tree.wsplit_req = (int)value;
     return GS_OK;
   }
@@ -1947,7 +1947,8 @@ gs_status gs_rhs(gs_ctx* c, const double* q, const double* p, int64_t N, const g
   e.F_out = c->out_a.as<double>();
   e.Phi_out = c->out_b.as<double>();
   int64_t cnt[2] = {0, 0};
-  if ((s = forward_rhs(S, 0, e, cnt))) return s;
+  // (no counts asked for: the lean walk, which lists the same entries)
+  if ((s = forward_rhs(S, 0, e, counts ? cnt : nullptr))) return s;
   if ((s = copy_out(c, F, c->out_a.p, b3, st)) || (s = copy_out(c, Phi, c->out_b.p, b3, st)))
     return s;
   if (counts) {
@@ -1993,7 +1994,7 @@ gs_status gs_adj_rhs(gs_ctx* c, const double* q, const double* p, const double* 
   e.dA_out = c->out_a.as<double>();
   e.dB_out = c->out_b.as<double>();
   int64_t cnt[2] = {0, 0};
-  if ((s = adjoint_rhs(S, 0, 0, e, cnt))) return s;
+  if ((s = adjoint_rhs(S, 0, 0, e, counts ? cnt : nullptr))) return s;
   if ((s = copy_out(c, dA, c->out_a.p, b3, st)) || (s = copy_out(c, dB, c->out_b.p, b3, st)))
     return s;
   if (counts) {

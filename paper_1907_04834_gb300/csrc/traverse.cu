@@ -122,25 +122,34 @@ __device__ __forceinline__ bool within(float ax, float ay, float az, float bx, f
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <= thr;
 }
 
-// Cut k (0 <= k <= wk) of the group's node range [nb, ne) into wk = 4 or 8
-// walk slices: nb, then L - D 2^(h-1-k) for k = 1 .. h-1, L, and
-// L + D 2^(k-h-1) for k = h+1 .. wk-1 (clamped to the range), then ne, with
-// h = wk/2, L the leaf of the group's middle point and
-// D = clamp((ne - nb) / 32, 256, 4096) * 8 / wk.  For wk = 8 the cuts are
-// L -/+ D0, 2 D0, 4 D0; for wk = 4 they are L -/+ 2 D0: the even cuts of the
-// eight, so the evaluation's four slices [cut 0, cut 1) ... are the same
-// node ranges either way.  Any cut points give the same interactions; these
-// spread a group's work over several warps, narrow slices near the group
-// where the walk opens most nodes.  The cuts depend only on the current
-// tree, so results are reproducible.
-__device__ __forceinline__ int walk_cut(const GroupInfo& gi, int k, int wk) {
+// Cut k (0 <= k <= 8) of the group's node range [nb, ne) into eight walk
+// slices: nb, then L - D 2^(3-k) for k = 1, 2, 3, L, and L + D 2^(k-5) for
+// k = 5, 6, 7 (clamped to the range), then ne, with L the leaf of the
+// group's middle point and D = clamp((ne - nb) / 32, 256, 4096): narrow
+// slices near the group, where the walk opens most nodes.
+__device__ __forceinline__ int walk_cut8(const GroupInfo& gi, int k) {
   if (k <= 0) return gi.nb;
-  if (k >= wk) return gi.ne;
-  const int h = wk >> 1, mid = gi.mid;
-  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096) * (8 / wk);
-  if (k < h) return max(gi.nb, mid - (D << (h - 1 - k)));
-  if (k == h) return mid;
-  return min(gi.ne, mid + (D << (k - h - 1)));
+  if (k >= 8) return gi.ne;
+  const int mid = gi.mid;
+  const int D = min(max((gi.ne - gi.nb) >> 5, 256), 4096);
+  if (k < 4) return max(gi.nb, mid - (D << (3 - k)));
+  if (k == 4) return mid;
+  return min(gi.ne, mid + (D << (k - 5)));
+}
+
+// Cut k (0 <= k <= wk) of the group's node range into wk = 4, 8 or 16 walk
+// slices: for 4 the even cuts of the eight, for 16 the eight and the
+// midpoints between them.  The evaluation's four slices [cut 0, cut wk/4),
+// ... are the same node ranges whatever wk is.  Any cut points give the
+// same interactions; finer walk slices only spread a group's walk over more
+// warps, so that no single long walk holds the GPU at the end of a launch.
+// The cuts depend only on the current tree, so results are reproducible.
+__device__ __forceinline__ int walk_cut(const GroupInfo& gi, int k, int wk) {
+  if (wk == 16) {
+    const int a = walk_cut8(gi, k >> 1);
+    return (k & 1) ? (a + walk_cut8(gi, (k >> 1) + 1)) >> 1 : a;
+  }
+  return walk_cut8(gi, k * (8 / wk));
 }
 
 // Slice evaluated by warp `wl` of a launch over all G * BH_SLICES slices

@@ -77,7 +77,7 @@ struct TreeArrays {
 // in a pool of chunks of BH_CHUNK entries; a walk list is the chain of chunks
 // starting at head[l] (next[c] links them in order).
 constexpr int BH_SLICES = 4;
-constexpr int BH_MAX_WK = 8;  // walk lists per group at most
+constexpr int BH_MAX_WK = 16;  // walk lists per group at most
 constexpr int BH_CHUNK = 64;
 struct BHLists {
   int2* ent;      // pool: n_chunks x BH_CHUNK entries {node, lane mask}
@@ -193,7 +193,7 @@ struct WalkGroups {
   int leaf;                // leaf-size variant: near nodes of <= leaf points taken exactly
   bool trunc;              // pure truncation: far nodes dropped, pairs cut at the threshold
   int crit;                // far test: 0 the paper's distance rule, 1 opening angle
-  int wsplit;              // walk lists per slice: 1 or 2 (a power of two)
+  int wsplit;              // walk lists per slice: 1, 2 or 4
   // Outside targets (tracer points walking this tree, forward only); xperm
   // NULL: the targets are the tree's own points.  Tracer groups are 32
   // consecutive tracers in tracer-code order over the whole tree.

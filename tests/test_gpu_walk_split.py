@@ -1,5 +1,5 @@
-"""The Barnes-Hut walk may cut each slice of a group's node range into two
-walk lists (option bh_walk_split).  The evaluation reads a slice's walk lists
+"""The Barnes-Hut walk may cut each slice of a group's node range into two or
+four walk lists (option bh_walk_split).  The evaluation reads a slice's walk lists
 as one entry sequence in fixed batches, and a slice sent to the fused re-walk
 (capped lists) is walked part after part with the lanes' state carried over,
 so right-hand sides, adjoints, gradients, tracers and interaction counts are
@@ -47,9 +47,10 @@ def test_walk_split_is_bit_exact(geom, n, seed, cap, mode, leaf):
 
     one, c1 = _run_split(1, cap, run)
     two, c2 = _run_split(2, cap, run)
-    assert c1 == c2
-    for a, b in zip(one, two):
-        assert torch.equal(a, b)
+    four, c4 = _run_split(4, cap, run)
+    assert c1 == c2 == c4
+    for a, b, c in zip(one, two, four):
+        assert torch.equal(a, b) and torch.equal(a, c)
 
 
 @pytest.mark.parametrize("cap", [0, 5])
@@ -63,13 +64,16 @@ def test_walk_split_tracers_bit_exact(cap):
 
     one = _run_split(1, cap, run)
     two = _run_split(2, cap, run)
-    for a, b in zip(one, two):
-        assert torch.equal(a, b)
+    four = _run_split(4, cap, run)
+    for a, b, c in zip(one, two, four):
+        assert torch.equal(a, b) and torch.equal(a, c)
 
 
 def test_walk_split_option_checked():
     with pytest.raises(Exception):
         gs.set_option("bh_walk_split", 3)
+    with pytest.raises(Exception):
+        gs.set_option("bh_walk_split", 8)
     gs.set_option("bh_walk_split", 0)
 
 
@@ -93,5 +97,6 @@ def test_walk_split_forest_bit_exact(cap):
 
     one = _run_split(1, cap, run)
     two = _run_split(2, cap, run)
-    for a, b in zip(one, two):
-        assert torch.equal(a, b)
+    four = _run_split(4, cap, run)
+    for a, b, c in zip(one, two, four):
+        assert torch.equal(a, b) and torch.equal(a, c)
