@@ -55,7 +55,14 @@ namespace gs {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int TR_WARPS = 4;
+// One warp per block: a block's slot frees as soon as its walk list or slice
+// is done, and the next one (longest first) starts there.  Measured on
+// blobs100k against four warps per block: walk 18.1 -> 16.0 ms and adjoint
+// evaluation 18.1 -> 17.6 ms per gradient (forward evaluation unchanged);
+// two warps per block, or warps taking walk lists from a common cursor,
+// 18.2 ms.
+constexpr int TR_WARPS = 1;
+constexpr int WK_WARPS = 1;
 constexpr int TR_CAP = 2 * BH_CHUNK;  // evaluation batch (entries staged at a time)
 
 // Per-lane own data (record of the lane's point).
@@ -570,20 +577,12 @@ __device__ __forceinline__ bool walk_paper(const TreeArrays& t, float4 (*sbox)[2
   return true;
 }
 
-// One warp per (group, slice): emits the ordered interaction list.
+// Walk list l of one group slice: emits its ordered interaction list.
 template <bool COUNT, bool VAR>
-__global__ void __launch_bounds__(TR_WARPS * 32)
-    k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
-              WalkGroups wg, int64_t* counts, const int* __restrict__ word) {
-  // word: NULL, or an order of the lists that is used when *L.worder_n says
-  // it holds as many lists as this walk has
-  __shared__ float4 s_box[TR_WARPS][32][2];
-  __shared__ int2 s_ent[TR_WARPS][2 * BH_CHUNK];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int wk = BH_SLICES * wg.wsplit;
-  const int nl = wg.G * wk, wl = blockIdx.x * TR_WARPS + w;
-  if (wl >= nl) return;
-  const int l = (word && *L.worder_n == nl) ? word[wl] : wl;
+__device__ __forceinline__ void walk_list(const TreeArrays& t, int N, const float4* raw,
+                                          float thr, const BHLists& L, const WalkGroups& wg,
+                                          int64_t* counts, int l, int wk, float4 (*sbox)[2],
+                                          int2* ent, int lane) {
   const int g = l / wk, k = l % wk;
   const GroupInfo gi = target_group(t, N, wg, g);
   const bool valid = lane < gi.count;
@@ -595,14 +594,14 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
   // (an empty slice may start at the node count: no node to test there)
   if (k > 0 && valid && x < end)
     resume = resume_at<VAR>(t, x, rr.x, rr.y, rr.z, thr, wg.leaf, wg.crit, resume);
-  ListSink sink{&L, s_ent[w], -1, -1, 0, 0, lane, false, 0, 0};
+  ListSink sink{&L, ent, -1, -1, 0, 0, lane, false, 0, 0};
   long long np = 0, nn = 0;
   bool done;
   if (!COUNT && !VAR)
-    done = walk_paper(t, s_box[w], x, end, rr, thr, resume, sink, lane);
+    done = walk_paper(t, sbox, x, end, rr, thr, resume, sink, lane);
   else
-    done = walk_nodes<COUNT, VAR>(t, s_box[w], x, end, rr, thr, wg.leaf, wg.trunc, wg.crit,
-                                  resume, sink, lane, np, nn);
+    done = walk_nodes<COUNT, VAR>(t, sbox, x, end, rr, thr, wg.leaf, wg.trunc, wg.crit, resume,
+                                  sink, lane, np, nn);
   sink.finish();
   done = done && !sink.ovf;
   if (lane == 0) {
@@ -614,6 +613,24 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[0]), (unsigned long long)np);
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts[1]), (unsigned long long)nn);
   }
+}
+
+// The list walk, one warp per walk list: the wl-th in the order `word` (when
+// it holds as many lists as this walk has; else in index order).
+template <bool COUNT, bool VAR>
+__global__ void __launch_bounds__(WK_WARPS * 32)
+    k_bh_walk(TreeArrays t, int N, const float4* __restrict__ raw, float thr, BHLists L,
+              WalkGroups wg, int64_t* counts, const int* __restrict__ word) {
+  __shared__ float4 s_box[WK_WARPS][32][2];
+  __shared__ int2 s_ent[WK_WARPS][2 * BH_CHUNK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int wk = BH_SLICES * wg.wsplit;
+  const int nl = wg.G * wk;
+  const bool ordered = word && *L.worder_n == nl;
+  const int wl = blockIdx.x * WK_WARPS + w;
+  if (wl >= nl) return;
+  walk_list<COUNT, VAR>(t, N, raw, thr, L, wg, counts, ordered ? word[wl] : wl, wk, s_box[w],
+                        s_ent[w], lane);
 }
 
 // ------------------------------------------------------------------ tally
@@ -766,9 +783,9 @@ __device__ __forceinline__ void finish_slice(const TreeArrays& t, int N, const B
 // The entries of the slice's walk lists are read as one sequence, TR_CAP
 // at a time (two list chunks; measured 4% faster than one), so the batches
 // (and the sums) are those of an unsplit walk.  The adjoint variant is held
-// to 128 registers (4 blocks per SM): measured faster than 3 blocks at 168.
+// to 128 registers (16 warps per SM): measured faster than 12 at 168.
 template <bool ADJ, bool TRUNC>
-__global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 4 : 1)
+__global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 16 / TR_WARPS : 1)
     k_bh_eval(TreeArrays t, int N, BHLists L, WalkGroups wg, float thr, int64_t* counts,
               const int* __restrict__ order, FwdEpi fe, AdjEpi ae, TracerEpi te) {
   constexpr int NR = (ADJ ? 12 : 6) + (TRUNC ? 3 : 0);
@@ -1095,18 +1112,18 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
                            const BHLists& L, const WalkGroups& wg, int64_t* counts,
                            bool scheduled, cudaStream_t st) {
   const int nl = wg.G * BH_SLICES * wg.wsplit;
-  const unsigned nb = warp_blocks(nl);
+  const unsigned nb = (unsigned)((nl + WK_WARPS - 1) / WK_WARPS);
   const bool var = wg.leaf > 1 || wg.trunc || wg.crit != 0;  // the paper's rule: lean walk
   // the previous walk's order (taken if it covers as many lists)
   const int* word = scheduled ? L.worder : nullptr;
   if (counts && var)
-    k_bh_walk<true, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
+    k_bh_walk<true, true><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else if (counts)
-    k_bh_walk<true, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
+    k_bh_walk<true, false><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else if (var)
-    k_bh_walk<false, true><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
+    k_bh_walk<false, true><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else
-    k_bh_walk<false, false><<<nb, TR_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
+    k_bh_walk<false, false><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   if (scheduled)
     k_list_order<<<2, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
                                               L.worder_n);
