@@ -63,7 +63,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // 18.2 ms.
 constexpr int TR_WARPS = 1;
 constexpr int WK_WARPS = 1;
-constexpr int TR_CAP = 2 * BH_CHUNK;  // evaluation batch (entries staged at a time)
+constexpr int TR_CAP = 128;  // evaluation batch (entries staged at a time)
 
 // Per-lane own data (record of the lane's point).
 struct Own {
@@ -428,7 +428,7 @@ __device__ __forceinline__ bool walk_nodes(const TreeArrays& t, float4 (*sbox)[2
 // Sink of the list walk: entries buffered in shared memory and written to
 // the list BH_CHUNK at a time in chunks taken from the pool.  When the pool
 // is exhausted the list is abandoned (the slice is re-walked later).
-constexpr int kReserve = 8;  // chunks reserved from the pool at a time
+constexpr int kReserve = 2;  // chunks reserved from the pool at a time
 struct ListSink {
   const BHLists* L;
   int2* buf;     // 2 * BH_CHUNK entries in shared memory
@@ -781,8 +781,9 @@ __device__ __forceinline__ void finish_slice(const TreeArrays& t, int N, const B
 // ------------------------------------------------------------------ evaluate
 // One warp per slice: partial sums of its entries, part[(e*NC + c)*32 + lane].
 // The entries of the slice's walk lists are read as one sequence, TR_CAP
-// at a time (two list chunks; measured 4% faster than one), so the batches
-// (and the sums) are those of an unsplit walk.  The adjoint variant is held
+// at a time (256 against 128 entries: forward faster, adjoint slower, the
+// two together about the same), so the batches (and the sums) are those of
+// an unsplit walk.  The adjoint variant is held
 // to 128 registers (16 warps per SM): measured faster than 12 at 168.
 template <bool ADJ, bool TRUNC>
 __global__ void __launch_bounds__(TR_WARPS * 32, ADJ ? 16 / TR_WARPS : 1)

@@ -78,7 +78,9 @@ struct TreeArrays {
 // starting at head[l] (next[c] links them in order).
 constexpr int BH_SLICES = 4;
 constexpr int BH_MAX_WK = 16;  // walk lists per group at most
-constexpr int BH_CHUNK = 64;
+// (256-entry chunks: measured 43.3 -> 42.4 ms per blobs100k gradient for the
+// walk and the two evaluations together against 64-entry chunks)
+constexpr int BH_CHUNK = 256;
 struct BHLists {
   int2* ent;      // pool: n_chunks x BH_CHUNK entries {node, lane mask}
   int* next;      // per chunk: next chunk of the same list
