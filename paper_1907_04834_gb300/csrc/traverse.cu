@@ -945,55 +945,103 @@ __global__ void __launch_bounds__(TR_WARPS * 32)
 
 // Longest-first orders of the walk lists (worder, and *worder_n = nw) and of
 // the nw / ws slices (order; a slice's length is that of its ws walk lists
-// together): one block each, a counting sort on length classes of about 12%
-// width (the leading bit and the three below it: 8 classes per octave,
-// monotone in the length).  Items of one class land in any order; every item
-// appears once.
-constexpr int kOrderThreads = 1024, kOrderClasses = 256;
+// together): a counting sort on length classes of about 12% width (the
+// leading bit and the three below it: 8 classes per octave, monotone in the
+// length), over up to kOrderMaxBlocks blocks per order, each a contiguous
+// range of items: per block and class the counts (k_order_count), their
+// exclusive scan in class-then-block order (k_order_scan), then each block
+// places its items from its offsets (k_order_place).  Items of one class
+// land in any order; every item appears once.  (One block per order took
+// 21 us per walk at N = 10^5 and 133 us at N = 10^6.)
+constexpr int kOrderThreads = 256, kOrderClasses = 256, kOrderMaxBlocks = 256;
+constexpr int kOrderPer = 2048;  // items per block at least (up to kOrderMaxBlocks blocks)
 __device__ __forceinline__ int len_class(int v) {
   if (v < 16) return max(v, 0);
   const int e = 31 - __clz(v);  // >= 4
   return min(kOrderClasses - 1, 16 + 8 * (e - 4) + ((v >> (e - 3)) & 7));
 }
+__host__ __device__ __forceinline__ int order_blocks(int n) {
+  return max(1, min(kOrderMaxBlocks, (n + kOrderPer - 1) / kOrderPer));
+}
+// order `kind` (0: walk lists, 1: slices): its item count, lists per item,
+// blocks, and block b's item range
+struct OrderPart {
+  int n, per, B, i0, i1;
+  __device__ OrderPart(int kind, int nw, int ws, int b) {
+    n = kind ? nw / ws : nw;
+    per = kind ? ws : 1;
+    B = order_blocks(n);
+    const int chunk = (n + B - 1) / B;
+    i0 = min(n, b * chunk);
+    i1 = min(n, i0 + chunk);
+  }
+  // class index kOrderClasses - 1 - class: longest first
+  __device__ int cls(const int* len, int e) const {
+    int v = 0;
+    for (int j = 0; j < per; j++) v += len[e * per + j];
+    return kOrderClasses - 1 - len_class(v);
+  }
+};
 
-__device__ void exclusive_scan_warp(int* cnt, int lane) {  // kOrderClasses counts
-  constexpr int per = kOrderClasses / 32;
+// grid (order blocks of the walk lists, 2): per block and class, the count
+// of its items;
+// hist[kind][c * B + b]
+__global__ void __launch_bounds__(kOrderThreads)
+    k_order_count(const int* __restrict__ len, int nw, int ws, int* hist) {
+  __shared__ int s_c[kOrderClasses];
+  const int kind = blockIdx.y, tid = threadIdx.x;
+  const OrderPart P(kind, nw, ws, blockIdx.x);
+  if ((int)blockIdx.x >= P.B) return;
+  for (int c = tid; c < kOrderClasses; c += kOrderThreads) s_c[c] = 0;
+  __syncthreads();
+  for (int e = P.i0 + tid; e < P.i1; e += kOrderThreads) atomicAdd(&s_c[P.cls(len, e)], 1);
+  __syncthreads();
+  int* h = hist + (size_t)kind * kOrderClasses * kOrderMaxBlocks;
+  for (int c = tid; c < kOrderClasses; c += kOrderThreads) h[c * P.B + blockIdx.x] = s_c[c];
+}
+
+// one block per order: exclusive scan of its kOrderClasses x B counts (each
+// thread a contiguous run of them)
+__global__ void __launch_bounds__(kOrderThreads) k_order_scan(int nw, int ws, int* hist) {
+  __shared__ int s_w[kOrderThreads / 32];
+  const int kind = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const OrderPart P(kind, nw, ws, 0);
+  int* h = hist + (size_t)kind * kOrderClasses * kOrderMaxBlocks;
+  const int m = kOrderClasses * P.B, run = (m + kOrderThreads - 1) / kOrderThreads;
+  const int a = min(m, tid * run), b = min(m, a + run);
   int loc = 0;
-  for (int k = 0; k < per; k++) loc += cnt[lane * per + k];
+  for (int k = a; k < b; k++) loc += h[k];
   int inc = loc;
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(FULL, inc, o);
     if (lane >= o) inc += v;
   }
-  int run = inc - loc;
-  for (int k = 0; k < per; k++) {
-    const int c = cnt[lane * per + k];
-    cnt[lane * per + k] = run;
-    run += c;
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < wid; k++) before += s_w[k];
+  int s = before + inc - loc;
+  for (int k = a; k < b; k++) {
+    const int c = h[k];
+    h[k] = s;
+    s += c;
   }
 }
 
+// grid as k_order_count: each block places its items from its offsets
 __global__ void __launch_bounds__(kOrderThreads)
-    k_list_order(const int* __restrict__ len, int nw, int ws, int* order, int* worder,
-                 int* worder_n) {
+    k_order_place(const int* __restrict__ len, int nw, int ws, const int* __restrict__ hist,
+                  int* order, int* worder, int* worder_n) {
   __shared__ int s_c[kOrderClasses];
-  const int tid = threadIdx.x;
-  const bool slices = blockIdx.x == 1;  // block 0: the walk lists, block 1: the slices
-  const int n = slices ? nw / ws : nw, per = slices ? ws : 1;
-  int* out = slices ? order : worder;
-  for (int b = tid; b < kOrderClasses; b += kOrderThreads) s_c[b] = 0;
+  const int kind = blockIdx.y, tid = threadIdx.x;
+  const OrderPart P(kind, nw, ws, blockIdx.x);
+  if ((int)blockIdx.x >= P.B) return;
+  const int* h = hist + (size_t)kind * kOrderClasses * kOrderMaxBlocks;
+  for (int c = tid; c < kOrderClasses; c += kOrderThreads) s_c[c] = h[c * P.B + blockIdx.x];
   __syncthreads();
-  auto cls = [&](int e) {  // class index kOrderClasses - 1 - class: longest first
-    int v = 0;
-    for (int j = 0; j < per; j++) v += len[e * per + j];
-    return kOrderClasses - 1 - len_class(v);
-  };
-  for (int e = tid; e < n; e += kOrderThreads) atomicAdd(&s_c[cls(e)], 1);
-  __syncthreads();
-  if (tid < 32) exclusive_scan_warp(s_c, tid);
-  __syncthreads();
-  for (int e = tid; e < n; e += kOrderThreads) out[atomicAdd(&s_c[cls(e)], 1)] = e;
-  if (!slices && tid == 0) *worder_n = nw;
+  int* out = kind ? order : worder;
+  for (int e = P.i0 + tid; e < P.i1; e += kOrderThreads) out[atomicAdd(&s_c[P.cls(len, e)], 1)] = e;
+  if (kind == 0 && blockIdx.x == 0 && tid == 0) *worder_n = nw;
 }
 
 inline unsigned warp_blocks(int64_t warps) { return (unsigned)((warps + TR_WARPS - 1) / TR_WARPS); }
@@ -1125,10 +1173,14 @@ cudaError_t launch_bh_walk(const TreeArrays& t, int N, const float4* raw, float 
     k_bh_walk<false, true><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
   else
     k_bh_walk<false, false><<<nb, WK_WARPS * 32, 0, st>>>(t, N, raw, thr, L, wg, counts, word);
-  if (scheduled)
-    k_list_order<<<2, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.order, L.worder,
-                                              L.worder_n);
-  note_launches(scheduled ? 2 : 1);
+  if (scheduled) {
+    const dim3 grid(order_blocks(nl), 2);
+    k_order_count<<<grid, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.ohist);
+    k_order_scan<<<2, kOrderThreads, 0, st>>>(nl, wg.wsplit, L.ohist);
+    k_order_place<<<grid, kOrderThreads, 0, st>>>(L.len, nl, wg.wsplit, L.ohist, L.order,
+                                                   L.worder, L.worder_n);
+  }
+  note_launches(scheduled ? 4 : 1);
   return cudaGetLastError();
 }
 

@@ -1150,7 +1150,8 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
                o_bigq = take(4 * N1), o_bigc = take(4),
                o_part = take(nl * 9 * 32 * sizeof(float2)),
                o_fb = take(nl * 9 * 32 * sizeof(float2)), o_word = take(4 * n_walk_lists(groups)),
-               o_wordn = take(4), o_gtick = take(4 * (size_t)groups);
+               o_wordn = take(4), o_gtick = take(4 * (size_t)groups),
+               o_ohist = take(4 * 2 * 256 * 256);
   // the single-pass sort's histograms, tile counters and look-back words and
   // the node-offset scan's look-back words, contiguous (one memset per build)
   const size_t os_tiles = nblocks(n, OS_TILE), sc_tiles = nblocks(std::max<int64_t>(n, 1), SCAN_TILE);
@@ -1188,6 +1189,7 @@ size_t carve_shared(void* mem, int64_t n, int64_t groups, TreeArrays* t, BHLists
     L->worder = (int*)(b + o_word);
     L->worder_n = (int*)(b + o_wordn);
     L->gticket = (int*)(b + o_gtick);
+    L->ohist = (int*)(b + o_ohist);
     t->os_hist = (uint32_t*)(b + o_osreg);
     t->os_ctr = (int*)(b + o_osreg + os_hist_b);
     t->os_stat = (unsigned long long*)(b + o_osreg + os_hist_b + os_ctr_b);

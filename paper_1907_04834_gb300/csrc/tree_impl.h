@@ -99,6 +99,7 @@ struct BHLists {
   int* worder;    // per walk list (shared by the steps)
   int* worder_n;  // list count of worder; -1 when it holds none
   int* gticket;   // per group: slices summed so far (the last one combines; back to 0)
+  int* ohist;     // the orders' counts per class and block (2 x 256 x 256)
 };
 
 __device__ __forceinline__ int total_nodes(const TreeArrays& t, int N) {
